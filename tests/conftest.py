@@ -1,0 +1,36 @@
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a GB300 and the built CUDA library")
+    config.addinivalue_line("markers", "slow: long-running CPU oracle case")
+
+
+def oracle_quadrature(quad):
+    """The oracle's own angular rule for a workload's quadrature descriptor."""
+    from oracle import quadrature as q
+    if quad[0] == "gl":
+        return q.gl_slab(quad[1])
+    return q.cl_hemisphere(quad[1], quad[2])
+
+
+def oracle_problem(wl, quad=None):
+    """oracle.transport.Problem from an inputs.Workload (both sides get the same arrays)."""
+    from oracle.transport import Problem
+    mu, eta, w = quad if quad is not None else oracle_quadrature(wl.quadrature)
+    x0, x1, y0, y1 = wl.domain
+    return Problem(wl.nx, wl.ny, x0, x1, y0, y1, mu, eta, w, wl.sigma_t.copy(),
+                   wl.sigma_s.copy(), wl.source.copy(), wl.c_dt, np.array(wl.inflow, dtype=float))
+
+
+@pytest.fixture
+def rng():
+    return np.random.default_rng(12345)

@@ -1,0 +1,124 @@
+"""Pins of the oracle's SI-DSA (Algorithm 1), DSA/CG and time step against direct solves
+and closed-form solutions."""
+import numpy as np
+import pytest
+
+from oracle import dense, dsa, sisa, stepper
+from oracle import quadrature as q
+from oracle import transport as tr
+from conftest import oracle_problem
+from paper_2603_19647_gb300 import inputs
+
+
+def _small_2d(rng, nx=6, ny=5, quad=(8, 4), c_dt=0.05, g=(0.3, 0.0, 0.5, 0.1)):
+    mu, eta, w = q.cl_hemisphere(*quad)
+    n = nx * ny
+    ss = rng.uniform(0.0, 20.0, n)
+    return tr.Problem(nx, ny, 0.0, 1.0, 0.0, 0.8, mu, eta, w, ss + rng.uniform(0.05, 1.0, n), ss,
+                      rng.uniform(0, 1, n), c_dt, np.array(g, float))
+
+
+def _small_1d(rng, n=14, c_dt=0.2):
+    mu, eta, w = q.gl_slab(8)
+    ss = rng.uniform(0.0, 30.0, n)
+    return tr.Problem(n, 1, 0.0, 2.0, 0.0, 1.0, mu, eta, w, ss + rng.uniform(0.01, 1.0, n), ss,
+                      rng.uniform(0, 1, n), c_dt, np.array([1.0, 0.2, 0, 0]))
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("rom", [False, True])
+def test_march_matches_direct_solve(dim, rom, rng):
+    p = _small_2d(rng) if dim == 2 else _small_1d(rng)
+    r = stepper.OracleRTE(p, eps_sisa=1e-13, rom=rom, cg_rtol=1e-10, eps_ig=1e-8, eps_pc=1e-8,
+                          eps_up=1e-10)
+    rho0 = rng.uniform(0, 1, p.ncell)
+    r.set_initial(rho0)
+    f = np.tile(rho0, (p.nv, 1))
+    for n in range(12):
+        r.step()
+        f, rho = dense.step(p, f)
+        assert np.linalg.norm(r.rho - rho) <= 1e-11 * np.linalg.norm(rho)
+        assert np.max(np.abs(r.f - f)) <= 1e-10 * np.max(np.abs(f))
+
+
+def test_infinite_medium_exponential_decay():
+    """Uniform medium, G = 0, isotropic uniform f0 = rho0 and inflow reset each step to
+    g^n = rho0 (1 + c dt sigma_a)^(-n): the solution stays uniform and decays exactly as
+    rho^n = rho0 (1 + c dt sigma_a)^(-n) (backward Euler of d rho/dt = -sigma_a rho)."""
+    mu, eta, w = q.cl_hemisphere(16, 4)
+    nx = ny = 10
+    n = nx * ny
+    st, ss, c_dt, rho0 = 2.0, 1.5, 0.3, 1.7
+    p = tr.Problem(nx, ny, 0, 1, 0, 1, mu, eta, w, np.full(n, st), np.full(n, ss), np.zeros(n),
+                   c_dt, np.zeros(4))
+    r = stepper.OracleRTE(p, eps_sisa=1e-14, cg_rtol=1e-12, rom=False)
+    r.set_initial(np.full(n, rho0))
+    for k in range(1, 8):
+        gk = rho0 * (1 + c_dt * (st - ss)) ** (-k)
+        r.set_inflow([gk] * 4)
+        r.step()
+        assert np.max(np.abs(r.rho - gk)) < 1e-12 * gk
+
+
+def test_dsa_matrix_and_cg(rng):
+    wl = inputs.checkerboard(n=16, quad=(8, 4))
+    p = oracle_problem(wl)
+    A = dsa.dsa_matrix(p)
+    Ad = A.toarray()
+    assert np.allclose(Ad, Ad.T, atol=0, rtol=0)
+    assert np.all(np.linalg.eigvalsh(Ad) > 0)
+    # interior rows: the face couplings cancel, leaving sigma_a~ = sigma_a + tau
+    Ad2 = Ad.reshape(16, 16, 256)
+    rowsum = Ad.sum(axis=1).reshape(16, 16)
+    sa = (p.sigma_t - p.sigma_s + p.tau).reshape(16, 16)
+    assert np.allclose(rowsum[1:-1, 1:-1], sa[1:-1, 1:-1], rtol=1e-12)
+    assert np.all(rowsum[0, :] > sa[0, :])
+    b = rng.uniform(-1, 1, 256)
+    x, its = dsa.cg(A, b, 1e-13, 1000)
+    assert np.linalg.norm(x - np.linalg.solve(Ad, b)) < 1e-11 * np.linalg.norm(x)
+    assert 0 < its < 256
+    # the Marshak term is the 1 / (h (2 + h / (2D))) of a vacuum face
+    D = 1 / (3 * (p.sigma_t[0] + p.tau))
+    h = p.hx
+    corner_extra = Ad[0, 0] - sa[0, 0] + Ad[0, 1] + Ad[0, 16]
+    assert abs(corner_extra - 2 / (h * (2 + h / (2 * D)))) < 1e-10 * abs(corner_extra)
+
+
+def test_si_contraction_bound(rng):
+    """Without SA each SI iteration contracts the error by at most max sigma_s / (sigma_t + tau)
+    in the max norm (each L_j^{-1} is a nonnegative matrix with row sums <= 1/(tau + sigma_t))."""
+    p = _small_2d(rng, nx=12, ny=12, quad=(16, 4), c_dt=1.0, g=(0, 0, 0, 0))
+    c = float(np.max(p.sigma_s / (p.sigma_t + p.tau)))
+    bt = tr.b_tilde(p, np.ones((p.nv, p.ncell)))
+    exact = np.linalg.solve(np.eye(p.ncell) - np.stack(
+        [tr.apply_T_sigma_s(p, e) for e in np.eye(p.ncell)], axis=1), bt)
+    rho = np.zeros(p.ncell)
+    e_prev = np.max(np.abs(rho - exact))
+    for _ in range(10):
+        rho = tr.apply_T_sigma_s(p, rho) + bt
+        e = np.max(np.abs(rho - exact))
+        assert e <= c * e_prev * (1 + 1e-12)
+        e_prev = e
+
+
+def test_dsa_accelerates(rng):
+    """SI-DSA needs far fewer sweeps than plain SI on a scattering-dominated step with
+    optically thin cells (sigma_t h < 1, the regime of every synthetic workload here)."""
+    mu, eta, w = q.cl_hemisphere(16, 4)
+    n = 64
+    ss = np.full(n * n, 50.0)
+    p = tr.Problem(n, n, 0, 1, 0, 1, mu, eta, w, ss + 0.01, ss, np.ones(n * n), 1.0, np.zeros(4))
+    bt = tr.b_tilde(p, np.zeros((p.nv, p.ncell)))
+    o = dict(stepper.DEFAULTS, eps_sisa=1e-8)
+    _, info = sisa.si_sa(p, np.zeros(p.ncell), bt, o, dsa.dsa_matrix(p))
+    assert info.iterations < 30
+    with pytest.raises(sisa.NoConvergence):
+        o2 = dict(o, max_iter=60)
+        rho = np.zeros(p.ncell)
+        for l in range(o2["max_iter"]):
+            new = tr.apply_T_sigma_s(p, rho) + bt
+            if np.max(np.abs(new - rho)) <= 1e-8 * np.max(np.abs(new)):
+                break
+            rho = new
+        else:
+            raise sisa.NoConvergence("plain SI")
