@@ -1,0 +1,203 @@
+/*
+ * rte.h -- C ABI of the GB300-native ROM-accelerated SI-DSA library (librte.so).
+ *
+ * Method: N. Liu and Z. Peng, "On-the-fly ROM-based acceleration of SI-DSA for implicit
+ * time marching of the radiative transfer equation".  The library solves the one-group
+ * linear RTE with isotropic scattering and isotropic inflow (Sec. 2, Eq. (rte)) with
+ *   - S_N directions (Sec. 2.1; Gauss-Legendre in 1D, Chebyshev-Legendre CL rule of App. A),
+ *   - backward Euler in time (Sec. 2.1, Eq. (time_discrete)), tau = 1/(c dt),
+ *   - upwind DG in space, lowest order Q0 member of Eq. (dg_space): one value per cell,
+ *   - memory-efficient SI with DSA (Sec. 2.3, Algorithm 1),
+ *   - on-the-fly DMD / incremental-SVD reduced models for the initial guess and the
+ *     first-iteration preconditioner (Sec. 3, Algorithm 2, App. B).
+ * Everything on the time-stepping path runs in CUDA kernels on one GPU (sm_103a); the host
+ * side only sequences them.
+ *
+ * Conventions (all calls):
+ *   - Every call returns rte_status; nothing throws or aborts across the ABI.  On failure
+ *     rte_last_error(h) returns a NUL-terminated message owned by the handle; after a failed
+ *     rte_create, rte_last_error(NULL) returns that call's message (per host thread).
+ *   - Array arguments are HOST pointers unless the name ends in _dev.  Input arrays are
+ *     copied during the call; the caller keeps ownership of every pointer it passes.
+ *   - Cell arrays have ncell = nx*ny entries, cell index c = i + nx*j (x fastest), FP64,
+ *     whatever the internal precision.
+ *   - Angular arrays are [n_dirs][ncell], direction order = the order rte_get_quadrature
+ *     reports (for RTE_Q_EXPLICIT: the caller's order).
+ *   - A handle is not thread-safe; use one handle per host thread.  All device work of a
+ *     handle is issued on its own CUDA stream on the device that was current at create.
+ */
+#ifndef RTE_H
+#define RTE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rte_s* rte_handle;
+
+typedef enum {
+  RTE_OK = 0,
+  RTE_EINVAL = 1,   /* invalid argument (detail in rte_last_error) */
+  RTE_ENOMEM = 2,   /* host or device allocation failed */
+  RTE_ENOCONV = 3,  /* SI-SA reached max_iter; state = last iterate, still usable */
+  RTE_ECUDA = 4,    /* a CUDA runtime call failed */
+  RTE_ETIMEOUT = 5, /* a bounded device-side wait ran out (the kernel returned early) */
+  RTE_ESTATE = 6    /* call not valid in the handle's current state */
+} rte_status;
+
+enum { RTE_Q_GL1D = 0, RTE_Q_CL_HEMI = 1, RTE_Q_EXPLICIT = 2 };
+enum { RTE_FP64 = 0, RTE_FP32 = 1, RTE_FP32_BF16F = 2 };
+enum { RTE_REL_INF = 0, RTE_ABS_INF = 1 };
+enum { RTE_ROM_OFF = 0, RTE_ROM_AUTO = 1, RTE_ROM_MANUAL = 2 };
+enum { RTE_ROM_IG = 0, RTE_ROM_PC = 1 };
+
+/* Uniform Cartesian mesh.  dim = 1: slab [x0,x1] with nx cells (ny must be 1);
+ * dim = 2: [x0,x1] x [y0,y1] with nx*ny rectangles (Sec. 2.1). */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double x0, x1, y0, y1;
+} rte_mesh;
+
+/* Angular quadrature (Sec. 2.1: weights sum to 1).
+ *   RTE_Q_GL1D    n_gl-point Gauss-Legendre rule in mu, weights / 2 (dim = 1).
+ *   RTE_Q_CL_HEMI CL(n_phi, n_gl) rule of App. A restricted to v_z > 0 with doubled
+ *                 weights (X-Y geometry); n_gl even; n_dirs = n_phi * n_gl / 2 (dim = 2).
+ *   RTE_Q_EXPLICIT n_dirs directions mu[], eta[] (eta ignored for dim = 1), weights w[].
+ *                 2D rules need the same number of directions in each quadrant and no
+ *                 direction on an axis; 1D rules the same number with mu > 0 and mu < 0. */
+typedef struct {
+  int kind;
+  int n_gl;
+  int n_phi;
+  int n_dirs;
+  const double* mu;
+  const double* eta;
+  const double* w;
+} rte_quadrature;
+
+typedef struct {
+  double eps_sisa;   /* Algorithm 1 stopping tolerance (default 1e-8) */
+  double eps_ig;     /* Phase 1 stop Eq. (ig_stop) and IG-ROM truncation (default 1e-6) */
+  double eps_pc;     /* Phase 2 stop Eq. (pc_stop) and PC-ROM truncation (default 1e-6) */
+  double eps_up;     /* Phase 3 update indicators, Sec. 3.2 (default 1e-6) */
+  int max_iter;      /* N_iter of Algorithm 1 (default 500) */
+  int r_max;         /* rank cap of each ROM, <= 64 (default 40) */
+  int precision;     /* RTE_FP64 (default) | RTE_FP32 (FP32 sweeps, FP64 refinement) */
+  int rom;           /* RTE_ROM_AUTO (default) | RTE_ROM_OFF | RTE_ROM_MANUAL */
+  int residual_norm; /* RTE_REL_INF (default): ||.||_inf relative to ||rho^{l-1/2}||_inf;
+                        RTE_ABS_INF: the paper's absolute test */
+  int up_rel;        /* 1 (default): eps_up multiplies ||rho^n||_2; 0: absolute */
+  double cg_rtol;    /* DSA conjugate-gradient tolerance ||r|| <= cg_rtol ||b|| (default 1e-6) */
+  int cg_max_iter;   /* default 500 */
+  int tune;          /* 1 (default): pick sweep tile shapes by timing at create; 0: heuristic */
+} rte_options;
+
+typedef struct {
+  int steps;            /* time steps taken */
+  int phase;            /* 1, 2 or 3 (Sec. 3.2); 0 with ROM off */
+  int last_iterations;  /* SI-SA iterations of the last step */
+  int last_cg_iterations;
+  long long total_iterations;
+  long long total_sweeps;   /* counted as in Sec. 4: 1 (b~) + iterations + 1 (f) per step */
+  long long total_cg_iterations;
+  int ig_rank, pc_rank;
+  int ig_updated, pc_updated;  /* last step */
+  double last_residual;        /* final ||rho^{l-1/2} - rho^{l-1}||_inf (relative if REL_INF) */
+  double last_ig_error;        /* ||rho_DMD^{n,(0)} - rho^n||_2, NaN when not applied */
+  double last_pc_error;        /* ||delta_rho_DMD^{n,(1)} - delta_rho^{n,(1)}||_2, NaN when not applied */
+  long long cell_direction_updates; /* upwind cell solves done (Sec. 4 sweeps x N_x N_v) */
+  double time_sweep_ms, time_dsa_ms, time_rom_ms, time_total_ms; /* device time by phase */
+  long long si_sweep_launches;  /* SI sweep kernels (one application of T Sigma_s each) */
+  double si_sweep_kernel_ms;    /* their summed duration, CUDA events around each launch */
+  long long f_sweep_launches;   /* fused end-of-step sweeps (two cell solves per cell-direction) */
+  double f_sweep_kernel_ms;
+  long long kernel_launches;    /* CUDA kernels this library launched inside rte_step / rte_rom_update */
+} rte_stats;
+
+/* Fill *opt with the defaults listed above. */
+void rte_default_options(rte_options* opt);
+
+/* Create a problem (Sec. 2 Eq. (rte), data of Eq. (kinetic_dg_discrete)).
+ * sigma_t, sigma_s, source: host [ncell]; requires finite values, sigma_s >= 0,
+ * sigma_t >= sigma_s (Sec. 2), c_dt > 0, quadrature weights summing to 1 within 1e-12.
+ * opt may be NULL (defaults).  Initial state: f^0 = 0, vacuum inflow.
+ * On success *out owns all device memory; on failure *out = NULL. */
+rte_status rte_create(rte_handle* out, const rte_mesh* mesh, const rte_quadrature* quad,
+                      const double* sigma_t, const double* sigma_s, const double* source,
+                      double c_dt, const rte_options* opt);
+
+/* Initial state: f^0_j = rho0 for every direction j (isotropic) when f0 == NULL, else
+ * f^0 = f0 [n_dirs][ncell] and rho0 is ignored (may be NULL).  Resets the step counter,
+ * statistics and both ROMs. */
+rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0);
+
+/* Isotropic inflow value per side, g = {west, east, south, north} (Eq. (boundary));
+ * 1D uses west and east.  Applies from the next step on. */
+rte_status rte_set_inflow(rte_handle h, const double g[4]);
+
+/* Issue all further device work of h on the caller's CUDA stream (a cudaStream_t of the
+ * handle's device, e.g. a torch stream); NULL returns to the handle's own stream.  The
+ * handle does not take ownership; the stream must outlive its use by h. */
+rte_status rte_set_stream(rte_handle h, void* cuda_stream);
+
+/* Return to the state given by the last rte_set_initial (kept on the device): step counter,
+ * statistics and ROMs reset, no host-device copy.  RTE_ESTATE before any rte_set_initial. */
+rte_status rte_restart(rte_handle h);
+
+/* Advance nsteps implicit steps (Algorithm 2 per step).  With rom = RTE_ROM_AUTO the ROM
+ * construction/update of each step runs inside; with RTE_ROM_MANUAL it runs only when the
+ * caller calls rte_rom_update after a step.  RTE_ENOCONV leaves the last iterate as rho^n. */
+rte_status rte_step(rte_handle h, int nsteps);
+
+/* ROM construction / adaptive update for the step just taken (the ROM branch of
+ * Algorithm 2).  RTE_ESTATE unless rom == RTE_ROM_MANUAL and a step has been taken
+ * since the last call. */
+rte_status rte_rom_update(rte_handle h);
+
+/* Copy rho^n (host [ncell]). */
+rte_status rte_get_scalar_flux(rte_handle h, double* rho);
+/* Copy f^n (host [n_dirs][ncell]). */
+rte_status rte_get_angular_flux(rte_handle h, double* f);
+/* Copy the directions and weights in the library's direction order (host [n_dirs] each). */
+rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta, double* w);
+rte_status rte_get_stats(rte_handle h, rte_stats* st);
+const char* rte_last_error(rte_handle h);
+/* Free everything; NULL-safe. */
+void rte_destroy(rte_handle h);
+
+/* ---------------- operator-level calls (one hot-path step each) ----------------
+ * These run exactly one step of the method on the handle's problem with host arrays in
+ * and out, so that each kernel can be checked on its own.  They do not advance time. */
+
+/* out = T Sigma_s rho (Sec. 2.3 Eq. (SI_rho) without b~): one SI sweep with zero inflow and
+ * the quadrature moment, in the handle's precision. */
+rte_status rte_op_sweep(rte_handle h, const double* rho, double* out);
+
+/* The fused sweep that ends a step (Eq. (sweep_to_obtain_f) then Eq.
+ * (implicit_linear_system_rho)): with the handle's current f (= f^{n-1}) and the given rho
+ * (= rho^n), f <- L^{-1}(Sigma_s rho + tau f + G + g^bc) in place, and
+ * btilde = sum_j w_j L_j^{-1}(tau f_j + G + g_j^bc) with the updated f.  btilde may be NULL. */
+rte_status rte_op_fsweep(rte_handle h, const double* rho, double* btilde);
+
+/* delta = C^{-1} Sigma_s residual (Eq. (rho_residual)) by conjugate gradients;
+ * *iterations (may be NULL) receives the CG count. */
+rte_status rte_op_dsa(rte_handle h, const double* residual, double* delta, int* iterations);
+
+/* Append the snapshot pair (x, b) to ROM `which` (RTE_ROM_IG / RTE_ROM_PC) by the
+ * incremental SVD of App. B; trunc_eps < 0 means no truncation (rank cap r_max still holds).
+ * *grew (may be NULL) = 1 when the rank grew. */
+rte_status rte_op_rom_append(rte_handle h, int which, const double* x, const double* b,
+                             double trunc_eps, int* grew);
+/* out = U c with A_r c = U^T rhs (Eq. (dmd-ig) / Eq. (dmd-sa)) for ROM `which`. */
+rte_status rte_op_rom_apply(rte_handle h, int which, const double* rhs, double* out);
+/* Rank, singular values (descending, [rank]) and optionally U ([rank][ncell]) and the
+ * reduced operator A_r = U^T W S^{-1} ([rank][rank], row-major); NULL skips an output. */
+rte_status rte_op_rom_get(rte_handle h, int which, int* rank, double* S, double* U, double* Ar);
+/* Drop both ROMs and the phase flags. */
+rte_status rte_op_rom_reset(rte_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_H */

@@ -1,0 +1,298 @@
+// Diffusion synthetic acceleration (Sec. 2.3 Eq. (rho_residual)):
+//   C delta = Sigma_s (rho^{l-1/2} - rho^{l-1}),
+// C the cell-centred diffusion discretisation of the correction equation Eq.
+// (discrete_correction_f) (sigma_a~ = tau + sigma_a, D = 1/(3 (tau + sigma_t)), zero inflow):
+// 5-point (1D: 3-point) stencil, harmonic-mean face coefficients 2 D_L D_R/((D_L+D_R) h^2),
+// Marshak vacuum faces 1/(h (2 + h/(2D))).  Solved by conjugate gradients (Sec. 4) in one
+// cooperative launch: every CG iteration is two grid-wide phases,
+//   (1) p <- r + beta p (double-buffered, neighbours recomputed from r and the old p),
+//       Ap = C p, and the block partials of p.Ap;
+//   (2) x += alpha p, r -= alpha Ap and the block partials of r.r,
+// separated by a bounded software grid barrier.  Every block sums the block partials in the
+// same fixed order, so alpha and beta are identical everywhere and bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "rte_internal.h"
+
+namespace rte {
+
+namespace {
+constexpr int CT = 256;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned BARRIER_SPIN_LIMIT = 1u << 22;
+
+struct CgArgs {
+  int nx, ny, n;
+  const double* diag;
+  const double* cx;
+  const double* cy;
+  const double* sig_s;
+  const double* residual;
+  const double* residual_b;   // optional: residual = residual - residual_b
+  double rtol2;
+  int max_iter;
+  double *r, *p0, *p1, *ap, *x;
+  double* partial;     // [2 * gridDim.x]
+  unsigned* bar;       // [0] arrive count, [1] generation, [2] error
+  double* delta;       // output (may alias x)
+  const double* rho_half;
+  double* rho_out;
+  double* q_out;
+  int* iters;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Grid barrier for a cooperative launch (all blocks co-resident).  Bounded: after
+// BARRIER_SPIN_LIMIT polls it records an error and lets the block continue.
+__device__ void grid_barrier(unsigned* bar, unsigned& gen) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned g = gen;
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicExch(&bar[1], g + 1u);
+    } else {
+      unsigned spins = 0;
+      while (ld_acquire(&bar[1]) == g) {
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          atomicExch(&bar[2], 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  gen += 1u;
+  __syncthreads();
+}
+
+__device__ double block_sum_store(double v, double* dst) {
+  __shared__ double sh[CT / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < CT / 32 ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) *dst = v;
+  }
+  __syncthreads();
+  return v;
+}
+
+// Sum of gridDim.x partials in a fixed order; result broadcast to the block.
+__device__ double grid_total(const double* part) {
+  __shared__ double tot;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(part + b);
+    s = warp_sum(s);
+    if (threadIdx.x == 0) tot = s;
+  }
+  __syncthreads();
+  const double v = tot;
+  __syncthreads();
+  return v;
+}
+
+__global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
+  unsigned gen = ld_acquire(&a.bar[1]);
+  const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
+  double* partA = a.partial;
+  double* partB = a.partial + gridDim.x;
+  // r = b = sig_s .* residual, x = 0, p = r
+  double acc = 0.0;
+  for (int c = tid; c < a.n; c += nth) {
+    const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
+    const double b = a.sig_s[c] * rc;
+    a.r[c] = b;
+    a.x[c] = 0.0;
+    a.p0[c] = b;
+    acc += b * b;
+  }
+  block_sum_store(acc, partB + blockIdx.x);
+  grid_barrier(a.bar, gen);
+  double rr = grid_total(partB);
+  const double bb = rr;
+  double beta = 0.0;
+  int it = 0;
+  double* pold = a.p0;
+  double* pnew = a.p1;
+  while (it < a.max_iter && rr > a.rtol2 * bb) {
+    // (1) p <- r + beta p ; Ap = C p ; p.Ap
+    acc = 0.0;
+    for (int c = tid; c < a.n; c += nth) {
+      const int i = c % a.nx;
+      // Neighbours belong to other blocks: read them through L2 (__ldcg), never a stale L1 line.
+      auto pval = [&](int k) {
+        return (it == 0) ? __ldcg(pold + k) : __ldcg(a.r + k) + beta * __ldcg(pold + k);
+      };
+      const double pc = pval(c);
+      double s = a.diag[c] * pc;
+      if (i + 1 < a.nx) s -= a.cx[c] * pval(c + 1);
+      if (i > 0) s -= a.cx[c - 1] * pval(c - 1);
+      if (a.ny > 1) {
+        if (c + a.nx < a.n) s -= a.cy[c] * pval(c + a.nx);
+        if (c - a.nx >= 0) s -= a.cy[c - a.nx] * pval(c - a.nx);
+      }
+      pnew[c] = pc;
+      a.ap[c] = s;
+      acc += pc * s;
+    }
+    block_sum_store(acc, partA + blockIdx.x);
+    grid_barrier(a.bar, gen);
+    const double alpha = rr / grid_total(partA);
+    // (2) x += alpha p ; r -= alpha Ap ; r.r
+    acc = 0.0;
+    for (int c = tid; c < a.n; c += nth) {
+      a.x[c] += alpha * pnew[c];
+      const double rc = a.r[c] - alpha * a.ap[c];
+      a.r[c] = rc;
+      acc += rc * rc;
+    }
+    block_sum_store(acc, partB + blockIdx.x);
+    grid_barrier(a.bar, gen);
+    const double rr_new = grid_total(partB);
+    beta = rr_new / rr;
+    rr = rr_new;
+    double* t = pold;
+    pold = pnew;
+    pnew = t;
+    ++it;
+  }
+  for (int c = tid; c < a.n; c += nth) {
+    const double d = a.x[c];
+    if (a.delta != a.x) a.delta[c] = d;
+    if (a.rho_out) {
+      const double r = a.rho_half[c] + d;
+      a.rho_out[c] = r;
+      a.q_out[c] = a.sig_s[c] * r;
+    }
+  }
+  if (tid == 0) *a.iters = it;
+}
+
+}  // namespace
+
+cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
+                      const double* sig_t, const double* sig_s, cudaStream_t s) {
+  const int n = nx * ny;
+  op.nx = nx;
+  op.ny = ny;
+  op.n = n;
+  std::vector<double> D(n), diag(n), cx(n, 0.0), cy(n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    D[c] = 1.0 / (3.0 * (sig_t[c] + tau));
+    diag[c] = sig_t[c] - sig_s[c] + tau;
+  }
+  auto face = [](double dl, double dr, double h) { return 2.0 * dl * dr / ((dl + dr) * h * h); };
+  auto marshak = [](double d, double h) { return 1.0 / (h * (2.0 + h / (2.0 * d))); };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const int c = i + nx * j;
+      if (i + 1 < nx) {
+        const double f = face(D[c], D[c + 1], hx);
+        cx[c] = f;
+        diag[c] += f;
+        diag[c + 1] += f;
+      }
+      if (i == 0) diag[c] += marshak(D[c], hx);
+      if (i == nx - 1) diag[c] += marshak(D[c], hx);
+      if (dim == 2) {
+        if (j + 1 < ny) {
+          const double f = face(D[c], D[c + nx], hy);
+          cy[c] = f;
+          diag[c] += f;
+          diag[c + nx] += f;
+        }
+        if (j == 0) diag[c] += marshak(D[c], hy);
+        if (j == ny - 1) diag[c] += marshak(D[c], hy);
+      }
+    }
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CT, 0);
+  if (per_sm < 1) per_sm = 1;
+  int want = (n + CT - 1) / CT;
+  int cap = per_sm * sms;
+  if (cap > 2 * sms) cap = 2 * sms;
+  op.blocks = want < cap ? want : cap;
+  if (op.blocks < 1) op.blocks = 1;
+  cudaError_t e;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  double** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x};
+  for (double** b : bufs) {
+    *b = nullptr;
+    if ((e = cudaMalloc(b, bytes)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMalloc(&op.partial, sizeof(double) * 2 * op.blocks)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&op.scal, 64)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(op.scal, 0, 64, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(op.diag, diag.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(op.cx, cx.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(op.cy, cy.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  return cudaStreamSynchronize(s);
+}
+
+void dsa_free(DsaOp& op) {
+  double* bufs[] = {op.diag, op.cx, op.cy, op.r, op.p0, op.p1, op.ap, op.x, op.partial, op.scal};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  op = DsaOp{};
+}
+
+cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
+                      const double* residual_b, double rtol, int max_iter, double* delta,
+                      const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
+                      cudaStream_t s) {
+  CgArgs a;
+  a.nx = op.nx;
+  a.ny = op.ny;
+  a.n = op.n;
+  a.diag = op.diag;
+  a.cx = op.cx;
+  a.cy = op.cy;
+  a.sig_s = sig_s;
+  a.residual = residual;
+  a.residual_b = residual_b;
+  a.rtol2 = rtol * rtol;
+  a.max_iter = max_iter;
+  a.r = op.r;
+  a.p0 = op.p0;
+  a.p1 = op.p1;
+  a.ap = op.ap;
+  a.x = op.x;
+  a.partial = op.partial;
+  a.bar = reinterpret_cast<unsigned*>(op.scal);
+  a.delta = delta ? delta : op.x;
+  a.rho_half = rho_half;
+  a.rho_out = rho_out;
+  a.q_out = q_out;
+  a.iters = iters_dev;
+  void* args[] = {&a};
+  ++g_launches;
+  return cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(op.blocks), dim3(CT), args, 0, s);
+}
+
+}  // namespace rte

@@ -1,0 +1,1021 @@
+// Host driver and C ABI of librte.so.
+//
+// The host side only sequences device work: it builds the angular rule and the direction
+// layout, owns the device buffers, and runs the control flow of Algorithm 1 (SI-SA) and
+// Algorithm 2 (on-the-fly ROM phases) of Liu & Peng.  Every arithmetic step on a cell
+// vector or on the angular flux is a CUDA kernel (sweep.cu, vec.cu, cg.cu, rom.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rte_internal.h"
+
+namespace rte {
+thread_local long long g_launches = 0;
+}
+
+using namespace rte;
+
+struct rte_s {
+  std::string err;
+  int device = 0;
+  cudaStream_t st = nullptr, own_st = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;
+  // problem
+  int dim = 2, nx = 0, ny = 0;
+  long ncell = 0;
+  double hx = 1, hy = 1, c_dt = 1, tau = 1;
+  rte_options opt{};
+  std::vector<double> mu_user, eta_user, w_user;  // library direction order
+  Layout L;
+  int R = 4, rows_per_blk = 4, nblk = 1;
+  // device: problem data
+  double *sig_t = nullptr, *sig_s = nullptr, *src = nullptr;
+  double *ca = nullptr, *cb = nullptr, *cw = nullptr;
+  int *fam_quad = nullptr, *dir_sign = nullptr;
+  double* inv_d = nullptr;
+  // device: angular flux and sweep scratch
+  double* f = nullptr;
+  double *pm = nullptr, *pm_a = nullptr, *edge = nullptr;
+  SweepCtrl* ctrl = nullptr;
+  double *psi_w = nullptr, *psi_w_a = nullptr;
+  // device: cell vectors
+  double *rho = nullptr, *rho_prev = nullptr, *rho_half = nullptr, *rho_half1 = nullptr;
+  double *rho0 = nullptr, *y = nullptr, *btilde = nullptr, *q = nullptr, *delta = nullptr;
+  double *tmp = nullptr, *tmp2 = nullptr, *tmp3 = nullptr, *delta_pc1 = nullptr;
+  double* resp[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *rho_init = nullptr, *f_init = nullptr;  // state of the last rte_set_initial
+  int init_kind = 0;                              // 0 none, 1 isotropic rho0, 2 explicit f0
+  double *partials = nullptr, *dotbuf = nullptr;
+  Norms* norms = nullptr;
+  int* cg_iters = nullptr;
+  DsaOp dsa{};
+  RomDev ig{}, pc{};
+  // state
+  double g[4] = {0, 0, 0, 0};
+  bool resp_ready = false;
+  bool y_valid = false;
+  bool flag_ig = false, flag_pc = false;
+  bool pending_rom = false;  // RTE_ROM_MANUAL: a step is waiting for rte_rom_update
+  // per-step record kept for the ROM update
+  bool ig_applied = false, pc_applied = false;
+  int last_iters = 0;
+  rte_stats stats{};
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+rte_status fail(rte_handle h, rte_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+rte_status cuda_fail(rte_handle h, cudaError_t e, const char* what) {
+  std::string m = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return fail(h, RTE_ECUDA, m);
+}
+
+#define CK(call)                                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);     \
+  } while (0)
+
+#define TRY(call)                    \
+  do {                               \
+    rte_status s_ = (call);          \
+    if (s_ != RTE_OK) return s_;     \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// Angular rules (Sec. 2.1, App. A).  Gauss-Legendre nodes by Newton's method on the
+// Legendre polynomial P_n (three-term recurrence), weights 2 / ((1 - x^2) P_n'(x)^2).
+// ---------------------------------------------------------------------------------------
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    // final derivative at the converged node
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[n - 1 - i] = z;  // ascending
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Build the library direction order (user view) for GL1D and CL_HEMI rules.
+rte_status make_rule(rte_handle h, const rte_quadrature* q, int dim) {
+  h->mu_user.clear();
+  h->eta_user.clear();
+  h->w_user.clear();
+  if (q->kind == RTE_Q_GL1D) {
+    if (dim != 1) return fail(h, RTE_EINVAL, "RTE_Q_GL1D needs dim = 1");
+    if (q->n_gl < 2 || q->n_gl % 2) return fail(h, RTE_EINVAL, "n_gl must be even and >= 2");
+    std::vector<double> x, w;
+    gauss_legendre(q->n_gl, x, w);
+    for (int i = 0; i < q->n_gl; ++i) {
+      h->mu_user.push_back(x[i]);
+      h->eta_user.push_back(0.0);
+      h->w_user.push_back(w[i] / 2.0);
+    }
+  } else if (q->kind == RTE_Q_CL_HEMI) {
+    if (dim != 2) return fail(h, RTE_EINVAL, "RTE_Q_CL_HEMI needs dim = 2");
+    if (q->n_gl < 2 || q->n_gl % 2 || q->n_phi < 4 || q->n_phi % 4)
+      return fail(h, RTE_EINVAL, "CL rule needs even n_gl >= 2 and n_phi a multiple of 4");
+    std::vector<double> x, w;
+    gauss_legendre(q->n_gl, x, w);
+    for (int j2 = 0; j2 < q->n_gl; ++j2) {
+      if (!(x[j2] > 0.0)) continue;
+      const double s = std::sqrt(1.0 - x[j2] * x[j2]);
+      for (int j1 = 1; j1 <= q->n_phi; ++j1) {
+        const double phi = (2.0 * j1 - 1.0) * M_PI / q->n_phi;
+        h->mu_user.push_back(std::cos(phi) * s);
+        h->eta_user.push_back(std::sin(phi) * s);
+        h->w_user.push_back(w[j2] / q->n_phi);  // (w/2) * (1/n_phi) doubled for the hemisphere
+      }
+    }
+  } else if (q->kind == RTE_Q_EXPLICIT) {
+    if (q->n_dirs < 2 || !q->mu || !q->w || (dim == 2 && !q->eta))
+      return fail(h, RTE_EINVAL, "explicit quadrature needs n_dirs >= 2 and mu, eta, w");
+    for (int i = 0; i < q->n_dirs; ++i) {
+      h->mu_user.push_back(q->mu[i]);
+      h->eta_user.push_back(dim == 2 ? q->eta[i] : 0.0);
+      h->w_user.push_back(q->w[i]);
+    }
+  } else {
+    return fail(h, RTE_EINVAL, "unknown quadrature kind");
+  }
+  double ws = 0.0;
+  for (size_t i = 0; i < h->w_user.size(); ++i) {
+    if (!std::isfinite(h->mu_user[i]) || !std::isfinite(h->eta_user[i]) ||
+        !std::isfinite(h->w_user[i]) || h->w_user[i] < 0.0)
+      return fail(h, RTE_EINVAL, "quadrature has a non-finite direction or a negative weight");
+    ws += h->w_user[i];
+  }
+  if (std::fabs(ws - 1.0) > 1e-12) return fail(h, RTE_EINVAL, "quadrature weights must sum to 1");
+  return RTE_OK;
+}
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Group the directions into families of one quadrant (2D) or half-range (1D).
+rte_status make_layout(rte_handle h) {
+  Layout& L = h->L;
+  L = Layout{};
+  L.dim = h->dim;
+  const int nv = (int)h->mu_user.size();
+  L.nv = nv;
+  L.slot_of_dir.assign(nv, -1);
+  const int nq = h->dim == 2 ? 4 : 2;
+  std::vector<std::vector<int>> byq(nq);
+  for (int d = 0; d < nv; ++d) {
+    const double mu = h->mu_user[d], eta = h->eta_user[d];
+    if (mu == 0.0 || (h->dim == 2 && eta == 0.0))
+      return fail(h, RTE_EINVAL, "a direction lies on a coordinate axis");
+    int qd = mu > 0 ? 0 : 1;
+    if (h->dim == 2 && eta < 0) qd += 2;
+    byq[qd].push_back(d);
+  }
+  const int dq = (int)byq[0].size();
+  for (int qd = 1; qd < nq; ++qd)
+    if ((int)byq[qd].size() != dq)
+      return fail(h, RTE_EINVAL, "every quadrant (half-range in 1D) needs the same number of directions");
+  if (h->dim == 1) {
+    L.dl = dq;
+    L.nfam = 2;
+    L.nslot = nv;
+  } else {
+    L.dl = dq >= 32 ? 32 : std::max(8, next_pow2(dq));
+    const int gpq = (dq + L.dl - 1) / L.dl;
+    L.nfam = 4 * gpq;
+    L.nslot = L.nfam * L.dl;
+  }
+  L.mu.assign(L.nslot, 0.0);
+  L.eta.assign(L.nslot, 0.0);
+  L.w.assign(L.nslot, 0.0);
+  L.fam_quadrant.assign(L.nfam, 0);
+  const int gpq = L.nfam / nq;
+  for (int qd = 0; qd < nq; ++qd) {
+    for (int g = 0; g < gpq; ++g) L.fam_quadrant[qd * gpq + g] = qd;
+    for (int k = 0; k < dq; ++k) {
+      const int slot = (h->dim == 1) ? qd * dq + k : (qd * gpq + k / L.dl) * L.dl + k % L.dl;
+      const int d = byq[qd][k];
+      L.slot_of_dir[d] = slot;
+      L.mu[slot] = h->mu_user[d];
+      L.eta[slot] = h->eta_user[d];
+      L.w[slot] = h->w_user[d];
+    }
+  }
+  return RTE_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+void free_all(rte_handle h) {
+  void* ptrs[] = {h->sig_t, h->sig_s, h->src, h->ca, h->cb, h->cw, h->fam_quad, h->dir_sign,
+                  h->inv_d, h->f, h->pm, h->pm_a, h->edge, h->ctrl, h->psi_w, h->psi_w_a,
+                  h->rho, h->rho_prev, h->rho_half, h->rho_half1, h->rho0, h->y, h->btilde,
+                  h->q, h->delta, h->tmp, h->tmp2, h->tmp3, h->delta_pc1, h->resp[0],
+                  h->resp[1], h->resp[2], h->resp[3], h->partials, h->dotbuf, h->norms,
+                  h->cg_iters, h->rho_init, h->f_init};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  dsa_free(h->dsa);
+  rom_free(h->ig);
+  rom_free(h->pc);
+  cudaEvent_t evs[] = {h->ev0, h->ev1, h->kev0, h->kev1};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (h->own_st) cudaStreamDestroy(h->own_st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Sweeps
+// ---------------------------------------------------------------------------------------
+void quadrant_ghosts(const double g[4], double gx[4], double gy[4]) {
+  for (int qd = 0; qd < 4; ++qd) {
+    gx[qd] = (qd & 1) == 0 ? g[0] : g[1];
+    gy[qd] = qd < 2 ? g[2] : g[3];
+  }
+}
+
+Sweep2DArgs<double> args2d(rte_handle h) {
+  Sweep2DArgs<double> a{};
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nfam = h->L.nfam;
+  a.nslot = h->L.nslot;
+  a.nblk = h->nblk;
+  a.rows_per_blk = h->rows_per_blk;
+  a.tau = h->tau;
+  a.a = h->ca;
+  a.b = h->cb;
+  a.w = h->cw;
+  a.fam_quad = h->fam_quad;
+  a.sig_t = h->sig_t;
+  a.inv_d = h->inv_d;
+  a.edge = h->edge;
+  a.ctrl = h->ctrl;
+  return a;
+}
+
+Sweep1DArgs<double> args1d(rte_handle h) {
+  Sweep1DArgs<double> a{};
+  a.nx = h->nx;
+  a.nslot = h->L.nslot;
+  a.tau = h->tau;
+  a.a = h->ca;
+  a.w = h->cw;
+  a.dir_sign = h->dir_sign;
+  a.sig_t = h->sig_t;
+  a.psi_w = h->psi_w;
+  return a;
+}
+
+// out = sum_j w_j L_j^{-1} q with isotropic source q and inflow g (nullptr: vacuum), as the
+// per-family partial moments in h->pm (2D) or the full moment in h->pm (1D, one "family").
+rte_status sweep_si_partials(rte_handle h, const double* q, const double* g) {
+  const double zero[4] = {0, 0, 0, 0};
+  if (!g) g = zero;
+  if (h->dim == 2) {
+    Sweep2DArgs<double> a = args2d(h);
+    a.q = q;
+    a.pm = h->pm;
+    quadrant_ghosts(g, a.gx, a.gy);
+    CK(launch_sweep2d<double>(a, 0, h->R, h->st));
+  } else {
+    Sweep1DArgs<double> a = args1d(h);
+    a.q = q;
+    a.g_lo = g[0];
+    a.g_hi = g[1];
+    CK(launch_sweep1d<double>(a, 0, h->st));
+    CK(launch_moment1d<double>(h->psi_w, h->L.nslot, (int)h->ncell, h->pm, h->st));
+  }
+  return RTE_OK;
+}
+
+int nparts(rte_handle h) { return h->dim == 2 ? h->L.nfam : 1; }
+
+rte_status sweep_si(rte_handle h, const double* q, const double* g, double* out) {
+  TRY(sweep_si_partials(h, q, g));
+  CK(launch_sum_partials(h->pm, nparts(h), (int)h->ncell, nullptr, out, h->st));
+  return RTE_OK;
+}
+
+// Fused end-of-step sweep: f <- L^-1(qa + tau f + g^bc) in place and
+// y = sum_j w_j L_j^-1(G + tau f^n) with zero inflow.
+rte_status sweep_f(rte_handle h, const double* qa, double* y_out) {
+  if (h->dim == 2) {
+    Sweep2DArgs<double> a = args2d(h);
+    a.q = qa;
+    a.g2 = h->src;
+    a.f = h->f;
+    a.pm = h->pm;
+    a.pm_a = nullptr;
+    quadrant_ghosts(h->g, a.gx, a.gy);
+    CK(launch_sweep2d<double>(a, 1, h->R, h->st));
+    CK(launch_sum_partials(h->pm, h->L.nfam, (int)h->ncell, nullptr, y_out, h->st));
+  } else {
+    Sweep1DArgs<double> a = args1d(h);
+    a.q = qa;
+    a.g2 = h->src;
+    a.f = h->f;
+    a.psi_w_a = nullptr;
+    a.g_lo = h->g[0];
+    a.g_hi = h->g[1];
+    CK(launch_sweep1d<double>(a, 1, h->st));
+    CK(launch_moment1d<double>(h->psi_w, h->L.nslot, (int)h->ncell, y_out, h->st));
+  }
+  return RTE_OK;
+}
+
+// y = sum_j w_j L_j^-1(G + tau f) from the stored f, zero inflow.
+rte_status sweep_y(rte_handle h, double* y_out) {
+  if (h->dim == 2) {
+    Sweep2DArgs<double> a = args2d(h);
+    a.g2 = h->src;
+    a.f = h->f;
+    a.pm = h->pm;
+    CK(launch_sweep2d<double>(a, 2, h->R, h->st));
+    CK(launch_sum_partials(h->pm, h->L.nfam, (int)h->ncell, nullptr, y_out, h->st));
+  } else {
+    Sweep1DArgs<double> a = args1d(h);
+    a.g2 = h->src;
+    a.f = h->f;
+    CK(launch_sweep1d<double>(a, 2, h->st));
+    CK(launch_moment1d<double>(h->psi_w, h->L.nslot, (int)h->ncell, y_out, h->st));
+  }
+  return RTE_OK;
+}
+
+rte_status check_sweep_error(rte_handle h) {
+  unsigned err = 0;
+  if (h->dim == 2) {
+    CK(cudaMemcpyAsync(&err, &h->ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (err) {
+      const size_t bytes = sizeof(SweepCtrl) + sizeof(unsigned) * h->L.nfam * h->nblk;
+      CK(cudaMemsetAsync(h->ctrl, 0, bytes, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      return fail(h, RTE_ETIMEOUT, "a bounded wait in the sweep ran out");
+    }
+  }
+  return RTE_OK;
+}
+
+// Responses to unit isotropic inflow on each side: b~ is linear in g, so
+// b~ = y + sum_s g_s resp_s (Eq. (implicit_linear_system_rho) with g_j^bc split off).
+rte_status ensure_responses(rte_handle h) {
+  if (h->resp_ready) return RTE_OK;
+  const int sides = h->dim == 2 ? 4 : 2;
+  for (int s = 0; s < sides; ++s) {
+    if (!h->resp[s]) CK(dalloc(&h->resp[s], h->ncell));
+    double g[4] = {0, 0, 0, 0};
+    g[s] = 1.0;
+    CK(cudaMemsetAsync(h->tmp, 0, sizeof(double) * h->ncell, h->st));
+    TRY(sweep_si(h, h->tmp, g, h->resp[s]));
+  }
+  h->resp_ready = true;
+  return RTE_OK;
+}
+
+rte_status make_btilde(rte_handle h) {
+  if (!h->y_valid) {
+    TRY(sweep_y(h, h->y));
+    h->y_valid = true;
+  }
+  CK(cudaMemcpyAsync(h->btilde, h->y, sizeof(double) * h->ncell, cudaMemcpyDeviceToDevice, h->st));
+  const int sides = h->dim == 2 ? 4 : 2;
+  bool any = false;
+  for (int s = 0; s < sides; ++s) any = any || h->g[s] != 0.0;
+  if (any) {
+    TRY(ensure_responses(h));
+    for (int s = 0; s < sides; ++s)
+      if (h->g[s] != 0.0)
+        CK(launch_axpby(1.0, h->btilde, h->g[s], h->resp[s], (int)h->ncell, h->btilde, h->st));
+  }
+  return RTE_OK;
+}
+
+rte_status dev_dot(rte_handle h, const double* x, const double* y, double* out) {
+  const int nb = vec_blocks((int)h->ncell);
+  CK(launch_dot(x, y, (int)h->ncell, h->partials, nb, h->dotbuf, h->st));
+  CK(cudaMemcpyAsync(out, h->dotbuf, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+float elapsed(rte_handle h) {
+  float ms = 0.f;
+  cudaEventRecord(h->ev1, h->st);
+  cudaEventSynchronize(h->ev1);
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  cudaEventRecord(h->ev0, h->st);
+  return ms;
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 1 on the current b~ from initial guess rho0.  Leaves rho^n in h->rho.
+// ---------------------------------------------------------------------------------------
+rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out) {
+  const int n = (int)h->ncell;
+  const int nb = vec_blocks(n);
+  CK(cudaMemcpyAsync(h->rho_prev, h->rho0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  CK(launch_scale_copy(h->rho_prev, h->sig_s, n, h->q, h->st));
+  int cg_total = 0;
+  bool conv = false;
+  int l = 0;
+  h->pc_applied = false;
+  for (l = 1; l <= h->opt.max_iter; ++l) {
+    cudaEventRecord(h->ev0, h->st);
+    cudaEventRecord(h->kev0, h->st);
+    TRY(sweep_si_partials(h, h->q, nullptr));
+    cudaEventRecord(h->kev1, h->st);
+    CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
+                               h->partials, nb, h->norms, h->st));
+    Norms nm;
+    CK(cudaMemcpyAsync(&nm, h->norms, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
+    h->stats.time_sweep_ms += elapsed(h);
+    {
+      float kms = 0.f;
+      cudaEventElapsedTime(&kms, h->kev0, h->kev1);
+      h->stats.si_sweep_kernel_ms += kms;
+      h->stats.si_sweep_launches += 1;
+    }
+    if (l == 1)
+      CK(cudaMemcpyAsync(h->rho_half1, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                         h->st));
+    const double res = h->opt.residual_norm == RTE_ABS_INF
+                           ? nm.diff_inf
+                           : (nm.half_inf > 0 ? nm.diff_inf / nm.half_inf : nm.diff_inf);
+    conv = h->opt.residual_norm == RTE_ABS_INF ? nm.diff_inf <= h->opt.eps_sisa
+                                               : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
+    h->stats.last_residual = res;
+    if (conv) break;
+    if (l == 1 && use_pc) {
+      // ROM preconditioner, Eq. (dmd-sa): delta = dU C_r^{-1} dU^T (rho^{1/2} - rho^{(0)})
+      CK(launch_axpby(1.0, h->rho_half, -1.0, h->rho0, n, h->tmp, h->st));
+      CK(rom_apply(h->pc, h->tmp, h->delta_pc1, h->st));
+      CK(launch_update_rho(h->rho_half, h->delta_pc1, h->sig_s, n, h->rho_prev, h->q, h->st));
+      h->pc_applied = true;
+      h->stats.time_rom_ms += elapsed(h);
+    } else {
+      // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta
+      CK(dsa_solve(h->dsa, h->sig_s, h->rho_half, h->rho_prev, h->opt.cg_rtol, h->opt.cg_max_iter,
+                   h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters, h->st));
+      int its = 0;
+      CK(cudaMemcpyAsync(&its, h->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      h->stats.time_dsa_ms += elapsed(h);
+      cg_total += its;
+    }
+  }
+  if (l > h->opt.max_iter) l = h->opt.max_iter;
+  CK(cudaMemcpyAsync(h->rho, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  h->stats.last_cg_iterations = cg_total;
+  h->stats.total_cg_iterations += cg_total;
+  *iters_out = l;
+  *converged_out = conv;
+  return RTE_OK;
+}
+
+// ROM construction / adaptive update for the step just taken (Algorithm 2, Sec. 3.2).
+rte_status rom_update(rte_handle h) {
+  const int n = (int)h->ncell;
+  cudaEventRecord(h->ev0, h->st);
+  double rn2 = 0.0;
+  TRY(dev_dot(h, h->rho, h->rho, &rn2));
+  const double thr = h->opt.eps_up * (h->opt.up_rel ? std::sqrt(rn2) : 1.0);
+  bool ig_up = false, pc_up = false;
+  h->stats.last_ig_error = NAN;
+  h->stats.last_pc_error = NAN;
+  int grew = 0;
+  double ratio = 0.0;
+  if (!h->flag_ig) {
+    CK(rom_append(h->ig, h->rho, h->btilde, -1.0, &grew, &ratio, h->st));
+    ig_up = true;
+    if (ratio <= h->opt.eps_ig || h->ig.rank >= h->opt.r_max) h->flag_ig = true;
+  } else {
+    double e2 = INFINITY;
+    if (h->ig_applied) {
+      CK(launch_axpby(1.0, h->rho0, -1.0, h->rho, n, h->tmp, h->st));
+      TRY(dev_dot(h, h->tmp, h->tmp, &e2));
+      h->stats.last_ig_error = std::sqrt(e2);
+    }
+    if (!(std::sqrt(e2) <= thr)) {
+      CK(rom_append(h->ig, h->rho, h->btilde, h->opt.eps_ig, &grew, &ratio, h->st));
+      ig_up = true;
+    }
+    const bool has_corr = h->last_iters > 1;
+    // d_rho1 = rho^n - rho^{n,1/2} (tmp2), d_b1 = rho^{n,1/2} - rho^{n,(0)} (tmp3)
+    CK(launch_axpby(1.0, h->rho, -1.0, h->rho_half1, n, h->tmp2, h->st));
+    CK(launch_axpby(1.0, h->rho_half1, -1.0, h->rho0, n, h->tmp3, h->st));
+    if (!h->flag_pc) {
+      if (has_corr) {
+        CK(rom_append(h->pc, h->tmp2, h->tmp3, -1.0, &grew, &ratio, h->st));
+        pc_up = true;
+        if (ratio <= h->opt.eps_pc || h->pc.rank >= h->opt.r_max) h->flag_pc = true;
+      }
+    } else if (has_corr) {
+      double p2 = INFINITY;
+      if (h->pc_applied) {
+        CK(launch_axpby(1.0, h->delta_pc1, -1.0, h->tmp2, n, h->tmp, h->st));
+        TRY(dev_dot(h, h->tmp, h->tmp, &p2));
+        h->stats.last_pc_error = std::sqrt(p2);
+      }
+      if (ig_up || !(std::sqrt(p2) <= thr)) {
+        CK(rom_append(h->pc, h->tmp2, h->tmp3, h->opt.eps_pc, &grew, &ratio, h->st));
+        pc_up = true;
+      }
+    }
+  }
+  h->stats.ig_updated = ig_up;
+  h->stats.pc_updated = pc_up;
+  h->stats.ig_rank = h->ig.rank;
+  h->stats.pc_rank = h->pc.rank;
+  h->stats.time_rom_ms += elapsed(h);
+  return RTE_OK;
+}
+
+rte_status one_step(rte_handle h) {
+  const int n = (int)h->ncell;
+  const bool rom_on = h->opt.rom != RTE_ROM_OFF;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaEventRecord(h->ev0, h->st);
+  TRY(make_btilde(h));
+  h->stats.time_sweep_ms += elapsed(h);
+  h->ig_applied = false;
+  if (rom_on && h->flag_ig && h->ig.lu_ok) {
+    CK(rom_apply(h->ig, h->btilde, h->rho0, h->st));   // Eq. (dmd-ig)
+    h->ig_applied = true;
+    h->stats.time_rom_ms += elapsed(h);
+  } else {
+    CK(cudaMemcpyAsync(h->rho0, h->rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  }
+  const bool use_pc = rom_on && h->flag_pc && h->pc.lu_ok;
+  int iters = 0;
+  bool conv = false;
+  TRY(si_sa(h, use_pc, &iters, &conv));
+  h->last_iters = iters;
+  // f^n and the next step's b~ (without inflow): Eq. (sweep_to_obtain_f), Eq. (implicit_linear_system_rho)
+  cudaEventRecord(h->ev0, h->st);
+  CK(launch_scale_copy(h->rho, h->sig_s, n, h->q, h->st));
+  CK(launch_axpby(1.0, h->q, 1.0, h->src, n, h->q, h->st));
+  cudaEventRecord(h->kev0, h->st);
+  TRY(sweep_f(h, h->q, h->y));
+  cudaEventRecord(h->kev1, h->st);
+  h->y_valid = true;
+  h->stats.time_sweep_ms += elapsed(h);
+  {
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, h->kev0, h->kev1);
+    h->stats.f_sweep_kernel_ms += kms;
+    h->stats.f_sweep_launches += 1;
+  }
+  TRY(check_sweep_error(h));
+  const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!h->flag_pc ? 2 : 3));
+  h->stats.phase = phase;
+  h->stats.steps += 1;
+  h->stats.last_iterations = iters;
+  h->stats.total_iterations += iters;
+  h->stats.total_sweeps += iters + 2;
+  h->stats.cell_direction_updates += (long long)(iters + 2) * h->ncell * h->L.nv;
+  if (!conv) return fail(h, RTE_ENOCONV, "SI-SA reached max_iter without meeting eps_sisa");
+  if (rom_on) {
+    if (h->opt.rom == RTE_ROM_AUTO)
+      TRY(rom_update(h));
+    else
+      h->pending_rom = true;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  auto t1 = std::chrono::steady_clock::now();
+  h->stats.time_total_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+  return RTE_OK;
+}
+
+bool finite_all(const double* v, long n) {
+  for (long i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+rte_status upload(rte_handle h, double* dst, const double* src, long n) {
+  CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+rte_status reset_state(rte_handle h) {
+  h->stats = rte_stats{};
+  h->flag_ig = h->flag_pc = false;
+  h->y_valid = false;
+  h->pending_rom = false;
+  h->ig.rank = 0;
+  h->pc.rank = 0;
+  h->ig.lu_ok = h->pc.lu_ok = 0;
+  return RTE_OK;
+}
+
+rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature* quad,
+                       const double* sigma_t, const double* sigma_s, const double* source,
+                       double c_dt, const rte_options* opt) {
+  if (!mesh || !quad || !sigma_t || !sigma_s || !source)
+    return fail(h, RTE_EINVAL, "mesh, quadrature and cross-section arrays are required");
+  h->opt = opt ? *opt : rte_options{};
+  if (!opt) rte_default_options(&h->opt);
+  if (mesh->dim != 1 && mesh->dim != 2) return fail(h, RTE_EINVAL, "dim must be 1 or 2");
+  if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1))
+    return fail(h, RTE_EINVAL, "bad cell counts");
+  if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0)))
+    return fail(h, RTE_EINVAL, "empty domain");
+  if (!(c_dt > 0.0) || !std::isfinite(c_dt)) return fail(h, RTE_EINVAL, "c_dt must be > 0");
+  if (h->opt.precision != RTE_FP64)
+    return fail(h, RTE_EINVAL, "this build supports precision = RTE_FP64");
+  if (h->opt.r_max < 1 || h->opt.r_max > 64) return fail(h, RTE_EINVAL, "r_max must be in [1, 64]");
+  if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
+  if (!(h->opt.eps_sisa >= 0.0)) return fail(h, RTE_EINVAL, "eps_sisa must be >= 0");
+  h->dim = mesh->dim;
+  h->nx = mesh->nx;
+  h->ny = mesh->ny;
+  h->ncell = (long)mesh->nx * mesh->ny;
+  if (h->ncell > (1L << 31) / 2) return fail(h, RTE_EINVAL, "too many cells");
+  h->hx = (mesh->x1 - mesh->x0) / mesh->nx;
+  h->hy = mesh->dim == 2 ? (mesh->y1 - mesh->y0) / mesh->ny : 1.0;
+  h->c_dt = c_dt;
+  h->tau = 1.0 / c_dt;
+  const long n = h->ncell;
+  if (!finite_all(sigma_t, n) || !finite_all(sigma_s, n) || !finite_all(source, n))
+    return fail(h, RTE_EINVAL, "non-finite cross section or source");
+  for (long i = 0; i < n; ++i)
+    if (sigma_s[i] < 0.0 || sigma_t[i] < sigma_s[i])
+      return fail(h, RTE_EINVAL, "need sigma_t >= sigma_s >= 0 in every cell");
+  TRY(make_rule(h, quad, h->dim));
+  TRY(make_layout(h));
+  CK(cudaGetDevice(&h->device));
+  CK(cudaStreamCreateWithFlags(&h->own_st, cudaStreamNonBlocking));
+  h->st = h->own_st;
+  CK(cudaEventCreate(&h->ev0));
+  CK(cudaEventCreate(&h->ev1));
+  CK(cudaEventCreate(&h->kev0));
+  CK(cudaEventCreate(&h->kev1));
+  const Layout& L = h->L;
+  // sweep tiling
+  if (h->dim == 2) {
+    h->R = std::min(4, L.dl);
+    h->rows_per_blk = (32 / L.dl) * h->R;
+    h->nblk = (h->ny + h->rows_per_blk - 1) / h->rows_per_blk;
+  }
+  CK(dalloc(&h->sig_t, n));
+  CK(dalloc(&h->sig_s, n));
+  CK(dalloc(&h->src, n));
+  TRY(upload(h, h->sig_t, sigma_t, n));
+  TRY(upload(h, h->sig_s, sigma_s, n));
+  TRY(upload(h, h->src, source, n));
+  std::vector<double> a(L.nslot), b(L.nslot);
+  std::vector<int> sign(L.nslot);
+  for (int s = 0; s < L.nslot; ++s) {
+    a[s] = std::fabs(L.mu[s]) / h->hx;
+    b[s] = h->dim == 2 ? std::fabs(L.eta[s]) / h->hy : 0.0;
+    sign[s] = L.mu[s] > 0 ? 1 : -1;
+  }
+  CK(dalloc(&h->ca, L.nslot));
+  CK(dalloc(&h->cb, L.nslot));
+  CK(dalloc(&h->cw, L.nslot));
+  CK(dalloc(&h->fam_quad, L.nfam));
+  CK(dalloc(&h->dir_sign, L.nslot));
+  TRY(upload(h, h->ca, a.data(), L.nslot));
+  TRY(upload(h, h->cb, b.data(), L.nslot));
+  TRY(upload(h, h->cw, L.w.data(), L.nslot));
+  CK(cudaMemcpy(h->fam_quad, L.fam_quadrant.data(), sizeof(int) * L.nfam, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dir_sign, sign.data(), sizeof(int) * L.nslot, cudaMemcpyHostToDevice));
+  CK(dalloc(&h->f, (size_t)n * L.nslot));
+  CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
+  if (h->dim == 2) {
+    CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
+    CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, h->inv_d, h->st));
+    CK(dalloc(&h->pm, (size_t)L.nfam * n));
+    CK(dalloc(&h->edge, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
+    const size_t cb_bytes = sizeof(SweepCtrl) + sizeof(unsigned) * L.nfam * h->nblk;
+    CK(cudaMalloc((void**)&h->ctrl, cb_bytes));
+    CK(cudaMemsetAsync(h->ctrl, 0, cb_bytes, h->st));
+  } else {
+    CK(dalloc(&h->pm, n));
+    CK(dalloc(&h->psi_w, (size_t)n * L.nslot));
+  }
+  double** vecs[] = {&h->rho, &h->rho_prev, &h->rho_half, &h->rho_half1, &h->rho0, &h->y,
+                     &h->btilde, &h->q, &h->delta, &h->tmp, &h->tmp2, &h->tmp3, &h->delta_pc1};
+  for (double** v : vecs) {
+    CK(dalloc(v, n));
+    CK(cudaMemsetAsync(*v, 0, sizeof(double) * n, h->st));
+  }
+  CK(dalloc(&h->partials, 3 * 1024));
+  CK(dalloc(&h->dotbuf, 4));
+  CK(dalloc(&h->norms, 1));
+  CK(dalloc(&h->cg_iters, 1));
+  CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st));
+  CK(rom_alloc(h->ig, (int)n, h->opt.r_max));
+  CK(rom_alloc(h->pc, (int)n, h->opt.r_max));
+  CK(cudaStreamSynchronize(h->st));
+  return reset_state(h);
+}
+
+}  // namespace
+
+// =========================================================================================
+// C ABI
+// =========================================================================================
+extern "C" {
+
+void rte_default_options(rte_options* o) {
+  if (!o) return;
+  *o = rte_options{};
+  o->eps_sisa = 1e-8;
+  o->eps_ig = 1e-6;
+  o->eps_pc = 1e-6;
+  o->eps_up = 1e-6;
+  o->max_iter = 500;
+  o->r_max = 40;
+  o->precision = RTE_FP64;
+  o->rom = RTE_ROM_AUTO;
+  o->residual_norm = RTE_REL_INF;
+  o->up_rel = 1;
+  o->cg_rtol = 1e-6;
+  o->cg_max_iter = 500;
+  o->tune = 1;
+}
+
+rte_status rte_create(rte_handle* out, const rte_mesh* mesh, const rte_quadrature* quad,
+                      const double* sigma_t, const double* sigma_s, const double* source,
+                      double c_dt, const rte_options* opt) {
+  if (!out) return RTE_EINVAL;
+  *out = nullptr;
+  rte_handle h = new (std::nothrow) rte_s();
+  if (!h) return RTE_ENOMEM;
+  rte_status s = create_impl(h, mesh, quad, sigma_t, sigma_s, source, c_dt, opt);
+  if (s != RTE_OK) {
+    g_create_error = h->err;   // the handle is gone; rte_last_error(NULL) reports it
+    free_all(h);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return RTE_OK;
+}
+
+rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
+  if (!h) return RTE_EINVAL;
+  const long n = h->ncell;
+  const Layout& L = h->L;
+  if (f0) {
+    if (!finite_all(f0, n * L.nv)) return fail(h, RTE_EINVAL, "non-finite f0");
+    std::vector<double> fl((size_t)n * L.nslot, 0.0), rho(n, 0.0);
+    for (int d = 0; d < L.nv; ++d) {
+      const int s = L.slot_of_dir[d];
+      for (long c = 0; c < n; ++c) fl[(size_t)c * L.nslot + s] = f0[(size_t)d * n + c];
+    }
+    for (int d = 0; d < L.nv; ++d)
+      for (long c = 0; c < n; ++c) rho[c] += h->w_user[d] * f0[(size_t)d * n + c];
+    TRY(upload(h, h->f, fl.data(), (long)fl.size()));
+    TRY(upload(h, h->rho, rho.data(), n));
+    if (!h->f_init) CK(dalloc(&h->f_init, (size_t)n * L.nslot));
+    CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * n * L.nslot, cudaMemcpyDeviceToDevice,
+                       h->st));
+    h->init_kind = 2;
+  } else {
+    if (!rho0) return fail(h, RTE_EINVAL, "rho0 or f0 is required");
+    if (!finite_all(rho0, n)) return fail(h, RTE_EINVAL, "non-finite rho0");
+    TRY(upload(h, h->rho, rho0, n));
+    CK(launch_isotropic_f(h->rho, (int)n, L.nslot, h->cw, h->f, h->st));
+    h->init_kind = 1;
+  }
+  if (!h->rho_init) CK(dalloc(&h->rho_init, n));
+  CK(cudaMemcpyAsync(h->rho_init, h->rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return reset_state(h);
+}
+
+rte_status rte_set_stream(rte_handle h, void* cuda_stream) {
+  if (!h) return RTE_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  h->st = cuda_stream ? (cudaStream_t)cuda_stream : h->own_st;
+  return RTE_OK;
+}
+
+rte_status rte_restart(rte_handle h) {
+  if (!h) return RTE_EINVAL;
+  if (h->init_kind == 0) return fail(h, RTE_ESTATE, "rte_set_initial has not been called");
+  const long n = h->ncell;
+  CK(cudaMemcpyAsync(h->rho, h->rho_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  if (h->init_kind == 2)
+    CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * n * h->L.nslot, cudaMemcpyDeviceToDevice,
+                       h->st));
+  else
+    CK(launch_isotropic_f(h->rho, (int)n, h->L.nslot, h->cw, h->f, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return reset_state(h);
+}
+
+rte_status rte_set_inflow(rte_handle h, const double g[4]) {
+  if (!h || !g) return RTE_EINVAL;
+  for (int s = 0; s < 4; ++s)
+    if (!std::isfinite(g[s])) return fail(h, RTE_EINVAL, "non-finite inflow");
+  for (int s = 0; s < 4; ++s) h->g[s] = (h->dim == 1 && s >= 2) ? 0.0 : g[s];
+  return RTE_OK;
+}
+
+rte_status rte_step(rte_handle h, int nsteps) {
+  if (!h) return RTE_EINVAL;
+  if (nsteps < 0) return fail(h, RTE_EINVAL, "nsteps must be >= 0");
+  if (h->pending_rom) return fail(h, RTE_ESTATE, "RTE_ROM_MANUAL: call rte_rom_update first");
+  const long long l0 = g_launches;
+  rte_status s = RTE_OK;
+  for (int k = 0; k < nsteps && s == RTE_OK; ++k) s = one_step(h);
+  h->stats.kernel_launches += g_launches - l0;
+  return s;
+}
+
+rte_status rte_rom_update(rte_handle h) {
+  if (!h) return RTE_EINVAL;
+  if (h->opt.rom != RTE_ROM_MANUAL || !h->pending_rom)
+    return fail(h, RTE_ESTATE, "no manual ROM update is pending");
+  h->pending_rom = false;
+  const long long l0 = g_launches;
+  rte_status s = rom_update(h);
+  h->stats.kernel_launches += g_launches - l0;
+  if (s != RTE_OK) return s;
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+rte_status rte_get_scalar_flux(rte_handle h, double* rho) {
+  if (!h || !rho) return RTE_EINVAL;
+  CK(cudaMemcpyAsync(rho, h->rho, sizeof(double) * h->ncell, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+rte_status rte_get_angular_flux(rte_handle h, double* f) {
+  if (!h || !f) return RTE_EINVAL;
+  const Layout& L = h->L;
+  const long n = h->ncell;
+  std::vector<double> fl((size_t)n * L.nslot);
+  CK(cudaMemcpyAsync(fl.data(), h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  for (int d = 0; d < L.nv; ++d) {
+    const int s = L.slot_of_dir[d];
+    for (long c = 0; c < n; ++c) f[(size_t)d * n + c] = fl[(size_t)c * L.nslot + s];
+  }
+  return RTE_OK;
+}
+
+rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta, double* w) {
+  if (!h) return RTE_EINVAL;
+  if (n_dirs) *n_dirs = h->L.nv;
+  for (int d = 0; d < h->L.nv; ++d) {
+    if (mu) mu[d] = h->mu_user[d];
+    if (eta) eta[d] = h->eta_user[d];
+    if (w) w[d] = h->w_user[d];
+  }
+  return RTE_OK;
+}
+
+rte_status rte_get_stats(rte_handle h, rte_stats* st) {
+  if (!h || !st) return RTE_EINVAL;
+  *st = h->stats;
+  st->ig_rank = h->ig.rank;
+  st->pc_rank = h->pc.rank;
+  return RTE_OK;
+}
+
+const char* rte_last_error(rte_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void rte_destroy(rte_handle h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+// ------------------------------- operator-level calls -------------------------------
+
+rte_status rte_op_sweep(rte_handle h, const double* rho, double* out) {
+  if (!h || !rho || !out) return RTE_EINVAL;
+  const int n = (int)h->ncell;
+  TRY(upload(h, h->tmp, rho, n));
+  CK(launch_scale_copy(h->tmp, h->sig_s, n, h->q, h->st));
+  TRY(sweep_si(h, h->q, nullptr, h->tmp2));
+  TRY(check_sweep_error(h));
+  CK(cudaMemcpyAsync(out, h->tmp2, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+rte_status rte_op_fsweep(rte_handle h, const double* rho, double* btilde) {
+  if (!h || !rho) return RTE_EINVAL;
+  const int n = (int)h->ncell;
+  TRY(upload(h, h->tmp, rho, n));
+  CK(launch_scale_copy(h->tmp, h->sig_s, n, h->q, h->st));
+  CK(launch_axpby(1.0, h->q, 1.0, h->src, n, h->q, h->st));
+  TRY(sweep_f(h, h->q, h->y));
+  h->y_valid = true;
+  TRY(check_sweep_error(h));
+  if (btilde) {
+    TRY(make_btilde(h));
+    CK(cudaMemcpyAsync(btilde, h->btilde, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+rte_status rte_op_dsa(rte_handle h, const double* residual, double* delta, int* iterations) {
+  if (!h || !residual || !delta) return RTE_EINVAL;
+  const int n = (int)h->ncell;
+  TRY(upload(h, h->tmp, residual, n));
+  CK(dsa_solve(h->dsa, h->sig_s, h->tmp, nullptr, h->opt.cg_rtol, h->opt.cg_max_iter, h->delta,
+               nullptr, nullptr, nullptr, h->cg_iters, h->st));
+  int its = 0;
+  CK(cudaMemcpyAsync(&its, h->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(delta, h->delta, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (iterations) *iterations = its;
+  return RTE_OK;
+}
+
+rte_status rte_op_rom_append(rte_handle h, int which, const double* x, const double* b,
+                             double trunc_eps, int* grew) {
+  if (!h || !x || !b || (which != RTE_ROM_IG && which != RTE_ROM_PC)) return RTE_EINVAL;
+  const int n = (int)h->ncell;
+  TRY(upload(h, h->tmp2, x, n));
+  TRY(upload(h, h->tmp3, b, n));
+  RomDev& R = which == RTE_ROM_IG ? h->ig : h->pc;
+  int g = 0;
+  double ratio = 0;
+  CK(rom_append(R, h->tmp2, h->tmp3, trunc_eps, &g, &ratio, h->st));
+  if (grew) *grew = g;
+  return RTE_OK;
+}
+
+rte_status rte_op_rom_apply(rte_handle h, int which, const double* rhs, double* out) {
+  if (!h || !rhs || !out || (which != RTE_ROM_IG && which != RTE_ROM_PC)) return RTE_EINVAL;
+  RomDev& R = which == RTE_ROM_IG ? h->ig : h->pc;
+  if (R.rank <= 0 || !R.lu_ok) return fail(h, RTE_ESTATE, "ROM is empty or its operator is singular");
+  const int n = (int)h->ncell;
+  TRY(upload(h, h->tmp2, rhs, n));
+  CK(rom_apply(R, h->tmp2, h->tmp3, h->st));
+  CK(cudaMemcpyAsync(out, h->tmp3, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RTE_OK;
+}
+
+rte_status rte_op_rom_get(rte_handle h, int which, int* rank, double* S, double* U, double* Ar) {
+  if (!h || (which != RTE_ROM_IG && which != RTE_ROM_PC)) return RTE_EINVAL;
+  RomDev& R = which == RTE_ROM_IG ? h->ig : h->pc;
+  if (rank) *rank = R.rank;
+  CK(rom_get(R, S, U, Ar, h->st));
+  return RTE_OK;
+}
+
+rte_status rte_op_rom_reset(rte_handle h) {
+  if (!h) return RTE_EINVAL;
+  h->ig.rank = h->pc.rank = 0;
+  h->ig.lu_ok = h->pc.lu_ok = 0;
+  h->flag_ig = h->flag_pc = false;
+  return RTE_OK;
+}
+
+}  // extern "C"

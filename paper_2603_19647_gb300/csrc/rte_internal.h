@@ -1,0 +1,161 @@
+// Internal declarations shared by the CUDA kernels and the host driver of librte.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rte.h"
+
+namespace rte {
+
+// Number of kernels launched by this library on the calling host thread (for reporting).
+extern thread_local long long g_launches;
+
+// ---------------------------------------------------------------------------------------
+// Direction layout.  The directions of a 2D rule fall into four quadrants that share one
+// upwind order each (Sec. 2.3: the sweep reorders cells along the upwind direction).  A
+// "family" is a group of dl directions of one quadrant that one lane group of a warp
+// sweeps together (lane = direction).  Slots are padded so every family has dl lanes; a
+// padded slot has weight 0.  1D slabs have two half-ranges (mu > 0, mu < 0).
+// ---------------------------------------------------------------------------------------
+struct Layout {
+  int dim = 2;
+  int nv = 0;        // caller directions
+  int dl = 32;       // lanes per family (power of two, <= 32)
+  int nfam = 0;      // families
+  int nslot = 0;     // nfam * dl
+  std::vector<int> slot_of_dir;    // caller direction -> slot
+  std::vector<int> fam_quadrant;   // family -> quadrant (2D: 0 (+,+) 1 (-,+) 2 (+,-) 3 (-,-); 1D: 0 (+) 1 (-))
+  std::vector<double> mu, eta, w;  // per slot
+};
+
+// Control block of one strip-chain sweep launch (self-resetting: the last CTA zeroes it).
+struct SweepCtrl {
+  unsigned int ticket;
+  unsigned int done;
+  unsigned int err;      // 1: a bounded wait ran out
+  unsigned int pad;
+  unsigned int flags[1]; // [nfam * nblk] columns published by each row block
+};
+
+// Arguments of the 2D strip-chain sweep (Sec. 2.3 transport sweep, Q0 upwind cell solve).
+template <class Real>
+struct Sweep2DArgs {
+  int nx, ny, nfam, nslot, nblk, rows_per_blk;
+  Real tau;
+  const Real* a;        // [nslot] |mu|/hx
+  const Real* b;        // [nslot] |eta|/hy
+  const Real* w;        // [nslot]
+  const int* fam_quad;  // [nfam]
+  const Real* sig_t;    // [ncell]
+  const Real* inv_d;    // [ncell][nslot] 1/(tau+sigma_t+a+b) or nullptr (computed)
+  // K1: isotropic source q = Sigma_s rho; K2 pass A: q = Sigma_s rho + G.
+  const Real* q;        // [ncell]
+  const Real* g2;       // K2 pass B isotropic source G [ncell]
+  Real* f;              // K2: [ncell][nslot] in / out (f^{n-1} -> f^n)
+  Real* pm;             // [nfam][ncell] partial moments (K1: of L^-1 q; K2: of pass B)
+  Real* pm_a;           // K2: [nfam][ncell] partial moments of f^n (may be nullptr)
+  Real gx[4], gy[4];    // per quadrant inflow ghost of pass A (K1: zero)
+  Real* edge;           // [nfam][nblk][nx][dl] (K2: two planes, A then B)
+  SweepCtrl* ctrl;
+};
+
+// Arguments of the 1D scan sweep (one CTA per slot).
+template <class Real>
+struct Sweep1DArgs {
+  int nx, nslot;
+  Real tau;
+  const Real* a;
+  const Real* w;
+  const int* dir_sign;  // [nslot] +1 / -1
+  const Real* sig_t;
+  const Real* q;        // [ncell]
+  const Real* g2;       // K2 pass B source
+  Real* f;              // [ncell][nslot]
+  Real* psi_w;          // scratch [nslot][ncell] of w * psi (moment input)
+  Real* psi_w_a;        // K2: scratch of w * f^n or nullptr
+  Real g_lo, g_hi;      // inflow at x0 (for mu > 0) and x1 (for mu < 0), pass A
+};
+
+// Launchers (sweep.cu).
+template <class Real>
+cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStream_t s);
+template <class Real>
+cudaError_t launch_sweep1d(const Sweep1DArgs<Real>& a, int mode, cudaStream_t s);
+template <class Real>
+cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s);
+template <class Real>
+cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
+                         int nslot, Real* inv_d, cudaStream_t s);
+
+// Vector kernels (vec.cu).
+struct Norms {             // device-side reduction results of one residual evaluation
+  double diff_inf, half_inf, diff_l2sq, pad;
+};
+cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
+                                    const double* rho_prev, int ncell, double* rho_half,
+                                    double* partials, int nblocks, Norms* out, cudaStream_t s);
+cudaError_t launch_update_rho(const double* rho_half, const double* delta, const double* sig_s,
+                              int ncell, double* rho, double* q, cudaStream_t s);
+cudaError_t launch_scale_copy(const double* x, const double* sig_s, int ncell, double* q,
+                              cudaStream_t s);
+cudaError_t launch_sum_partials(const double* pm, int nfam, int ncell, const double* add,
+                                double* out, cudaStream_t s);
+cudaError_t launch_axpby(double alpha, const double* x, double beta, const double* y, int n,
+                         double* out, cudaStream_t s);
+cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, const double* wslot,
+                               double* f, cudaStream_t s);
+cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
+                       double* out, cudaStream_t s);
+int vec_blocks(int n);
+
+// DSA (cg.cu): 5-point (1D: 3-point) diffusion operator with Marshak vacuum faces.
+struct DsaOp {
+  int nx, ny, n;
+  double* diag;   // [n]
+  double* cx;     // [n] coupling of cell c with c+1 (0 at the east edge)
+  double* cy;     // [n] coupling of cell c with c+nx (0 at the north edge / 1D)
+  // CG workspace
+  double *r, *p0, *p1, *ap, *x;
+  double* partial;   // [2 * blocks]
+  double* scal;      // [8] device scalars
+  int blocks;
+};
+cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
+                      const double* sig_t_host, const double* sig_s_host, cudaStream_t s);
+void dsa_free(DsaOp& op);
+// delta = C^{-1} (sig_s .* (residual - residual_b)) (residual_b may be nullptr);
+// rho_out = rho_half + delta and q_out = sig_s .* rho_out when rho_out != nullptr.
+// Iteration count to *iters_dev (device int).
+cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
+                      const double* residual_b, double rtol, int max_iter, double* delta,
+                      const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
+                      cudaStream_t s);
+
+// ROM (rom.cu).
+struct RomDev {
+  int n, r_max, rank;
+  double* U;      // [r_max+1][n] column-major (column k at U + k*n)
+  double* W;      // [r_max+1][n]  (W = B V)
+  double* Utmp;   // [r_max+1][n]
+  double* Wtmp;   // [r_max+1][n]
+  double* S;      // [r_max+1]
+  double* core;   // small workspace
+  double* lu;     // [r_max*r_max] LU of A_r, row-major, with pivots
+  int* piv;
+  double* proj;   // [r_max+1] projections
+  double* partial;
+  int lu_ok;
+};
+cudaError_t rom_alloc(RomDev& R, int n, int r_max);
+void rom_free(RomDev& R);
+// Incremental SVD append (App. B).  Returns new rank in *rank_out (host), grew flag.
+cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc_eps,
+                       int* grew, double* smallest_ratio, cudaStream_t s);
+// out = U A_r^{-1} U^T rhs.  Returns cudaErrorInvalidValue if the LU is not available.
+cudaError_t rom_apply(RomDev& R, const double* rhs, double* out, cudaStream_t s);
+cudaError_t rom_get(RomDev& R, double* S, double* U, double* Ar, cudaStream_t s);
+
+}  // namespace rte

@@ -1,0 +1,209 @@
+// Cell-vector kernels of the SI-SA loop (Algorithm 1): the residual and convergence test of
+// Sec. 2.3 (||rho^{l-1/2} - rho^{l-1}||_inf), the density update rho^l = rho^{l-1/2} + delta,
+// and small reductions.  All FP64; reductions use a fixed block partition and a fixed
+// summation order, so results are bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include "rte_internal.h"
+
+namespace rte {
+
+namespace {
+constexpr int VT = 256;
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+// rho_half = sum_f pm[f] + btilde; diff = rho_half - rho_prev; per-block max|diff|,
+// max|rho_half|, sum diff^2.
+__global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
+                                        const double* __restrict__ btilde,
+                                        const double* __restrict__ rho_prev, int n,
+                                        double* __restrict__ rho_half, double* partials) {
+  __shared__ double sh[3][VT / 32];
+  double dinf = 0.0, hinf = 0.0, d2 = 0.0;
+  for (int c = blockIdx.x * VT + threadIdx.x; c < n; c += gridDim.x * VT) {
+    double s = 0.0;
+    for (int f = 0; f < nfam; ++f) s += pm[(long)f * n + c];
+    s += btilde[c];
+    rho_half[c] = s;
+    const double d = s - rho_prev[c];
+    dinf = fmax(dinf, fabs(d));
+    hinf = fmax(hinf, fabs(s));
+    d2 += d * d;
+  }
+  dinf = warp_max(dinf);
+  hinf = warp_max(hinf);
+  d2 = warp_sum(d2);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[0][w] = dinf;
+    sh[1][w] = hinf;
+    sh[2][w] = d2;
+  }
+  __syncthreads();
+  if (w == 0) {
+    dinf = l < VT / 32 ? sh[0][l] : 0.0;
+    hinf = l < VT / 32 ? sh[1][l] : 0.0;
+    d2 = l < VT / 32 ? sh[2][l] : 0.0;
+    dinf = warp_max(dinf);
+    hinf = warp_max(hinf);
+    d2 = warp_sum(d2);
+    if (l == 0) {
+      partials[3 * blockIdx.x + 0] = dinf;
+      partials[3 * blockIdx.x + 1] = hinf;
+      partials[3 * blockIdx.x + 2] = d2;
+    }
+  }
+}
+
+__global__ void finish_norms_kernel(const double* partials, int nblocks, Norms* out) {
+  double dinf = 0.0, hinf = 0.0, d2 = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) {
+    dinf = fmax(dinf, partials[3 * b]);
+    hinf = fmax(hinf, partials[3 * b + 1]);
+    d2 += partials[3 * b + 2];
+  }
+  dinf = warp_max(dinf);
+  hinf = warp_max(hinf);
+  d2 = warp_sum(d2);
+  if (threadIdx.x == 0) {
+    out->diff_inf = dinf;
+    out->half_inf = hinf;
+    out->diff_l2sq = d2;
+  }
+}
+
+__global__ void update_rho_kernel(const double* rho_half, const double* delta, const double* sig_s,
+                                  int n, double* rho, double* q) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  const double r = rho_half[c] + delta[c];
+  rho[c] = r;
+  q[c] = sig_s[c] * r;
+}
+
+__global__ void scale_copy_kernel(const double* x, const double* sig_s, int n, double* q) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  q[c] = sig_s[c] * x[c];
+}
+
+__global__ void sum_partials_kernel(const double* pm, int nfam, int n, const double* add,
+                                    double* out) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  double s = 0.0;
+  for (int f = 0; f < nfam; ++f) s += pm[(long)f * n + c];
+  if (add) s += add[c];
+  out[c] = s;
+}
+
+__global__ void axpby_kernel(double alpha, const double* x, double beta, const double* y, int n,
+                             double* out) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  out[c] = alpha * x[c] + beta * y[c];
+}
+
+__global__ void isotropic_f_kernel(const double* rho, int n, int nslot, const double* wslot,
+                                   double* f) {
+  const long i = (long)blockIdx.x * VT + threadIdx.x;
+  if (i >= (long)n * nslot) return;
+  const long c = i / nslot;
+  f[i] = rho[c];
+}
+
+__global__ void dot_partial_kernel(const double* x, const double* y, int n, double* partials) {
+  __shared__ double sh[VT / 32];
+  double s = 0.0;
+  for (int c = blockIdx.x * VT + threadIdx.x; c < n; c += gridDim.x * VT) s += x[c] * y[c];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < VT / 32 ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void dot_finish_kernel(const double* partials, int nblocks, double* out) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) s += partials[b];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+}  // namespace
+
+int vec_blocks(int n) {
+  int b = (n + VT - 1) / VT;
+  return b < 1 ? 1 : (b > 1024 ? 1024 : b);
+}
+
+cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
+                                    const double* rho_prev, int n, double* rho_half,
+                                    double* partials, int nblocks, Norms* out, cudaStream_t s) {
+  ++g_launches;
+  combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, partials);
+  ++g_launches;
+  finish_norms_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_rho(const double* rho_half, const double* delta, const double* sig_s,
+                              int n, double* rho, double* q, cudaStream_t s) {
+  ++g_launches;
+  update_rho_kernel<<<(n + VT - 1) / VT, VT, 0, s>>>(rho_half, delta, sig_s, n, rho, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(const double* x, const double* sig_s, int n, double* q,
+                              cudaStream_t s) {
+  ++g_launches;
+  scale_copy_kernel<<<(n + VT - 1) / VT, VT, 0, s>>>(x, sig_s, n, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* pm, int nfam, int n, const double* add, double* out,
+                                cudaStream_t s) {
+  ++g_launches;
+  sum_partials_kernel<<<(n + VT - 1) / VT, VT, 0, s>>>(pm, nfam, n, add, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double alpha, const double* x, double beta, const double* y, int n,
+                         double* out, cudaStream_t s) {
+  ++g_launches;
+  axpby_kernel<<<(n + VT - 1) / VT, VT, 0, s>>>(alpha, x, beta, y, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, const double* wslot, double* f,
+                               cudaStream_t s) {
+  const long tot = (long)n * nslot;
+  ++g_launches;
+  isotropic_f_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, wslot, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
+                       double* out, cudaStream_t s) {
+  ++g_launches;
+  dot_partial_kernel<<<nblocks, VT, 0, s>>>(x, y, n, partials);
+  ++g_launches;
+  dot_finish_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rte

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of librte.so (include/rte.h): argument marshalling only.
+
+Every function below calls the C entry point of the same name; all arithmetic of the method
+runs in the library's CUDA kernels.  There is no Python or CPU fallback: ``load()`` raises
+when the library has not been built, and every call raises ``RteError`` on a non-OK status.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librte.so")
+
+RTE_OK, RTE_EINVAL, RTE_ENOMEM, RTE_ENOCONV, RTE_ECUDA, RTE_ETIMEOUT, RTE_ESTATE = range(7)
+RTE_Q_GL1D, RTE_Q_CL_HEMI, RTE_Q_EXPLICIT = range(3)
+RTE_FP64, RTE_FP32, RTE_FP32_BF16F = range(3)
+RTE_REL_INF, RTE_ABS_INF = range(2)
+RTE_ROM_OFF, RTE_ROM_AUTO, RTE_ROM_MANUAL = range(3)
+RTE_ROM_IG, RTE_ROM_PC = range(2)
+STATUS_NAMES = {0: "RTE_OK", 1: "RTE_EINVAL", 2: "RTE_ENOMEM", 3: "RTE_ENOCONV", 4: "RTE_ECUDA",
+                5: "RTE_ETIMEOUT", 6: "RTE_ESTATE"}
+
+
+class RteError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Quadrature(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_gl", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("n_dirs", ctypes.c_int), ("mu", _dp), ("eta", _dp), ("w", _dp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps_sisa", ctypes.c_double), ("eps_ig", ctypes.c_double),
+                ("eps_pc", ctypes.c_double), ("eps_up", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("r_max", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rom", ctypes.c_int), ("residual_norm", ctypes.c_int), ("up_rel", ctypes.c_int),
+                ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("phase", ctypes.c_int), ("last_iterations", ctypes.c_int),
+                ("last_cg_iterations", ctypes.c_int), ("total_iterations", ctypes.c_longlong),
+                ("total_sweeps", ctypes.c_longlong), ("total_cg_iterations", ctypes.c_longlong),
+                ("ig_rank", ctypes.c_int), ("pc_rank", ctypes.c_int), ("ig_updated", ctypes.c_int),
+                ("pc_updated", ctypes.c_int), ("last_residual", ctypes.c_double),
+                ("last_ig_error", ctypes.c_double), ("last_pc_error", ctypes.c_double),
+                ("cell_direction_updates", ctypes.c_longlong), ("time_sweep_ms", ctypes.c_double),
+                ("time_dsa_ms", ctypes.c_double), ("time_rom_ms", ctypes.c_double),
+                ("time_total_ms", ctypes.c_double), ("si_sweep_launches", ctypes.c_longlong),
+                ("si_sweep_kernel_ms", ctypes.c_double), ("f_sweep_launches", ctypes.c_longlong),
+                ("f_sweep_kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "rte_default_options": (None, [ctypes.POINTER(Options)]),
+    "rte_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Mesh), ctypes.POINTER(Quadrature),
+                                  _dp, _dp, _dp, ctypes.c_double, ctypes.POINTER(Options)]),
+    "rte_set_initial": (ctypes.c_int, [_vp, _dp, _dp]),
+    "rte_set_inflow": (ctypes.c_int, [_vp, _dp]),
+    "rte_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rte_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "rte_restart": (ctypes.c_int, [_vp]),
+    "rte_rom_update": (ctypes.c_int, [_vp]),
+    "rte_get_scalar_flux": (ctypes.c_int, [_vp, _dp]),
+    "rte_get_angular_flux": (ctypes.c_int, [_vp, _dp]),
+    "rte_get_quadrature": (ctypes.c_int, [_vp, _ip, _dp, _dp, _dp]),
+    "rte_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+    "rte_last_error": (ctypes.c_char_p, [_vp]),
+    "rte_destroy": (None, [_vp]),
+    "rte_op_sweep": (ctypes.c_int, [_vp, _dp, _dp]),
+    "rte_op_fsweep": (ctypes.c_int, [_vp, _dp, _dp]),
+    "rte_op_dsa": (ctypes.c_int, [_vp, _dp, _dp, _ip]),
+    "rte_op_rom_append": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, ctypes.c_double, _ip]),
+    "rte_op_rom_apply": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
+    "rte_op_rom_get": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp, _dp, _dp]),
+    "rte_op_rom_reset": (ctypes.c_int, [_vp]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load librte.so (built by paper_2603_19647_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def default_options(**kw):
+    o = Options()
+    load().rte_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """One problem instance (an ``rte_handle``).  Methods mirror the C calls one to one."""
+
+    def __init__(self, ptr, ncell, nv):
+        self.ptr = ptr
+        self.ncell = ncell
+        self.nv = nv
+
+    def _check(self, status):
+        if status != RTE_OK:
+            msg = load().rte_last_error(self.ptr).decode()
+            raise RteError(status, msg)
+
+    # lifecycle -----------------------------------------------------------------------
+    def rte_destroy(self):
+        if self.ptr:
+            load().rte_destroy(self.ptr)
+            self.ptr = None
+
+    destroy = rte_destroy
+
+    def __del__(self):
+        try:
+            self.rte_destroy()
+        except Exception:
+            pass
+
+    def rte_set_initial(self, rho0=None, f0=None):
+        rho0 = None if rho0 is None else _f64(rho0, self.ncell)
+        f0 = None if f0 is None else _f64(f0, self.ncell * self.nv)
+        self._check(load().rte_set_initial(self.ptr, _p(rho0), _p(f0)))
+
+    def rte_set_inflow(self, g):
+        g = _f64(g, 4)
+        self._check(load().rte_set_inflow(self.ptr, _p(g)))
+
+    def rte_set_stream(self, stream_ptr):
+        """stream_ptr: an integer cudaStream_t (e.g. torch.cuda.Stream().cuda_stream) or None."""
+        self._check(load().rte_set_stream(self.ptr, None if stream_ptr is None else
+                                          ctypes.c_void_p(int(stream_ptr))))
+
+    def rte_restart(self):
+        self._check(load().rte_restart(self.ptr))
+
+    def rte_step(self, nsteps=1):
+        self._check(load().rte_step(self.ptr, int(nsteps)))
+
+    def rte_rom_update(self):
+        self._check(load().rte_rom_update(self.ptr))
+
+    def rte_get_scalar_flux(self):
+        out = np.empty(self.ncell)
+        self._check(load().rte_get_scalar_flux(self.ptr, _p(out)))
+        return out
+
+    def rte_get_angular_flux(self):
+        out = np.empty((self.nv, self.ncell))
+        self._check(load().rte_get_angular_flux(self.ptr, _p(out)))
+        return out
+
+    def rte_get_quadrature(self):
+        n = ctypes.c_int(0)
+        mu, eta, w = np.empty(self.nv), np.empty(self.nv), np.empty(self.nv)
+        self._check(load().rte_get_quadrature(self.ptr, ctypes.byref(n), _p(mu), _p(eta), _p(w)))
+        return mu, eta, w
+
+    def rte_get_stats(self):
+        st = Stats()
+        self._check(load().rte_get_stats(self.ptr, ctypes.byref(st)))
+        return st.as_dict()
+
+    # operator-level calls ------------------------------------------------------------
+    def rte_op_sweep(self, rho):
+        rho = _f64(rho, self.ncell)
+        out = np.empty(self.ncell)
+        self._check(load().rte_op_sweep(self.ptr, _p(rho), _p(out)))
+        return out
+
+    def rte_op_fsweep(self, rho):
+        rho = _f64(rho, self.ncell)
+        out = np.empty(self.ncell)
+        self._check(load().rte_op_fsweep(self.ptr, _p(rho), _p(out)))
+        return out
+
+    def rte_op_dsa(self, residual):
+        r = _f64(residual, self.ncell)
+        out = np.empty(self.ncell)
+        its = ctypes.c_int(0)
+        self._check(load().rte_op_dsa(self.ptr, _p(r), _p(out), ctypes.byref(its)))
+        return out, its.value
+
+    def rte_op_rom_append(self, which, x, b, trunc_eps=-1.0):
+        x = _f64(x, self.ncell)
+        b = _f64(b, self.ncell)
+        grew = ctypes.c_int(0)
+        self._check(load().rte_op_rom_append(self.ptr, int(which), _p(x), _p(b), float(trunc_eps),
+                                             ctypes.byref(grew)))
+        return bool(grew.value)
+
+    def rte_op_rom_apply(self, which, rhs):
+        rhs = _f64(rhs, self.ncell)
+        out = np.empty(self.ncell)
+        self._check(load().rte_op_rom_apply(self.ptr, int(which), _p(rhs), _p(out)))
+        return out
+
+    def rte_op_rom_get(self, which):
+        r = ctypes.c_int(0)
+        self._check(load().rte_op_rom_get(self.ptr, int(which), ctypes.byref(r), None, None, None))
+        r = r.value
+        S, U, Ar = np.empty(r), np.empty((r, self.ncell)), np.empty((r, r))
+        if r:
+            self._check(load().rte_op_rom_get(self.ptr, int(which), None, _p(S), _p(U), _p(Ar)))
+        return S, U, Ar
+
+    def rte_op_rom_reset(self):
+        self._check(load().rte_op_rom_reset(self.ptr))
+
+
+def rte_create(mesh: Mesh, quad: Quadrature, sigma_t, sigma_s, source, c_dt, options=None):
+    """rte_create; returns a Handle.  mesh / quad: ctypes structs (see ``mesh_from`` and
+    ``quadrature_from``); arrays are per cell, x fastest."""
+    lib = load()
+    n = mesh.nx * mesh.ny
+    st, ss, G = _f64(sigma_t, n), _f64(sigma_s, n), _f64(source, n)
+    h = _vp()
+    opt = ctypes.byref(options) if options is not None else None
+    status = lib.rte_create(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), _p(st), _p(ss),
+                            _p(G), float(c_dt), opt)
+    if status != RTE_OK:
+        raise RteError(status, lib.rte_last_error(None).decode())
+    nv = ctypes.c_int(0)
+    lib.rte_get_quadrature(h, ctypes.byref(nv), None, None, None)
+    return Handle(h, n, nv.value)
+
+
+def mesh_from(workload):
+    x0, x1, y0, y1 = workload.domain
+    dim = 1 if workload.quadrature[0] == "gl" else 2
+    return Mesh(dim, workload.nx, workload.ny, x0, x1, y0, y1)
+
+
+def quadrature_from(desc=None, mu=None, eta=None, w=None):
+    """A Quadrature struct from a workload descriptor ("gl", n) / ("cl_hemi", n_phi, n_vz), or
+    from explicit arrays (kept alive on the returned struct)."""
+    if mu is not None:
+        mu, w = _f64(mu), _f64(w)
+        eta = np.zeros_like(mu) if eta is None else _f64(eta)
+        q = Quadrature(RTE_Q_EXPLICIT, 0, 0, mu.size, _p(mu), _p(eta), _p(w))
+        q._keep = (mu, eta, w)
+        return q
+    if desc[0] == "gl":
+        return Quadrature(RTE_Q_GL1D, desc[1], 0, 0, None, None, None)
+    return Quadrature(RTE_Q_CL_HEMI, desc[2], desc[1], 0, None, None, None)
+
+
+def create_from_workload(wl, options=None, quad=None):
+    """rte_create + rte_set_initial for an inputs.Workload (inflow set when nonzero)."""
+    h = rte_create(mesh_from(wl), quad if quad is not None else quadrature_from(wl.quadrature),
+                   wl.sigma_t, wl.sigma_s, wl.source, wl.c_dt, options)
+    h.rte_set_initial(wl.rho0)
+    if np.any(wl.inflow):
+        h.rte_set_inflow(wl.inflow)
+    return h

@@ -1,0 +1,71 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point declared in
+include/rte.h, and rejects invalid problems with RTE_EINVAL before touching the GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2603_19647_gb300 import build as gbuild
+from paper_2603_19647_gb300 import rte
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return rte.load()
+
+
+def _declared():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(rte_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(rte._SIGS)
+
+
+def test_default_options(lib):
+    o = rte.default_options()
+    assert (o.eps_sisa, o.eps_ig, o.eps_pc, o.eps_up) == (1e-8, 1e-6, 1e-6, 1e-6)
+    assert (o.max_iter, o.r_max, o.cg_rtol, o.cg_max_iter) == (500, 40, 1e-6, 500)
+
+
+def _create(**kw):
+    args = dict(mesh=rte.Mesh(2, 4, 4, 0, 1, 0, 1), quad=rte.quadrature_from(("cl_hemi", 8, 4)),
+                sigma_t=np.ones(16), sigma_s=np.full(16, 0.5), source=np.zeros(16), c_dt=0.1)
+    args.update(kw)
+    return rte.rte_create(**args)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(sigma_s=np.full(16, 2.0)),                       # sigma_t < sigma_s
+    dict(sigma_s=np.full(16, -0.1)),                      # sigma_s < 0
+    dict(sigma_t=np.r_[np.ones(15), np.nan]),             # non-finite
+    dict(c_dt=0.0),
+    dict(c_dt=-1.0),
+    dict(mesh=rte.Mesh(3, 4, 4, 0, 1, 0, 1)),
+    dict(mesh=rte.Mesh(2, 4, 4, 1, 0, 0, 1)),             # empty domain
+    dict(quad=rte.quadrature_from(("cl_hemi", 6, 4))),    # n_phi not a multiple of 4
+    dict(quad=rte.quadrature_from(mu=[0.5, -0.5], eta=[0.5, 0.5], w=[0.5, 0.6])),  # sum w != 1
+    dict(quad=rte.quadrature_from(mu=[0.5, -0.5, 0.5, -0.5], eta=[0.5, 0.5, -0.5, 0.0],
+                                  w=[0.25] * 4)),         # a direction on an axis
+    dict(options=rte.default_options(r_max=65)),
+    dict(options=rte.default_options(precision=7)),
+])
+def test_invalid_problems_rejected(lib, bad):
+    with pytest.raises(rte.RteError) as ei:
+        _create(**bad)
+    assert ei.value.status == rte.RTE_EINVAL
+    assert len(str(ei.value)) > 12
