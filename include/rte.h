@@ -91,6 +91,9 @@ typedef struct {
   double cg_rtol;    /* DSA conjugate-gradient tolerance ||r|| <= cg_rtol ||b|| (default 1e-6) */
   int cg_max_iter;   /* default 500 */
   int tune;          /* 1 (default): pick sweep tile shapes by timing at create; 0: heuristic */
+  int sweep_rows;    /* 2D sweep: rows per lane group, 1, 2, 4 or 8 (0 = automatic) */
+  int sweep_lanes;   /* 2D sweep: directions per lane group, 8, 16 or 32 (0 = automatic) */
+  int sweep_warps;   /* 2D sweep: warps per CTA, 1..8 (0 = automatic); reduced to fit shared memory */
 } rte_options;
 
 typedef struct {

@@ -9,7 +9,8 @@
 // Append (App. B, Eq. (svd_core)), one snapshot pair (x, b):
 //   p = U^T x;  q~ = x - U p;  repeated once (classical Gram-Schmidt twice);
 //   alpha = ||q~||; the rank grows iff alpha > 1e-12 ||x|| (else q is dropped);
-//   K = [[S, p], [0, alpha]] = U_c S_c V_c^T  (one-sided Jacobi, FP64, one CTA);
+//   K = [[S, p], [0, alpha]] = U_c S_c V_c^T  (secular equation of the broken-arrow form,
+//   FP64, csvd.cu);
 //   keep = r+1 (or r), truncated to s_k / sum s > eps when asked, capped at r_max;
 //   U <- [U q] U_c(:, :keep);  W <- [W b] V_c(:, :keep);
 //   G <- U_c^T [[G, U^T b], [q^T W, q^T b]] V_c;  A_r = G S^{-1}, LU with partial pivoting.
@@ -119,141 +120,6 @@ Scr scr_of(double* core) {
   return s;
 }
 constexpr long SCR_DOUBLES = 4 * MAXR + 16 + 4 * MAXR * MAXR;
-
-// One-sided Jacobi SVD of the (r+1) x (r+1) core K = [[S, p], [0, alpha]] in one CTA
-// (round-robin pair ordering, one warp per pair), then sorting, growth and truncation.
-__global__ void __launch_bounds__(1024) core_svd_kernel(const double* S, int r, Scr sc,
-                                                        double trunc_eps, int r_max) {
-  extern __shared__ double smem[];
-  const int n = r + 1;
-  const int np = n + (n & 1);
-  const int ld = np;  // column stride
-  double* M = smem;             // [np][ld] columns
-  double* V = M + np * ld;      // [np][ld]
-  __shared__ int s_rot;
-  __shared__ double s_sig[MAXR + 1];
-  __shared__ int s_ord[MAXR + 1];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const double xn = sqrt(sc.sc[0]);
-  const double alpha = sqrt(fmax(sc.sc[1], 0.0));
-  const bool grew = alpha > 1e-12 * xn;
-  for (int e = tid; e < np * ld; e += blockDim.x) {
-    M[e] = 0.0;
-    V[e] = 0.0;
-  }
-  __syncthreads();
-  for (int i = tid; i < n; i += blockDim.x) {
-    if (i < r) {
-      M[i * ld + i] = S[i];
-      M[r * ld + i] = sc.p[i];   // column r, row i
-    } else {
-      M[r * ld + r] = grew ? alpha : 0.0;
-    }
-  }
-  for (int i = tid; i < np; i += blockDim.x) V[i * ld + i] = 1.0;
-  __syncthreads();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int rd = 0; rd < np - 1; ++rd) {
-      for (int k = warp; k < np / 2; k += nw) {
-        int i, j;
-        if (k == 0) {
-          i = np - 1;
-          j = rd;
-        } else {
-          i = (rd + k) % (np - 1);
-          j = (rd - k + np - 1) % (np - 1);
-        }
-        double* mi = M + i * ld;
-        double* mj = M + j * ld;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int e = lane; e < n; e += 32) {
-          a += mi[e] * mi[e];
-          b += mj[e] * mj[e];
-          g += mi[e] * mj[e];
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g != 0.0 && fabs(g) > 1e-15 * sqrt(a * b)) {
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double s = c * t;
-          for (int e = lane; e < n; e += 32) {
-            const double x = mi[e], y = mj[e];
-            mi[e] = c * x - s * y;
-            mj[e] = s * x + c * y;
-          }
-          double* vi = V + i * ld;
-          double* vj = V + j * ld;
-          for (int e = lane; e < np; e += 32) {
-            const double x = vi[e], y = vj[e];
-            vi[e] = c * x - s * y;
-            vj[e] = s * x + c * y;
-          }
-          if (lane == 0) atomicAdd(&s_rot, 1);
-        }
-      }
-      __syncthreads();
-    }
-    const int rot = s_rot;
-    __syncthreads();
-    if (rot == 0) break;
-  }
-  // singular values = column norms
-  for (int j = warp; j < n; j += nw) {
-    double a = 0.0;
-    for (int e = lane; e < n; e += 32) a += M[j * ld + e] * M[j * ld + e];
-    a = warp_sum(a);
-    if (lane == 0) s_sig[j] = sqrt(a);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int j = 0; j < n; ++j) s_ord[j] = j;
-    for (int a = 0; a < n; ++a) {  // selection sort, descending
-      int best = a;
-      for (int b = a + 1; b < n; ++b)
-        if (s_sig[s_ord[b]] > s_sig[s_ord[best]]) best = b;
-      const int t = s_ord[a];
-      s_ord[a] = s_ord[best];
-      s_ord[best] = t;
-    }
-    int keep = grew ? n : r;
-    double ratio = 0.0;
-    if (grew && n > 0) {
-      double tot = 0.0;
-      for (int a = 0; a < n; ++a) tot += s_sig[s_ord[a]];
-      ratio = tot > 0.0 ? s_sig[s_ord[n - 1]] / tot : 0.0;
-    }
-    if (trunc_eps >= 0.0 && keep > 0) {
-      double tot = 0.0;
-      for (int a = 0; a < keep; ++a) tot += s_sig[s_ord[a]];
-      int k2 = 0;
-      for (int a = 0; a < keep; ++a)
-        if (s_sig[s_ord[a]] / tot > trunc_eps) ++k2;
-      keep = k2;
-    }
-    if (keep > r_max) keep = r_max;
-    sc.sc[3] = grew ? 1.0 / alpha : 0.0;
-    sc.sc[4] = keep;
-    sc.sc[5] = grew ? 1.0 : 0.0;
-    sc.sc[6] = ratio;
-  }
-  __syncthreads();
-  const int keep = (int)sc.sc[4];
-  // U_c(:, a) = M(:, ord[a]) / sigma, V_c(:, a) = V(:, ord[a]) for a < keep
-  for (int e = tid; e < n * keep; e += blockDim.x) {
-    const int a = e / n, row = e % n;
-    const int j = s_ord[a];
-    const double sg = s_sig[j];
-    sc.Uc[a * n + row] = sg > 0.0 ? M[j * ld + row] / sg : 0.0;
-    sc.Vc[a * n + row] = V[j * ld + row];
-  }
-  // new singular values go to sc.p2 temporarily (S is rewritten after the G update)
-  for (int a = tid; a < keep; a += blockDim.x) sc.p2[a] = s_sig[s_ord[a]];
-}
 
 // scaled copy q = q~ * (1/alpha) (0 when the rank does not grow)
 __global__ void scale_q_kernel(double* q, long n, const double* sc) {
@@ -428,7 +294,6 @@ __global__ void add_vec_kernel(double* a, const double* b, int r) {
   if ((int)threadIdx.x < r) a[threadIdx.x] += b[threadIdx.x];
 }
 
-constexpr int CORE_SMEM = 2 * 66 * 66 * (int)sizeof(double);
 constexpr int GLU_SMEM = 3 * MAXR * MAXR * (int)sizeof(double);
 constexpr int ROT_SMEM = (MAXR * MAXR + ROT_ROWS * (MAXR + 1)) * (int)sizeof(double);
 
@@ -458,7 +323,9 @@ cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc
   }
   if ((e = dot(q, q, n, R.partial, sc.sc + 1, s)) != cudaSuccess) return e;
   ++g_launches;
-  core_svd_kernel<<<1, 1024, CORE_SMEM, s>>>(R.S, r, sc, trunc_eps, R.r_max);
+  if ((e = core_svd_secular(R.S, r, sc.p, sc.sc, sc.Uc, sc.Vc, sc.p2, trunc_eps, R.r_max, R.sec,
+                            s)) != cudaSuccess)
+    return e;
   ++g_launches;
   scale_q_kernel<<<vb, 256, 0, s>>>(q, n, sc.sc);
   if (r > 0 && (e = gemv_t(R.W, n, r, q, R.partial, sc.wq, 0, s)) != cudaSuccess) return e;
@@ -539,9 +406,7 @@ cudaError_t rom_alloc(RomDev& R, int n, int r_max) {
   if ((e = cudaMalloc(&R.piv, sizeof(int) * MAXR)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&R.proj, sizeof(double) * MAXR)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&R.partial, sizeof(double) * MAXR * 256)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(core_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                CORE_SMEM)) != cudaSuccess)
-    return e;
+  if ((e = cudaMalloc(&R.sec, sizeof(double) * secular_scratch_doubles())) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(g_update_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 GLU_SMEM)) != cudaSuccess)
     return e;
@@ -552,7 +417,7 @@ cudaError_t rom_alloc(RomDev& R, int n, int r_max) {
 }
 
 void rom_free(RomDev& R) {
-  double* d[] = {R.U, R.W, R.Utmp, R.Wtmp, R.S, R.core, R.lu, R.proj, R.partial};
+  double* d[] = {R.U, R.W, R.Utmp, R.Wtmp, R.S, R.core, R.lu, R.proj, R.partial, R.sec};
   for (double* p : d)
     if (p) cudaFree(p);
   if (R.piv) cudaFree(R.piv);

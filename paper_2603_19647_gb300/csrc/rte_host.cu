@@ -35,7 +35,7 @@ struct rte_s {
   rte_options opt{};
   std::vector<double> mu_user, eta_user, w_user;  // library direction order
   Layout L;
-  int R = 4, rows_per_blk = 4, nblk = 1;
+  int R = 2, W = 4, rows_per_blk = 8, nblk = 1;
   // device: problem data
   double *sig_t = nullptr, *sig_s = nullptr, *src = nullptr;
   double *ca = nullptr, *cb = nullptr, *cw = nullptr;
@@ -184,6 +184,11 @@ rte_status make_rule(rte_handle h, const rte_quadrature* q, int dim) {
   return RTE_OK;
 }
 
+// Angular flux layout on the device: [family][cell][lane], slot = family * dl + lane.
+size_t f_index(const Layout& L, long ncell, long c, int slot) {
+  return ((size_t)(slot / L.dl) * ncell + c) * L.dl + slot % L.dl;
+}
+
 int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -218,6 +223,7 @@ rte_status make_layout(rte_handle h) {
     L.nslot = nv;
   } else {
     L.dl = dq >= 32 ? 32 : std::max(8, next_pow2(dq));
+    if (h->opt.sweep_lanes) L.dl = h->opt.sweep_lanes;
     const int gpq = (dq + L.dl - 1) / L.dl;
     L.nfam = 4 * gpq;
     L.nslot = L.nfam * L.dl;
@@ -669,6 +675,14 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
     return fail(h, RTE_EINVAL, "this build supports precision = RTE_FP64");
   if (h->opt.r_max < 1 || h->opt.r_max > 64) return fail(h, RTE_EINVAL, "r_max must be in [1, 64]");
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
+  if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
+      h->opt.sweep_lanes != 32)
+    return fail(h, RTE_EINVAL, "sweep_lanes must be 0, 8, 16 or 32");
+  if (h->opt.sweep_rows != 0 && h->opt.sweep_rows != 1 && h->opt.sweep_rows != 2 &&
+      h->opt.sweep_rows != 4 && h->opt.sweep_rows != 8)
+    return fail(h, RTE_EINVAL, "sweep_rows must be 0, 1, 2, 4 or 8");
+  if (h->opt.sweep_warps < 0 || h->opt.sweep_warps > 8)
+    return fail(h, RTE_EINVAL, "sweep_warps must be in [0, 8]");
   if (!(h->opt.eps_sisa >= 0.0)) return fail(h, RTE_EINVAL, "eps_sisa must be >= 0");
   h->dim = mesh->dim;
   h->nx = mesh->nx;
@@ -697,8 +711,12 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   const Layout& L = h->L;
   // sweep tiling
   if (h->dim == 2) {
-    h->R = std::min(4, L.dl);
-    h->rows_per_blk = (32 / L.dl) * h->R;
+    h->R = std::min(h->opt.sweep_rows ? h->opt.sweep_rows : 2, L.dl);
+    h->W = h->opt.sweep_warps ? h->opt.sweep_warps : 4;
+    // fewer warps per CTA when the fused sweep's staging would not fit in shared memory
+    while (h->W > 1 && sweep2d_smem_bytes(sizeof(double), L.dl, h->R, h->W, 1, true) > 200 * 1024)
+      --h->W;
+    h->rows_per_blk = h->W * (32 / L.dl) * h->R;
     h->nblk = (h->ny + h->rows_per_blk - 1) / h->rows_per_blk;
   }
   CK(dalloc(&h->sig_t, n));
@@ -728,7 +746,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
   if (h->dim == 2) {
     CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
-    CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, h->inv_d, h->st));
+    CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, L.dl, h->inv_d, h->st));
     CK(dalloc(&h->pm, (size_t)L.nfam * n));
     CK(dalloc(&h->edge, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
     const size_t cb_bytes = sizeof(SweepCtrl) + sizeof(unsigned) * L.nfam * h->nblk;
@@ -807,7 +825,7 @@ rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
     std::vector<double> fl((size_t)n * L.nslot, 0.0), rho(n, 0.0);
     for (int d = 0; d < L.nv; ++d) {
       const int s = L.slot_of_dir[d];
-      for (long c = 0; c < n; ++c) fl[(size_t)c * L.nslot + s] = f0[(size_t)d * n + c];
+      for (long c = 0; c < n; ++c) fl[f_index(L, n, c, s)] = f0[(size_t)d * n + c];
     }
     for (int d = 0; d < L.nv; ++d)
       for (long c = 0; c < n; ++c) rho[c] += h->w_user[d] * f0[(size_t)d * n + c];
@@ -821,7 +839,7 @@ rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
     if (!rho0) return fail(h, RTE_EINVAL, "rho0 or f0 is required");
     if (!finite_all(rho0, n)) return fail(h, RTE_EINVAL, "non-finite rho0");
     TRY(upload(h, h->rho, rho0, n));
-    CK(launch_isotropic_f(h->rho, (int)n, L.nslot, h->cw, h->f, h->st));
+    CK(launch_isotropic_f(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
     h->init_kind = 1;
   }
   if (!h->rho_init) CK(dalloc(&h->rho_init, n));
@@ -846,7 +864,7 @@ rte_status rte_restart(rte_handle h) {
     CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * n * h->L.nslot, cudaMemcpyDeviceToDevice,
                        h->st));
   else
-    CK(launch_isotropic_f(h->rho, (int)n, h->L.nslot, h->cw, h->f, h->st));
+    CK(launch_isotropic_f(h->rho, (int)n, h->L.nslot, h->L.dl, h->f, h->st));
   CK(cudaStreamSynchronize(h->st));
   return reset_state(h);
 }
@@ -899,7 +917,7 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
   CK(cudaStreamSynchronize(h->st));
   for (int d = 0; d < L.nv; ++d) {
     const int s = L.slot_of_dir[d];
-    for (long c = 0; c < n; ++c) f[(size_t)d * n + c] = fl[(size_t)c * L.nslot + s];
+    for (long c = 0; c < n; ++c) f[(size_t)d * n + c] = fl[f_index(L, n, c, s)];
   }
   return RTE_OK;
 }
@@ -938,8 +956,17 @@ rte_status rte_op_sweep(rte_handle h, const double* rho, double* out) {
   const int n = (int)h->ncell;
   TRY(upload(h, h->tmp, rho, n));
   CK(launch_scale_copy(h->tmp, h->sig_s, n, h->q, h->st));
-  TRY(sweep_si(h, h->q, nullptr, h->tmp2));
+  cudaEventRecord(h->kev0, h->st);
+  TRY(sweep_si_partials(h, h->q, nullptr));
+  cudaEventRecord(h->kev1, h->st);
+  CK(launch_sum_partials(h->pm, nparts(h), n, nullptr, h->tmp2, h->st));
   TRY(check_sweep_error(h));
+  {
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, h->kev0, h->kev1);
+    h->stats.si_sweep_kernel_ms += kms;
+    h->stats.si_sweep_launches += 1;
+  }
   CK(cudaMemcpyAsync(out, h->tmp2, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return RTE_OK;

@@ -50,11 +50,11 @@ struct Sweep2DArgs {
   const Real* w;        // [nslot]
   const int* fam_quad;  // [nfam]
   const Real* sig_t;    // [ncell]
-  const Real* inv_d;    // [ncell][nslot] 1/(tau+sigma_t+a+b) or nullptr (computed)
+  const Real* inv_d;    // [nfam][ncell][dl] 1/(tau+sigma_t+a+b) or nullptr (computed)
   // K1: isotropic source q = Sigma_s rho; K2 pass A: q = Sigma_s rho + G.
   const Real* q;        // [ncell]
   const Real* g2;       // K2 pass B isotropic source G [ncell]
-  Real* f;              // K2: [ncell][nslot] in / out (f^{n-1} -> f^n)
+  Real* f;              // K2: [nfam][ncell][dl] in / out (f^{n-1} -> f^n)
   Real* pm;             // [nfam][ncell] partial moments (K1: of L^-1 q; K2: of pass B)
   Real* pm_a;           // K2: [nfam][ncell] partial moments of f^n (may be nullptr)
   Real gx[4], gy[4];    // per quadrant inflow ghost of pass A (K1: zero)
@@ -73,22 +73,25 @@ struct Sweep1DArgs {
   const Real* sig_t;
   const Real* q;        // [ncell]
   const Real* g2;       // K2 pass B source
-  Real* f;              // [ncell][nslot]
+  Real* f;              // [2][ncell][nslot/2]
   Real* psi_w;          // scratch [nslot][ncell] of w * psi (moment input)
   Real* psi_w_a;        // K2: scratch of w * f^n or nullptr
   Real g_lo, g_hi;      // inflow at x0 (for mu > 0) and x1 (for mu < 0), pass A
 };
 
 // Launchers (sweep.cu).
+// Dynamic shared memory of one 2D sweep CTA (the launcher rejects more than 200 KiB).
+size_t sweep2d_smem_bytes(size_t real, int dl, int R, int W, int mode, bool table);
 template <class Real>
 cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStream_t s);
 template <class Real>
 cudaError_t launch_sweep1d(const Sweep1DArgs<Real>& a, int mode, cudaStream_t s);
 template <class Real>
 cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s);
+// inv_d in the family layout [fam][cell][dl]
 template <class Real>
 cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
-                         int nslot, Real* inv_d, cudaStream_t s);
+                         int nslot, int dl, Real* inv_d, cudaStream_t s);
 
 // Vector kernels (vec.cu).
 struct Norms {             // device-side reduction results of one residual evaluation
@@ -105,8 +108,8 @@ cudaError_t launch_sum_partials(const double* pm, int nfam, int ncell, const dou
                                 double* out, cudaStream_t s);
 cudaError_t launch_axpby(double alpha, const double* x, double beta, const double* y, int n,
                          double* out, cudaStream_t s);
-cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, const double* wslot,
-                               double* f, cudaStream_t s);
+cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, int dl, double* f,
+                               cudaStream_t s);
 cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
                        double* out, cudaStream_t s);
 int vec_blocks(int n);
@@ -147,8 +150,15 @@ struct RomDev {
   int* piv;
   double* proj;   // [r_max+1] projections
   double* partial;
+  double* sec;    // scratch of the core SVD
   int lu_ok;
 };
+// SVD of the core [[diag(S), p], [0, alpha]] (csvd.cu); alpha^2 and ||x||^2 in sc[1], sc[0];
+// writes U_c, V_c, the new singular values, and keep / grew / ratio into sc[3..6].
+long secular_scratch_doubles();
+cudaError_t core_svd_secular(const double* S, int r, const double* p, double* sc, double* Uc,
+                             double* Vc, double* snew, double trunc_eps, int r_max,
+                             double* scratch, cudaStream_t s);
 cudaError_t rom_alloc(RomDev& R, int n, int r_max);
 void rom_free(RomDev& R);
 // Incremental SVD append (App. B).  Returns new rank in *rank_out (host), grew flag.

@@ -73,19 +73,75 @@ struct TReduce {
   }
 };
 
+// cp.async helpers (global -> shared, zero-fill when the source is absent).
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+template <class Real>
+__device__ __forceinline__ void cp_async(Real* smem, const Real* gmem, bool valid) {
+  if constexpr (sizeof(Real) == 8)
+    cp_async_8(smem, gmem, valid);
+  else
+    cp_async_4(smem, gmem, valid);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // MODE 0: SI sweep (K1): S = q with the given inflow ghosts (zero for SI), moment of psi.
 // MODE 2: y = L^-1(g2 + tau f) from the stored f, zero inflow, moment of y.
 // MODE 1: fused f sweep (K2): pass A  f^n = L^-1(q + tau f^{n-1}) with inflow ghosts,
 //         pass B  y = L^-1(g2 + tau f^n) with zero inflow; moment of B (and of A).
-template <class Real, int DL, int R, int MODE, bool TABLE>
-__global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs<Real> A) {
+//
+// CTA = W warps stacked vertically; warp w = NG lane groups of R rows (RW = NG R rows).
+// Global step t: warp w works at local step t - w L (L = K + RW - 1), so the bottom row of
+// warp w-1 reaches column x a whole chunk of K steps before warp w needs it; the hand-off
+// goes through a shared-memory ring and one __syncthreads per chunk.  The per-cell data of
+// chunk c+1 (sigma_t, sources) is copied to shared memory with cp.async while chunk c runs;
+// for row r of warp w the staged column index is simply the step index within the chunk.
+template <class Real, int DL, int R, int K, int MODE, bool TABLE>
+__global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A) {
   constexpr int NG = 32 / DL;
+  constexpr int RW = NG * R;
+  constexpr int L = K + RW - 1;
+  constexpr int RING = 2 * K;
+  constexpr int NP = (MODE == 1) ? 2 : 1;            // planes (recurrences) carried
+  constexpr bool STAGE_F = MODE != 0;
+  constexpr int V = DL * (int)sizeof(Real) / 16;     // 16-byte pieces per cell of a family
   static_assert(R <= DL, "rows per lane group must not exceed the lane count");
-  const int lane = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int W = blockDim.x >> 5;
+  const int RC = W * RW;
+  // shared memory: [2][RC][K][DL] table / f, then [2][RC][K] scalars, then the hand-off ring
+  Real* tab_s = reinterpret_cast<Real*>(smraw);                   // 1/d (TABLE)
+  Real* f_s = tab_s + (TABLE ? 2 * RC * K * DL : 0);              // f^{n-1} (MODE 1, 2)
+  Real* st_s = f_s + (STAGE_F ? 2 * RC * K * DL : 0);             // sigma_t (no TABLE)
+  Real* qa_s = st_s + (TABLE ? 0 : 2 * RC * K);                   // q (MODE 0, 1)
+  Real* g2_s = qa_s + (MODE != 2 ? 2 * RC * K : 0);               // g2 (MODE 1, 2)
+  Real* hand = g2_s + (MODE != 0 ? 2 * RC * K : 0);               // [NP][W-1][RING][DL]
+  __shared__ unsigned s_ticket;
+  __shared__ int s_abandon;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gi = lane / DL, dl = lane % DL;
-  unsigned t0 = 0;
-  if (lane == 0) t0 = atomicAdd(&A.ctrl->ticket, 1u);
-  const unsigned ticket = __shfl_sync(FULL, t0, 0);
+  if (tid == 0) {
+    s_ticket = atomicAdd(&A.ctrl->ticket, 1u);
+    s_abandon = 0;
+  }
+  __syncthreads();
+  const unsigned ticket = s_ticket;
   const int blk = (int)(ticket / (unsigned)A.nfam);
   const int fam = (int)(ticket % (unsigned)A.nfam);
   const int quad = A.fam_quad[fam];
@@ -96,9 +152,12 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs<Real> A) 
   const int slot = fam * DL + dl;
   const Real ca = A.a[slot], cb = A.b[slot], cw = A.w[slot];
   const Real ct = A.tau + ca + cb;
-  const int row0 = blk * A.rows_per_blk + gi * R;
+  const int rowblk0 = blk * RC;                     // first sweep-order row of this CTA
+  const int row0 = rowblk0 + warp * RW + gi * R;    // lane group's row m = 0
   const Real gx = A.gx[quad];
   const Real gy = A.gy[quad];
+  const Real* tab_fam = TABLE ? A.inv_d + (size_t)fam * ncell * DL : nullptr;
+  Real* f_fam = STAGE_F ? A.f + (size_t)fam * ncell * DL : nullptr;
 
   Real psA[R], psB[R];
 #pragma unroll
@@ -113,84 +172,136 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs<Real> A) 
   Real* edge_out = A.edge + ((size_t)(fam * A.nblk + blk) * nx) * DL;
   unsigned* flag_in = &A.ctrl->flags[fam * A.nblk + (has_up ? blk - 1 : 0)];
   unsigned* flag_out = &A.ctrl->flags[fam * A.nblk + blk];
-  const int nsteps = nx + NG * R - 1;
-  bool abandon = false;
+  const int T = nx + RW - 1 + (W - 1) * L;
+  const int nchunk = (T + K - 1) / K;
 
-  for (int tb = 0; tb < nsteps; tb += KCHUNK) {
-    // Top inflow of this row block: the previous block's bottom row, KCHUNK columns at once.
-    Real ebA[KCHUNK], ebB[KCHUNK];
-    if (has_up && tb < nx) {
-      const unsigned need = (unsigned)min(tb + KCHUNK, nx);
-      if (lane == 0 && !abandon) {
-        unsigned spins = 0;
-        while (ld_acquire(flag_in) < need) {
-          if (++spins > SPIN_LIMIT || ld_acquire(&A.ctrl->err) != 0u) {
-            atomicExch(&A.ctrl->err, 1u);
-            abandon = true;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      abandon = __shfl_sync(FULL, abandon, 0);
-      __syncwarp();
-      __threadfence();
-#pragma unroll
-      for (int k = 0; k < KCHUNK; ++k) {
-        const int x = tb + k;
-        ebA[k] = (gi == 0 && x < nx) ? ldcg(edge_in + (size_t)x * DL + dl) : Real(0);
-        if constexpr (MODE == 1)
-          ebB[k] = (gi == 0 && x < nx) ? ldcg(edge_in + plane + (size_t)x * DL + dl) : Real(0);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < KCHUNK; ++k) {
-        ebA[k] = gy;
-        ebB[k] = Real(0);
+  // Copy the data of chunk c into buffer c & 1: for row r (warp w, row rr in the warp) and
+  // step k of the chunk, the cell at column x = cK + k - wL - rr.
+  auto stage = [&](int c) {
+    const int buf = c & 1;
+    if constexpr (TABLE || STAGE_F) {
+      for (int e = tid; e < RC * K * V; e += blockDim.x) {
+        const int v = e % V, rk = e / V;
+        const int r = rk / K, k = rk % K;
+        const int w = r / RW, rr = r % RW;
+        const int x = c * K + k - w * L - rr;
+        const int jj = rowblk0 + r;
+        const bool ok = x >= 0 && x < nx && jj < ny;
+        const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
+        const int o = ((buf * RC + r) * K + k) * DL + v * (16 / (int)sizeof(Real));
+        const size_t g = (size_t)cell * DL + v * (16 / sizeof(Real));
+        if constexpr (TABLE) cp_async_16(tab_s + o, tab_fam + g, ok);
+        if constexpr (STAGE_F) cp_async_16(f_s + o, f_fam + g, ok);
       }
     }
+    for (int e = tid; e < RC * K; e += blockDim.x) {
+      const int r = e / K, k = e % K;
+      const int w = r / RW, rr = r % RW;
+      const int x = c * K + k - w * L - rr;
+      const int jj = rowblk0 + r;
+      const bool ok = x >= 0 && x < nx && jj < ny;
+      const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
+      const int o = (buf * RC + r) * K + k;
+      if constexpr (!TABLE) cp_async(st_s + o, A.sig_t + cell, ok);
+      if constexpr (MODE != 2) cp_async(qa_s + o, A.q + cell, ok);
+      if constexpr (MODE != 0) cp_async(g2_s + o, A.g2 + cell, ok);
+    }
+    cp_async_commit();
+  };
+
+  stage(0);
+  for (int c = 0; c < nchunk; ++c) {
+    // Chunk c's copies (issued one chunk earlier) have landed for this thread; the barrier
+    // makes every thread's copies and the previous chunk's hand-off writes visible, and
+    // guarantees that nobody still reads buffer (c+1)&1, which the next stage overwrites.
+    cp_async_wait0();
+    __syncthreads();
+    if (c + 1 < nchunk) stage(c + 1);
+    const int buf = c & 1;
+    const int tb = c * K;
+    // top inflow of warp 0: previous row block's bottom row (global) or the inflow ghost
+    Real ebA[K], ebB[K];
+    if (warp == 0) {
+      if (has_up && tb < nx) {
+        const unsigned need = (unsigned)min(tb + K, nx);
+        if (lane == 0 && !s_abandon) {
+          unsigned spins = 0;
+          while (ld_acquire(flag_in) < need) {
+            if (++spins > SPIN_LIMIT || ld_acquire(&A.ctrl->err) != 0u) {
+              atomicExch(&A.ctrl->err, 1u);
+              s_abandon = 1;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        __syncwarp();
+        __threadfence();
 #pragma unroll
-    for (int k = 0; k < KCHUNK; ++k) {
-      const int t = tb + k;
-      if (t >= nsteps) break;
+        for (int k = 0; k < K; ++k) {
+          const int x = tb + k;
+          ebA[k] = (gi == 0 && x < nx) ? ldcg(edge_in + (size_t)x * DL + dl) : Real(0);
+          if constexpr (MODE == 1)
+            ebB[k] = (gi == 0 && x < nx) ? ldcg(edge_in + plane + (size_t)x * DL + dl) : Real(0);
+          else
+            ebB[k] = Real(0);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          ebA[k] = gy;
+          ebB[k] = Real(0);
+        }
+      }
+    }
+    const int tw0 = tb - warp * L;   // warp-local step of k = 0
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int tw = tw0 + k;
       Real upA = __shfl_up_sync(FULL, psA[R - 1], DL);
       Real upB = __shfl_up_sync(FULL, psB[R - 1], DL);
       if (gi == 0) {
-        upA = ebA[k];
-        upB = ebB[k];
+        if (warp == 0) {
+          upA = ebA[k];
+          upB = ebB[k];
+        } else {
+          const int slot_r = ((tw % RING) + RING) % RING;   // column of row 0 = tw
+          upA = hand[((0 * (W - 1) + warp - 1) * RING + slot_r) * DL + dl];
+          if constexpr (MODE == 1) upB = hand[((1 * (W - 1) + warp - 1) * RING + slot_r) * DL + dl];
+        }
       }
       Real mom[R], momA[R];
 #pragma unroll
       for (int m = R - 1; m >= 0; --m) {
-        const int x = t - m - gi * R;
+        const int x = tw - m - gi * R;
         const int jj = row0 + m;
         mom[m] = Real(0);
         momA[m] = Real(0);
         if (x >= 0 && x < nx && jj < ny) {
-          const int px = xpos ? x : nx - 1 - x;
-          const int py = ypos ? jj : ny - 1 - jj;
-          const long cell = (long)py * nx + px;
-          const Real dinv = TABLE ? A.inv_d[cell * A.nslot + slot] : recip(ct + A.sig_t[cell]);
+          const int r = warp * RW + gi * R + m;
+          const int o = (buf * RC + r) * K + k;
+          const int od = o * DL + dl;
+          Real dinv;
+          if constexpr (TABLE) dinv = tab_s[od];
+          else dinv = recip(ct + st_s[o]);
           const Real uA = (m == 0) ? upA : psA[m > 0 ? m - 1 : 0];
           if constexpr (MODE == 0) {
-            const Real v = (A.q[cell] + ca * psA[m] + cb * uA) * dinv;
+            const Real v = (qa_s[o] + ca * psA[m] + cb * uA) * dinv;
             psA[m] = v;
             mom[m] = cw * v;
           } else if constexpr (MODE == 2) {
-            // y = L^-1 (g2 + tau f) with the stored f, zero inflow (the recurrence runs in psA)
-            const Real v = (A.g2[cell] + A.tau * A.f[cell * A.nslot + slot] + ca * psA[m] +
-                            cb * uA) * dinv;
+            const Real v = (g2_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA) * dinv;
             psA[m] = v;
             mom[m] = cw * v;
           } else {
-            Real* fp = A.f + cell * A.nslot + slot;
-            const Real sa = A.q[cell] + A.tau * (*fp);
-            const Real va = (sa + ca * psA[m] + cb * uA) * dinv;
+            const Real va = (qa_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA) * dinv;
             psA[m] = va;
-            *fp = va;
+            const int px = xpos ? x : nx - 1 - x;
+            const int py = ypos ? jj : ny - 1 - jj;
+            f_fam[((long)py * nx + px) * DL + dl] = va;
             momA[m] = cw * va;
             const Real uB = (m == 0) ? upB : psB[m > 0 ? m - 1 : 0];
-            const Real vb = (A.g2[cell] + A.tau * va + ca * psB[m] + cb * uB) * dinv;
+            const Real vb = (g2_s[o] + A.tau * va + ca * psB[m] + cb * uB) * dinv;
             psB[m] = vb;
             mom[m] = cw * vb;
           }
@@ -203,7 +314,7 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs<Real> A) 
       }
       if ((dl & (DL / R - 1)) == 0) {
         const int m = dl / (DL / R);
-        const int x = t - m - gi * R;
+        const int x = tw - m - gi * R;
         const int jj = row0 + m;
         if (x >= 0 && x < nx && jj < ny) {
           const int px = xpos ? x : nx - 1 - x;
@@ -215,23 +326,33 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs<Real> A) 
           }
         }
       }
-      // Bottom row of the block goes to the next row block.
-      const int xb = t - (R - 1) - (NG - 1) * R;
-      if (has_down && xb >= 0 && xb < nx) {
-        if (gi == NG - 1) {
+      // bottom row of this warp: to the next warp (shared ring) or the next CTA (global)
+      const int xb = tw - (R - 1) - (NG - 1) * R;
+      if (gi == NG - 1 && xb >= 0 && xb < nx) {
+        if (warp < W - 1) {
+          const int slot_r = xb % RING;
+          hand[((0 * (W - 1) + warp) * RING + slot_r) * DL + dl] = psA[R - 1];
+          if constexpr (MODE == 1) hand[((1 * (W - 1) + warp) * RING + slot_r) * DL + dl] = psB[R - 1];
+        } else if (has_down) {
           edge_out[(size_t)xb * DL + dl] = psA[R - 1];
           if constexpr (MODE == 1) edge_out[plane + (size_t)xb * DL + dl] = psB[R - 1];
         }
-        if ((xb + 1) % KCHUNK == 0 || xb == nx - 1) {
-          __threadfence();
-          __syncwarp();
-          if (lane == 0) st_release(flag_out, (unsigned)(xb + 1));
-        }
+      }
+    }
+    // publish the columns the bottom row finished in this chunk
+    if (warp == W - 1 && has_down) {
+      const int xlast = tb + K - 1 - (W - 1) * L - (RW - 1);
+      if (xlast >= 0) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(flag_out, (unsigned)min(xlast + 1, nx));
       }
     }
   }
+  cp_async_wait0();
   // Self-reset of the control block by the last CTA to finish.
-  if (lane == 0) {
+  __syncthreads();
+  if (tid == 0) {
     __threadfence();
     const unsigned total = (unsigned)(A.nfam * A.nblk);
     if (atomicAdd(&A.ctrl->done, 1u) == total - 1) {
@@ -243,14 +364,45 @@ __global__ void __launch_bounds__(32) sweep2d_kernel(const Sweep2DArgs<Real> A) 
   }
 }
 
+constexpr int KSTEP = 8;   // columns per chunk
+
+}  // namespace
+
+inline size_t sweep2d_smem_bytes_impl(size_t real, int dl, int R, int W, int mode, bool table) {
+  const int K = 8;
+  const int RW = (32 / dl) * R, RC = W * RW, np = mode == 1 ? 2 : 1;
+  size_t n = 0;
+  if (table) n += 2 * RC * K * dl;
+  if (mode != 0) n += 2 * RC * K * dl;
+  if (!table) n += 2 * RC * K;
+  if (mode != 2) n += 2 * RC * K;
+  if (mode != 0) n += 2 * RC * K;
+  n += np * (W - 1) * 2 * K * dl;
+  return real * n;
+}
+
+namespace {
+
 template <class Real, int DL, int R, int MODE>
 cudaError_t launch_dl_r(const Sweep2DArgs<Real>& a, cudaStream_t s) {
+  constexpr int NG = 32 / DL;
+  constexpr int RW = NG * R;
+  const int W = a.rows_per_blk / RW;
+  if (W < 1 || W > 8 || W * RW != a.rows_per_blk) return cudaErrorInvalidValue;
+  const bool table = a.inv_d != nullptr;
+  const size_t smem = sweep2d_smem_bytes_impl(sizeof(Real), DL, R, W, MODE, table);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  auto kern = table ? sweep2d_kernel<Real, DL, R, KSTEP, MODE, true>
+                    : sweep2d_kernel<Real, DL, R, KSTEP, MODE, false>;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[table]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set[table] = true;
+  }
   const dim3 grid((unsigned)(a.nfam * a.nblk));
   ++g_launches;
-  if (a.inv_d)
-    sweep2d_kernel<Real, DL, R, MODE, true><<<grid, 32, 0, s>>>(a);
-  else
-    sweep2d_kernel<Real, DL, R, MODE, false><<<grid, 32, 0, s>>>(a);
+  kern<<<grid, 32 * W, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -332,6 +484,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
   __shared__ Aff<Real> sh[64];
   const int slot = blockIdx.x;
   const int nx = A.nx;
+  const int dlh = A.nslot / 2;   // f layout [half-range][cell][direction in half-range]
+  const long fbase = (long)(slot / dlh) * nx * dlh + slot % dlh;
   const int chunk = (nx + SCAN_THREADS - 1) / SCAN_THREADS;
   const int k0 = threadIdx.x * chunk;
   const int k1 = min(nx, k0 + chunk);
@@ -344,7 +498,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
     const int c = pos ? k : nx - 1 - k;
     const Real dinv = Real(1) / (ct + A.sig_t[c]);
     Real s = (MODE == 2) ? A.g2[c] : A.q[c];
-    if (MODE != 0) s += A.tau * A.f[(long)c * A.nslot + slot];
+    if (MODE != 0) s += A.tau * A.f[fbase + (long)c * dlh];
     mine = compose(mine, Aff<Real>{ca * dinv, s * dinv});
   }
   const Real gA = (MODE == 2) ? Real(0) : (pos ? A.g_lo : A.g_hi);
@@ -354,11 +508,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
     const Real dinv = Real(1) / (ct + A.sig_t[c]);
     Real s = (MODE == 2) ? A.g2[c] : A.q[c];
     if (MODE == 2) {
-      s += A.tau * A.f[(long)c * A.nslot + slot];
+      s += A.tau * A.f[fbase + (long)c * dlh];
       psi = (s + ca * psi) * dinv;
       A.psi_w[(long)slot * nx + c] = cw * psi;
     } else if (MODE == 1) {
-      Real* fp = A.f + (long)c * A.nslot + slot;
+      Real* fp = A.f + fbase + (long)c * dlh;
       s += A.tau * (*fp);
       psi = (s + ca * psi) * dinv;
       *fp = psi;
@@ -374,14 +528,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
     for (int k = k0; k < k1; ++k) {
       const int c = pos ? k : nx - 1 - k;
       const Real dinv = Real(1) / (ct + A.sig_t[c]);
-      const Real s = A.g2[c] + A.tau * A.f[(long)c * A.nslot + slot];
+      const Real s = A.g2[c] + A.tau * A.f[fbase + (long)c * dlh];
       mb = compose(mb, Aff<Real>{ca * dinv, s * dinv});
     }
     Real y = block_scan_entry(mb, Real(0), sh);
     for (int k = k0; k < k1; ++k) {
       const int c = pos ? k : nx - 1 - k;
       const Real dinv = Real(1) / (ct + A.sig_t[c]);
-      const Real s = A.g2[c] + A.tau * A.f[(long)c * A.nslot + slot];
+      const Real s = A.g2[c] + A.tau * A.f[fbase + (long)c * dlh];
       y = (s + ca * y) * dinv;
       A.psi_w[(long)slot * nx + c] = cw * y;
     }
@@ -399,11 +553,13 @@ __global__ void moment1d_kernel(const Real* psi_w, int nslot, int ncell, Real* o
 
 template <class Real>
 __global__ void inv_d_kernel(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
-                             int nslot, Real* inv_d) {
+                             int nslot, int dl, Real* inv_d) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)ncell * nslot) return;
-  const long c = i / nslot;
-  const int s = (int)(i % nslot);
+  // family layout [fam][cell][dl] with dl = 32 / 16 / 8 lanes: i = (fam * ncell + c) * dl + lane
+  const long lanei = i % dl, rest = i / dl;
+  const long c = rest % ncell, fam = rest / ncell;
+  const int s = (int)(fam * dl + lanei);
   inv_d[i] = Real(1) / (tau + sig_t[c] + a[s] + b[s]);
 }
 
@@ -455,6 +611,10 @@ RTE_SWEEP_EXTERN(float, 0)
 RTE_SWEEP_EXTERN(float, 1)
 RTE_SWEEP_EXTERN(float, 2)
 #endif
+size_t sweep2d_smem_bytes(size_t real, int dl, int R, int W, int mode, bool table) {
+  return sweep2d_smem_bytes_impl(real, dl, R, W, mode, table);
+}
+
 template <class Real>
 cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStream_t s) {
   const int dl = a.nslot / a.nfam;
@@ -484,11 +644,11 @@ cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, 
 
 template <class Real>
 cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
-                         int nslot, Real* inv_d, cudaStream_t s) {
+                         int nslot, int dl, Real* inv_d, cudaStream_t s) {
   const long n = (long)ncell * nslot;
   ++g_launches;
   inv_d_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sig_t, a, b, tau, ncell, nslot,
-                                                                 inv_d);
+                                                                 dl, inv_d);
   return cudaGetLastError();
 }
 
@@ -499,9 +659,9 @@ template cudaError_t launch_sweep1d<float>(const Sweep1DArgs<float>&, int, cudaS
 template cudaError_t launch_moment1d<double>(const double*, int, int, double*, cudaStream_t);
 template cudaError_t launch_moment1d<float>(const float*, int, int, float*, cudaStream_t);
 template cudaError_t launch_inv_d<double>(const double*, const double*, const double*, double, int,
-                                          int, double*, cudaStream_t);
+                                          int, int, double*, cudaStream_t);
 template cudaError_t launch_inv_d<float>(const float*, const float*, const float*, float, int, int,
-                                         float*, cudaStream_t);
+                                         int, float*, cudaStream_t);
 #endif  // base part
 
 }  // namespace rte

@@ -115,11 +115,11 @@ __global__ void axpby_kernel(double alpha, const double* x, double beta, const d
   out[c] = alpha * x[c] + beta * y[c];
 }
 
-__global__ void isotropic_f_kernel(const double* rho, int n, int nslot, const double* wslot,
-                                   double* f) {
+// f = rho in every direction; f layout [family][cell][lane] with nslot / dl families.
+__global__ void isotropic_f_kernel(const double* rho, int n, int nslot, int dl, double* f) {
   const long i = (long)blockIdx.x * VT + threadIdx.x;
   if (i >= (long)n * nslot) return;
-  const long c = i / nslot;
+  const long c = (i / dl) % n;
   f[i] = rho[c];
 }
 
@@ -189,11 +189,11 @@ cudaError_t launch_axpby(double alpha, const double* x, double beta, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, const double* wslot, double* f,
+cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, int dl, double* f,
                                cudaStream_t s) {
   const long tot = (long)n * nslot;
   ++g_launches;
-  isotropic_f_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, wslot, f);
+  isotropic_f_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, dl, f);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,9 @@ class Options(ctypes.Structure):
                 ("eps_pc", ctypes.c_double), ("eps_up", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("r_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("rom", ctypes.c_int), ("residual_norm", ctypes.c_int), ("up_rel", ctypes.c_int),
-                ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int)]
+                ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int),
+                ("sweep_rows", ctypes.c_int), ("sweep_lanes", ctypes.c_int),
+                ("sweep_warps", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

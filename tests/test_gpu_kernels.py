@@ -54,6 +54,32 @@ def test_sweep_2d(quad, shape):
     h.destroy()
 
 
+@pytest.mark.parametrize("lanes,rows,warps", [(32, 1, 1), (32, 2, 4), (32, 8, 8), (16, 4, 3),
+                                               (8, 2, 8), (8, 8, 2), (16, 1, 5)])
+@pytest.mark.parametrize("mode", ["si", "f"])
+def test_sweep_2d_tilings(lanes, rows, warps, mode):
+    """Every tile shape (directions per lane group, rows per lane group, warps per CTA) gives
+    the same SI sweep and fused f sweep, on a ragged grid."""
+    wl, rng = _hetero_2d(45, 53, (32, 8), seed=lanes + rows + warps)
+    h, p = make_pair(wl, sweep_lanes=lanes, sweep_rows=rows, sweep_warps=warps)
+    if mode == "si":
+        rho = rng.uniform(-1, 1, wl.ncell)
+        assert rel_l2(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)) < 1e-12
+    else:
+        perm, _, _ = match_directions(h, wl.quadrature)
+        f0 = rng.uniform(0, 1, (p.nv, wl.ncell))
+        h.rte_set_initial(f0=f0[perm])
+        g = np.array([0.3, 0.6, 0.2, 0.9])
+        h.rte_set_inflow(g)
+        p.inflow = g
+        rho = rng.uniform(0, 1, wl.ncell)
+        bt = h.rte_op_fsweep(rho)
+        f_ref, _ = tr.final_f(p, rho, f0)
+        assert rel_l2(h.rte_get_angular_flux(), f_ref[perm]) < 1e-12
+        assert rel_l2(bt, tr.b_tilde(p, f_ref)) < 1e-12
+    h.destroy()
+
+
 @pytest.mark.parametrize("n,nd", [(1, 16), (7, 4), (256, 16), (1000, 8), (4097, 16)])
 def test_sweep_1d(n, nd):
     rng = np.random.default_rng(n)
