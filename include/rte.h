@@ -200,6 +200,35 @@ rte_status rte_op_rom_get(rte_handle h, int which, int* rank, double* S, double*
 /* Drop both ROMs and the phase flags. */
 rte_status rte_op_rom_reset(rte_handle h);
 
+/* ---------------- allocation-free diffusion solve ----------------
+ * The paper has no counterpart of this call: it is a service for callers that cannot
+ * allocate device memory, such as code running inside another framework's fixed,
+ * pre-reserved memory budget (where a cudaMalloc can fail) or latency-critical code that
+ * must not trigger the device-wide synchronisation of cudaMalloc / cudaFree.
+ *
+ * It computes the same DSA correction as rte_op_dsa, delta = C^{-1} (sigma_s .* residual)
+ * (Eq. (rho_residual), CG from zero until ||r|| <= cg_rtol ||b||), for the mesh
+ * [x0,x1] x [y0,y1] with nx * ny cells (dim = 1: ny = 1) and time step c_dt, on the stream
+ * `stream` (a cudaStream_t, NULL = the legacy default stream) of the current device.
+ *   - sigma_t_dev, sigma_s_dev, residual_dev: device [nx*ny] inputs; delta_dev: device
+ *     [nx*ny] output; all owned by the caller.  *iterations (host, may be NULL) = CG count.
+ *   - All scratch (operator coefficients, CG vectors, reduction and barrier words) lives in
+ *     one library-owned device array of fixed size, which every GPU that loads the library
+ *     holds until the process exits.  nx * ny above 65536 is rejected with RTE_EINVAL.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.  The first
+ *     call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ *     first call before any stream capture.
+ *   - Every call shares the one array and leaves the last call's contents in it; calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on it.
+ *   - The call waits for its stream to finish the solve before returning.
+ * Errors: RTE_EINVAL (sizes, NULL pointers), RTE_ECUDA, RTE_ETIMEOUT; the message is
+ * available from rte_last_error(NULL) on the calling thread. */
+rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0,
+                                 double y1, double c_dt, const double* sigma_t_dev,
+                                 const double* sigma_s_dev, const double* residual_dev,
+                                 double cg_rtol, int cg_max_iter, double* delta_dev,
+                                 int* iterations, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

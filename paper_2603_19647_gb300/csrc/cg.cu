@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "rte_internal.h"
@@ -293,6 +295,178 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   void* args[] = {&a};
   ++g_launches;
   return cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(op.blocks), dim3(CT), args, 0, s);
+}
+
+}  // namespace rte
+
+// =========================================================================================
+// Allocation-free DSA solve: the same diffusion operator and conjugate gradients, with every
+// scratch vector in one file-scope device array instead of memory allocated by the caller or
+// by a handle.  The array exists on every GPU that loads the library, until the process exits.
+// =========================================================================================
+namespace rte {
+
+namespace {
+constexpr int NOALLOC_MAX_CELLS = 65536;   // 256 x 256 cells
+constexpr int NOALLOC_MAX_BLOCKS = 512;
+// diag, cx, cy, r, p0, p1, ap, x  (8 cell vectors) | partial sums | barrier + iteration words
+constexpr long NOALLOC_DOUBLES = 8L * NOALLOC_MAX_CELLS + 2L * NOALLOC_MAX_BLOCKS + 8;
+static __device__ __align__(256) double g_dsa_noalloc_scratch[NOALLOC_DOUBLES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[MAX_DEVICES] = {};
+
+// Row c of the diffusion operator (same formulas as dsa_setup), one thread per cell.
+__global__ void dsa_coeff_kernel(int dim, int nx, int ny, double hx, double hy, double tau,
+                                 const double* sig_t, const double* sig_s, double* diag,
+                                 double* cx, double* cy) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nx * ny;
+  if (c >= n) return;
+  const int i = c % nx, j = c / nx;
+  auto D = [&](int k) { return 1.0 / (3.0 * (sig_t[k] + tau)); };
+  auto face = [](double dl, double dr, double h) { return 2.0 * dl * dr / ((dl + dr) * h * h); };
+  auto marshak = [](double d, double h) { return 1.0 / (h * (2.0 + h / (2.0 * d))); };
+  const double dc = D(c);
+  double dg = sig_t[c] - sig_s[c] + tau;
+  double fx = 0.0, fy = 0.0;
+  if (i + 1 < nx) {
+    fx = face(dc, D(c + 1), hx);
+    dg += fx;
+  }
+  if (i > 0) dg += face(D(c - 1), dc, hx);
+  if (i == 0) dg += marshak(dc, hx);
+  if (i == nx - 1) dg += marshak(dc, hx);
+  if (dim == 2) {
+    if (j + 1 < ny) {
+      fy = face(dc, D(c + nx), hy);
+      dg += fy;
+    }
+    if (j > 0) dg += face(D(c - nx), dc, hy);
+    if (j == 0) dg += marshak(dc, hy);
+    if (j == ny - 1) dg += marshak(dc, hy);
+  }
+  diag[c] = dg;
+  cx[c] = fx;
+  cy[c] = fy;
+}
+
+// Device address of the scratch array on the current device; looked up once per device.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_dsa_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0, double y1,
+                             double c_dt, const double* sigma_t_dev, const double* sigma_s_dev,
+                             const double* residual_dev, double cg_rtol, int cg_max_iter,
+                             double* delta_dev, int* iterations, void* stream, std::string* err) {
+  if ((dim != 1 && dim != 2) || nx < 1 || ny < 1 || (dim == 1 && ny != 1)) {
+    *err = "rte_dsa_solve_noalloc: bad mesh";
+    return RTE_EINVAL;
+  }
+  if ((long)nx * ny > NOALLOC_MAX_CELLS) {
+    *err = "rte_dsa_solve_noalloc: nx*ny exceeds the fixed scratch capacity of " +
+           std::to_string(NOALLOC_MAX_CELLS) + " cells";
+    return RTE_EINVAL;
+  }
+  if (!(x1 > x0) || (dim == 2 && !(y1 > y0)) || !(c_dt > 0.0) || !(cg_rtol >= 0.0) ||
+      cg_max_iter < 0 || !sigma_t_dev || !sigma_s_dev || !residual_dev || !delta_dev) {
+    *err = "rte_dsa_solve_noalloc: bad argument";
+    return RTE_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) {
+    *err = std::string("rte_dsa_solve_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return RTE_ECUDA;
+  }
+  const int n = nx * ny;
+  const long M = NOALLOC_MAX_CELLS;
+  double* diag = base;
+  double* cx = base + M;
+  double* cy = base + 2 * M;
+  double* partial = base + 8 * M;
+  unsigned* words = reinterpret_cast<unsigned*>(base + 8 * M + 2 * NOALLOC_MAX_BLOCKS);
+  int* iters_dev = reinterpret_cast<int*>(words + 4);
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CT, 0);
+  int blocks = (n + CT - 1) / CT;
+  int cap = (per_sm < 1 ? 1 : per_sm) * sms;
+  if (cap > 2 * sms) cap = 2 * sms;
+  if (cap > NOALLOC_MAX_BLOCKS) cap = NOALLOC_MAX_BLOCKS;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  // barrier count, generation, error flag and the iteration count start at zero
+  if ((e = cudaMemsetAsync(words, 0, 8 * sizeof(unsigned), s)) != cudaSuccess) {
+    *err = std::string("rte_dsa_solve_noalloc: ") + cudaGetErrorString(e);
+    return RTE_ECUDA;
+  }
+  const double hx = (x1 - x0) / nx, hy = dim == 2 ? (y1 - y0) / ny : 1.0;
+  ++g_launches;
+  dsa_coeff_kernel<<<(n + 255) / 256, 256, 0, s>>>(dim, nx, ny, hx, hy, 1.0 / c_dt, sigma_t_dev,
+                                                   sigma_s_dev, diag, cx, cy);
+  CgArgs a;
+  a.nx = nx;
+  a.ny = ny;
+  a.n = n;
+  a.diag = diag;
+  a.cx = cx;
+  a.cy = cy;
+  a.sig_s = sigma_s_dev;
+  a.residual = residual_dev;
+  a.residual_b = nullptr;
+  a.rtol2 = cg_rtol * cg_rtol;
+  a.max_iter = cg_max_iter;
+  a.r = base + 3 * M;
+  a.p0 = base + 4 * M;
+  a.p1 = base + 5 * M;
+  a.ap = base + 6 * M;
+  a.x = base + 7 * M;
+  a.partial = partial;
+  a.bar = words;
+  a.delta = delta_dev;
+  a.rho_half = nullptr;
+  a.rho_out = nullptr;
+  a.q_out = nullptr;
+  a.iters = iters_dev;
+  void* args[] = {&a};
+  ++g_launches;
+  e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(CT), args, 0, s);
+  if (e != cudaSuccess) {
+    *err = std::string("rte_dsa_solve_noalloc: ") + cudaGetErrorString(e);
+    return RTE_ECUDA;
+  }
+  unsigned host_words[8];
+  if ((e = cudaMemcpyAsync(host_words, words, sizeof(host_words), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    *err = std::string("rte_dsa_solve_noalloc: ") + cudaGetErrorString(e);
+    return RTE_ECUDA;
+  }
+  if (iterations) *iterations = (int)host_words[4];
+  if (host_words[2] != 0u) {
+    *err = "rte_dsa_solve_noalloc: a bounded grid-barrier wait ran out";
+    return RTE_ETIMEOUT;
+  }
+  return RTE_OK;
 }
 
 }  // namespace rte

@@ -1037,6 +1037,19 @@ rte_status rte_op_rom_get(rte_handle h, int which, int* rank, double* S, double*
   return RTE_OK;
 }
 
+rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0,
+                                 double y1, double c_dt, const double* sigma_t_dev,
+                                 const double* sigma_s_dev, const double* residual_dev,
+                                 double cg_rtol, int cg_max_iter, double* delta_dev,
+                                 int* iterations, void* stream) {
+  std::string err;
+  const rte_status s = dsa_solve_noalloc(dim, nx, ny, x0, x1, y0, y1, c_dt, sigma_t_dev,
+                                         sigma_s_dev, residual_dev, cg_rtol, cg_max_iter,
+                                         delta_dev, iterations, stream, &err);
+  if (s != RTE_OK) g_create_error = err;
+  return s;
+}
+
 rte_status rte_op_rom_reset(rte_handle h) {
   if (!h) return RTE_EINVAL;
   h->ig.rank = h->pc.rank = 0;

@@ -137,6 +137,12 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
                       const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
                       cudaStream_t s);
 
+// Allocation-free DSA solve behind rte_dsa_solve_noalloc (cg.cu); *err receives the message.
+rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0, double y1,
+                             double c_dt, const double* sigma_t_dev, const double* sigma_s_dev,
+                             const double* residual_dev, double cg_rtol, int cg_max_iter,
+                             double* delta_dev, int* iterations, void* stream, std::string* err);
+
 // ROM (rom.cu).
 struct RomDev {
   int n, r_max, rank;

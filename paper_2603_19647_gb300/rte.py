@@ -96,6 +96,10 @@ _SIGS = {
     "rte_op_rom_apply": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "rte_op_rom_get": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp, _dp, _dp]),
     "rte_op_rom_reset": (ctypes.c_int, [_vp]),
+    "rte_dsa_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, _vp, _vp, _vp, ctypes.c_double,
+                                             ctypes.c_int, _vp, _ip, _vp]),
 }
 
 
@@ -268,6 +272,22 @@ def rte_create(mesh: Mesh, quad: Quadrature, sigma_t, sigma_s, source, c_dt, opt
     nv = ctypes.c_int(0)
     lib.rte_get_quadrature(h, ctypes.byref(nv), None, None, None)
     return Handle(h, n, nv.value)
+
+
+def rte_dsa_solve_noalloc(dim, nx, ny, x0, x1, y0, y1, c_dt, sigma_t_dev, sigma_s_dev,
+                          residual_dev, cg_rtol, cg_max_iter, delta_dev, stream=None):
+    """rte_dsa_solve_noalloc with device pointers given as integers (e.g. tensor.data_ptr());
+    returns the CG iteration count."""
+    its = ctypes.c_int(0)
+    lib = load()
+    status = lib.rte_dsa_solve_noalloc(int(dim), int(nx), int(ny), float(x0), float(x1), float(y0),
+                                       float(y1), float(c_dt), _vp(sigma_t_dev), _vp(sigma_s_dev),
+                                       _vp(residual_dev), float(cg_rtol), int(cg_max_iter),
+                                       _vp(delta_dev), ctypes.byref(its),
+                                       None if stream is None else _vp(int(stream)))
+    if status != RTE_OK:
+        raise RteError(status, lib.rte_last_error(None).decode())
+    return its.value
 
 
 def mesh_from(workload):
