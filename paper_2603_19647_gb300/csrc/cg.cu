@@ -76,7 +76,7 @@ __device__ void grid_barrier(unsigned* bar, unsigned& gen) {
           atomicExch(&bar[2], 1u);
           break;
         }
-        __nanosleep(32);
+        if (spins > 1024) __nanosleep(32);
       }
     }
     __threadfence();

@@ -11,8 +11,10 @@
 // and the singular vectors are v_k ~ (z_j / (d_j^2 - sigma_k^2))_j,
 // u_k ~ (-1, d_j z_j / (d_j^2 - sigma_k^2))_j.
 // Each root is bracketed, written as sigma_k^2 = d_s^2 + mu (s the nearer pole, so that
-// d_j^2 - sigma_k^2 = (d_j - d_s)(d_j + d_s) - mu is formed without cancellation), and
-// found by bisection on the ordered bit pattern of mu (relative accuracy at any scale).
+// d_j^2 - sigma_k^2 = (d_j - d_s)(d_j + d_s) - mu is formed without cancellation), located
+// by bisection on the ordered bit pattern of mu (which reaches any scale quickly) and
+// finished by rational steps (pole term exact, the other terms linearised, as in the
+// classical secular-equation solvers) kept inside the bisection bracket.
 // For orthogonal vectors z is replaced by the z^ for which the computed roots are exact
 // (Gu and Eisenstat's formula, the Loewner theorem):
 //   z^_j^2 = (s_n^2 - d_j^2) prod_{i<j} (s_i^2 - d_j^2)/(d_i^2 - d_j^2)
@@ -157,19 +159,73 @@ __global__ void __launch_bounds__(32) sec_root_kernel(Sec q) {
     hi = zn * zn;
   }
   const double ds = q.d[(int)q.act[s]];
-  // bisection on the bit pattern of t >= 0: h(t) increasing, h(0+) = -inf, h(hi) >= 0
+  // h(t) = +-g(+-t) is increasing on (0, hi] with h(0+) = -inf and h(hi) >= 0.  A few steps
+  // of bisection on the bit pattern of t (which halves the exponent range first, so any scale
+  // is bracketed quickly) are followed by Newton steps on h kept inside the bracket [a, b];
+  // a Newton step that leaves the bracket or stalls is replaced by a bit-pattern bisection.
   long long a = __double_as_longlong(lo), b = __double_as_longlong(hi);
-  for (int it = 0; it < 80 && b - a > 1; ++it) {
+  for (int it = 0; it < 4 && b - a > 1; ++it) {
     const long long m = a + (b - a) / 2;
     const double t = __longlong_as_double(m);
     const double g = sec_g(q, na, ds, neg ? -t : t, lane);
-    const double h = neg ? -g : g;
-    if (h > 0.0) b = m; else a = m;
+    if ((neg ? -g : g) > 0.0) b = m; else a = m;
   }
-  const double ta = __longlong_as_double(a), tb = __longlong_as_double(b);
-  const double ga = sec_g(q, na, ds, neg ? -ta : ta, lane);
-  const double gb = sec_g(q, na, ds, neg ? -tb : tb, lane);
-  const double t = (a > 0 && fabs(ga) < fabs(gb)) ? ta : tb;
+  // Rational steps: with the pole term z_s^2 / (0 - mu) kept exact and the rest
+  // R(mu) = sum_{j != s} z_j^2 / (delta_j - mu) linearised at the current mu, g = 0 becomes
+  // R1 x^2 + (1 + R0 - R1 mu) x - z_s^2 = 0 for the new mu = x (one root of each sign).
+  const int ps = (int)q.act[s];
+  const double A2 = q.z[ps] * q.z[ps];
+  double t = __longlong_as_double(a + (b - a) / 2);
+  for (int it = 0; it < 60 && b - a > 1; ++it) {
+    const double mu = neg ? -t : t;
+    double r0 = 0.0, r1 = 0.0;
+    for (int e = lane; e < na; e += 32) {
+      const int j = (int)q.act[e];
+      if (j == ps) continue;
+      const double dj = q.d[j], zj = q.z[j];
+      const double w = zj / ((dj - ds) * (dj + ds) - mu);
+      r0 += zj * w;
+      r1 += w * w;
+    }
+    r0 = warp_sum(r0);
+    r1 = warp_sum(r1);
+    const double g = 1.0 + r0 - A2 / mu;
+    const double h = neg ? -g : g;
+    const long long tbits = __double_as_longlong(t);
+    if (h > 0.0) b = tbits; else a = tbits;
+    if (b - a <= 1) break;
+    const double bq = 1.0 + r0 - r1 * mu;
+    double x;
+    if (r1 > 0.0) {
+      const double sq = sqrt(bq * bq + 4.0 * r1 * A2);
+      if (!neg) x = bq >= 0.0 ? 2.0 * A2 / (bq + sq) : (sq - bq) / (2.0 * r1);
+      else x = bq <= 0.0 ? 2.0 * A2 / (bq - sq) : (-bq - sq) / (2.0 * r1);
+    } else {
+      x = A2 / bq;
+    }
+    double tn = neg ? -x : x;
+    if (tn > 0.0 && fabs(tn - t) <= 4.440892098500626e-16 * fabs(t)) {
+      t = tn;   // converged to the resolution of t
+      break;
+    }
+    const long long nbits = __double_as_longlong(tn);
+    if (!(tn > 0.0) || nbits <= a || nbits >= b) tn = __longlong_as_double(a + (b - a) / 2);
+    t = tn;
+  }
+  {
+    const double ta = __longlong_as_double(a), tbv = __longlong_as_double(b);
+    const double ga = a > 0 ? sec_g(q, na, ds, neg ? -ta : ta, lane) : -1e300;
+    const double gb = sec_g(q, na, ds, neg ? -tbv : tbv, lane);
+    const double gt = sec_g(q, na, ds, neg ? -t : t, lane);
+    // the best of the bracket ends and the last iterate
+    double best = tbv, bv = fabs(gb);
+    if (a > 0 && fabs(ga) < bv) {
+      best = ta;
+      bv = fabs(ga);
+    }
+    if (t > 0.0 && fabs(gt) < bv) best = t;
+    t = best;
+  }
   if (lane == 0) {
     q.mu[k] = neg ? -t : t;
     q.sidx[k] = s;
@@ -280,10 +336,17 @@ __global__ void __launch_bounds__(256) sec_finish_kernel(int r, Sec q, double* s
   const bool grew = alpha > 1e-12 * xn;
   if (tid == 0) {
     for (int j = 0; j < n; ++j) ord[j] = j;
-    for (int a = 0; a < n; ++a) {   // selection sort, descending
+    // selection sort, descending, on the bit patterns (non-negative doubles order like integers)
+    for (int a = 0; a < n; ++a) {
       int best = a;
-      for (int b = a + 1; b < n; ++b)
-        if (q.sig[ord[b]] > q.sig[ord[best]]) best = b;
+      long long bb = __double_as_longlong(q.sig[ord[a]]);
+      for (int b = a + 1; b < n; ++b) {
+        const long long vb = __double_as_longlong(q.sig[ord[b]]);
+        if (vb > bb) {
+          best = b;
+          bb = vb;
+        }
+      }
       const int t = ord[a];
       ord[a] = ord[best];
       ord[best] = t;

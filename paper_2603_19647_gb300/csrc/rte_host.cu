@@ -354,7 +354,6 @@ rte_status sweep_f(rte_handle h, const double* qa, double* y_out) {
     a.g2 = h->src;
     a.f = h->f;
     a.pm = h->pm;
-    a.pm_a = nullptr;
     quadrant_ghosts(h->g, a.gx, a.gy);
     CK(launch_sweep2d<double>(a, 1, h->R, h->st));
     CK(launch_sum_partials(h->pm, h->L.nfam, (int)h->ncell, nullptr, y_out, h->st));
@@ -652,9 +651,8 @@ rte_status reset_state(rte_handle h) {
   h->flag_ig = h->flag_pc = false;
   h->y_valid = false;
   h->pending_rom = false;
-  h->ig.rank = 0;
-  h->pc.rank = 0;
-  h->ig.lu_ok = h->pc.lu_ok = 0;
+  rom_reset(h->ig);
+  rom_reset(h->pc);
   return RTE_OK;
 }
 
@@ -1052,8 +1050,8 @@ rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, 
 
 rte_status rte_op_rom_reset(rte_handle h) {
   if (!h) return RTE_EINVAL;
-  h->ig.rank = h->pc.rank = 0;
-  h->ig.lu_ok = h->pc.lu_ok = 0;
+  rom_reset(h->ig);
+  rom_reset(h->pc);
   h->flag_ig = h->flag_pc = false;
   return RTE_OK;
 }

@@ -56,7 +56,6 @@ struct Sweep2DArgs {
   const Real* g2;       // K2 pass B isotropic source G [ncell]
   Real* f;              // K2: [nfam][ncell][dl] in / out (f^{n-1} -> f^n)
   Real* pm;             // [nfam][ncell] partial moments (K1: of L^-1 q; K2: of pass B)
-  Real* pm_a;           // K2: [nfam][ncell] partial moments of f^n (may be nullptr)
   Real gx[4], gy[4];    // per quadrant inflow ghost of pass A (K1: zero)
   Real* edge;           // [nfam][nblk][nx][dl] (K2: two planes, A then B)
   SweepCtrl* ctrl;
@@ -146,15 +145,17 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
 // ROM (rom.cu).
 struct RomDev {
   int n, r_max, rank;
-  double* U;      // [r_max+1][n] column-major (column k at U + k*n)
-  double* W;      // [r_max+1][n]  (W = B V)
-  double* Utmp;   // [r_max+1][n]
-  double* Wtmp;   // [r_max+1][n]
+  int wu, ww;     // columns in use of U0 and W0
+  double* U;      // U0: [WCAP][n] column-major (column k at U + k*n); U = U0 Q
+  double* W;      // W0: [WCAP][n]; W = W0 P (W = B V)
+  double* Utmp;   // [WCAP][n]
+  double* Wtmp;   // [WCAP][n]
+  double *Q, *P, *Qtmp, *Ptmp;   // [WCAP][65] row-major small factors
   double* S;      // [r_max+1]
   double* core;   // small workspace
-  double* lu;     // [r_max*r_max] LU of A_r, row-major, with pivots
+  double* lu;     // [r_max*r_max] A_r^{-1}, row-major
   int* piv;
-  double* proj;   // [r_max+1] projections
+  double* proj;   // [2*(r_max+1)] projections and reduced coordinates
   double* partial;
   double* sec;    // scratch of the core SVD
   int lu_ok;
@@ -167,6 +168,7 @@ cudaError_t core_svd_secular(const double* S, int r, const double* p, double* sc
                              double* scratch, cudaStream_t s);
 cudaError_t rom_alloc(RomDev& R, int n, int r_max);
 void rom_free(RomDev& R);
+void rom_reset(RomDev& R);   // empty ROM (rank 0), keeps the allocation
 // Incremental SVD append (App. B).  Returns new rank in *rank_out (host), grew flag.
 cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc_eps,
                        int* grew, double* smallest_ratio, cudaStream_t s);

@@ -27,7 +27,8 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int KCHUNK = 8;            // columns per published edge chunk
-constexpr unsigned SPIN_LIMIT = 1u << 20;
+constexpr unsigned SPIN_LIMIT = 1u << 20;        // global-flag polls (sleeping after the first 256)
+constexpr unsigned SMEM_SPIN_LIMIT = 1u << 26;   // shared-counter polls (about a second)
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -50,8 +51,11 @@ __device__ __forceinline__ Real ldcg(const Real* p) {
   return __ldcg(p);
 }
 
-// Transpose-reduce R values over the DL lanes of a lane group: after it, lane dl holds the
-// group-wide sum of value index m = dl / (DL / R).
+// Transpose-reduce N values over the DL lanes of a lane group.  Each round with offset O
+// halves the values a lane keeps (the lane with bit O set keeps the upper half) and adds the
+// partner's copy; once one value is left the remaining rounds are plain butterflies.  After
+// it, for N >= DL lane dl holds in v[i] (i < N/DL) the group sum of value index
+// dl * (N/DL) + i; for N < DL it holds in v[0] the sum of value index dl / (DL/N).
 template <class Real, int N, int O>
 struct TReduce {
   static __device__ __forceinline__ void run(Real* v, int dl) {
@@ -105,40 +109,51 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // MODE 1: fused f sweep (K2): pass A  f^n = L^-1(q + tau f^{n-1}) with inflow ghosts,
 //         pass B  y = L^-1(g2 + tau f^n) with zero inflow; moment of B (and of A).
 //
-// CTA = W warps stacked vertically; warp w = NG lane groups of R rows (RW = NG R rows).
-// Global step t: warp w works at local step t - w L (L = K + RW - 1), so the bottom row of
-// warp w-1 reaches column x a whole chunk of K steps before warp w needs it; the hand-off
-// goes through a shared-memory ring and one __syncthreads per chunk.  The per-cell data of
-// chunk c+1 (sigma_t, sources) is copied to shared memory with cp.async while chunk c runs;
-// for row r of warp w the staged column index is simply the step index within the chunk.
+// CTA = W warps stacked vertically, each a pipeline stage: warp w owns RW = NG R rows and
+// works through the columns in chunks of K.  The bottom row of warp w-1 is handed to warp w
+// step by step through a shared ring: the producer bumps a shared progress counter after
+// every column, the consumer re-reads it (bounded spin) only when its cached copy says the
+// column is not there yet, and reports how far it has read once per chunk so the producer
+// may reuse ring slots.  Each warp stages the per-cell data of its next chunk into its own
+// shared buffers with cp.async while it computes the current one.  Warp 0 takes its top row
+// from the CTA above through global memory behind a release flag, a chunk at a time.  No
+// CTA-wide barrier runs inside the column loop.
 template <class Real, int DL, int R, int K, int MODE, bool TABLE>
 __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A) {
   constexpr int NG = 32 / DL;
   constexpr int RW = NG * R;
-  constexpr int L = K + RW - 1;
-  constexpr int RING = 2 * K;
+  constexpr int RING = 4 * K;
   constexpr int NP = (MODE == 1) ? 2 : 1;            // planes (recurrences) carried
   constexpr bool STAGE_F = MODE != 0;
   constexpr int V = DL * (int)sizeof(Real) / 16;     // 16-byte pieces per cell of a family
+  constexpr int PER_DL = (TABLE ? 1 : 0) + (STAGE_F ? 1 : 0);              // [RW][K][DL] arrays
+  constexpr int PER_S = (TABLE ? 0 : 1) + (MODE != 2 ? 1 : 0) + (MODE != 0 ? 1 : 0);  // [RW][K]
+  constexpr int WARP_REALS = 2 * RW * K * (PER_DL * DL + PER_S);
   static_assert(R <= DL, "rows per lane group must not exceed the lane count");
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int W = blockDim.x >> 5;
-  const int RC = W * RW;
-  // shared memory: [2][RC][K][DL] table / f, then [2][RC][K] scalars, then the hand-off ring
-  Real* tab_s = reinterpret_cast<Real*>(smraw);                   // 1/d (TABLE)
-  Real* f_s = tab_s + (TABLE ? 2 * RC * K * DL : 0);              // f^{n-1} (MODE 1, 2)
-  Real* st_s = f_s + (STAGE_F ? 2 * RC * K * DL : 0);             // sigma_t (no TABLE)
-  Real* qa_s = st_s + (TABLE ? 0 : 2 * RC * K);                   // q (MODE 0, 1)
-  Real* g2_s = qa_s + (MODE != 2 ? 2 * RC * K : 0);               // g2 (MODE 1, 2)
-  Real* hand = g2_s + (MODE != 0 ? 2 * RC * K : 0);               // [NP][W-1][RING][DL]
   __shared__ unsigned s_ticket;
-  __shared__ int s_abandon;
+  __shared__ volatile int s_prod[8];    // columns of its bottom row warp w has put in the ring
+  __shared__ volatile int s_cons[8];    // columns of the ring above warp w has consumed
+  __shared__ volatile int s_abandon;
 
+  const int W = blockDim.x >> 5;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gi = lane / DL, dl = lane % DL;
+  // per-warp staging buffers, then the W-1 rings
+  Real* wbuf = reinterpret_cast<Real*>(smraw) + (size_t)warp * WARP_REALS;
+  Real* tab_s = wbuf;                                            // [2][RW][K][DL]
+  Real* f_s = tab_s + (TABLE ? 2 * RW * K * DL : 0);             // [2][RW][K][DL]
+  Real* st_s = f_s + (STAGE_F ? 2 * RW * K * DL : 0);            // [2][RW][K]
+  Real* qa_s = st_s + (TABLE ? 0 : 2 * RW * K);
+  Real* g2_s = qa_s + (MODE != 2 ? 2 * RW * K : 0);
+  Real* rings = reinterpret_cast<Real*>(smraw) + (size_t)W * WARP_REALS;  // [W-1][NP][RING][DL]
   if (tid == 0) {
     s_ticket = atomicAdd(&A.ctrl->ticket, 1u);
     s_abandon = 0;
+  }
+  if (tid < 8) {
+    s_prod[tid] = 0;
+    s_cons[tid] = 0;
   }
   __syncthreads();
   const unsigned ticket = s_ticket;
@@ -152,12 +167,14 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   const int slot = fam * DL + dl;
   const Real ca = A.a[slot], cb = A.b[slot], cw = A.w[slot];
   const Real ct = A.tau + ca + cb;
-  const int rowblk0 = blk * RC;                     // first sweep-order row of this CTA
-  const int row0 = rowblk0 + warp * RW + gi * R;    // lane group's row m = 0
+  const int wrow0 = blk * A.rows_per_blk + warp * RW;   // first sweep-order row of this warp
+  const int row0 = wrow0 + gi * R;                       // lane group's row m = 0
   const Real gx = A.gx[quad];
   const Real gy = A.gy[quad];
   const Real* tab_fam = TABLE ? A.inv_d + (size_t)fam * ncell * DL : nullptr;
   Real* f_fam = STAGE_F ? A.f + (size_t)fam * ncell * DL : nullptr;
+  Real* ring_in = warp > 0 ? rings + (size_t)(warp - 1) * NP * RING * DL : nullptr;
+  Real* ring_out = warp < W - 1 ? rings + (size_t)warp * NP * RING * DL : nullptr;
 
   Real psA[R], psB[R];
 #pragma unroll
@@ -172,36 +189,33 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   Real* edge_out = A.edge + ((size_t)(fam * A.nblk + blk) * nx) * DL;
   unsigned* flag_in = &A.ctrl->flags[fam * A.nblk + (has_up ? blk - 1 : 0)];
   unsigned* flag_out = &A.ctrl->flags[fam * A.nblk + blk];
-  const int T = nx + RW - 1 + (W - 1) * L;
+  const int T = nx + RW - 1;              // warp-local steps: row rr handles column t - rr
   const int nchunk = (T + K - 1) / K;
 
-  // Copy the data of chunk c into buffer c & 1: for row r (warp w, row rr in the warp) and
-  // step k of the chunk, the cell at column x = cK + k - wL - rr.
+  // Copy this warp's data of chunk c into its buffer c & 1: row rr, step k -> column c K + k - rr.
   auto stage = [&](int c) {
     const int buf = c & 1;
     if constexpr (TABLE || STAGE_F) {
-      for (int e = tid; e < RC * K * V; e += blockDim.x) {
+      for (int e = lane; e < RW * K * V; e += 32) {
         const int v = e % V, rk = e / V;
-        const int r = rk / K, k = rk % K;
-        const int w = r / RW, rr = r % RW;
-        const int x = c * K + k - w * L - rr;
-        const int jj = rowblk0 + r;
+        const int rr = rk / K, k = rk % K;
+        const int x = c * K + k - rr;
+        const int jj = wrow0 + rr;
         const bool ok = x >= 0 && x < nx && jj < ny;
         const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
-        const int o = ((buf * RC + r) * K + k) * DL + v * (16 / (int)sizeof(Real));
+        const int o = ((buf * RW + rr) * K + k) * DL + v * (16 / (int)sizeof(Real));
         const size_t g = (size_t)cell * DL + v * (16 / sizeof(Real));
         if constexpr (TABLE) cp_async_16(tab_s + o, tab_fam + g, ok);
         if constexpr (STAGE_F) cp_async_16(f_s + o, f_fam + g, ok);
       }
     }
-    for (int e = tid; e < RC * K; e += blockDim.x) {
-      const int r = e / K, k = e % K;
-      const int w = r / RW, rr = r % RW;
-      const int x = c * K + k - w * L - rr;
-      const int jj = rowblk0 + r;
+    for (int e = lane; e < RW * K; e += 32) {
+      const int rr = e / K, k = e % K;
+      const int x = c * K + k - rr;
+      const int jj = wrow0 + rr;
       const bool ok = x >= 0 && x < nx && jj < ny;
       const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
-      const int o = (buf * RC + r) * K + k;
+      const int o = (buf * RW + rr) * K + k;
       if constexpr (!TABLE) cp_async(st_s + o, A.sig_t + cell, ok);
       if constexpr (MODE != 2) cp_async(qa_s + o, A.q + cell, ok);
       if constexpr (MODE != 0) cp_async(g2_s + o, A.g2 + cell, ok);
@@ -209,30 +223,31 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
     cp_async_commit();
   };
 
+  int known_prod = 0;   // lower bound of s_prod[warp - 1] seen by this warp
+  int known_cons = 0;   // lower bound of s_cons[warp + 1] seen by this warp
+
   stage(0);
   for (int c = 0; c < nchunk; ++c) {
-    // Chunk c's copies (issued one chunk earlier) have landed for this thread; the barrier
-    // makes every thread's copies and the previous chunk's hand-off writes visible, and
-    // guarantees that nobody still reads buffer (c+1)&1, which the next stage overwrites.
     cp_async_wait0();
-    __syncthreads();
-    if (c + 1 < nchunk) stage(c + 1);
+    __syncwarp();                       // chunk c's staged data is visible to the warp
+    if (c + 1 < nchunk) stage(c + 1);   // buffer (c+1)&1 was last read in chunk c-1
     const int buf = c & 1;
     const int tb = c * K;
-    // top inflow of warp 0: previous row block's bottom row (global) or the inflow ghost
+    // Top row input for columns [tb, tb + K): lane group 0, row 0 handles column t at step t.
     Real ebA[K], ebB[K];
+    Real mb[K * R];   // unweighted cell values of this chunk, reduced at its end
+    const int need = min(tb + K, nx);
     if (warp == 0) {
       if (has_up && tb < nx) {
-        const unsigned need = (unsigned)min(tb + K, nx);
         if (lane == 0 && !s_abandon) {
           unsigned spins = 0;
-          while (ld_acquire(flag_in) < need) {
+          while (ld_acquire(flag_in) < (unsigned)need) {
             if (++spins > SPIN_LIMIT || ld_acquire(&A.ctrl->err) != 0u) {
               atomicExch(&A.ctrl->err, 1u);
               s_abandon = 1;
               break;
             }
-            __nanosleep(64);
+            if (spins > 256) __nanosleep(64);
           }
         }
         __syncwarp();
@@ -254,32 +269,48 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
         }
       }
     }
-    const int tw0 = tb - warp * L;   // warp-local step of k = 0
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int tw = tw0 + k;
+      const int t = tb + k;
       Real upA = __shfl_up_sync(FULL, psA[R - 1], DL);
       Real upB = __shfl_up_sync(FULL, psB[R - 1], DL);
-      if (gi == 0) {
-        if (warp == 0) {
-          upA = ebA[k];
-          upB = ebB[k];
-        } else {
-          const int slot_r = ((tw % RING) + RING) % RING;   // column of row 0 = tw
-          upA = hand[((0 * (W - 1) + warp - 1) * RING + slot_r) * DL + dl];
-          if constexpr (MODE == 1) upB = hand[((1 * (W - 1) + warp - 1) * RING + slot_r) * DL + dl];
+      if (warp > 0 && t < nx) {
+        // column t of the warp above's bottom row, handed over step by step
+        if (known_prod <= t) {
+          int kp = 0;
+          if (lane == 0) {
+            unsigned spins = 0;
+            while ((kp = s_prod[warp - 1]) <= t && !s_abandon) {
+              if (++spins > SMEM_SPIN_LIMIT) {
+                atomicExch(&A.ctrl->err, 1u);
+                s_abandon = 1;
+                break;
+              }
+            }
+          }
+          known_prod = __shfl_sync(FULL, kp, 0);
+          __threadfence_block();
+        }
+        const int rs = (t % RING) * DL + dl;
+        ebA[k] = ring_in[rs];
+        if constexpr (MODE == 1) ebB[k] = ring_in[RING * DL + rs];
+        if (k == K - 1 || t == nx - 1) {
+          __syncwarp();
+          if (lane == 0) s_cons[warp] = t + 1;   // ring slots of columns <= t may be reused
         }
       }
-      Real mom[R], momA[R];
+      if (gi == 0) {
+        upA = ebA[k];
+        upB = ebB[k];
+      }
 #pragma unroll
       for (int m = R - 1; m >= 0; --m) {
-        const int x = tw - m - gi * R;
+        const int x = t - m - gi * R;
         const int jj = row0 + m;
-        mom[m] = Real(0);
-        momA[m] = Real(0);
+        mb[k * R + m] = Real(0);
         if (x >= 0 && x < nx && jj < ny) {
-          const int r = warp * RW + gi * R + m;
-          const int o = (buf * RC + r) * K + k;
+          const int rr = gi * R + m;
+          const int o = (buf * RW + rr) * K + k;
           const int od = o * DL + dl;
           Real dinv;
           if constexpr (TABLE) dinv = tab_s[od];
@@ -288,65 +319,92 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
           if constexpr (MODE == 0) {
             const Real v = (qa_s[o] + ca * psA[m] + cb * uA) * dinv;
             psA[m] = v;
-            mom[m] = cw * v;
+            mb[k * R + m] = v;
           } else if constexpr (MODE == 2) {
             const Real v = (g2_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA) * dinv;
             psA[m] = v;
-            mom[m] = cw * v;
+            mb[k * R + m] = v;
           } else {
             const Real va = (qa_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA) * dinv;
             psA[m] = va;
             const int px = xpos ? x : nx - 1 - x;
             const int py = ypos ? jj : ny - 1 - jj;
             f_fam[((long)py * nx + px) * DL + dl] = va;
-            momA[m] = cw * va;
             const Real uB = (m == 0) ? upB : psB[m > 0 ? m - 1 : 0];
             const Real vb = (g2_s[o] + A.tau * va + ca * psB[m] + cb * uB) * dinv;
             psB[m] = vb;
-            mom[m] = cw * vb;
+            mb[k * R + m] = vb;
           }
         }
       }
-      // Quadrature moment over the lane group's directions, one partial per family.
-      TReduce<Real, R, DL / 2>::run(mom, dl);
-      if constexpr (MODE == 1) {
-        if (A.pm_a) TReduce<Real, R, DL / 2>::run(momA, dl);
-      }
-      if ((dl & (DL / R - 1)) == 0) {
-        const int m = dl / (DL / R);
-        const int x = tw - m - gi * R;
-        const int jj = row0 + m;
-        if (x >= 0 && x < nx && jj < ny) {
-          const int px = xpos ? x : nx - 1 - x;
-          const int py = ypos ? jj : ny - 1 - jj;
-          const long cell = (long)py * nx + px;
-          A.pm[fam * ncell + cell] = mom[0];
-          if constexpr (MODE == 1) {
-            if (A.pm_a) A.pm_a[fam * ncell + cell] = momA[0];
-          }
-        }
-      }
-      // bottom row of this warp: to the next warp (shared ring) or the next CTA (global)
-      const int xb = tw - (R - 1) - (NG - 1) * R;
-      if (gi == NG - 1 && xb >= 0 && xb < nx) {
+      // bottom row of this warp: to the warp below (shared ring) or the next CTA (global)
+      const int xb = t - (RW - 1);
+      if (xb >= 0 && xb < nx) {
         if (warp < W - 1) {
-          const int slot_r = xb % RING;
-          hand[((0 * (W - 1) + warp) * RING + slot_r) * DL + dl] = psA[R - 1];
-          if constexpr (MODE == 1) hand[((1 * (W - 1) + warp) * RING + slot_r) * DL + dl] = psB[R - 1];
-        } else if (has_down) {
+          // slot of column xb - RING must have been read by the warp below
+          if (xb - RING >= known_cons) {
+            int kc = 0;
+            if (lane == 0) {
+              unsigned spins = 0;
+              while ((kc = s_cons[warp + 1]) <= xb - RING && !s_abandon) {
+                if (++spins > SMEM_SPIN_LIMIT) {
+                  atomicExch(&A.ctrl->err, 1u);
+                  s_abandon = 1;
+                  break;
+                }
+              }
+            }
+            known_cons = __shfl_sync(FULL, kc, 0);
+          }
+          if (gi == NG - 1) {
+            const int rs = (xb % RING) * DL + dl;
+            ring_out[rs] = psA[R - 1];
+            if constexpr (MODE == 1) ring_out[RING * DL + rs] = psB[R - 1];
+          }
+          __syncwarp();
+          __threadfence_block();
+          if (lane == 0) s_prod[warp] = xb + 1;
+        } else if (has_down && gi == NG - 1) {
           edge_out[(size_t)xb * DL + dl] = psA[R - 1];
           if constexpr (MODE == 1) edge_out[plane + (size_t)xb * DL + dl] = psB[R - 1];
         }
       }
     }
-    // publish the columns the bottom row finished in this chunk
-    if (warp == W - 1 && has_down) {
-      const int xlast = tb + K - 1 - (W - 1) * L - (RW - 1);
-      if (xlast >= 0) {
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release(flag_out, (unsigned)min(xlast + 1, nx));
+    // Quadrature moment of the chunk: weights, then one transpose-reduce over the lane
+    // group's directions for all K x R cells; one partial per family and cell.
+    {
+      constexpr int NV = K * R;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) mb[i] *= cw;
+      TReduce<Real, NV, DL / 2>::run(mb, dl);
+      constexpr int PER = NV >= DL ? NV / DL : 1;
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        int idx;
+        bool writer;
+        if constexpr (NV >= DL) {
+          idx = dl * PER + i;
+          writer = true;
+        } else {
+          idx = dl / (DL / NV);
+          writer = (dl & (DL / NV - 1)) == 0;
+        }
+        const int k = idx / R, m = idx % R;
+        const int x = tb + k - m - gi * R;
+        const int jj = row0 + m;
+        if (writer && x >= 0 && x < nx && jj < ny) {
+          const int px = xpos ? x : nx - 1 - x;
+          const int py = ypos ? jj : ny - 1 - jj;
+          A.pm[fam * ncell + (long)py * nx + px] = mb[i];
+        }
       }
+    }
+    // publish the bottom-row columns finished in this chunk
+    const int done = min(tb + K - (RW - 1), nx);
+    if (done > 0 && warp == W - 1 && has_down) {
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release(flag_out, (unsigned)done);
     }
   }
   cp_async_wait0();
@@ -370,15 +428,11 @@ constexpr int KSTEP = 8;   // columns per chunk
 
 inline size_t sweep2d_smem_bytes_impl(size_t real, int dl, int R, int W, int mode, bool table) {
   const int K = 8;
-  const int RW = (32 / dl) * R, RC = W * RW, np = mode == 1 ? 2 : 1;
-  size_t n = 0;
-  if (table) n += 2 * RC * K * dl;
-  if (mode != 0) n += 2 * RC * K * dl;
-  if (!table) n += 2 * RC * K;
-  if (mode != 2) n += 2 * RC * K;
-  if (mode != 0) n += 2 * RC * K;
-  n += np * (W - 1) * 2 * K * dl;
-  return real * n;
+  const int RW = (32 / dl) * R, np = mode == 1 ? 2 : 1;
+  const int per_dl = (table ? 1 : 0) + (mode != 0 ? 1 : 0);
+  const int per_s = (table ? 0 : 1) + (mode != 2 ? 1 : 0) + (mode != 0 ? 1 : 0);
+  const size_t warp_reals = (size_t)2 * RW * K * (per_dl * dl + per_s);
+  return real * (W * warp_reals + (size_t)(W - 1) * np * 4 * K * dl);
 }
 
 namespace {
