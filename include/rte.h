@@ -83,7 +83,8 @@ typedef struct {
   double eps_up;     /* Phase 3 update indicators, Sec. 3.2 (default 1e-6) */
   int max_iter;      /* N_iter of Algorithm 1 (default 500) */
   int r_max;         /* rank cap of each ROM, <= 64 (default 40) */
-  int precision;     /* RTE_FP64 (default) | RTE_FP32 (FP32 sweeps, FP64 refinement) */
+  int precision;     /* RTE_FP64 (default) | RTE_FP32: sweeps and f in FP32, the SI residual,
+                        DSA and ROMs in FP64 (iterative refinement of the SI increments) */
   int rom;           /* RTE_ROM_AUTO (default) | RTE_ROM_OFF | RTE_ROM_MANUAL */
   int residual_norm; /* RTE_REL_INF (default): ||.||_inf relative to ||rho^{l-1/2}||_inf;
                         RTE_ABS_INF: the paper's absolute test */

@@ -46,6 +46,13 @@ struct rte_s {
   double *pm = nullptr, *pm_a = nullptr, *edge = nullptr;
   SweepCtrl* ctrl = nullptr;
   double *psi_w = nullptr, *psi_w_a = nullptr;
+  // FP32 mode (RTE_FP32): sweep data in float; FP64 refinement state
+  bool fp32 = false;
+  float *sig_t_f = nullptr, *src_f = nullptr, *ca_f = nullptr, *cb_f = nullptr, *cw_f = nullptr;
+  float *f_f = nullptr, *pm_f = nullptr, *edge_f = nullptr, *psi_w_f = nullptr, *q_f = nullptr;
+  float *cth_f = nullptr, *ctl_f = nullptr;   // tau + a + b per slot as an exact hi / lo pair
+  float *f_init_f = nullptr;
+  double *y_ir = nullptr, *rho_ref = nullptr;   // y_ir = T Sigma_s rho_ref, accumulated in FP64
   // device: cell vectors
   double *rho = nullptr, *rho_prev = nullptr, *rho_half = nullptr, *rho_half1 = nullptr;
   double *rho0 = nullptr, *y = nullptr, *btilde = nullptr, *q = nullptr, *delta = nullptr;
@@ -260,7 +267,9 @@ void free_all(rte_handle h) {
                   h->rho, h->rho_prev, h->rho_half, h->rho_half1, h->rho0, h->y, h->btilde,
                   h->q, h->delta, h->tmp, h->tmp2, h->tmp3, h->delta_pc1, h->resp[0],
                   h->resp[1], h->resp[2], h->resp[3], h->partials, h->dotbuf, h->norms,
-                  h->cg_iters, h->rho_init, h->f_init};
+                  h->cg_iters, h->rho_init, h->f_init, h->sig_t_f, h->src_f, h->ca_f,
+                  h->cb_f, h->cw_f, h->f_f, h->pm_f, h->edge_f, h->psi_w_f, h->q_f, h->f_init_f,
+                  h->y_ir, h->rho_ref, h->cth_f, h->ctl_f};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   dsa_free(h->dsa);
@@ -275,118 +284,188 @@ void free_all(rte_handle h) {
 // ---------------------------------------------------------------------------------------
 // Sweeps
 // ---------------------------------------------------------------------------------------
-void quadrant_ghosts(const double g[4], double gx[4], double gy[4]) {
-  for (int qd = 0; qd < 4; ++qd) {
-    gx[qd] = (qd & 1) == 0 ? g[0] : g[1];
-    gy[qd] = qd < 2 ? g[2] : g[3];
-  }
+
+// Device data of the sweeps in one precision.
+template <class Real>
+struct SV {
+  const Real *sig_t, *src, *ca, *cb, *cw, *inv_d, *cth, *ctl;
+  Real *f, *pm, *edge, *psi_w, *q;
+};
+SV<double> sv64(rte_handle h) {
+  return {h->sig_t, h->src, h->ca, h->cb, h->cw, h->inv_d, nullptr, nullptr,
+          h->f, h->pm, h->edge, h->psi_w, h->q};
+}
+SV<float> sv32(rte_handle h) {
+  return {h->sig_t_f, h->src_f, h->ca_f, h->cb_f, h->cw_f, nullptr, h->cth_f, h->ctl_f,
+          h->f_f, h->pm_f, h->edge_f, h->psi_w_f, h->q_f};
 }
 
-Sweep2DArgs<double> args2d(rte_handle h) {
-  Sweep2DArgs<double> a{};
+template <class Real>
+Sweep2DArgs<Real> args2d(rte_handle h, const SV<Real>& v) {
+  Sweep2DArgs<Real> a{};
   a.nx = h->nx;
   a.ny = h->ny;
   a.nfam = h->L.nfam;
   a.nslot = h->L.nslot;
   a.nblk = h->nblk;
   a.rows_per_blk = h->rows_per_blk;
-  a.tau = h->tau;
-  a.a = h->ca;
-  a.b = h->cb;
-  a.w = h->cw;
+  a.tau = (Real)h->tau;
+  a.a = v.ca;
+  a.b = v.cb;
+  a.w = v.cw;
   a.fam_quad = h->fam_quad;
-  a.sig_t = h->sig_t;
-  a.inv_d = h->inv_d;
-  a.edge = h->edge;
+  a.sig_t = v.sig_t;
+  a.inv_d = v.inv_d;
+  a.cth = v.cth;
+  a.ctl = v.ctl;
+  a.edge = v.edge;
   a.ctrl = h->ctrl;
   return a;
 }
 
-Sweep1DArgs<double> args1d(rte_handle h) {
-  Sweep1DArgs<double> a{};
+template <class Real>
+Sweep1DArgs<Real> args1d(rte_handle h, const SV<Real>& v) {
+  Sweep1DArgs<Real> a{};
   a.nx = h->nx;
   a.nslot = h->L.nslot;
-  a.tau = h->tau;
-  a.a = h->ca;
-  a.w = h->cw;
+  a.tau = (Real)h->tau;
+  a.a = v.ca;
+  a.w = v.cw;
   a.dir_sign = h->dir_sign;
-  a.sig_t = h->sig_t;
-  a.psi_w = h->psi_w;
+  a.cth = v.cth;
+  a.ctl = v.ctl;
+  a.sig_t = v.sig_t;
+  a.psi_w = v.psi_w;
   return a;
 }
 
-// out = sum_j w_j L_j^{-1} q with isotropic source q and inflow g (nullptr: vacuum), as the
-// per-family partial moments in h->pm (2D) or the full moment in h->pm (1D, one "family").
-rte_status sweep_si_partials(rte_handle h, const double* q, const double* g) {
+template <class Real>
+void ghosts(const double g[4], Real gx[4], Real gy[4]) {
+  for (int qd = 0; qd < 4; ++qd) {
+    gx[qd] = (Real)((qd & 1) == 0 ? g[0] : g[1]);
+    gy[qd] = (Real)(qd < 2 ? g[2] : g[3]);
+  }
+}
+
+// Partial moments (pm) of sum_j w_j L_j^{-1} q for the isotropic source in v.q, inflow g
+// (nullptr: vacuum): per family in 2D, the full moment in 1D.
+template <class Real>
+rte_status k1(rte_handle h, const SV<Real>& v, const double* g) {
   const double zero[4] = {0, 0, 0, 0};
   if (!g) g = zero;
   if (h->dim == 2) {
-    Sweep2DArgs<double> a = args2d(h);
-    a.q = q;
-    a.pm = h->pm;
-    quadrant_ghosts(g, a.gx, a.gy);
-    CK(launch_sweep2d<double>(a, 0, h->R, h->st));
+    Sweep2DArgs<Real> a = args2d(h, v);
+    a.q = v.q;
+    a.pm = v.pm;
+    ghosts(g, a.gx, a.gy);
+    CK(launch_sweep2d<Real>(a, 0, h->R, h->st));
   } else {
-    Sweep1DArgs<double> a = args1d(h);
-    a.q = q;
-    a.g_lo = g[0];
-    a.g_hi = g[1];
-    CK(launch_sweep1d<double>(a, 0, h->st));
-    CK(launch_moment1d<double>(h->psi_w, h->L.nslot, (int)h->ncell, h->pm, h->st));
+    Sweep1DArgs<Real> a = args1d(h, v);
+    a.q = v.q;
+    a.g_lo = (Real)g[0];
+    a.g_hi = (Real)g[1];
+    CK(launch_sweep1d<Real>(a, 0, h->st));
+    CK(launch_moment1d<Real>(v.psi_w, h->L.nslot, (int)h->ncell, v.pm, h->st));
+  }
+  return RTE_OK;
+}
+
+// Fused end-of-step sweep with the pass-A source already in v.q (sigma_s rho + G):
+// f <- L^-1(q + tau f + g^bc) in place; pm <- partial moments of L^-1(G + tau f^n), zero inflow.
+template <class Real>
+rte_status k2(rte_handle h, const SV<Real>& v) {
+  if (h->dim == 2) {
+    Sweep2DArgs<Real> a = args2d(h, v);
+    a.q = v.q;
+    a.g2 = v.src;
+    a.f = v.f;
+    a.pm = v.pm;
+    ghosts(h->g, a.gx, a.gy);
+    CK(launch_sweep2d<Real>(a, 1, h->R, h->st));
+  } else {
+    Sweep1DArgs<Real> a = args1d(h, v);
+    a.q = v.q;
+    a.g2 = v.src;
+    a.f = v.f;
+    a.psi_w_a = nullptr;
+    a.g_lo = (Real)h->g[0];
+    a.g_hi = (Real)h->g[1];
+    CK(launch_sweep1d<Real>(a, 1, h->st));
+    CK(launch_moment1d<Real>(v.psi_w, h->L.nslot, (int)h->ncell, v.pm, h->st));
+  }
+  return RTE_OK;
+}
+
+// pm <- partial moments of L^-1(G + tau f) from the stored f, zero inflow.
+template <class Real>
+rte_status ky(rte_handle h, const SV<Real>& v) {
+  if (h->dim == 2) {
+    Sweep2DArgs<Real> a = args2d(h, v);
+    a.g2 = v.src;
+    a.f = v.f;
+    a.pm = v.pm;
+    CK(launch_sweep2d<Real>(a, 2, h->R, h->st));
+  } else {
+    Sweep1DArgs<Real> a = args1d(h, v);
+    a.g2 = v.src;
+    a.f = v.f;
+    CK(launch_sweep1d<Real>(a, 2, h->st));
+    CK(launch_moment1d<Real>(v.psi_w, h->L.nslot, (int)h->ncell, v.pm, h->st));
   }
   return RTE_OK;
 }
 
 int nparts(rte_handle h) { return h->dim == 2 ? h->L.nfam : 1; }
 
-rte_status sweep_si(rte_handle h, const double* q, const double* g, double* out) {
-  TRY(sweep_si_partials(h, q, g));
-  CK(launch_sum_partials(h->pm, nparts(h), (int)h->ncell, nullptr, out, h->st));
+// The sweep source q of the current precision: sigma_s (x - xref) (xref may be nullptr).
+rte_status set_q(rte_handle h, const double* x, const double* xref) {
+  if (h->fp32) CK(launch_scaled_diff<float>(x, xref, h->sig_s, (int)h->ncell, h->q_f, h->st));
+  else CK(launch_scaled_diff<double>(x, xref, h->sig_s, (int)h->ncell, h->q, h->st));
+  return RTE_OK;
+}
+// Pass-A source sigma_s rho + G of the fused sweep.
+rte_status set_qa(rte_handle h, const double* rho) {
+  if (h->fp32) CK(launch_scaled_plus<float>(rho, h->sig_s, h->src, (int)h->ncell, h->q_f, h->st));
+  else CK(launch_scaled_plus<double>(rho, h->sig_s, h->src, (int)h->ncell, h->q, h->st));
+  return RTE_OK;
+}
+// out (+)= sum of the partial moments, in FP64.
+rte_status sum_pm(rte_handle h, double* out, int accumulate) {
+  if (h->fp32) CK(launch_sum_pm<float>(h->pm_f, nparts(h), (int)h->ncell, out, accumulate, h->st));
+  else CK(launch_sum_pm<double>(h->pm, nparts(h), (int)h->ncell, out, accumulate, h->st));
+  return RTE_OK;
+}
+rte_status sweep_q(rte_handle h, const double* g) {
+  return h->fp32 ? k1<float>(h, sv32(h), g) : k1<double>(h, sv64(h), g);
+}
+
+// out = sum_j w_j L_j^{-1} (sigma_s rho) with inflow g, FP64 out, in the handle's precision.
+rte_status sweep_si(rte_handle h, const double* rho_or_null, const double* g, double* out) {
+  if (rho_or_null) TRY(set_q(h, rho_or_null, nullptr));
+  else {
+    if (h->fp32) CK(cudaMemsetAsync(h->q_f, 0, sizeof(float) * h->ncell, h->st));
+    else CK(cudaMemsetAsync(h->q, 0, sizeof(double) * h->ncell, h->st));
+  }
+  TRY(sweep_q(h, g));
+  TRY(sum_pm(h, out, 0));
   return RTE_OK;
 }
 
-// Fused end-of-step sweep: f <- L^-1(qa + tau f + g^bc) in place and
+// Fused end-of-step sweep: f <- L^-1(sigma_s rho + tau f + G + g^bc) in place and
 // y = sum_j w_j L_j^-1(G + tau f^n) with zero inflow.
-rte_status sweep_f(rte_handle h, const double* qa, double* y_out) {
-  if (h->dim == 2) {
-    Sweep2DArgs<double> a = args2d(h);
-    a.q = qa;
-    a.g2 = h->src;
-    a.f = h->f;
-    a.pm = h->pm;
-    quadrant_ghosts(h->g, a.gx, a.gy);
-    CK(launch_sweep2d<double>(a, 1, h->R, h->st));
-    CK(launch_sum_partials(h->pm, h->L.nfam, (int)h->ncell, nullptr, y_out, h->st));
-  } else {
-    Sweep1DArgs<double> a = args1d(h);
-    a.q = qa;
-    a.g2 = h->src;
-    a.f = h->f;
-    a.psi_w_a = nullptr;
-    a.g_lo = h->g[0];
-    a.g_hi = h->g[1];
-    CK(launch_sweep1d<double>(a, 1, h->st));
-    CK(launch_moment1d<double>(h->psi_w, h->L.nslot, (int)h->ncell, y_out, h->st));
-  }
+rte_status sweep_f(rte_handle h, const double* rho, double* y_out) {
+  TRY(set_qa(h, rho));
+  if (h->fp32) TRY(k2<float>(h, sv32(h)));
+  else TRY(k2<double>(h, sv64(h)));
+  TRY(sum_pm(h, y_out, 0));
   return RTE_OK;
 }
 
 // y = sum_j w_j L_j^-1(G + tau f) from the stored f, zero inflow.
 rte_status sweep_y(rte_handle h, double* y_out) {
-  if (h->dim == 2) {
-    Sweep2DArgs<double> a = args2d(h);
-    a.g2 = h->src;
-    a.f = h->f;
-    a.pm = h->pm;
-    CK(launch_sweep2d<double>(a, 2, h->R, h->st));
-    CK(launch_sum_partials(h->pm, h->L.nfam, (int)h->ncell, nullptr, y_out, h->st));
-  } else {
-    Sweep1DArgs<double> a = args1d(h);
-    a.g2 = h->src;
-    a.f = h->f;
-    CK(launch_sweep1d<double>(a, 2, h->st));
-    CK(launch_moment1d<double>(h->psi_w, h->L.nslot, (int)h->ncell, y_out, h->st));
-  }
+  if (h->fp32) TRY(ky<float>(h, sv32(h)));
+  else TRY(ky<double>(h, sv64(h)));
+  TRY(sum_pm(h, y_out, 0));
   return RTE_OK;
 }
 
@@ -414,8 +493,7 @@ rte_status ensure_responses(rte_handle h) {
     if (!h->resp[s]) CK(dalloc(&h->resp[s], h->ncell));
     double g[4] = {0, 0, 0, 0};
     g[s] = 1.0;
-    CK(cudaMemsetAsync(h->tmp, 0, sizeof(double) * h->ncell, h->st));
-    TRY(sweep_si(h, h->tmp, g, h->resp[s]));
+    TRY(sweep_si(h, nullptr, g, h->resp[s]));
   }
   h->resp_ready = true;
   return RTE_OK;
@@ -463,18 +541,37 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
   const int n = (int)h->ncell;
   const int nb = vec_blocks(n);
   CK(cudaMemcpyAsync(h->rho_prev, h->rho0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  CK(launch_scale_copy(h->rho_prev, h->sig_s, n, h->q, h->st));
+  // FP64: each iteration sweeps sigma_s rho^{l-1}.  FP32 (iterative refinement): the sweeps
+  // act on the increments rho^{l-1} - rho_ref in FP32 and their results accumulate into the
+  // FP64 y_ir = T Sigma_s rho_ref, so rho^{l-1/2} = y_ir + b~ carries FP64 accuracy in the
+  // residual; the first increment is measured from the last swept iterate of the previous step.
+  auto sweep_increment = [&]() -> rte_status {
+    cudaEventRecord(h->kev0, h->st);
+    if (h->fp32) {
+      CK(launch_scaled_diff_update<float>(h->rho_prev, h->rho_ref, h->sig_s, n, h->q_f, h->st));
+      TRY(sweep_q(h, nullptr));
+      cudaEventRecord(h->kev1, h->st);
+      TRY(sum_pm(h, h->y_ir, 1));
+    } else {
+      TRY(set_q(h, h->rho_prev, nullptr));
+      TRY(sweep_q(h, nullptr));
+      cudaEventRecord(h->kev1, h->st);
+    }
+    return RTE_OK;
+  };
   int cg_total = 0;
   bool conv = false;
   int l = 0;
   h->pc_applied = false;
+  cudaEventRecord(h->ev0, h->st);
+  TRY(sweep_increment());
   for (l = 1; l <= h->opt.max_iter; ++l) {
-    cudaEventRecord(h->ev0, h->st);
-    cudaEventRecord(h->kev0, h->st);
-    TRY(sweep_si_partials(h, h->q, nullptr));
-    cudaEventRecord(h->kev1, h->st);
-    CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
-                               h->partials, nb, h->norms, h->st));
+    if (h->fp32)
+      CK(launch_combine_residual(h->y_ir, 1, h->btilde, h->rho_prev, n, h->rho_half, h->partials,
+                                 nb, h->norms, h->st));
+    else
+      CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
+                                 h->partials, nb, h->norms, h->st));
     Norms nm;
     CK(cudaMemcpyAsync(&nm, h->norms, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
     h->stats.time_sweep_ms += elapsed(h);
@@ -494,6 +591,7 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
                                                : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
     h->stats.last_residual = res;
     if (conv) break;
+    if (l == h->opt.max_iter) break;
     if (l == 1 && use_pc) {
       // ROM preconditioner, Eq. (dmd-sa): delta = dU C_r^{-1} dU^T (rho^{1/2} - rho^{(0)})
       CK(launch_axpby(1.0, h->rho_half, -1.0, h->rho0, n, h->tmp, h->st));
@@ -510,6 +608,7 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
       h->stats.time_dsa_ms += elapsed(h);
       cg_total += its;
     }
+    TRY(sweep_increment());
   }
   if (l > h->opt.max_iter) l = h->opt.max_iter;
   CK(cudaMemcpyAsync(h->rho, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
@@ -600,10 +699,8 @@ rte_status one_step(rte_handle h) {
   h->last_iters = iters;
   // f^n and the next step's b~ (without inflow): Eq. (sweep_to_obtain_f), Eq. (implicit_linear_system_rho)
   cudaEventRecord(h->ev0, h->st);
-  CK(launch_scale_copy(h->rho, h->sig_s, n, h->q, h->st));
-  CK(launch_axpby(1.0, h->q, 1.0, h->src, n, h->q, h->st));
   cudaEventRecord(h->kev0, h->st);
-  TRY(sweep_f(h, h->q, h->y));
+  TRY(sweep_f(h, h->rho, h->y));
   cudaEventRecord(h->kev1, h->st);
   h->y_valid = true;
   h->stats.time_sweep_ms += elapsed(h);
@@ -647,6 +744,12 @@ rte_status upload(rte_handle h, double* dst, const double* src, long n) {
 }
 
 rte_status reset_state(rte_handle h) {
+  if (h->fp32) {
+    // refinement state: y_ir = T Sigma_s rho_ref with rho_ref = 0
+    CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ncell, h->st));
+    CK(cudaMemsetAsync(h->rho_ref, 0, sizeof(double) * h->ncell, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   h->stats = rte_stats{};
   h->flag_ig = h->flag_pc = false;
   h->y_valid = false;
@@ -654,6 +757,25 @@ rte_status reset_state(rte_handle h) {
   rom_reset(h->ig);
   rom_reset(h->pc);
   return RTE_OK;
+}
+
+// Nudge FP32 weights by whole units in the last place, largest first, until their exact
+// (FP64) sum is as close to 1 as the grid of the smallest weight allows.
+void balance_weights(std::vector<float>& w) {
+  std::vector<int> order(w.size());
+  for (size_t i = 0; i < w.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+  auto deficit = [&]() {
+    double s = 0.0;
+    for (float v : w) s += (double)v;
+    return 1.0 - s;
+  };
+  for (int k : order) {
+    if (w[k] <= 0.0f) continue;
+    const double ulp = (double)std::nextafter(w[k], 2.0f * w[k] + 1.0f) - (double)w[k];
+    const double steps = std::nearbyint(deficit() / ulp);
+    if (steps != 0.0) w[k] = (float)((double)w[k] + steps * ulp);
+  }
 }
 
 rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature* quad,
@@ -669,8 +791,9 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0)))
     return fail(h, RTE_EINVAL, "empty domain");
   if (!(c_dt > 0.0) || !std::isfinite(c_dt)) return fail(h, RTE_EINVAL, "c_dt must be > 0");
-  if (h->opt.precision != RTE_FP64)
-    return fail(h, RTE_EINVAL, "this build supports precision = RTE_FP64");
+  if (h->opt.precision != RTE_FP64 && h->opt.precision != RTE_FP32)
+    return fail(h, RTE_EINVAL, "precision must be RTE_FP64 or RTE_FP32");
+  h->fp32 = h->opt.precision == RTE_FP32;
   if (h->opt.r_max < 1 || h->opt.r_max > 64) return fail(h, RTE_EINVAL, "r_max must be in [1, 64]");
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
@@ -712,7 +835,8 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
     h->R = std::min(h->opt.sweep_rows ? h->opt.sweep_rows : 2, L.dl);
     h->W = h->opt.sweep_warps ? h->opt.sweep_warps : 4;
     // fewer warps per CTA when the fused sweep's staging would not fit in shared memory
-    while (h->W > 1 && sweep2d_smem_bytes(sizeof(double), L.dl, h->R, h->W, 1, true) > 200 * 1024)
+    const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
+    while (h->W > 1 && sweep2d_smem_bytes(real, L.dl, h->R, h->W, 1, !h->fp32) > 200 * 1024)
       --h->W;
     h->rows_per_blk = h->W * (32 / L.dl) * h->R;
     h->nblk = (h->ny + h->rows_per_blk - 1) / h->rows_per_blk;
@@ -740,19 +864,66 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   TRY(upload(h, h->cw, L.w.data(), L.nslot));
   CK(cudaMemcpy(h->fam_quad, L.fam_quadrant.data(), sizeof(int) * L.nfam, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->dir_sign, sign.data(), sizeof(int) * L.nslot, cudaMemcpyHostToDevice));
-  CK(dalloc(&h->f, (size_t)n * L.nslot));
-  CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
+  if (!h->fp32) {
+    CK(dalloc(&h->f, (size_t)n * L.nslot));
+    CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
+  } else {
+    CK(dalloc(&h->f_f, (size_t)n * L.nslot));
+    CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * n * L.nslot, h->st));
+    CK(dalloc(&h->sig_t_f, n));
+    CK(dalloc(&h->src_f, n));
+    CK(launch_to_float(h->sig_t, n, h->sig_t_f, h->st));
+    CK(launch_to_float(h->src, n, h->src_f, h->st));
+    // FP32 coefficients: a, b, tau and sigma_t rounded once; tau + a + b of each slot kept
+    // exactly as a hi / lo pair, and the weights nudged by whole ulps so that their exact
+    // sum is 1 again.  The FP32 sweeps then apply the exact Q0 operator of these rounded
+    // coefficients, which conserves particles like the FP64 one.
+    std::vector<float> a32(L.nslot), b32(L.nslot), cth(L.nslot), ctl(L.nslot), w32(L.nslot);
+    const double tau32 = (double)(float)h->tau;
+    for (int s = 0; s < L.nslot; ++s) {
+      a32[s] = (float)a[s];
+      b32[s] = (float)b[s];
+      const double ct = tau32 + (double)a32[s] + (double)b32[s];
+      cth[s] = (float)ct;
+      ctl[s] = (float)(ct - (double)cth[s]);
+      w32[s] = (float)L.w[s];
+    }
+    balance_weights(w32);
+    CK(dalloc(&h->ca_f, L.nslot));
+    CK(dalloc(&h->cb_f, L.nslot));
+    CK(dalloc(&h->cw_f, L.nslot));
+    CK(dalloc(&h->cth_f, L.nslot));
+    CK(dalloc(&h->ctl_f, L.nslot));
+    float* hv[] = {a32.data(), b32.data(), w32.data(), cth.data(), ctl.data()};
+    float* dv[] = {h->ca_f, h->cb_f, h->cw_f, h->cth_f, h->ctl_f};
+    for (int i = 0; i < 5; ++i)
+      CK(cudaMemcpy(dv[i], hv[i], sizeof(float) * L.nslot, cudaMemcpyHostToDevice));
+    CK(dalloc(&h->q_f, n));
+    CK(dalloc(&h->y_ir, n));
+    CK(dalloc(&h->rho_ref, n));
+  }
   if (h->dim == 2) {
-    CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
-    CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, L.dl, h->inv_d, h->st));
-    CK(dalloc(&h->pm, (size_t)L.nfam * n));
-    CK(dalloc(&h->edge, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
+    if (!h->fp32) {
+      CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
+      CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, L.dl, h->inv_d,
+                              h->st));
+      CK(dalloc(&h->pm, (size_t)L.nfam * n));
+      CK(dalloc(&h->edge, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
+    } else {
+      CK(dalloc(&h->pm_f, (size_t)L.nfam * n));
+      CK(dalloc(&h->edge_f, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
+    }
     const size_t cb_bytes = sizeof(SweepCtrl) + sizeof(unsigned) * L.nfam * h->nblk;
     CK(cudaMalloc((void**)&h->ctrl, cb_bytes));
     CK(cudaMemsetAsync(h->ctrl, 0, cb_bytes, h->st));
   } else {
-    CK(dalloc(&h->pm, n));
-    CK(dalloc(&h->psi_w, (size_t)n * L.nslot));
+    if (!h->fp32) {
+      CK(dalloc(&h->pm, n));
+      CK(dalloc(&h->psi_w, (size_t)n * L.nslot));
+    } else {
+      CK(dalloc(&h->pm_f, n));
+      CK(dalloc(&h->psi_w_f, (size_t)n * L.nslot));
+    }
   }
   double** vecs[] = {&h->rho, &h->rho_prev, &h->rho_half, &h->rho_half1, &h->rho0, &h->y,
                      &h->btilde, &h->q, &h->delta, &h->tmp, &h->tmp2, &h->tmp3, &h->delta_pc1};
@@ -827,17 +998,27 @@ rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
     }
     for (int d = 0; d < L.nv; ++d)
       for (long c = 0; c < n; ++c) rho[c] += h->w_user[d] * f0[(size_t)d * n + c];
-    TRY(upload(h, h->f, fl.data(), (long)fl.size()));
     TRY(upload(h, h->rho, rho.data(), n));
-    if (!h->f_init) CK(dalloc(&h->f_init, (size_t)n * L.nslot));
-    CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * n * L.nslot, cudaMemcpyDeviceToDevice,
-                       h->st));
+    if (!h->fp32) {
+      TRY(upload(h, h->f, fl.data(), (long)fl.size()));
+      if (!h->f_init) CK(dalloc(&h->f_init, (size_t)n * L.nslot));
+      CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * n * L.nslot, cudaMemcpyDeviceToDevice,
+                         h->st));
+    } else {
+      std::vector<float> ff(fl.begin(), fl.end());
+      CK(cudaMemcpyAsync(h->f_f, ff.data(), sizeof(float) * ff.size(), cudaMemcpyHostToDevice, h->st));
+      if (!h->f_init_f) CK(dalloc(&h->f_init_f, (size_t)n * L.nslot));
+      CK(cudaMemcpyAsync(h->f_init_f, h->f_f, sizeof(float) * n * L.nslot, cudaMemcpyDeviceToDevice,
+                         h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
     h->init_kind = 2;
   } else {
     if (!rho0) return fail(h, RTE_EINVAL, "rho0 or f0 is required");
     if (!finite_all(rho0, n)) return fail(h, RTE_EINVAL, "non-finite rho0");
     TRY(upload(h, h->rho, rho0, n));
-    CK(launch_isotropic_f(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
+    if (!h->fp32) CK(launch_isotropic_f(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
+    else CK(launch_isotropic_f32(h->rho, (int)n, L.nslot, L.dl, h->f_f, h->st));
     h->init_kind = 1;
   }
   if (!h->rho_init) CK(dalloc(&h->rho_init, n));
@@ -858,11 +1039,16 @@ rte_status rte_restart(rte_handle h) {
   if (h->init_kind == 0) return fail(h, RTE_ESTATE, "rte_set_initial has not been called");
   const long n = h->ncell;
   CK(cudaMemcpyAsync(h->rho, h->rho_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  if (h->init_kind == 2)
+  if (h->init_kind == 2 && !h->fp32)
     CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * n * h->L.nslot, cudaMemcpyDeviceToDevice,
                        h->st));
-  else
+  else if (h->init_kind == 2)
+    CK(cudaMemcpyAsync(h->f_f, h->f_init_f, sizeof(float) * n * h->L.nslot,
+                       cudaMemcpyDeviceToDevice, h->st));
+  else if (!h->fp32)
     CK(launch_isotropic_f(h->rho, (int)n, h->L.nslot, h->L.dl, h->f, h->st));
+  else
+    CK(launch_isotropic_f32(h->rho, (int)n, h->L.nslot, h->L.dl, h->f_f, h->st));
   CK(cudaStreamSynchronize(h->st));
   return reset_state(h);
 }
@@ -911,8 +1097,15 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
   const Layout& L = h->L;
   const long n = h->ncell;
   std::vector<double> fl((size_t)n * L.nslot);
-  CK(cudaMemcpyAsync(fl.data(), h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  if (!h->fp32) {
+    CK(cudaMemcpyAsync(fl.data(), h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  } else {
+    std::vector<float> ff(fl.size());
+    CK(cudaMemcpyAsync(ff.data(), h->f_f, sizeof(float) * ff.size(), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (size_t i = 0; i < ff.size(); ++i) fl[i] = ff[i];
+  }
   for (int d = 0; d < L.nv; ++d) {
     const int s = L.slot_of_dir[d];
     for (long c = 0; c < n; ++c) f[(size_t)d * n + c] = fl[f_index(L, n, c, s)];
@@ -953,11 +1146,11 @@ rte_status rte_op_sweep(rte_handle h, const double* rho, double* out) {
   if (!h || !rho || !out) return RTE_EINVAL;
   const int n = (int)h->ncell;
   TRY(upload(h, h->tmp, rho, n));
-  CK(launch_scale_copy(h->tmp, h->sig_s, n, h->q, h->st));
+  TRY(set_q(h, h->tmp, nullptr));
   cudaEventRecord(h->kev0, h->st);
-  TRY(sweep_si_partials(h, h->q, nullptr));
+  TRY(sweep_q(h, nullptr));
   cudaEventRecord(h->kev1, h->st);
-  CK(launch_sum_partials(h->pm, nparts(h), n, nullptr, h->tmp2, h->st));
+  TRY(sum_pm(h, h->tmp2, 0));
   TRY(check_sweep_error(h));
   {
     float kms = 0.f;
@@ -974,9 +1167,7 @@ rte_status rte_op_fsweep(rte_handle h, const double* rho, double* btilde) {
   if (!h || !rho) return RTE_EINVAL;
   const int n = (int)h->ncell;
   TRY(upload(h, h->tmp, rho, n));
-  CK(launch_scale_copy(h->tmp, h->sig_s, n, h->q, h->st));
-  CK(launch_axpby(1.0, h->q, 1.0, h->src, n, h->q, h->st));
-  TRY(sweep_f(h, h->q, h->y));
+  TRY(sweep_f(h, h->tmp, h->y));
   h->y_valid = true;
   TRY(check_sweep_error(h));
   if (btilde) {

@@ -51,6 +51,8 @@ struct Sweep2DArgs {
   const int* fam_quad;  // [nfam]
   const Real* sig_t;    // [ncell]
   const Real* inv_d;    // [nfam][ncell][dl] 1/(tau+sigma_t+a+b) or nullptr (computed)
+  const Real* cth;      // [nslot] tau + a + b, high part, or nullptr (formed from tau, a, b)
+  const Real* ctl;      // [nslot] its low part (FP32: the exact sum is cth + ctl)
   // K1: isotropic source q = Sigma_s rho; K2 pass A: q = Sigma_s rho + G.
   const Real* q;        // [ncell]
   const Real* g2;       // K2 pass B isotropic source G [ncell]
@@ -69,6 +71,8 @@ struct Sweep1DArgs {
   const Real* a;
   const Real* w;
   const int* dir_sign;  // [nslot] +1 / -1
+  const Real* cth;      // [nslot] tau + a split as hi / lo (FP32), or nullptr
+  const Real* ctl;
   const Real* sig_t;
   const Real* q;        // [ncell]
   const Real* g2;       // K2 pass B source
@@ -112,6 +116,22 @@ cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, int dl, 
 cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
                        double* out, cudaStream_t s);
 int vec_blocks(int n);
+// Sources of the sweeps in their precision (FP32 mode: float).
+template <class Real>
+cudaError_t launch_scaled_diff(const double* x, const double* xref, const double* sig_s, int n,
+                               Real* out, cudaStream_t s);        // Real(sigma_s (x - xref))
+template <class Real>
+cudaError_t launch_scaled_diff_update(const double* x, double* xref, const double* sig_s, int n,
+                                      Real* out, cudaStream_t s); // same, then xref <- x
+template <class Real>
+cudaError_t launch_scaled_plus(const double* rho, const double* sig_s, const double* src, int n,
+                               Real* out, cudaStream_t s);        // Real(sigma_s rho + G)
+template <class Real>
+cudaError_t launch_sum_pm(const Real* pm, int nfam, int n, double* out, int accumulate,
+                          cudaStream_t s);                        // out (+)= sum_f pm (FP64)
+cudaError_t launch_isotropic_f32(const double* rho, int n, int nslot, int dl, float* f,
+                                 cudaStream_t s);
+cudaError_t launch_to_float(const double* x, long n, float* y, cudaStream_t s);
 
 // DSA (cg.cu): 5-point (1D: 3-point) diffusion operator with Marshak vacuum faces.
 struct DsaOp {

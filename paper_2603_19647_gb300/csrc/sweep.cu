@@ -46,6 +46,31 @@ __device__ __forceinline__ float recip(float x) {
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// 1 / (ch + cl + s) as an unevaluated pair h + l, to about 2^-46 relative, in FP32.
+// ch + cl is tau + a + b of the direction (exact, split on the host) and s is sigma_t of the
+// cell: the sum is formed exactly (Knuth's TwoSum, then a renormalisation), the reciprocal by
+// one Newton correction whose residual 1 - d_h g_h is exact under FMA.  With it the FP32
+// sweeps are the exact Q0 operator of the FP32-rounded coefficients (conservative, no
+// per-step bias), not an operator whose division is off by an ulp.
+struct Rcp2 {
+  float h, l;
+};
+__device__ __forceinline__ Rcp2 rcp_pair(float ch, float cl, float s) {
+  const float sum = ch + s;
+  const float bb = sum - ch;
+  float e = (ch - (sum - bb)) + (s - bb);
+  e += cl;
+  const float dh = sum + e;
+  const float dl = e - (dh - sum);
+  const float gh = recip(dh);
+  float r = fmaf(-dh, gh, 1.0f);
+  r = fmaf(-dl, gh, r);
+  return {gh, r * gh};
+}
+// t * (h + l): the low part only in FP32 (l = 0 in FP64).
+__device__ __forceinline__ float scale2(float t, float h, float l) { return fmaf(t, h, t * l); }
+__device__ __forceinline__ double scale2(double t, double h, double) { return t * h; }
+
 template <class Real>
 __device__ __forceinline__ Real ldcg(const Real* p) {
   return __ldcg(p);
@@ -166,7 +191,9 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   const long ncell = (long)nx * ny;
   const int slot = fam * DL + dl;
   const Real ca = A.a[slot], cb = A.b[slot], cw = A.w[slot];
-  const Real ct = A.tau + ca + cb;
+  // tau + a + b of this direction: hi / lo pair in FP32 (exact), one value in FP64
+  const Real ct = A.cth ? A.cth[slot] : A.tau + ca + cb;
+  const Real ctl = A.ctl ? A.ctl[slot] : Real(0);
   const int wrow0 = blk * A.rows_per_blk + warp * RW;   // first sweep-order row of this warp
   const int row0 = wrow0 + gi * R;                       // lane group's row m = 0
   const Real gx = A.gx[quad];
@@ -312,26 +339,33 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
           const int rr = gi * R + m;
           const int o = (buf * RW + rr) * K + k;
           const int od = o * DL + dl;
-          Real dinv;
-          if constexpr (TABLE) dinv = tab_s[od];
-          else dinv = recip(ct + st_s[o]);
+          Real dinv, dinvl = Real(0);
+          if constexpr (TABLE) {
+            dinv = tab_s[od];
+          } else if constexpr (sizeof(Real) == 4) {
+            const Rcp2 rp = rcp_pair(ct, ctl, st_s[o]);
+            dinv = rp.h;
+            dinvl = rp.l;
+          } else {
+            dinv = recip(ct + st_s[o]);
+          }
           const Real uA = (m == 0) ? upA : psA[m > 0 ? m - 1 : 0];
           if constexpr (MODE == 0) {
-            const Real v = (qa_s[o] + ca * psA[m] + cb * uA) * dinv;
+            const Real v = scale2(qa_s[o] + ca * psA[m] + cb * uA, dinv, dinvl);
             psA[m] = v;
             mb[k * R + m] = v;
           } else if constexpr (MODE == 2) {
-            const Real v = (g2_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA) * dinv;
+            const Real v = scale2(g2_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA, dinv, dinvl);
             psA[m] = v;
             mb[k * R + m] = v;
           } else {
-            const Real va = (qa_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA) * dinv;
+            const Real va = scale2(qa_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA, dinv, dinvl);
             psA[m] = va;
             const int px = xpos ? x : nx - 1 - x;
             const int py = ypos ? jj : ny - 1 - jj;
             f_fam[((long)py * nx + px) * DL + dl] = va;
             const Real uB = (m == 0) ? upB : psB[m > 0 ? m - 1 : 0];
-            const Real vb = (g2_s[o] + A.tau * va + ca * psB[m] + cb * uB) * dinv;
+            const Real vb = scale2(g2_s[o] + A.tau * va + ca * psB[m] + cb * uB, dinv, dinvl);
             psB[m] = vb;
             mb[k * R + m] = vb;
           }
@@ -533,9 +567,30 @@ __device__ Real block_scan_entry(Aff<Real> mine, Real g, Aff<Real>* sh) {
   return ex.a * g + ex.b;
 }
 
+// Per-cell coefficient of the 1D recurrence psi_c = (s_c + a psi_{c-1}) / d_c: the reciprocal
+// of d_c as a pair (FP32) or a value (FP64), and d_c itself in FP64 for the scan.
+template <class Real>
+struct Cell1D {
+  Real h, l;
+  double d;
+};
+template <class Real>
+__device__ __forceinline__ Cell1D<Real> cell1d(Real ct, Real ctl, Real sig) {
+  if constexpr (sizeof(Real) == 4) {
+    const Rcp2 rp = rcp_pair(ct, ctl, sig);
+    return {rp.h, rp.l, (double)ct + (double)ctl + (double)sig};
+  } else {
+    const double d = ct + sig;
+    return {Real(1) / d, Real(0), d};
+  }
+}
+
+// The block scan composes the cells' affine maps in FP64 in both precisions (its products
+// of a / d_c are per-direction coefficients, where an FP32 rounding would bias the
+// operator); each thread then runs its cells' recurrence in the run precision.
 template <class Real, int MODE>
 __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs<Real> A) {
-  __shared__ Aff<Real> sh[64];
+  __shared__ Aff<double> sh[64];
   const int slot = blockIdx.x;
   const int nx = A.nx;
   const int dlh = A.nslot / 2;   // f layout [half-range][cell][direction in half-range]
@@ -545,52 +600,53 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
   const int k1 = min(nx, k0 + chunk);
   const bool pos = A.dir_sign[slot] > 0;
   const Real ca = A.a[slot], cw = A.w[slot];
-  const Real ct = A.tau + ca;
+  const Real ct = A.cth ? A.cth[slot] : A.tau + ca;
+  const Real ctl = A.ctl ? A.ctl[slot] : Real(0);
   // pass A (MODE 1) or the only pass (MODE 0)
-  Aff<Real> mine{Real(1), Real(0)};
+  Aff<double> mine{1.0, 0.0};
   for (int k = k0; k < k1; ++k) {
     const int c = pos ? k : nx - 1 - k;
-    const Real dinv = Real(1) / (ct + A.sig_t[c]);
+    const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
     Real s = (MODE == 2) ? A.g2[c] : A.q[c];
     if (MODE != 0) s += A.tau * A.f[fbase + (long)c * dlh];
-    mine = compose(mine, Aff<Real>{ca * dinv, s * dinv});
+    mine = compose(mine, Aff<double>{(double)ca / cc.d, (double)s / cc.d});
   }
   const Real gA = (MODE == 2) ? Real(0) : (pos ? A.g_lo : A.g_hi);
-  Real psi = block_scan_entry(mine, gA, sh);
+  Real psi = (Real)block_scan_entry(mine, (double)gA, sh);
   for (int k = k0; k < k1; ++k) {
     const int c = pos ? k : nx - 1 - k;
-    const Real dinv = Real(1) / (ct + A.sig_t[c]);
+    const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
     Real s = (MODE == 2) ? A.g2[c] : A.q[c];
     if (MODE == 2) {
       s += A.tau * A.f[fbase + (long)c * dlh];
-      psi = (s + ca * psi) * dinv;
+      psi = scale2(s + ca * psi, cc.h, cc.l);
       A.psi_w[(long)slot * nx + c] = cw * psi;
     } else if (MODE == 1) {
       Real* fp = A.f + fbase + (long)c * dlh;
       s += A.tau * (*fp);
-      psi = (s + ca * psi) * dinv;
+      psi = scale2(s + ca * psi, cc.h, cc.l);
       *fp = psi;
       if (A.psi_w_a) A.psi_w_a[(long)slot * nx + c] = cw * psi;
     } else {
-      psi = (s + ca * psi) * dinv;
+      psi = scale2(s + ca * psi, cc.h, cc.l);
       A.psi_w[(long)slot * nx + c] = cw * psi;
     }
   }
   if (MODE == 1) {
     // pass B: y = L^-1 (g2 + tau f^n), zero inflow; this thread reads back its own writes.
-    Aff<Real> mb{Real(1), Real(0)};
+    Aff<double> mb{1.0, 0.0};
     for (int k = k0; k < k1; ++k) {
       const int c = pos ? k : nx - 1 - k;
-      const Real dinv = Real(1) / (ct + A.sig_t[c]);
+      const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
       const Real s = A.g2[c] + A.tau * A.f[fbase + (long)c * dlh];
-      mb = compose(mb, Aff<Real>{ca * dinv, s * dinv});
+      mb = compose(mb, Aff<double>{(double)ca / cc.d, (double)s / cc.d});
     }
-    Real y = block_scan_entry(mb, Real(0), sh);
+    Real y = (Real)block_scan_entry(mb, 0.0, sh);
     for (int k = k0; k < k1; ++k) {
       const int c = pos ? k : nx - 1 - k;
-      const Real dinv = Real(1) / (ct + A.sig_t[c]);
+      const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
       const Real s = A.g2[c] + A.tau * A.f[fbase + (long)c * dlh];
-      y = (s + ca * y) * dinv;
+      y = scale2(s + ca * y, cc.h, cc.l);
       A.psi_w[(long)slot * nx + c] = cw * y;
     }
   }

@@ -144,7 +144,105 @@ __global__ void dot_finish_kernel(const double* partials, int nblocks, double* o
   if (threadIdx.x == 0) *out = s;
 }
 
+// out = Real(sigma_s (x - xref)) (xref may be nullptr); with `update`, xref <- x afterwards.
+template <class Real>
+__global__ void scaled_diff_kernel(const double* x, double* xref, const double* sig_s, int n,
+                                   Real* out, int update) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  const double xv = x[c];
+  const double d = xref ? xv - xref[c] : xv;
+  out[c] = (Real)(sig_s[c] * d);
+  if (update) xref[c] = xv;
+}
+
+// out = Real(sigma_s rho + G)
+template <class Real>
+__global__ void scaled_plus_kernel(const double* rho, const double* sig_s, const double* src,
+                                   int n, Real* out) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  out[c] = (Real)(sig_s[c] * rho[c] + src[c]);
+}
+
+// out (+)= sum over families of pm, accumulated in FP64 in family order
+template <class Real>
+__global__ void sum_pm_kernel(const Real* pm, int nfam, int n, double* out, int accumulate) {
+  const int c = blockIdx.x * VT + threadIdx.x;
+  if (c >= n) return;
+  double s = 0.0;
+  for (int f = 0; f < nfam; ++f) s += (double)pm[(long)f * n + c];
+  out[c] = accumulate ? out[c] + s : s;
+}
+
+__global__ void isotropic_f32_kernel(const double* rho, int n, int nslot, int dl, float* f) {
+  const long i = (long)blockIdx.x * VT + threadIdx.x;
+  if (i >= (long)n * nslot) return;
+  f[i] = (float)rho[(i / dl) % n];
+}
+
+__global__ void to_float_kernel(const double* x, long n, float* y) {
+  const long i = (long)blockIdx.x * VT + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
 }  // namespace
+
+template <class Real>
+cudaError_t launch_scaled_diff(const double* x, const double* xref, const double* sig_s, int n,
+                               Real* out, cudaStream_t s) {
+  ++g_launches;
+  scaled_diff_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(x, const_cast<double*>(xref), sig_s, n,
+                                                            out, 0);
+  return cudaGetLastError();
+}
+template <class Real>
+cudaError_t launch_scaled_diff_update(const double* x, double* xref, const double* sig_s, int n,
+                                      Real* out, cudaStream_t s) {
+  ++g_launches;
+  scaled_diff_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(x, xref, sig_s, n, out, 1);
+  return cudaGetLastError();
+}
+template <class Real>
+cudaError_t launch_scaled_plus(const double* rho, const double* sig_s, const double* src, int n,
+                               Real* out, cudaStream_t s) {
+  ++g_launches;
+  scaled_plus_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(rho, sig_s, src, n, out);
+  return cudaGetLastError();
+}
+template <class Real>
+cudaError_t launch_sum_pm(const Real* pm, int nfam, int n, double* out, int accumulate,
+                          cudaStream_t s) {
+  ++g_launches;
+  sum_pm_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(pm, nfam, n, out, accumulate);
+  return cudaGetLastError();
+}
+cudaError_t launch_isotropic_f32(const double* rho, int n, int nslot, int dl, float* f,
+                                 cudaStream_t s) {
+  const long tot = (long)n * nslot;
+  ++g_launches;
+  isotropic_f32_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, dl, f);
+  return cudaGetLastError();
+}
+cudaError_t launch_to_float(const double* x, long n, float* y, cudaStream_t s) {
+  ++g_launches;
+  to_float_kernel<<<(unsigned)((n + VT - 1) / VT), VT, 0, s>>>(x, n, y);
+  return cudaGetLastError();
+}
+template cudaError_t launch_scaled_diff<double>(const double*, const double*, const double*, int,
+                                                double*, cudaStream_t);
+template cudaError_t launch_scaled_diff<float>(const double*, const double*, const double*, int,
+                                               float*, cudaStream_t);
+template cudaError_t launch_scaled_diff_update<float>(const double*, double*, const double*, int,
+                                                      float*, cudaStream_t);
+template cudaError_t launch_scaled_diff_update<double>(const double*, double*, const double*, int,
+                                                       double*, cudaStream_t);
+template cudaError_t launch_scaled_plus<double>(const double*, const double*, const double*, int,
+                                                double*, cudaStream_t);
+template cudaError_t launch_scaled_plus<float>(const double*, const double*, const double*, int,
+                                               float*, cudaStream_t);
+template cudaError_t launch_sum_pm<double>(const double*, int, int, double*, int, cudaStream_t);
+template cudaError_t launch_sum_pm<float>(const float*, int, int, double*, int, cudaStream_t);
 
 int vec_blocks(int n) {
   int b = (n + VT - 1) / VT;
