@@ -117,6 +117,9 @@ typedef struct {
   long long f_sweep_launches;   /* fused end-of-step sweeps (two cell solves per cell-direction) */
   double f_sweep_kernel_ms;
   long long kernel_launches;    /* CUDA kernels this library launched inside rte_step / rte_rom_update */
+  /* 2D sweep tiling in use: directions per lane group, then rows per lane group and warps
+   * per CTA of the SI sweep and of the fused f sweep; sweep_tuned = 1 when measured */
+  int sweep_lanes, sweep_si_rows, sweep_si_warps, sweep_f_rows, sweep_f_warps, sweep_tuned;
 } rte_stats;
 
 /* Fill *opt with the defaults listed above. */

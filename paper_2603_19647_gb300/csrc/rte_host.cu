@@ -11,6 +11,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -28,6 +31,19 @@ struct rte_s {
   int device = 0;
   cudaStream_t st = nullptr, own_st = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;
+  // event pool and recorded spans of the device-time statistics
+  std::vector<cudaEvent_t> evpool;
+  int evnext = 0;
+  struct Span {
+    int kind, a, b;
+  };
+  std::vector<Span> spans;
+  // second stream: the ROM update overlaps the fused f sweep
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_rho = nullptr, ev_r0 = nullptr, ev_r1 = nullptr;
+  Norms* h_norms = nullptr;   // pinned
+  int* h_cg = nullptr;        // pinned, CG counts of one SI-SA solve
+  int cg_slots = 0;
   // problem
   int dim = 2, nx = 0, ny = 0;
   long ncell = 0;
@@ -35,7 +51,12 @@ struct rte_s {
   rte_options opt{};
   std::vector<double> mu_user, eta_user, w_user;  // library direction order
   Layout L;
-  int R = 2, W = 4, rows_per_blk = 8, nblk = 1;
+  // 2D sweep tiles: [0] for the SI sweep and the y sweep, [1] for the fused f sweep
+  struct Tile {
+    int R = 1, W = 8, rpb = 32, nblk = 1;
+  } tile[2];
+  int nblk_max = 1;   // edge buffers and control flags are sized for the larger tile count
+  bool tuned = false;
   // device: problem data
   double *sig_t = nullptr, *sig_s = nullptr, *src = nullptr;
   double *ca = nullptr, *cb = nullptr, *cw = nullptr;
@@ -203,7 +224,7 @@ int next_pow2(int v) {
 }
 
 // Group the directions into families of one quadrant (2D) or half-range (1D).
-rte_status make_layout(rte_handle h) {
+rte_status make_layout(rte_handle h, int dl_force) {
   Layout& L = h->L;
   L = Layout{};
   L.dim = h->dim;
@@ -231,6 +252,7 @@ rte_status make_layout(rte_handle h) {
   } else {
     L.dl = dq >= 32 ? 32 : std::max(8, next_pow2(dq));
     if (h->opt.sweep_lanes) L.dl = h->opt.sweep_lanes;
+    if (dl_force) L.dl = dl_force;
     const int gpq = (dq + L.dl - 1) / L.dl;
     L.nfam = 4 * gpq;
     L.nslot = L.nfam * L.dl;
@@ -275,9 +297,13 @@ void free_all(rte_handle h) {
   dsa_free(h->dsa);
   rom_free(h->ig);
   rom_free(h->pc);
-  cudaEvent_t evs[] = {h->ev0, h->ev1, h->kev0, h->kev1};
+  cudaEvent_t evs[] = {h->ev0, h->ev1, h->kev0, h->kev1, h->ev_rho, h->ev_r0, h->ev_r1};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  if (h->st2) cudaStreamDestroy(h->st2);
+  if (h->h_norms) cudaFreeHost(h->h_norms);
+  if (h->h_cg) cudaFreeHost(h->h_cg);
   if (h->own_st) cudaStreamDestroy(h->own_st);
 }
 
@@ -301,14 +327,15 @@ SV<float> sv32(rte_handle h) {
 }
 
 template <class Real>
-Sweep2DArgs<Real> args2d(rte_handle h, const SV<Real>& v) {
+Sweep2DArgs<Real> args2d(rte_handle h, const SV<Real>& v, int mode) {
+  const auto& tl = h->tile[mode == 1 ? 1 : 0];
   Sweep2DArgs<Real> a{};
   a.nx = h->nx;
   a.ny = h->ny;
   a.nfam = h->L.nfam;
   a.nslot = h->L.nslot;
-  a.nblk = h->nblk;
-  a.rows_per_blk = h->rows_per_blk;
+  a.nblk = tl.nblk;
+  a.rows_per_blk = tl.rpb;
   a.tau = (Real)h->tau;
   a.a = v.ca;
   a.b = v.cb;
@@ -354,11 +381,11 @@ rte_status k1(rte_handle h, const SV<Real>& v, const double* g) {
   const double zero[4] = {0, 0, 0, 0};
   if (!g) g = zero;
   if (h->dim == 2) {
-    Sweep2DArgs<Real> a = args2d(h, v);
+    Sweep2DArgs<Real> a = args2d(h, v, 0);
     a.q = v.q;
     a.pm = v.pm;
     ghosts(g, a.gx, a.gy);
-    CK(launch_sweep2d<Real>(a, 0, h->R, h->st));
+    CK(launch_sweep2d<Real>(a, 0, h->tile[0].R, h->st));
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.q = v.q;
@@ -375,13 +402,13 @@ rte_status k1(rte_handle h, const SV<Real>& v, const double* g) {
 template <class Real>
 rte_status k2(rte_handle h, const SV<Real>& v) {
   if (h->dim == 2) {
-    Sweep2DArgs<Real> a = args2d(h, v);
+    Sweep2DArgs<Real> a = args2d(h, v, 1);
     a.q = v.q;
     a.g2 = v.src;
     a.f = v.f;
     a.pm = v.pm;
     ghosts(h->g, a.gx, a.gy);
-    CK(launch_sweep2d<Real>(a, 1, h->R, h->st));
+    CK(launch_sweep2d<Real>(a, 1, h->tile[1].R, h->st));
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.q = v.q;
@@ -400,11 +427,11 @@ rte_status k2(rte_handle h, const SV<Real>& v) {
 template <class Real>
 rte_status ky(rte_handle h, const SV<Real>& v) {
   if (h->dim == 2) {
-    Sweep2DArgs<Real> a = args2d(h, v);
+    Sweep2DArgs<Real> a = args2d(h, v, 2);
     a.g2 = v.src;
     a.f = v.f;
     a.pm = v.pm;
-    CK(launch_sweep2d<Real>(a, 2, h->R, h->st));
+    CK(launch_sweep2d<Real>(a, 2, h->tile[0].R, h->st));
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.g2 = v.src;
@@ -475,7 +502,7 @@ rte_status check_sweep_error(rte_handle h) {
     CK(cudaMemcpyAsync(&err, &h->ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (err) {
-      const size_t bytes = sizeof(SweepCtrl) + sizeof(unsigned) * h->L.nfam * h->nblk;
+      const size_t bytes = sizeof(SweepCtrl) + sizeof(unsigned) * h->L.nfam * h->nblk_max;
       CK(cudaMemsetAsync(h->ctrl, 0, bytes, h->st));
       CK(cudaStreamSynchronize(h->st));
       return fail(h, RTE_ETIMEOUT, "a bounded wait in the sweep ran out");
@@ -525,17 +552,53 @@ rte_status dev_dot(rte_handle h, const double* x, const double* y, double* out) 
   return RTE_OK;
 }
 
-float elapsed(rte_handle h) {
-  float ms = 0.f;
-  cudaEventRecord(h->ev1, h->st);
-  cudaEventSynchronize(h->ev1);
-  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-  cudaEventRecord(h->ev0, h->st);
-  return ms;
+// ---------------------------------------------------------------------------------------
+// Device-time accounting without host waits: events are recorded into a per-handle pool as
+// the work is queued, and the spans between them are read once the step's work is done.
+// ---------------------------------------------------------------------------------------
+enum SpanKind { SPAN_SWEEP = 0, SPAN_DSA, SPAN_ROM, SPAN_K1, SPAN_K2 };
+
+int rec(rte_handle h) {
+  if (h->evnext == (int)h->evpool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->evpool.push_back(e);
+  }
+  const int i = h->evnext++;
+  cudaEventRecord(h->evpool[i], h->st);
+  return i;
+}
+
+void span(rte_handle h, int kind, int a, int b) {
+  if (a >= 0 && b >= 0) h->spans.push_back({kind, a, b});
+}
+
+// Adds the recorded spans to the statistics; the caller has synchronised the stream.
+void resolve_spans(rte_handle h) {
+  for (const auto& sp : h->spans) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->evpool[sp.a], h->evpool[sp.b]) != cudaSuccess) continue;
+    switch (sp.kind) {
+      case SPAN_SWEEP: h->stats.time_sweep_ms += ms; break;
+      case SPAN_DSA: h->stats.time_dsa_ms += ms; break;
+      case SPAN_ROM: h->stats.time_rom_ms += ms; break;
+      case SPAN_K1:
+        h->stats.si_sweep_kernel_ms += ms;
+        h->stats.si_sweep_launches += 1;
+        break;
+      default:
+        h->stats.f_sweep_kernel_ms += ms;
+        h->stats.f_sweep_launches += 1;
+        break;
+    }
+  }
+  h->spans.clear();
+  h->evnext = 0;
 }
 
 // ---------------------------------------------------------------------------------------
-// Algorithm 1 on the current b~ from initial guess rho0.  Leaves rho^n in h->rho.
+// Algorithm 1 on the current b~ from initial guess rho0.  Leaves rho^n in h->rho.  The host
+// waits once per iteration, for the two norms of the stopping test.
 // ---------------------------------------------------------------------------------------
 rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out) {
   const int n = (int)h->ncell;
@@ -546,24 +609,23 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
   // FP64 y_ir = T Sigma_s rho_ref, so rho^{l-1/2} = y_ir + b~ carries FP64 accuracy in the
   // residual; the first increment is measured from the last swept iterate of the previous step.
   auto sweep_increment = [&]() -> rte_status {
-    cudaEventRecord(h->kev0, h->st);
+    const int k0 = rec(h);
     if (h->fp32) {
       CK(launch_scaled_diff_update<float>(h->rho_prev, h->rho_ref, h->sig_s, n, h->q_f, h->st));
       TRY(sweep_q(h, nullptr));
-      cudaEventRecord(h->kev1, h->st);
+      span(h, SPAN_K1, k0, rec(h));
       TRY(sum_pm(h, h->y_ir, 1));
     } else {
       TRY(set_q(h, h->rho_prev, nullptr));
       TRY(sweep_q(h, nullptr));
-      cudaEventRecord(h->kev1, h->st);
+      span(h, SPAN_K1, k0, rec(h));
     }
     return RTE_OK;
   };
-  int cg_total = 0;
   bool conv = false;
   int l = 0;
   h->pc_applied = false;
-  cudaEventRecord(h->ev0, h->st);
+  int mark = rec(h);
   TRY(sweep_increment());
   for (l = 1; l <= h->opt.max_iter; ++l) {
     if (h->fp32)
@@ -572,18 +634,15 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
     else
       CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
                                  h->partials, nb, h->norms, h->st));
-    Norms nm;
-    CK(cudaMemcpyAsync(&nm, h->norms, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
-    h->stats.time_sweep_ms += elapsed(h);
-    {
-      float kms = 0.f;
-      cudaEventElapsedTime(&kms, h->kev0, h->kev1);
-      h->stats.si_sweep_kernel_ms += kms;
-      h->stats.si_sweep_launches += 1;
-    }
+    CK(cudaMemcpyAsync(h->h_norms, h->norms, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
+    int m = rec(h);
+    span(h, SPAN_SWEEP, mark, m);
+    mark = m;
     if (l == 1)
       CK(cudaMemcpyAsync(h->rho_half1, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                          h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const Norms nm = *h->h_norms;
     const double res = h->opt.residual_norm == RTE_ABS_INF
                            ? nm.diff_inf
                            : (nm.half_inf > 0 ? nm.diff_inf / nm.half_inf : nm.diff_inf);
@@ -598,31 +657,49 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
       CK(rom_apply(h->pc, h->tmp, h->delta_pc1, h->st));
       CK(launch_update_rho(h->rho_half, h->delta_pc1, h->sig_s, n, h->rho_prev, h->q, h->st));
       h->pc_applied = true;
-      h->stats.time_rom_ms += elapsed(h);
+      m = rec(h);
+      span(h, SPAN_ROM, mark, m);
+      mark = m;
     } else {
-      // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta
+      // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta.  Its
+      // iteration count stays on the device until the step ends.
       CK(dsa_solve(h->dsa, h->sig_s, h->rho_half, h->rho_prev, h->opt.cg_rtol, h->opt.cg_max_iter,
-                   h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters, h->st));
-      int its = 0;
-      CK(cudaMemcpyAsync(&its, h->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-      h->stats.time_dsa_ms += elapsed(h);
-      cg_total += its;
+                   h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters + l, h->st));
+      m = rec(h);
+      span(h, SPAN_DSA, mark, m);
+      mark = m;
     }
     TRY(sweep_increment());
   }
   if (l > h->opt.max_iter) l = h->opt.max_iter;
   CK(cudaMemcpyAsync(h->rho, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  h->stats.last_cg_iterations = cg_total;
-  h->stats.total_cg_iterations += cg_total;
+  // CG counts of this solve: slots 1 .. l-1 written by the DSA calls (the PC step leaves its
+  // slot at zero)
+  CK(cudaMemcpyAsync(h->h_cg, h->cg_iters, sizeof(int) * (l + 1), cudaMemcpyDeviceToHost, h->st));
+  h->cg_slots = l + 1;
   *iters_out = l;
   *converged_out = conv;
   return RTE_OK;
 }
 
-// ROM construction / adaptive update for the step just taken (Algorithm 2, Sec. 3.2).
+// Sums the CG counts copied at the end of si_sa (after the stream is synchronised) and clears
+// the device slots for the next solve.
+rte_status finish_cg_counts(rte_handle h) {
+  int cg = 0;
+  for (int i = 0; i < h->cg_slots; ++i) cg += h->h_cg[i];
+  h->stats.last_cg_iterations = cg;
+  h->stats.total_cg_iterations += cg;
+  if (h->cg_slots > 0)
+    CK(cudaMemsetAsync(h->cg_iters, 0, sizeof(int) * h->cg_slots, h->st));
+  h->cg_slots = 0;
+  return RTE_OK;
+}
+
+// ROM construction / adaptive update for the step just taken (Algorithm 2, Sec. 3.2).  Runs on
+// whatever stream h->st names; one_step gives it a second stream so that it overlaps the
+// fused f sweep, which neither reads nor writes what it uses.
 rte_status rom_update(rte_handle h) {
   const int n = (int)h->ncell;
-  cudaEventRecord(h->ev0, h->st);
   double rn2 = 0.0;
   TRY(dev_dot(h, h->rho, h->rho, &rn2));
   const double thr = h->opt.eps_up * (h->opt.up_rel ? std::sqrt(rn2) : 1.0);
@@ -673,7 +750,6 @@ rte_status rom_update(rte_handle h) {
   h->stats.pc_updated = pc_up;
   h->stats.ig_rank = h->ig.rank;
   h->stats.pc_rank = h->pc.rank;
-  h->stats.time_rom_ms += elapsed(h);
   return RTE_OK;
 }
 
@@ -681,14 +757,21 @@ rte_status one_step(rte_handle h) {
   const int n = (int)h->ncell;
   const bool rom_on = h->opt.rom != RTE_ROM_OFF;
   auto t0 = std::chrono::steady_clock::now();
-  cudaEventRecord(h->ev0, h->st);
+  if (!h->spans.empty()) {   // left over by a failed call
+    CK(cudaStreamSynchronize(h->st));
+    resolve_spans(h);
+  }
+  int mark = rec(h);
   TRY(make_btilde(h));
-  h->stats.time_sweep_ms += elapsed(h);
+  int m = rec(h);
+  span(h, SPAN_SWEEP, mark, m);
+  mark = m;
   h->ig_applied = false;
   if (rom_on && h->flag_ig && h->ig.lu_ok) {
     CK(rom_apply(h->ig, h->btilde, h->rho0, h->st));   // Eq. (dmd-ig)
     h->ig_applied = true;
-    h->stats.time_rom_ms += elapsed(h);
+    m = rec(h);
+    span(h, SPAN_ROM, mark, m);
   } else {
     CK(cudaMemcpyAsync(h->rho0, h->rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   }
@@ -697,21 +780,39 @@ rte_status one_step(rte_handle h) {
   bool conv = false;
   TRY(si_sa(h, use_pc, &iters, &conv));
   h->last_iters = iters;
+  // the phase this step ran in (the ROM update below may end it)
+  const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!h->flag_pc ? 2 : 3));
+  // rho^n is final: the ROM update may start beside the fused sweep
+  CK(cudaEventRecord(h->ev_rho, h->st));
   // f^n and the next step's b~ (without inflow): Eq. (sweep_to_obtain_f), Eq. (implicit_linear_system_rho)
-  cudaEventRecord(h->ev0, h->st);
-  cudaEventRecord(h->kev0, h->st);
+  mark = rec(h);
   TRY(sweep_f(h, h->rho, h->y));
-  cudaEventRecord(h->kev1, h->st);
+  m = rec(h);
+  span(h, SPAN_K2, mark, m);
+  span(h, SPAN_SWEEP, mark, m);
   h->y_valid = true;
-  h->stats.time_sweep_ms += elapsed(h);
-  {
-    float kms = 0.f;
-    cudaEventElapsedTime(&kms, h->kev0, h->kev1);
-    h->stats.f_sweep_kernel_ms += kms;
-    h->stats.f_sweep_launches += 1;
+  bool rom_ran = false;
+  rte_status rom_status = RTE_OK;
+  if (rom_on && conv && h->opt.rom == RTE_ROM_AUTO) {
+    CK(cudaStreamWaitEvent(h->st2, h->ev_rho, 0));
+    cudaStream_t main = h->st;
+    h->st = h->st2;
+    cudaEventRecord(h->ev_r0, h->st2);
+    rom_status = rom_update(h);
+    cudaEventRecord(h->ev_r1, h->st2);
+    h->st = main;
+    CK(cudaStreamWaitEvent(h->st, h->ev_r1, 0));   // the next step applies the updated ROMs
+    rom_ran = true;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  resolve_spans(h);
+  TRY(finish_cg_counts(h));
+  if (rom_ran) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_r0, h->ev_r1) == cudaSuccess) h->stats.time_rom_ms += ms;
   }
   TRY(check_sweep_error(h));
-  const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!h->flag_pc ? 2 : 3));
+  TRY(rom_status);
   h->stats.phase = phase;
   h->stats.steps += 1;
   h->stats.last_iterations = iters;
@@ -719,13 +820,7 @@ rte_status one_step(rte_handle h) {
   h->stats.total_sweeps += iters + 2;
   h->stats.cell_direction_updates += (long long)(iters + 2) * h->ncell * h->L.nv;
   if (!conv) return fail(h, RTE_ENOCONV, "SI-SA reached max_iter without meeting eps_sisa");
-  if (rom_on) {
-    if (h->opt.rom == RTE_ROM_AUTO)
-      TRY(rom_update(h));
-    else
-      h->pending_rom = true;
-  }
-  CK(cudaStreamSynchronize(h->st));
+  if (rom_on && h->opt.rom == RTE_ROM_MANUAL) h->pending_rom = true;
   auto t1 = std::chrono::steady_clock::now();
   h->stats.time_total_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
   return RTE_OK;
@@ -778,6 +873,243 @@ void balance_weights(std::vector<float>& w) {
   }
 }
 
+// Per-slot direction data of the current layout: a = |mu|/hx, b = |eta|/hy, the weights, the
+// quadrant of each family and the sign of mu; in FP32 mode also their FP32 forms.
+rte_status setup_slots(rte_handle h) {
+  const Layout& L = h->L;
+  std::vector<double> a(L.nslot), b(L.nslot);
+  std::vector<int> sign(L.nslot);
+  for (int s = 0; s < L.nslot; ++s) {
+    a[s] = std::fabs(L.mu[s]) / h->hx;
+    b[s] = h->dim == 2 ? std::fabs(L.eta[s]) / h->hy : 0.0;
+    sign[s] = L.mu[s] > 0 ? 1 : -1;
+  }
+  CK(dalloc(&h->ca, L.nslot));
+  CK(dalloc(&h->cb, L.nslot));
+  CK(dalloc(&h->cw, L.nslot));
+  CK(dalloc(&h->fam_quad, L.nfam));
+  CK(dalloc(&h->dir_sign, L.nslot));
+  TRY(upload(h, h->ca, a.data(), L.nslot));
+  TRY(upload(h, h->cb, b.data(), L.nslot));
+  TRY(upload(h, h->cw, L.w.data(), L.nslot));
+  CK(cudaMemcpy(h->fam_quad, L.fam_quadrant.data(), sizeof(int) * L.nfam, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dir_sign, sign.data(), sizeof(int) * L.nslot, cudaMemcpyHostToDevice));
+  if (h->fp32) {
+    // FP32 coefficients: a, b, tau and sigma_t rounded once; tau + a + b of each slot kept
+    // exactly as a hi / lo pair, and the weights nudged by whole ulps so that their exact
+    // sum is 1 again.  The FP32 sweeps then apply the exact Q0 operator of these rounded
+    // coefficients, which conserves particles like the FP64 one.
+    std::vector<float> a32(L.nslot), b32(L.nslot), cth(L.nslot), ctl(L.nslot), w32(L.nslot);
+    const double tau32 = (double)(float)h->tau;
+    for (int s = 0; s < L.nslot; ++s) {
+      a32[s] = (float)a[s];
+      b32[s] = (float)b[s];
+      const double ct = tau32 + (double)a32[s] + (double)b32[s];
+      cth[s] = (float)ct;
+      ctl[s] = (float)(ct - (double)cth[s]);
+      w32[s] = (float)L.w[s];
+    }
+    balance_weights(w32);
+    CK(dalloc(&h->ca_f, L.nslot));
+    CK(dalloc(&h->cb_f, L.nslot));
+    CK(dalloc(&h->cw_f, L.nslot));
+    CK(dalloc(&h->cth_f, L.nslot));
+    CK(dalloc(&h->ctl_f, L.nslot));
+    float* hv[] = {a32.data(), b32.data(), w32.data(), cth.data(), ctl.data()};
+    float* dv[] = {h->ca_f, h->cb_f, h->cw_f, h->cth_f, h->ctl_f};
+    for (int i = 0; i < 5; ++i)
+      CK(cudaMemcpy(dv[i], hv[i], sizeof(float) * L.nslot, cudaMemcpyHostToDevice));
+  }
+  return RTE_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_slots(rte_handle h) {
+  dfree(h->ca), dfree(h->cb), dfree(h->cw), dfree(h->fam_quad), dfree(h->dir_sign);
+  dfree(h->ca_f), dfree(h->cb_f), dfree(h->cw_f), dfree(h->cth_f), dfree(h->ctl_f);
+}
+
+// Angular flux, partial-moment, face (edge) and control buffers of the sweeps, for the
+// current layout; the edge buffers and flags are sized for nblk_max row blocks.
+rte_status alloc_sweep(rte_handle h) {
+  const Layout& L = h->L;
+  const long n = h->ncell;
+  if (!h->fp32) {
+    CK(dalloc(&h->f, (size_t)n * L.nslot));
+    CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
+  } else {
+    CK(dalloc(&h->f_f, (size_t)n * L.nslot));
+    CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * n * L.nslot, h->st));
+  }
+  if (h->dim == 2) {
+    const size_t edge = (size_t)2 * L.nfam * h->nblk_max * h->nx * L.dl;
+    if (!h->fp32) {
+      CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
+      CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, L.dl, h->inv_d,
+                              h->st));
+      CK(dalloc(&h->pm, (size_t)L.nfam * n));
+      CK(dalloc(&h->edge, edge));
+    } else {
+      CK(dalloc(&h->pm_f, (size_t)L.nfam * n));
+      CK(dalloc(&h->edge_f, edge));
+    }
+    const size_t cb_bytes = sizeof(SweepCtrl) + sizeof(unsigned) * L.nfam * h->nblk_max;
+    CK(cudaMalloc((void**)&h->ctrl, cb_bytes));
+    CK(cudaMemsetAsync(h->ctrl, 0, cb_bytes, h->st));
+  } else {
+    if (!h->fp32) {
+      CK(dalloc(&h->pm, n));
+      CK(dalloc(&h->psi_w, (size_t)n * L.nslot));
+    } else {
+      CK(dalloc(&h->pm_f, n));
+      CK(dalloc(&h->psi_w_f, (size_t)n * L.nslot));
+    }
+  }
+  return RTE_OK;
+}
+
+void free_sweep(rte_handle h) {
+  dfree(h->f), dfree(h->f_f), dfree(h->inv_d), dfree(h->pm), dfree(h->pm_f), dfree(h->edge);
+  dfree(h->edge_f), dfree(h->ctrl), dfree(h->psi_w), dfree(h->psi_w_f);
+}
+
+void set_tile(rte_handle h, rte_s::Tile& tl, int R, int W) {
+  tl.R = R;
+  tl.W = W;
+  tl.rpb = W * (32 / h->L.dl) * R;
+  tl.nblk = (h->ny + tl.rpb - 1) / tl.rpb;
+}
+
+// A tile is usable when R <= dl and every sweep kind's staging fits the 200 KiB the
+// launcher allows.
+bool tile_fits(rte_handle h, int dl, int R, int W) {
+  if (R > dl) return false;
+  const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
+  for (int mode = 0; mode < 3; ++mode)
+    if (sweep2d_smem_bytes(real, dl, R, W, mode, !h->fp32) > 200 * 1024) return false;
+  return true;
+}
+
+// Mean device time of two launches of one sweep kind (0: SI sweep, 1: fused f sweep) after
+// one warm-up launch.
+rte_status time_sweeps(rte_handle h, int kind, float* ms) {
+  auto run = [&]() -> rte_status {
+    return kind == 0 ? sweep_q(h, nullptr) : sweep_f(h, h->rho, h->y);
+  };
+  TRY(run());
+  CK(cudaEventRecord(h->kev0, h->st));
+  for (int i = 0; i < 2; ++i) TRY(run());
+  CK(cudaEventRecord(h->kev1, h->st));
+  CK(cudaEventSynchronize(h->kev1));
+  TRY(check_sweep_error(h));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, h->kev0, h->kev1));
+  *ms = 0.5f * t;
+  return RTE_OK;
+}
+
+struct TuneKey {
+  int device, nx, ny, nv, fp32;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(device, nx, ny, nv, fp32) < std::tie(o.device, o.nx, o.ny, o.nv, o.fp32);
+  }
+};
+struct TuneVal {
+  int dl, r0, w0, r1, w1;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+// Direction lanes per family (dl) and the tiles (R rows per lane group, W warps per CTA) of
+// the two sweep kinds.  With options.tune every usable (dl, R, W) is timed on this problem's
+// own data (zero flux; the kernels' work does not depend on the values) and the choice with
+// the least 3 t_SI + t_f is kept, once per (device, grid, direction count, precision) and
+// process.  Explicit sweep_* options, or tune = 0, give the fixed choice instead.
+rte_status choose_tiles(rte_handle h, int* dl_out) {
+  const int dq = (int)h->mu_user.size() / 4;
+  const int dl_max = dq >= 32 ? 32 : std::max(8, next_pow2(dq));
+  const bool fixed = h->opt.sweep_lanes || h->opt.sweep_rows || h->opt.sweep_warps || !h->opt.tune;
+  if (fixed) {
+    int dl = h->opt.sweep_lanes ? h->opt.sweep_lanes
+                                : std::min(dl_max, (!h->fp32 && h->ncell >= 512L * 512) ? 32 : 8);
+    int R = std::min(h->opt.sweep_rows ? h->opt.sweep_rows : (h->fp32 ? 2 : 1), dl);
+    int W = h->opt.sweep_warps ? h->opt.sweep_warps : 8;
+    while (W > 1 && !tile_fits(h, dl, R, W)) --W;
+    h->tile[0].R = h->tile[1].R = R;
+    h->tile[0].W = h->tile[1].W = W;
+    *dl_out = dl;
+    return RTE_OK;
+  }
+  const TuneKey key{h->device, h->nx, h->ny, (int)h->mu_user.size(), h->fp32 ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const TuneVal& v = it->second;
+      h->tile[0].R = v.r0, h->tile[0].W = v.w0, h->tile[1].R = v.r1, h->tile[1].W = v.w1;
+      *dl_out = v.dl;
+      h->tuned = true;
+      return RTE_OK;
+    }
+  }
+  float best = INFINITY;
+  TuneVal bv{0, 1, 8, 1, 8};
+  const int dls[3] = {8, 16, 32};
+  for (int dl : dls) {
+    if (dl > dl_max) continue;
+    TRY(make_layout(h, dl));
+    std::vector<std::pair<int, int>> cand;
+    const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8};
+    for (int R : rs)
+      for (int W : ws)
+        if (tile_fits(h, dl, R, W)) cand.push_back({R, W});
+    if (cand.empty()) continue;
+    int nb = 1;
+    for (auto& c : cand) {
+      rte_s::Tile tl;
+      set_tile(h, tl, c.first, c.second);
+      nb = std::max(nb, tl.nblk);
+    }
+    h->nblk_max = nb;
+    TRY(setup_slots(h));
+    TRY(alloc_sweep(h));
+    TRY(set_q(h, h->src, nullptr));
+    float t1b = INFINITY, t2b = INFINITY;
+    std::pair<int, int> c1 = cand[0], c2 = cand[0];
+    for (auto& c : cand) {
+      set_tile(h, h->tile[0], c.first, c.second);
+      set_tile(h, h->tile[1], c.first, c.second);
+      float t1 = 0.f, t2 = 0.f;
+      TRY(time_sweeps(h, 0, &t1));
+      TRY(time_sweeps(h, 1, &t2));
+      if (t1 < t1b) t1b = t1, c1 = c;
+      if (t2 < t2b) t2b = t2, c2 = c;
+    }
+    CK(cudaStreamSynchronize(h->st));
+    free_sweep(h);
+    free_slots(h);
+    const float score = 3.f * t1b + t2b;
+    if (score < best) {
+      best = score;
+      bv = TuneVal{dl, c1.first, c1.second, c2.first, c2.second};
+    }
+  }
+  if (bv.dl == 0) return fail(h, RTE_EINVAL, "no sweep tile fits in shared memory");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = bv;
+  }
+  h->tile[0].R = bv.r0, h->tile[0].W = bv.w0, h->tile[1].R = bv.r1, h->tile[1].W = bv.w1;
+  *dl_out = bv.dl;
+  h->tuned = true;
+  return RTE_OK;
+}
+
 rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature* quad,
                        const double* sigma_t, const double* sigma_s, const double* source,
                        double c_dt, const rte_options* opt) {
@@ -821,7 +1153,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
     if (sigma_s[i] < 0.0 || sigma_t[i] < sigma_s[i])
       return fail(h, RTE_EINVAL, "need sigma_t >= sigma_s >= 0 in every cell");
   TRY(make_rule(h, quad, h->dim));
-  TRY(make_layout(h));
+  TRY(make_layout(h, 0));   // validates the directions before any device work
   CK(cudaGetDevice(&h->device));
   CK(cudaStreamCreateWithFlags(&h->own_st, cudaStreamNonBlocking));
   h->st = h->own_st;
@@ -829,101 +1161,27 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(cudaEventCreate(&h->ev1));
   CK(cudaEventCreate(&h->kev0));
   CK(cudaEventCreate(&h->kev1));
-  const Layout& L = h->L;
-  // sweep tiling
-  if (h->dim == 2) {
-    h->R = std::min(h->opt.sweep_rows ? h->opt.sweep_rows : 2, L.dl);
-    h->W = h->opt.sweep_warps ? h->opt.sweep_warps : 4;
-    // fewer warps per CTA when the fused sweep's staging would not fit in shared memory
-    const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
-    while (h->W > 1 && sweep2d_smem_bytes(real, L.dl, h->R, h->W, 1, !h->fp32) > 200 * 1024)
-      --h->W;
-    h->rows_per_blk = h->W * (32 / L.dl) * h->R;
-    h->nblk = (h->ny + h->rows_per_blk - 1) / h->rows_per_blk;
-  }
+  CK(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_rho, cudaEventDisableTiming));
+  CK(cudaEventCreate(&h->ev_r0));
+  CK(cudaEventCreate(&h->ev_r1));
+  CK(cudaMallocHost((void**)&h->h_norms, sizeof(Norms)));
+  CK(cudaMallocHost((void**)&h->h_cg, sizeof(int) * (h->opt.max_iter + 2)));
+  // data that does not depend on the direction layout
   CK(dalloc(&h->sig_t, n));
   CK(dalloc(&h->sig_s, n));
   CK(dalloc(&h->src, n));
   TRY(upload(h, h->sig_t, sigma_t, n));
   TRY(upload(h, h->sig_s, sigma_s, n));
   TRY(upload(h, h->src, source, n));
-  std::vector<double> a(L.nslot), b(L.nslot);
-  std::vector<int> sign(L.nslot);
-  for (int s = 0; s < L.nslot; ++s) {
-    a[s] = std::fabs(L.mu[s]) / h->hx;
-    b[s] = h->dim == 2 ? std::fabs(L.eta[s]) / h->hy : 0.0;
-    sign[s] = L.mu[s] > 0 ? 1 : -1;
-  }
-  CK(dalloc(&h->ca, L.nslot));
-  CK(dalloc(&h->cb, L.nslot));
-  CK(dalloc(&h->cw, L.nslot));
-  CK(dalloc(&h->fam_quad, L.nfam));
-  CK(dalloc(&h->dir_sign, L.nslot));
-  TRY(upload(h, h->ca, a.data(), L.nslot));
-  TRY(upload(h, h->cb, b.data(), L.nslot));
-  TRY(upload(h, h->cw, L.w.data(), L.nslot));
-  CK(cudaMemcpy(h->fam_quad, L.fam_quadrant.data(), sizeof(int) * L.nfam, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->dir_sign, sign.data(), sizeof(int) * L.nslot, cudaMemcpyHostToDevice));
-  if (!h->fp32) {
-    CK(dalloc(&h->f, (size_t)n * L.nslot));
-    CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
-  } else {
-    CK(dalloc(&h->f_f, (size_t)n * L.nslot));
-    CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * n * L.nslot, h->st));
+  if (h->fp32) {
     CK(dalloc(&h->sig_t_f, n));
     CK(dalloc(&h->src_f, n));
     CK(launch_to_float(h->sig_t, n, h->sig_t_f, h->st));
     CK(launch_to_float(h->src, n, h->src_f, h->st));
-    // FP32 coefficients: a, b, tau and sigma_t rounded once; tau + a + b of each slot kept
-    // exactly as a hi / lo pair, and the weights nudged by whole ulps so that their exact
-    // sum is 1 again.  The FP32 sweeps then apply the exact Q0 operator of these rounded
-    // coefficients, which conserves particles like the FP64 one.
-    std::vector<float> a32(L.nslot), b32(L.nslot), cth(L.nslot), ctl(L.nslot), w32(L.nslot);
-    const double tau32 = (double)(float)h->tau;
-    for (int s = 0; s < L.nslot; ++s) {
-      a32[s] = (float)a[s];
-      b32[s] = (float)b[s];
-      const double ct = tau32 + (double)a32[s] + (double)b32[s];
-      cth[s] = (float)ct;
-      ctl[s] = (float)(ct - (double)cth[s]);
-      w32[s] = (float)L.w[s];
-    }
-    balance_weights(w32);
-    CK(dalloc(&h->ca_f, L.nslot));
-    CK(dalloc(&h->cb_f, L.nslot));
-    CK(dalloc(&h->cw_f, L.nslot));
-    CK(dalloc(&h->cth_f, L.nslot));
-    CK(dalloc(&h->ctl_f, L.nslot));
-    float* hv[] = {a32.data(), b32.data(), w32.data(), cth.data(), ctl.data()};
-    float* dv[] = {h->ca_f, h->cb_f, h->cw_f, h->cth_f, h->ctl_f};
-    for (int i = 0; i < 5; ++i)
-      CK(cudaMemcpy(dv[i], hv[i], sizeof(float) * L.nslot, cudaMemcpyHostToDevice));
     CK(dalloc(&h->q_f, n));
     CK(dalloc(&h->y_ir, n));
     CK(dalloc(&h->rho_ref, n));
-  }
-  if (h->dim == 2) {
-    if (!h->fp32) {
-      CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
-      CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, L.dl, h->inv_d,
-                              h->st));
-      CK(dalloc(&h->pm, (size_t)L.nfam * n));
-      CK(dalloc(&h->edge, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
-    } else {
-      CK(dalloc(&h->pm_f, (size_t)L.nfam * n));
-      CK(dalloc(&h->edge_f, (size_t)2 * L.nfam * h->nblk * h->nx * L.dl));
-    }
-    const size_t cb_bytes = sizeof(SweepCtrl) + sizeof(unsigned) * L.nfam * h->nblk;
-    CK(cudaMalloc((void**)&h->ctrl, cb_bytes));
-    CK(cudaMemsetAsync(h->ctrl, 0, cb_bytes, h->st));
-  } else {
-    if (!h->fp32) {
-      CK(dalloc(&h->pm, n));
-      CK(dalloc(&h->psi_w, (size_t)n * L.nslot));
-    } else {
-      CK(dalloc(&h->pm_f, n));
-      CK(dalloc(&h->psi_w_f, (size_t)n * L.nslot));
-    }
   }
   double** vecs[] = {&h->rho, &h->rho_prev, &h->rho_half, &h->rho_half1, &h->rho0, &h->y,
                      &h->btilde, &h->q, &h->delta, &h->tmp, &h->tmp2, &h->tmp3, &h->delta_pc1};
@@ -934,7 +1192,18 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(dalloc(&h->partials, 3 * 1024));
   CK(dalloc(&h->dotbuf, 4));
   CK(dalloc(&h->norms, 1));
-  CK(dalloc(&h->cg_iters, 1));
+  CK(dalloc(&h->cg_iters, (size_t)h->opt.max_iter + 2));
+  CK(cudaMemsetAsync(h->cg_iters, 0, sizeof(int) * (h->opt.max_iter + 2), h->st));
+  // direction layout and sweep tiles: measured (tune), else the fixed choice
+  int dl = 0;
+  if (h->dim == 2) TRY(choose_tiles(h, &dl));
+  TRY(make_layout(h, dl));
+  if (h->dim == 2) {
+    for (auto& tl : h->tile) set_tile(h, tl, tl.R, tl.W);
+    h->nblk_max = std::max(h->tile[0].nblk, h->tile[1].nblk);
+  }
+  TRY(setup_slots(h));
+  TRY(alloc_sweep(h));
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st));
   CK(rom_alloc(h->ig, (int)n, h->opt.r_max));
   CK(rom_alloc(h->pc, (int)n, h->opt.r_max));
@@ -1078,10 +1347,14 @@ rte_status rte_rom_update(rte_handle h) {
     return fail(h, RTE_ESTATE, "no manual ROM update is pending");
   h->pending_rom = false;
   const long long l0 = g_launches;
+  cudaEventRecord(h->ev_r0, h->st);
   rte_status s = rom_update(h);
+  cudaEventRecord(h->ev_r1, h->st);
   h->stats.kernel_launches += g_launches - l0;
   if (s != RTE_OK) return s;
   CK(cudaStreamSynchronize(h->st));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, h->ev_r0, h->ev_r1) == cudaSuccess) h->stats.time_rom_ms += ms;
   return RTE_OK;
 }
 
@@ -1129,6 +1402,14 @@ rte_status rte_get_stats(rte_handle h, rte_stats* st) {
   *st = h->stats;
   st->ig_rank = h->ig.rank;
   st->pc_rank = h->pc.rank;
+  if (h->dim == 2) {
+    st->sweep_lanes = h->L.dl;
+    st->sweep_si_rows = h->tile[0].R;
+    st->sweep_si_warps = h->tile[0].W;
+    st->sweep_f_rows = h->tile[1].R;
+    st->sweep_f_warps = h->tile[1].W;
+    st->sweep_tuned = h->tuned ? 1 : 0;
+  }
   return RTE_OK;
 }
 
@@ -1167,9 +1448,17 @@ rte_status rte_op_fsweep(rte_handle h, const double* rho, double* btilde) {
   if (!h || !rho) return RTE_EINVAL;
   const int n = (int)h->ncell;
   TRY(upload(h, h->tmp, rho, n));
+  cudaEventRecord(h->kev0, h->st);
   TRY(sweep_f(h, h->tmp, h->y));
+  cudaEventRecord(h->kev1, h->st);
   h->y_valid = true;
   TRY(check_sweep_error(h));
+  {
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, h->kev0, h->kev1);
+    h->stats.f_sweep_kernel_ms += kms;
+    h->stats.f_sweep_launches += 1;
+  }
   if (btilde) {
     TRY(make_btilde(h));
     CK(cudaMemcpyAsync(btilde, h->btilde, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));

@@ -63,7 +63,10 @@ class Stats(ctypes.Structure):
                 ("time_dsa_ms", ctypes.c_double), ("time_rom_ms", ctypes.c_double),
                 ("time_total_ms", ctypes.c_double), ("si_sweep_launches", ctypes.c_longlong),
                 ("si_sweep_kernel_ms", ctypes.c_double), ("f_sweep_launches", ctypes.c_longlong),
-                ("f_sweep_kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+                ("f_sweep_kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+                ("sweep_lanes", ctypes.c_int), ("sweep_si_rows", ctypes.c_int),
+                ("sweep_si_warps", ctypes.c_int), ("sweep_f_rows", ctypes.c_int),
+                ("sweep_f_warps", ctypes.c_int), ("sweep_tuned", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
