@@ -117,6 +117,19 @@ def profiled_traffic():
         return None
 
 
+def reduce_over_ranks(dist, total_ms, updates, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the sum of all
+    ranks' updates (dist None: one process)."""
+    if dist is None:
+        return float(total_ms), float(updates)
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def oracle_sample(wl, budget_s, min_steps=2):
     """Time the CPU oracle's march on the workload for about budget_s seconds."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -241,16 +254,7 @@ def run_ours(args):
     wall_rom = time.perf_counter() - wall0
     ms_plain, agg_plain = timed_marches(h_plain, args.steps)
 
-    total_ms = sum(ms_rom)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(agg_rom["updates"])], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        updates_all = float(u.item())
-    else:
-        updates_all = float(agg_rom["updates"])
+    total_ms, updates_all = reduce_over_ranks(dist, sum(ms_rom), agg_rom["updates"], "cuda")
     value = updates_all / (total_ms / 1e3)
 
     # e2e: the user's call sequence with host buffers (pinned): create, set_initial, march,
