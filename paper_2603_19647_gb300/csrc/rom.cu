@@ -223,10 +223,10 @@ __global__ void gx_times_vc_kernel(int r, Scr sc) {
   }
 }
 
-// G = U_c^T T  (keep x keep); one block per output column.
-__global__ void uct_times_t_kernel(int r, Scr sc) {
+// G = U_c^T T  (keep x keep); one block per output column.  Skipped when the gate is 0.
+__global__ void uct_times_t_kernel(int r, Scr sc, const int* gate) {
   const int n = r + 1, keep = (int)sc.sc[4], b = blockIdx.x;
-  if (b >= keep) return;
+  if (b >= keep || (gate && *gate == 0)) return;
   for (int a = threadIdx.x; a < keep; a += blockDim.x) {
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += sc.Uc[a * n + i] * sc.T[i * keep + b];
@@ -242,8 +242,11 @@ __device__ __forceinline__ unsigned long long mag_bits(double x) {
 
 // S <- new singular values; A_r = G S^{-1}; its inverse by Gauss-Jordan elimination with
 // partial pivoting (row-major, keep x keep) into inv.  Pivot search: warp-wide argmax on
-// the magnitude bits.  lu_ok = 0 when a pivot falls below 1e-14 max |A_r|.
-__global__ void __launch_bounds__(256) inverse_kernel(Scr sc, double* S, double* inv) {
+// the magnitude bits.  lu_ok = 0 when a pivot falls below 1e-14 max |A_r|.  Skipped when
+// the gate is 0 (the ROM keeps its state).
+__global__ void __launch_bounds__(256) inverse_kernel(Scr sc, double* S, double* inv,
+                                                      const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double A[(MAXR - 1) * (MAXR - 1)];
   __shared__ double B[(MAXR - 1) * (MAXR - 1)];
   __shared__ int s_ok, s_piv;
@@ -398,6 +401,37 @@ __global__ void identity_kernel(double* M, int k) {
   }
 }
 
+// Q <- Qtmp and P <- Ptmp (rows x keep of each, ld MAXR) when the gate is open.
+__global__ void factor_commit_kernel(const double* Qtmp, double* Q, int qrows, const double* Ptmp,
+                                     double* P, int prows, const double* sc, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int keep = (int)sc[4];
+  const bool grow = sc[5] != 0.0;
+  const int qr = qrows + (grow ? 1 : 0);
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < (qr + prows + 1) * keep;
+       e += blockDim.x * gridDim.x) {
+    const int i = e / keep, j = e % keep;
+    if (i < qr) Q[i * MAXR + j] = Qtmp[i * MAXR + j];
+    else P[(i - qr) * MAXR + j] = Ptmp[(i - qr) * MAXR + j];
+  }
+}
+
+// Outcome of one append in st[0..6]: rank, columns of U0, columns of W0, lu_ok, grew, ran,
+// stop ratio (the state before the append when the gate is closed).
+__global__ void append_finish_kernel(int r, int wu, int ww, const double* sc, const int* gate,
+                                     double* st) {
+  if (threadIdx.x != 0) return;
+  const bool on = !gate || *gate != 0;
+  const bool g = on && sc[5] != 0.0;
+  st[0] = on ? sc[4] : r;
+  st[1] = wu + (g ? 1 : 0);
+  st[2] = ww + (on ? 1 : 0);
+  st[3] = on ? sc[7] : -1.0;   // -1: unchanged
+  st[4] = g ? 1.0 : 0.0;
+  st[5] = on ? 1.0 : 0.0;
+  st[6] = on ? sc[6] : 0.0;
+}
+
 int gemv_blocks(long n) {
   long b = (n + GT - 1) / GT;
   if (b > 256) b = 256;
@@ -467,14 +501,16 @@ cudaError_t compact(RomDev& R, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc_eps, int* grew,
-                       double* ratio, cudaStream_t s) {
+cudaError_t rom_append_async(RomDev& R, const double* x, const double* b, double trunc_eps,
+                             const int* gate, cudaStream_t s) {
   const long n = R.n;
   const int r = R.rank;
   Scr sc = scr_of(R.core);
   double* q = R.U + (long)R.wu * n;   // next column of U0 holds q~, then q
   const unsigned vb = (unsigned)((n + 255) / 256);
   cudaError_t e;
+  // Everything up to the commit writes scratch only (the new columns of U0 and W0 lie beyond
+  // the columns in use), so a closed gate needs no test before it.
   if ((e = dot(x, x, n, R.partial, sc.sc + 0, s)) != cudaSuccess) return e;
   if (r > 0) {
     // classical Gram-Schmidt, twice: p = U^T x, q~ = x - U p; p2 = U^T q~, q~ -= U p2
@@ -504,37 +540,49 @@ cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc
   if ((e = cudaMemcpyAsync(R.W + (long)R.ww * n, b, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                            s)) != cudaSuccess)
     return e;
-  // G, A_r and its LU
+  // G, A_r and its inverse (committed only through an open gate)
   ++g_launches;
   build_gx_kernel<<<1, 256, 0, s>>>(r, sc);
   ++g_launches;
   gx_times_vc_kernel<<<r + 1, 64, 0, s>>>(r, sc);
   ++g_launches;
-  uct_times_t_kernel<<<r + 1, 64, 0, s>>>(r, sc);
+  uct_times_t_kernel<<<r + 1, 64, 0, s>>>(r, sc, gate);
   ++g_launches;
-  inverse_kernel<<<1, 256, 0, s>>>(sc, R.S, R.lu);
+  inverse_kernel<<<1, 256, 0, s>>>(sc, R.S, R.lu, gate);
   // factors: Q' = [[Q,0],[0,1]] U_c or Q U_c(0:r) ; P' = [[P,0],[0,1]] V_c
   ++g_launches;
   factor_update_kernel<<<r + 1, 64, 0, s>>>(R.Q, R.wu, r, sc.Uc, sc.sc, -1, R.Qtmp);
   ++g_launches;
   factor_update_kernel<<<r + 1, 64, 0, s>>>(R.P, R.ww, r, sc.Vc, sc.sc, 1, R.Ptmp);
+  ++g_launches;
+  factor_commit_kernel<<<8, 256, 0, s>>>(R.Qtmp, R.Q, R.wu, R.Ptmp, R.P, R.ww, sc.sc, gate);
+  ++g_launches;
+  append_finish_kernel<<<1, 32, 0, s>>>(r, R.wu, R.ww, sc.sc, gate, R.dstate);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  double h[8];
-  if ((e = cudaMemcpyAsync(h, sc.sc, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  std::swap(R.Q, R.Qtmp);
-  std::swap(R.P, R.Ptmp);
-  const bool g = h[5] != 0.0;
-  R.rank = (int)h[4];
-  R.wu += g ? 1 : 0;
-  R.ww += 1;
-  R.lu_ok = (h[7] != 0.0) ? 1 : 0;
-  if (R.wu >= WCAP - 1 || R.ww >= WCAP - 1) {
-    if ((e = compact(R, s)) != cudaSuccess) return e;
-  }
-  if (grew) *grew = g;
+  return cudaMemcpyAsync(R.hstate, R.dstate, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t rom_commit(RomDev& R, int* ran, int* grew, double* ratio, cudaStream_t s) {
+  const double* h = R.hstate;
+  const bool on = h[5] != 0.0;
+  if (ran) *ran = on;
+  if (grew) *grew = h[4] != 0.0;
   if (ratio) *ratio = h[6];
+  if (!on) return cudaSuccess;
+  R.rank = (int)h[0];
+  R.wu = (int)h[1];
+  R.ww = (int)h[2];
+  R.lu_ok = (h[3] != 0.0) ? 1 : 0;
+  if (R.wu >= WCAP - 1 || R.ww >= WCAP - 1) return compact(R, s);
   return cudaSuccess;
+}
+
+cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc_eps, int* grew,
+                       double* ratio, cudaStream_t s) {
+  cudaError_t e = rom_append_async(R, x, b, trunc_eps, nullptr, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  return rom_commit(R, nullptr, grew, ratio, s);
 }
 
 cudaError_t rom_apply(RomDev& R, const double* rhs, double* out, cudaStream_t s) {
@@ -598,6 +646,8 @@ cudaError_t rom_alloc(RomDev& R, int n, int r_max) {
   if ((e = cudaMalloc(&R.partial, sizeof(double) * WCAP * (nbp > 256 ? nbp : 256))) != cudaSuccess)
     return e;
   if ((e = cudaMalloc(&R.sec, sizeof(double) * secular_scratch_doubles())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&R.dstate, sizeof(double) * 8)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&R.hstate, sizeof(double) * 8)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tall_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 TALL_SMEM)) != cudaSuccess)
     return e;
@@ -612,9 +662,10 @@ void rom_reset(RomDev& R) {
 
 void rom_free(RomDev& R) {
   double* d[] = {R.U, R.W, R.Utmp, R.Wtmp, R.Q, R.P, R.Qtmp, R.Ptmp, R.S, R.core, R.lu,
-                 R.proj, R.partial, R.sec};
+                 R.proj, R.partial, R.sec, R.dstate};
   for (double* p : d)
     if (p) cudaFree(p);
+  if (R.hstate) cudaFreeHost(R.hstate);
   if (R.piv) cudaFree(R.piv);
   R = RomDev{};
 }

@@ -39,11 +39,21 @@ struct rte_s {
   };
   std::vector<Span> spans;
   // second stream: the ROM update overlaps the fused f sweep
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t ev_rho = nullptr, ev_r0 = nullptr, ev_r1 = nullptr;
+  cudaStream_t st2 = nullptr, st3 = nullptr;   // st3: the PC-ROM's part of the update
+  cudaEvent_t ev_rho = nullptr, ev_r0 = nullptr, ev_r1 = nullptr, ev_gate = nullptr,
+              ev_pc = nullptr;
   Norms* h_norms = nullptr;   // pinned
   int* h_cg = nullptr;        // pinned, CG counts of one SI-SA solve
   int cg_slots = 0;
+  // ROM update queued on the device, finished on the host after the step's last wait
+  struct RomPending {
+    bool queued = false, ig = false, pc = false, ig_building = false, pc_building = false;
+    bool ig_err = false, pc_err = false;
+  } rom_pend;
+  double* rom_dv = nullptr;        // [4] device scalars of the indicators
+  double* h_rom_dv = nullptr;      // pinned copy
+  int* rom_gate = nullptr;         // [2] device gates (IG, PC)
+  double* rom_partials = nullptr;  // dot partials of the ROM stream
   // problem
   int dim = 2, nx = 0, ny = 0;
   long ncell = 0;
@@ -297,13 +307,19 @@ void free_all(rte_handle h) {
   dsa_free(h->dsa);
   rom_free(h->ig);
   rom_free(h->pc);
-  cudaEvent_t evs[] = {h->ev0, h->ev1, h->kev0, h->kev1, h->ev_rho, h->ev_r0, h->ev_r1};
+  cudaEvent_t evs[] = {h->ev0,    h->ev1,    h->kev0,    h->kev1, h->ev_rho,
+                       h->ev_r0, h->ev_r1, h->ev_gate, h->ev_pc};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   if (h->st2) cudaStreamDestroy(h->st2);
+  if (h->st3) cudaStreamDestroy(h->st3);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->h_cg) cudaFreeHost(h->h_cg);
+  if (h->h_rom_dv) cudaFreeHost(h->h_rom_dv);
+  if (h->rom_dv) cudaFree(h->rom_dv);
+  if (h->rom_gate) cudaFree(h->rom_gate);
+  if (h->rom_partials) cudaFree(h->rom_partials);
   if (h->own_st) cudaStreamDestroy(h->own_st);
 }
 
@@ -544,14 +560,6 @@ rte_status make_btilde(rte_handle h) {
   return RTE_OK;
 }
 
-rte_status dev_dot(rte_handle h, const double* x, const double* y, double* out) {
-  const int nb = vec_blocks((int)h->ncell);
-  CK(launch_dot(x, y, (int)h->ncell, h->partials, nb, h->dotbuf, h->st));
-  CK(cudaMemcpyAsync(out, h->dotbuf, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  return RTE_OK;
-}
-
 // ---------------------------------------------------------------------------------------
 // Device-time accounting without host waits: events are recorded into a per-handle pool as
 // the work is queued, and the spans between them are read once the step's work is done.
@@ -695,59 +703,86 @@ rte_status finish_cg_counts(rte_handle h) {
   return RTE_OK;
 }
 
-// ROM construction / adaptive update for the step just taken (Algorithm 2, Sec. 3.2).  Runs on
-// whatever stream h->st names; one_step gives it a second stream so that it overlaps the
-// fused f sweep, which neither reads nor writes what it uses.
-rte_status rom_update(rte_handle h) {
+// ROM construction / adaptive update for the step just taken (Algorithm 2, Sec. 3.2), in
+// two halves.  rom_update_enqueue queues every product, indicator and append on h->st
+// without waiting: the indicator tests of Phase 3 become device gates that leave a ROM
+// unchanged when closed.  rom_update_finish runs after the stream has passed that work and
+// folds the outcome into the host view (ranks, Flag_IG / Flag_PC, statistics).  one_step
+// runs the first half on a second stream beside the fused f sweep, which neither reads nor
+// writes what it uses.
+rte_status rom_update_enqueue(rte_handle h) {
   const int n = (int)h->ncell;
-  double rn2 = 0.0;
-  TRY(dev_dot(h, h->rho, h->rho, &rn2));
-  const double thr = h->opt.eps_up * (h->opt.up_rel ? std::sqrt(rn2) : 1.0);
-  bool ig_up = false, pc_up = false;
-  h->stats.last_ig_error = NAN;
-  h->stats.last_pc_error = NAN;
-  int grew = 0;
-  double ratio = 0.0;
+  const int nb = vec_blocks(n);
+  auto& pd = h->rom_pend;
+  pd = rte_s::RomPending{};
+  double* dv = h->rom_dv;   // [0] ||rho^n||^2  [1] IG indicator^2  [2] PC indicator^2
+  double* part_pc = h->rom_partials + 3 * 1024;
+  CK(launch_dot(h->rho, h->rho, n, h->rom_partials, nb, dv + 0, h->st));
   if (!h->flag_ig) {
-    CK(rom_append(h->ig, h->rho, h->btilde, -1.0, &grew, &ratio, h->st));
-    ig_up = true;
-    if (ratio <= h->opt.eps_ig || h->ig.rank >= h->opt.r_max) h->flag_ig = true;
+    // Phase 1: the IG-ROM takes every snapshot pair (rho^n, b~^{n-1}), untruncated
+    CK(rom_append_async(h->ig, h->rho, h->btilde, -1.0, nullptr, h->st));
+    pd.ig = pd.ig_building = true;
   } else {
-    double e2 = INFINITY;
     if (h->ig_applied) {
       CK(launch_axpby(1.0, h->rho0, -1.0, h->rho, n, h->tmp, h->st));
-      TRY(dev_dot(h, h->tmp, h->tmp, &e2));
-      h->stats.last_ig_error = std::sqrt(e2);
+      CK(launch_dot(h->tmp, h->tmp, n, h->rom_partials, nb, dv + 1, h->st));
     }
-    if (!(std::sqrt(e2) <= thr)) {
-      CK(rom_append(h->ig, h->rho, h->btilde, h->opt.eps_ig, &grew, &ratio, h->st));
-      ig_up = true;
-    }
+    CK(launch_rom_gate(dv + 1, dv + 0, h->opt.eps_up, h->opt.up_rel, !h->ig_applied, nullptr,
+                       h->rom_gate + 0, h->st));
+    // The PC-ROM's work depends on the IG gate only: it runs on a third stream beside the
+    // IG append (its own scratch: tmp2, tmp3, delta, the second partials block).
+    CK(cudaEventRecord(h->ev_gate, h->st));
+    CK(cudaStreamWaitEvent(h->st3, h->ev_gate, 0));
+    CK(rom_append_async(h->ig, h->rho, h->btilde, h->opt.eps_ig, h->rom_gate + 0, h->st));
+    pd.ig = true;
+    pd.ig_err = h->ig_applied;
     const bool has_corr = h->last_iters > 1;
+    cudaStream_t s3 = h->st3;
     // d_rho1 = rho^n - rho^{n,1/2} (tmp2), d_b1 = rho^{n,1/2} - rho^{n,(0)} (tmp3)
-    CK(launch_axpby(1.0, h->rho, -1.0, h->rho_half1, n, h->tmp2, h->st));
-    CK(launch_axpby(1.0, h->rho_half1, -1.0, h->rho0, n, h->tmp3, h->st));
+    CK(launch_axpby(1.0, h->rho, -1.0, h->rho_half1, n, h->tmp2, s3));
+    CK(launch_axpby(1.0, h->rho_half1, -1.0, h->rho0, n, h->tmp3, s3));
     if (!h->flag_pc) {
-      if (has_corr) {
-        CK(rom_append(h->pc, h->tmp2, h->tmp3, -1.0, &grew, &ratio, h->st));
-        pc_up = true;
-        if (ratio <= h->opt.eps_pc || h->pc.rank >= h->opt.r_max) h->flag_pc = true;
+      if (has_corr) {   // Phase 2: the PC-ROM takes every correction pair, untruncated
+        CK(rom_append_async(h->pc, h->tmp2, h->tmp3, -1.0, nullptr, s3));
+        pd.pc = pd.pc_building = true;
       }
     } else if (has_corr) {
-      double p2 = INFINITY;
       if (h->pc_applied) {
-        CK(launch_axpby(1.0, h->delta_pc1, -1.0, h->tmp2, n, h->tmp, h->st));
-        TRY(dev_dot(h, h->tmp, h->tmp, &p2));
-        h->stats.last_pc_error = std::sqrt(p2);
+        CK(launch_axpby(1.0, h->delta_pc1, -1.0, h->tmp2, n, h->delta, s3));
+        CK(launch_dot(h->delta, h->delta, n, part_pc, nb, dv + 2, s3));
       }
-      if (ig_up || !(std::sqrt(p2) <= thr)) {
-        CK(rom_append(h->pc, h->tmp2, h->tmp3, h->opt.eps_pc, &grew, &ratio, h->st));
-        pc_up = true;
-      }
+      CK(launch_rom_gate(dv + 2, dv + 0, h->opt.eps_up, h->opt.up_rel, !h->pc_applied,
+                         h->rom_gate + 0, h->rom_gate + 1, s3));
+      CK(rom_append_async(h->pc, h->tmp2, h->tmp3, h->opt.eps_pc, h->rom_gate + 1, s3));
+      pd.pc = true;
+      pd.pc_err = h->pc_applied;
     }
+    CK(cudaEventRecord(h->ev_pc, s3));
+    CK(cudaStreamWaitEvent(h->st, h->ev_pc, 0));
   }
-  h->stats.ig_updated = ig_up;
-  h->stats.pc_updated = pc_up;
+  CK(cudaMemcpyAsync(h->h_rom_dv, dv, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->st));
+  pd.queued = true;
+  return RTE_OK;
+}
+
+rte_status rom_update_finish(rte_handle h) {
+  auto& pd = h->rom_pend;
+  if (!pd.queued) return RTE_OK;
+  pd.queued = false;
+  int ig_ran = 0, pc_ran = 0;
+  double ratio = 0.0;
+  if (pd.ig) {
+    CK(rom_commit(h->ig, &ig_ran, nullptr, &ratio, h->st));
+    if (pd.ig_building && (ratio <= h->opt.eps_ig || h->ig.rank >= h->opt.r_max)) h->flag_ig = true;
+  }
+  if (pd.pc) {
+    CK(rom_commit(h->pc, &pc_ran, nullptr, &ratio, h->st));
+    if (pd.pc_building && (ratio <= h->opt.eps_pc || h->pc.rank >= h->opt.r_max)) h->flag_pc = true;
+  }
+  h->stats.last_ig_error = pd.ig_err ? std::sqrt(h->h_rom_dv[1]) : NAN;
+  h->stats.last_pc_error = pd.pc_err ? std::sqrt(h->h_rom_dv[2]) : NAN;
+  h->stats.ig_updated = ig_ran;
+  h->stats.pc_updated = pc_ran;
   h->stats.ig_rank = h->ig.rank;
   h->stats.pc_rank = h->pc.rank;
   return RTE_OK;
@@ -798,7 +833,7 @@ rte_status one_step(rte_handle h) {
     cudaStream_t main = h->st;
     h->st = h->st2;
     cudaEventRecord(h->ev_r0, h->st2);
-    rom_status = rom_update(h);
+    rom_status = rom_update_enqueue(h);
     cudaEventRecord(h->ev_r1, h->st2);
     h->st = main;
     CK(cudaStreamWaitEvent(h->st, h->ev_r1, 0));   // the next step applies the updated ROMs
@@ -807,12 +842,13 @@ rte_status one_step(rte_handle h) {
   CK(cudaStreamSynchronize(h->st));
   resolve_spans(h);
   TRY(finish_cg_counts(h));
+  TRY(rom_status);
   if (rom_ran) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev_r0, h->ev_r1) == cudaSuccess) h->stats.time_rom_ms += ms;
+    TRY(rom_update_finish(h));
   }
   TRY(check_sweep_error(h));
-  TRY(rom_status);
   h->stats.phase = phase;
   h->stats.steps += 1;
   h->stats.last_iterations = iters;
@@ -846,6 +882,7 @@ rte_status reset_state(rte_handle h) {
     CK(cudaStreamSynchronize(h->st));
   }
   h->stats = rte_stats{};
+  h->rom_pend = rte_s::RomPending{};
   h->flag_ig = h->flag_pc = false;
   h->y_valid = false;
   h->pending_rom = false;
@@ -1162,11 +1199,19 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(cudaEventCreate(&h->kev0));
   CK(cudaEventCreate(&h->kev1));
   CK(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&h->st3, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_gate, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_pc, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_rho, cudaEventDisableTiming));
   CK(cudaEventCreate(&h->ev_r0));
   CK(cudaEventCreate(&h->ev_r1));
   CK(cudaMallocHost((void**)&h->h_norms, sizeof(Norms)));
   CK(cudaMallocHost((void**)&h->h_cg, sizeof(int) * (h->opt.max_iter + 2)));
+  CK(cudaMallocHost((void**)&h->h_rom_dv, sizeof(double) * 4));
+  CK(cudaMalloc((void**)&h->rom_dv, sizeof(double) * 4));
+  CK(cudaMemset(h->rom_dv, 0, sizeof(double) * 4));
+  CK(cudaMalloc((void**)&h->rom_gate, sizeof(int) * 2));
+  CK(dalloc(&h->rom_partials, 2 * 3 * 1024));
   // data that does not depend on the direction layout
   CK(dalloc(&h->sig_t, n));
   CK(dalloc(&h->sig_s, n));
@@ -1348,13 +1393,15 @@ rte_status rte_rom_update(rte_handle h) {
   h->pending_rom = false;
   const long long l0 = g_launches;
   cudaEventRecord(h->ev_r0, h->st);
-  rte_status s = rom_update(h);
+  rte_status s = rom_update_enqueue(h);
   cudaEventRecord(h->ev_r1, h->st);
   h->stats.kernel_launches += g_launches - l0;
   if (s != RTE_OK) return s;
   CK(cudaStreamSynchronize(h->st));
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, h->ev_r0, h->ev_r1) == cudaSuccess) h->stats.time_rom_ms += ms;
+  TRY(rom_update_finish(h));
+  CK(cudaStreamSynchronize(h->st));   // a compaction queued by the commit
   return RTE_OK;
 }
 

@@ -116,6 +116,8 @@ cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, int dl, 
 cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
                        double* out, cudaStream_t s);
 int vec_blocks(int n);
+cudaError_t launch_rom_gate(const double* e2, const double* n2, double eps_up, int rel, int force,
+                            const int* also, int* gate, cudaStream_t s);
 // Sources of the sweeps in their precision (FP32 mode: float).
 template <class Real>
 cudaError_t launch_scaled_diff(const double* x, const double* xref, const double* sig_s, int n,
@@ -178,6 +180,8 @@ struct RomDev {
   double* proj;   // [2*(r_max+1)] projections and reduced coordinates
   double* partial;
   double* sec;    // scratch of the core SVD
+  double* dstate; // [8] outcome of the last append (device), see rom_append_async
+  double* hstate; // [8] pinned host copy of it
   int lu_ok;
 };
 // SVD of the core [[diag(S), p], [0, alpha]] (csvd.cu); alpha^2 and ||x||^2 in sc[1], sc[0];
@@ -189,9 +193,18 @@ cudaError_t core_svd_secular(const double* S, int r, const double* p, double* sc
 cudaError_t rom_alloc(RomDev& R, int n, int r_max);
 void rom_free(RomDev& R);
 void rom_reset(RomDev& R);   // empty ROM (rank 0), keeps the allocation
-// Incremental SVD append (App. B).  Returns new rank in *rank_out (host), grew flag.
+// Incremental SVD append (App. B), synchronous: updates the host view (rank, columns in
+// use, lu_ok) before returning, with the grew flag and the stop ratio s_last / sum s.
 cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc_eps,
                        int* grew, double* smallest_ratio, cudaStream_t s);
+// The same append queued without any host wait.  gate: device int, 0 = leave the ROM as it
+// is (the work still runs, into scratch), nullptr = always.  The host view is stale until
+// rom_commit runs after the stream has passed the append.
+cudaError_t rom_append_async(RomDev& R, const double* x, const double* b, double trunc_eps,
+                             const int* gate, cudaStream_t s);
+// Folds the outcome of the last rom_append_async into the host view (compacting the factored
+// bases when full, queued on s); ran = the gate was open.
+cudaError_t rom_commit(RomDev& R, int* ran, int* grew, double* smallest_ratio, cudaStream_t s);
 // out = U A_r^{-1} U^T rhs.  Returns cudaErrorInvalidValue if the LU is not available.
 cudaError_t rom_apply(RomDev& R, const double* rhs, double* out, cudaStream_t s);
 cudaError_t rom_get(RomDev& R, double* S, double* U, double* Ar, cudaStream_t s);

@@ -295,6 +295,25 @@ cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, int dl, doub
   return cudaGetLastError();
 }
 
+namespace {
+// ROM update gate of Algorithm 2: open when forced, when the gate it follows is open, or when
+// the indicator sqrt(e2) exceeds eps_up (times ||rho|| = sqrt(n2) when relative).
+__global__ void rom_gate_kernel(const double* e2, const double* n2, double eps_up, int rel,
+                                int force, const int* also, int* gate) {
+  if (threadIdx.x != 0) return;
+  const double thr = eps_up * (rel ? sqrt(*n2) : 1.0);
+  const bool open = force || (also && *also != 0) || !(sqrt(*e2) <= thr);
+  *gate = open ? 1 : 0;
+}
+}  // namespace
+
+cudaError_t launch_rom_gate(const double* e2, const double* n2, double eps_up, int rel, int force,
+                            const int* also, int* gate, cudaStream_t s) {
+  ++g_launches;
+  rom_gate_kernel<<<1, 32, 0, s>>>(e2, n2, eps_up, rel, force, also, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
                        double* out, cudaStream_t s) {
   ++g_launches;
