@@ -233,6 +233,45 @@ rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, 
                                  double cg_rtol, int cg_max_iter, double* delta_dev,
                                  int* iterations, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched instances.  Many independent problems (their own grid, quadrature, cross
+ * sections, c_dt and initial flux) marched side by side on one GPU: every instance is a
+ * full rte_handle on its own CUDA streams, and rte_batch_step steps all of them
+ * concurrently, one host thread per instance, so that their kernels overlap on the device
+ * (small grids leave most SMs idle on their own).  Algorithm 2 runs per instance, exactly
+ * as rte_step would run it.
+ * ------------------------------------------------------------------------------------- */
+typedef struct rte_batch_s* rte_batch;
+
+typedef struct {
+  rte_mesh mesh;
+  rte_quadrature quad;
+  const double* sigma_t;   /* host [ncell] */
+  const double* sigma_s;   /* host [ncell] */
+  const double* source;    /* host [ncell] */
+  const double* rho0;      /* host [ncell]: isotropic initial flux f0 = rho0, or NULL (zero) */
+  double c_dt;
+} rte_problem;
+
+/* Create `count` instances (1 .. 4096) with the same options (NULL = defaults).  Arrays are
+ * copied.  On failure nothing is kept; rte_last_error(NULL) names the failing instance. */
+rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* problems,
+                            const rte_options* opt);
+/* nsteps implicit steps of every instance, concurrently.  Returns the first non-OK status
+ * in instance order (RTE_ENOCONV, RTE_ECUDA, ...); each instance's own status and message
+ * stay available through rte_batch_status and rte_last_error(rte_batch_instance(b, i)). */
+rte_status rte_batch_step(rte_batch b, int nsteps);
+/* Back to every instance's initial state (rte_restart on each). */
+rte_status rte_batch_restart(rte_batch b);
+int rte_batch_size(rte_batch b);
+/* The handle of instance i (owned by the batch; valid until rte_batch_destroy) for the
+ * per-instance calls (rte_get_scalar_flux, rte_get_stats, rte_set_inflow, ...) between
+ * batch steps; NULL when i is out of range. */
+rte_handle rte_batch_instance(rte_batch b, int i);
+/* Status of instance i in the last rte_batch_step (RTE_EINVAL when i is out of range). */
+rte_status rte_batch_status(rte_batch b, int i);
+void rte_batch_destroy(rte_batch b);   /* NULL-safe */
+
 #ifdef __cplusplus
 }
 #endif

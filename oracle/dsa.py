@@ -9,9 +9,14 @@ limit (Sec. 2, D = 1/(3 sigma)) is
 
 The paper's fully consistent DSA belongs to its Q1 scheme and is given only by citation
 (Sec. 4); for the Q0 scheme the oracle uses the cell-centred 5-point (1D: 3-point)
-discretisation with harmonic-mean face coefficients 2 D_L D_R / ((D_L + D_R) h^2) and a
-Marshak vacuum condition on every boundary face (outgoing current rho_b / 2 in the
-normalisation sum_j w_j = 1), whose cell term is 1 / (h (2 + h / (2 D))).
+discretisation with harmonic-mean face couplings and a Marshak vacuum condition on every
+boundary face (outgoing current rho_b / 2 in the normalisation sum_j w_j = 1), each floored
+at the coupling the upwind Q0 sweep itself applies to an isotropic flux across a face, the
+half-range current sum_{Omega.n > 0} w Omega.n = 1/4 (the interior-penalty floor of the
+modified-interior-penalty diffusion form for piecewise constants):
+    interior face:  max(2 D_L D_R / ((D_L + D_R) h), 1/4) / h
+    vacuum face:    max(1 / (2 + h / (2 D)), 1/4) / h.
+Without the floor the operator under-couples optically thick cells and SI-DSA can diverge.
 The linear system is solved by conjugate gradients (Sec. 4 uses CG).
 """
 import numpy as np
@@ -29,8 +34,11 @@ def dsa_matrix(p):
     idx = np.arange(nx * ny).reshape(ny, nx)
 
     def faces(DL, DR, h, iL, iR):
-        c = 2.0 * DL * DR / ((DL + DR) * h * h)
+        c = np.maximum(2.0 * DL * DR / ((DL + DR) * h), 0.25) / h
         return c, iL, iR
+
+    def vacuum(Db, h):
+        return np.maximum(1.0 / (2.0 + h / (2.0 * Db)), 0.25) / h
 
     hx = p.hx
     # x faces
@@ -41,8 +49,8 @@ def dsa_matrix(p):
         rows += [iL.ravel(), iR.ravel()]
         cols += [iR.ravel(), iL.ravel()]
         vals += [-c.ravel(), -c.ravel()]
-    diag[:, 0] += 1.0 / (hx * (2.0 + hx / (2.0 * D[:, 0])))
-    diag[:, -1] += 1.0 / (hx * (2.0 + hx / (2.0 * D[:, -1])))
+    diag[:, 0] += vacuum(D[:, 0], hx)
+    diag[:, -1] += vacuum(D[:, -1], hx)
     if p.dim == 2:
         hy = p.hy
         if ny > 1:
@@ -52,8 +60,8 @@ def dsa_matrix(p):
             rows += [iL.ravel(), iR.ravel()]
             cols += [iR.ravel(), iL.ravel()]
             vals += [-c.ravel(), -c.ravel()]
-        diag[0, :] += 1.0 / (hy * (2.0 + hy / (2.0 * D[0, :])))
-        diag[-1, :] += 1.0 / (hy * (2.0 + hy / (2.0 * D[-1, :])))
+        diag[0, :] += vacuum(D[0, :], hy)
+        diag[-1, :] += vacuum(D[-1, :], hy)
     rows.append(idx.ravel())
     cols.append(idx.ravel())
     vals.append(diag.ravel())

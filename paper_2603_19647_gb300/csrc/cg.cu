@@ -204,8 +204,8 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
     D[c] = 1.0 / (3.0 * (sig_t[c] + tau));
     diag[c] = sig_t[c] - sig_s[c] + tau;
   }
-  auto face = [](double dl, double dr, double h) { return 2.0 * dl * dr / ((dl + dr) * h * h); };
-  auto marshak = [](double d, double h) { return 1.0 / (h * (2.0 + h / (2.0 * d))); };
+  auto face = [](double dl, double dr, double h) { return fmax(2.0 * dl * dr / ((dl + dr) * h), 0.25) / h; };
+  auto marshak = [](double d, double h) { return fmax(1.0 / (2.0 + h / (2.0 * d)), 0.25) / h; };
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       const int c = i + nx * j;
@@ -326,8 +326,8 @@ __global__ void dsa_coeff_kernel(int dim, int nx, int ny, double hx, double hy, 
   if (c >= n) return;
   const int i = c % nx, j = c / nx;
   auto D = [&](int k) { return 1.0 / (3.0 * (sig_t[k] + tau)); };
-  auto face = [](double dl, double dr, double h) { return 2.0 * dl * dr / ((dl + dr) * h * h); };
-  auto marshak = [](double d, double h) { return 1.0 / (h * (2.0 + h / (2.0 * d))); };
+  auto face = [](double dl, double dr, double h) { return fmax(2.0 * dl * dr / ((dl + dr) * h), 0.25) / h; };
+  auto marshak = [](double d, double h) { return fmax(1.0 / (2.0 + h / (2.0 * d)), 0.25) / h; };
   const double dc = D(c);
   double dg = sig_t[c] - sig_s[c] + tau;
   double fx = 0.0, fy = 0.0;

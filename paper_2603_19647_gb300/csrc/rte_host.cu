@@ -16,6 +16,7 @@
 #include <tuple>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rte_internal.h"
@@ -45,6 +46,9 @@ struct rte_s {
   Norms* h_norms = nullptr;   // pinned
   int* h_cg = nullptr;        // pinned, CG counts of one SI-SA solve
   int cg_slots = 0;
+  bool blocking = false;             // wait on ev_wait (sleeping) instead of spinning
+  cudaEvent_t ev_wait = nullptr;     // blocking-sync event
+  unsigned* h_err = nullptr;         // pinned copy of the sweeps' error word
   // ROM update queued on the device, finished on the host after the step's last wait
   struct RomPending {
     bool queued = false, ig = false, pc = false, ig_building = false, pc_building = false;
@@ -316,6 +320,8 @@ void free_all(rte_handle h) {
   if (h->st3) cudaStreamDestroy(h->st3);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->h_cg) cudaFreeHost(h->h_cg);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->ev_wait) cudaEventDestroy(h->ev_wait);
   if (h->h_rom_dv) cudaFreeHost(h->h_rom_dv);
   if (h->rom_dv) cudaFree(h->rom_dv);
   if (h->rom_gate) cudaFree(h->rom_gate);
@@ -512,6 +518,45 @@ rte_status sweep_y(rte_handle h, double* y_out) {
   return RTE_OK;
 }
 
+// Wait for the handle's stream.  Batched instances (each stepped by its own host thread)
+// wait on a blocking-sync event so that the thread sleeps instead of spinning.
+rte_status host_wait(rte_handle h) {
+  if (h->blocking) {
+    CK(cudaEventRecord(h->ev_wait, h->st));
+    CK(cudaEventSynchronize(h->ev_wait));
+  } else {
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return RTE_OK;
+}
+
+// The sweeps' error word (a bounded wait that ran out), copied to pinned memory with the
+// step's other results; check_sweep_error_after reads it once the stream has been waited for.
+// The same for the CG's grid barrier (word 2 of its barrier block).
+rte_status queue_sweep_error(rte_handle h) {
+  if (h->dim == 2)
+    CK(cudaMemcpyAsync(h->h_err, &h->ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_err + 1, reinterpret_cast<unsigned*>(h->dsa.scal) + 2, sizeof(unsigned),
+                     cudaMemcpyDeviceToHost, h->st));
+  return RTE_OK;
+}
+rte_status check_sweep_error_after(rte_handle h) {
+  if (h->dim == 2 && h->h_err[0]) {
+    h->h_err[0] = 0;
+    const size_t bytes = sizeof(SweepCtrl) + sizeof(unsigned) * h->L.nfam * h->nblk_max;
+    CK(cudaMemsetAsync(h->ctrl, 0, bytes, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return fail(h, RTE_ETIMEOUT, "a bounded wait in the sweep ran out");
+  }
+  if (h->h_err[1]) {
+    h->h_err[1] = 0;
+    CK(cudaMemsetAsync(h->dsa.scal, 0, 4 * sizeof(unsigned), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return fail(h, RTE_ETIMEOUT, "a bounded grid-barrier wait in the DSA solve ran out");
+  }
+  return RTE_OK;
+}
+
 rte_status check_sweep_error(rte_handle h) {
   unsigned err = 0;
   if (h->dim == 2) {
@@ -649,7 +694,7 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
     if (l == 1)
       CK(cudaMemcpyAsync(h->rho_half1, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                          h->st));
-    CK(cudaStreamSynchronize(h->st));
+    TRY(host_wait(h));
     const Norms nm = *h->h_norms;
     const double res = h->opt.residual_norm == RTE_ABS_INF
                            ? nm.diff_inf
@@ -839,7 +884,8 @@ rte_status one_step(rte_handle h) {
     CK(cudaStreamWaitEvent(h->st, h->ev_r1, 0));   // the next step applies the updated ROMs
     rom_ran = true;
   }
-  CK(cudaStreamSynchronize(h->st));
+  TRY(queue_sweep_error(h));
+  TRY(host_wait(h));
   resolve_spans(h);
   TRY(finish_cg_counts(h));
   TRY(rom_status);
@@ -848,7 +894,7 @@ rte_status one_step(rte_handle h) {
     if (cudaEventElapsedTime(&ms, h->ev_r0, h->ev_r1) == cudaSuccess) h->stats.time_rom_ms += ms;
     TRY(rom_update_finish(h));
   }
-  TRY(check_sweep_error(h));
+  TRY(check_sweep_error_after(h));
   h->stats.phase = phase;
   h->stats.steps += 1;
   h->stats.last_iterations = iters;
@@ -1147,9 +1193,10 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
   return RTE_OK;
 }
 
-rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature* quad,
-                       const double* sigma_t, const double* sigma_s, const double* source,
-                       double c_dt, const rte_options* opt) {
+// Host-side checks of rte_create (no device work): options, mesh, cross sections, rule.
+rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature* quad,
+                         const double* sigma_t, const double* sigma_s, const double* source,
+                         double c_dt, const rte_options* opt) {
   if (!mesh || !quad || !sigma_t || !sigma_s || !source)
     return fail(h, RTE_EINVAL, "mesh, quadrature and cross-section arrays are required");
   h->opt = opt ? *opt : rte_options{};
@@ -1191,6 +1238,14 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
       return fail(h, RTE_EINVAL, "need sigma_t >= sigma_s >= 0 in every cell");
   TRY(make_rule(h, quad, h->dim));
   TRY(make_layout(h, 0));   // validates the directions before any device work
+  return RTE_OK;
+}
+
+rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature* quad,
+                       const double* sigma_t, const double* sigma_s, const double* source,
+                       double c_dt, const rte_options* opt) {
+  TRY(validate_impl(h, mesh, quad, sigma_t, sigma_s, source, c_dt, opt));
+  const long n = h->ncell;
   CK(cudaGetDevice(&h->device));
   CK(cudaStreamCreateWithFlags(&h->own_st, cudaStreamNonBlocking));
   h->st = h->own_st;
@@ -1208,6 +1263,9 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(cudaMallocHost((void**)&h->h_norms, sizeof(Norms)));
   CK(cudaMallocHost((void**)&h->h_cg, sizeof(int) * (h->opt.max_iter + 2)));
   CK(cudaMallocHost((void**)&h->h_rom_dv, sizeof(double) * 4));
+  CK(cudaMallocHost((void**)&h->h_err, 2 * sizeof(unsigned)));
+  h->h_err[0] = h->h_err[1] = 0;
+  CK(cudaEventCreateWithFlags(&h->ev_wait, cudaEventBlockingSync | cudaEventDisableTiming));
   CK(cudaMalloc((void**)&h->rom_dv, sizeof(double) * 4));
   CK(cudaMemset(h->rom_dv, 0, sizeof(double) * 4));
   CK(cudaMalloc((void**)&h->rom_gate, sizeof(int) * 2));
@@ -1581,6 +1639,111 @@ rte_status rte_op_rom_reset(rte_handle h) {
   rom_reset(h->pc);
   h->flag_ig = h->flag_pc = false;
   return RTE_OK;
+}
+
+}  // extern "C"
+
+// =========================================================================================
+// Batched instances: one full handle per problem, stepped by one host thread each.
+// =========================================================================================
+struct rte_batch_s {
+  std::vector<rte_handle> h;
+  std::vector<rte_status> status;
+};
+
+extern "C" {
+
+rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* problems,
+                            const rte_options* opt) {
+  if (!out) return RTE_EINVAL;
+  *out = nullptr;
+  if (count < 1 || count > 4096 || !problems) {
+    g_create_error = "count must be in [1, 4096] and problems non-NULL";
+    return RTE_EINVAL;
+  }
+  rte_batch b = new (std::nothrow) rte_batch_s();
+  if (!b) return RTE_ENOMEM;
+  b->h.assign(count, nullptr);
+  b->status.assign(count, RTE_OK);
+  for (int i = 0; i < count; ++i) {   // every instance's host-side checks first
+    const rte_problem& p = problems[i];
+    rte_s probe;
+    const rte_status s = validate_impl(&probe, &p.mesh, &p.quad, p.sigma_t, p.sigma_s, p.source,
+                                       p.c_dt, opt);
+    if (s != RTE_OK) {
+      g_create_error = "instance " + std::to_string(i) + ": " + probe.err;
+      delete b;
+      return s;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    const rte_problem& p = problems[i];
+    rte_status s = rte_create(&b->h[i], &p.mesh, &p.quad, p.sigma_t, p.sigma_s, p.source, p.c_dt,
+                              opt);
+    if (s == RTE_OK) {
+      b->h[i]->blocking = true;
+      if (p.rho0) {
+        s = rte_set_initial(b->h[i], p.rho0, nullptr);
+      } else {
+        std::vector<double> z((size_t)b->h[i]->ncell, 0.0);
+        s = rte_set_initial(b->h[i], z.data(), nullptr);
+      }
+      if (s != RTE_OK) g_create_error = b->h[i]->err;
+    }
+    if (s != RTE_OK) {
+      g_create_error = "instance " + std::to_string(i) + ": " + g_create_error;
+      rte_batch_destroy(b);
+      return s;
+    }
+  }
+  *out = b;
+  return RTE_OK;
+}
+
+rte_status rte_batch_step(rte_batch b, int nsteps) {
+  if (!b) return RTE_EINVAL;
+  if (nsteps < 0) return RTE_EINVAL;
+  const int count = (int)b->h.size();
+  std::vector<std::thread> th;
+  th.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    th.emplace_back([b, i, nsteps]() {
+      rte_handle h = b->h[i];
+      if (cudaSetDevice(h->device) != cudaSuccess) {
+        b->status[i] = RTE_ECUDA;
+        return;
+      }
+      b->status[i] = rte_step(h, nsteps);
+    });
+  }
+  for (auto& t : th) t.join();
+  for (int i = 0; i < count; ++i)
+    if (b->status[i] != RTE_OK) return b->status[i];
+  return RTE_OK;
+}
+
+rte_status rte_batch_restart(rte_batch b) {
+  if (!b) return RTE_EINVAL;
+  for (rte_handle h : b->h) TRY(rte_restart(h));
+  return RTE_OK;
+}
+
+int rte_batch_size(rte_batch b) { return b ? (int)b->h.size() : 0; }
+
+rte_handle rte_batch_instance(rte_batch b, int i) {
+  if (!b || i < 0 || i >= (int)b->h.size()) return nullptr;
+  return b->h[i];
+}
+
+rte_status rte_batch_status(rte_batch b, int i) {
+  if (!b || i < 0 || i >= (int)b->h.size()) return RTE_EINVAL;
+  return b->status[i];
+}
+
+void rte_batch_destroy(rte_batch b) {
+  if (!b) return;
+  for (rte_handle h : b->h) rte_destroy(h);
+  delete b;
 }
 
 }  // extern "C"

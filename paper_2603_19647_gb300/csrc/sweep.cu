@@ -19,6 +19,8 @@
 // evaluated as a block-wide associative scan of affine maps.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "rte_internal.h"
 
 namespace rte {
@@ -482,8 +484,8 @@ cudaError_t launch_dl_r(const Sweep2DArgs<Real>& a, cudaStream_t s) {
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto kern = table ? sweep2d_kernel<Real, DL, R, KSTEP, MODE, true>
                     : sweep2d_kernel<Real, DL, R, KSTEP, MODE, false>;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[table]) {
+  static std::atomic<bool> attr_set[2] = {false, false};   // host threads of a batch share it
+  if (!attr_set[table].load()) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set[table] = true;

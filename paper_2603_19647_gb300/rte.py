@@ -42,6 +42,11 @@ class Quadrature(ctypes.Structure):
                 ("n_dirs", ctypes.c_int), ("mu", _dp), ("eta", _dp), ("w", _dp)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("mesh", Mesh), ("quad", Quadrature), ("sigma_t", _dp), ("sigma_s", _dp),
+                ("source", _dp), ("rho0", _dp), ("c_dt", ctypes.c_double)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("eps_sisa", ctypes.c_double), ("eps_ig", ctypes.c_double),
                 ("eps_pc", ctypes.c_double), ("eps_up", ctypes.c_double),
@@ -99,6 +104,14 @@ _SIGS = {
     "rte_op_rom_apply": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "rte_op_rom_get": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp, _dp, _dp]),
     "rte_op_rom_reset": (ctypes.c_int, [_vp]),
+    "rte_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(Problem),
+                                        ctypes.POINTER(Options)]),
+    "rte_batch_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rte_batch_restart": (ctypes.c_int, [_vp]),
+    "rte_batch_size": (ctypes.c_int, [_vp]),
+    "rte_batch_instance": (_vp, [_vp, ctypes.c_int]),
+    "rte_batch_status": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rte_batch_destroy": (None, [_vp]),
     "rte_dsa_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _vp, _vp, _vp, ctypes.c_double,
@@ -157,9 +170,9 @@ class Handle:
 
     # lifecycle -----------------------------------------------------------------------
     def rte_destroy(self):
-        if self.ptr:
+        if self.ptr and not getattr(self, "_owned_by_batch", False):
             load().rte_destroy(self.ptr)
-            self.ptr = None
+        self.ptr = None
 
     destroy = rte_destroy
 
@@ -321,3 +334,72 @@ def create_from_workload(wl, options=None, quad=None):
     if np.any(wl.inflow):
         h.rte_set_inflow(wl.inflow)
     return h
+
+
+class Batch:
+    """Batched instances (``rte_batch``): independent problems stepped side by side."""
+
+    def __init__(self, ptr, handles, keep):
+        self.ptr = ptr
+        self.handles = handles
+        self._keep = keep
+
+    def rte_batch_step(self, nsteps=1):
+        status = load().rte_batch_step(self.ptr, int(nsteps))
+        if status != RTE_OK:
+            bad = [i for i in range(len(self.handles)) if load().rte_batch_status(self.ptr, i) != RTE_OK]
+            msg = load().rte_last_error(self.handles[bad[0]].ptr).decode() if bad else ""
+            raise RteError(status, f"instance {bad[0] if bad else '?'}: {msg}")
+
+    def rte_batch_restart(self):
+        status = load().rte_batch_restart(self.ptr)
+        if status != RTE_OK:
+            raise RteError(status, "rte_batch_restart")
+
+    def instance(self, i):
+        return self.handles[i]
+
+    def destroy(self):
+        if self.ptr:
+            load().rte_batch_destroy(self.ptr)
+            self.ptr = None
+            for h in self.handles:
+                h.ptr = None
+
+    def __len__(self):
+        return len(self.handles)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def rte_batch_create(workloads, options=None):
+    """rte_batch_create for a list of inputs.Workload (isotropic initial flux rho0 each)."""
+    lib = load()
+    n = len(workloads)
+    probs = (Problem * n)()
+    keep = []
+    for i, wl in enumerate(workloads):
+        nc = wl.nx * wl.ny
+        arrs = [_f64(wl.sigma_t, nc), _f64(wl.sigma_s, nc), _f64(wl.source, nc), _f64(wl.rho0, nc)]
+        q = quadrature_from(wl.quadrature)
+        keep.append((arrs, q))
+        probs[i] = Problem(mesh_from(wl), q, _p(arrs[0]), _p(arrs[1]), _p(arrs[2]), _p(arrs[3]),
+                           float(wl.c_dt))
+    b = _vp()
+    opt = ctypes.byref(options) if options is not None else None
+    status = lib.rte_batch_create(ctypes.byref(b), n, probs, opt)
+    if status != RTE_OK:
+        raise RteError(status, lib.rte_last_error(None).decode())
+    handles = []
+    for i, wl in enumerate(workloads):
+        hp = lib.rte_batch_instance(b, i)
+        nv = ctypes.c_int(0)
+        lib.rte_get_quadrature(hp, ctypes.byref(nv), None, None, None)
+        h = Handle(_vp(hp), wl.nx * wl.ny, nv.value)
+        h._owned_by_batch = True
+        handles.append(h)
+    return Batch(b, handles, keep)

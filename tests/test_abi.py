@@ -69,3 +69,15 @@ def test_invalid_problems_rejected(lib, bad):
         _create(**bad)
     assert ei.value.status == rte.RTE_EINVAL
     assert len(str(ei.value)) > 12
+
+
+def test_batch_create_rejects_bad_instance(lib):
+    """Validation of every instance happens before any device work; the message names the
+    failing instance."""
+    from paper_2603_19647_gb300 import inputs
+    wls = inputs.batched(count=3, seed=4, scale=0.05)
+    wls[1].sigma_s = wls[1].sigma_t + 1.0      # sigma_s > sigma_t
+    with pytest.raises(rte.RteError) as ei:
+        rte.rte_batch_create(wls)
+    assert ei.value.status == rte.RTE_EINVAL
+    assert "instance 1" in str(ei.value)

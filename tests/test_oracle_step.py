@@ -77,11 +77,14 @@ def test_dsa_matrix_and_cg(rng):
     x, its = dsa.cg(A, b, 1e-13, 1000)
     assert np.linalg.norm(x - np.linalg.solve(Ad, b)) < 1e-11 * np.linalg.norm(x)
     assert 0 < its < 256
-    # the Marshak term is the 1 / (h (2 + h / (2D))) of a vacuum face
+    # a vacuum face adds max(1 / (2 + h / (2D)), 1/4) / h: the Marshak current, floored at
+    # the half-range current 1/4 of an isotropic flux (here the floor is active: the corner
+    # block has sigma_t h = 6.3)
     D = 1 / (3 * (p.sigma_t[0] + p.tau))
     h = p.hx
     corner_extra = Ad[0, 0] - sa[0, 0] + Ad[0, 1] + Ad[0, 16]
-    assert abs(corner_extra - 2 / (h * (2 + h / (2 * D)))) < 1e-10 * abs(corner_extra)
+    assert abs(corner_extra - 2 * max(1 / (2 + h / (2 * D)), 0.25) / h) < 1e-10 * abs(corner_extra)
+    assert abs(corner_extra - 2 * 0.25 / h) < 1e-10 * abs(corner_extra)
 
 
 def test_si_contraction_bound(rng):
@@ -122,3 +125,26 @@ def test_dsa_accelerates(rng):
             rho = new
         else:
             raise sisa.NoConvergence("plain SI")
+
+
+def test_dsa_contracts_in_thick_heterogeneous_cells():
+    """SI-DSA must contract from any start (a random error excites every mode), also where
+    cells are optically thick and strongly scattering (log-normal sigma_s with std 3 on a
+    64^2 grid: sigma_t h up to ~10^3).  Measured factor per iteration: 0.009 with the
+    half-range floor of the face couplings, 0.41 without it (and above 1, i.e. divergence, on
+    the larger grids of the batched workload), so the bound 0.1 pins the floor."""
+    wl = inputs.lognormal(n=64, std=3.0, seed=3, c_dt=0.005, quad=(16, 8))
+    p = oracle_problem(wl)
+    A = dsa.dsa_matrix(p)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(p.ncell)
+    res = []
+    for _ in range(10):
+        h = tr.apply_T_sigma_s(p, x)
+        d = h - x
+        res.append(np.max(np.abs(d)))
+        delta, _ = dsa.dsa_correction(p, A, d, 1e-8, 2000)
+        x = h + delta
+    rates = [res[i + 1] / res[i] for i in range(len(res) - 1)]
+    assert max(rates[3:]) < 0.1, rates
+    assert res[-1] < 1e-10 * res[0]
