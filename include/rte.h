@@ -95,6 +95,8 @@ typedef struct {
   int sweep_rows;    /* 2D sweep: rows per lane group, 1, 2, 4 or 8 (0 = automatic) */
   int sweep_lanes;   /* 2D sweep: directions per lane group, 8, 16 or 32 (0 = automatic) */
   int sweep_warps;   /* 2D sweep: warps per CTA, 1..8 (0 = automatic); reduced to fit shared memory */
+  int lookahead;     /* 1: queue SI iteration l+1 before reading the stopping test of l (work
+                        past convergence skips itself on the device); 0 (default): wait first */
 } rte_options;
 
 typedef struct {

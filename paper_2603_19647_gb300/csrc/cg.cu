@@ -44,6 +44,7 @@ struct CgArgs {
   double* rho_out;
   double* q_out;
   int* iters;
+  const unsigned* skip;   // set: the whole solve is skipped (speculative SI-SA work)
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -115,6 +116,7 @@ __device__ double grid_total(const double* part) {
 }
 
 __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
+  if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
   const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
   double* partA = a.partial;
@@ -267,8 +269,9 @@ void dsa_free(DsaOp& op) {
 cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
                       const double* residual_b, double rtol, int max_iter, double* delta,
                       const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
-                      cudaStream_t s) {
-  CgArgs a;
+                      cudaStream_t s, const unsigned* skip) {
+  CgArgs a{};
+  a.skip = skip;
   a.nx = op.nx;
   a.ny = op.ny;
   a.n = op.n;
@@ -423,7 +426,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   ++g_launches;
   dsa_coeff_kernel<<<(n + 255) / 256, 256, 0, s>>>(dim, nx, ny, hx, hy, 1.0 / c_dt, sigma_t_dev,
                                                    sigma_s_dev, diag, cx, cy);
-  CgArgs a;
+  CgArgs a{};
   a.nx = nx;
   a.ny = ny;
   a.n = n;

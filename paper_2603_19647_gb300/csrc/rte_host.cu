@@ -36,9 +36,13 @@ struct rte_s {
   std::vector<cudaEvent_t> evpool;
   int evnext = 0;
   struct Span {
-    int kind, a, b;
+    int kind, a, b, iter;   // iter > 0: work of SI iteration iter, dropped if it never ran
   };
   std::vector<Span> spans;
+  unsigned* d_conv = nullptr;             // skip word of the speculative SI-SA loop
+  const unsigned* skip_now = nullptr;     // skip word the sweep helpers pass on (or none)
+  cudaEvent_t ev_norm[2] = {nullptr, nullptr};     // spin-wait
+  cudaEvent_t ev_norm_b[2] = {nullptr, nullptr};   // blocking-sync (batched instances)
   // second stream: the ROM update overlaps the fused f sweep
   cudaStream_t st2 = nullptr, st3 = nullptr;   // st3: the PC-ROM's part of the update
   cudaEvent_t ev_rho = nullptr, ev_r0 = nullptr, ev_r1 = nullptr, ev_gate = nullptr,
@@ -321,6 +325,11 @@ void free_all(rte_handle h) {
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->h_cg) cudaFreeHost(h->h_cg);
   if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->d_conv) cudaFree(h->d_conv);
+  for (cudaEvent_t e : h->ev_norm)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_norm_b)
+    if (e) cudaEventDestroy(e);
   if (h->ev_wait) cudaEventDestroy(h->ev_wait);
   if (h->h_rom_dv) cudaFreeHost(h->h_rom_dv);
   if (h->rom_dv) cudaFree(h->rom_dv);
@@ -362,6 +371,7 @@ Sweep2DArgs<Real> args2d(rte_handle h, const SV<Real>& v, int mode) {
   a.a = v.ca;
   a.b = v.cb;
   a.w = v.cw;
+  a.skip = h->skip_now;
   a.fam_quad = h->fam_quad;
   a.sig_t = v.sig_t;
   a.inv_d = v.inv_d;
@@ -381,6 +391,7 @@ Sweep1DArgs<Real> args1d(rte_handle h, const SV<Real>& v) {
   a.a = v.ca;
   a.w = v.cw;
   a.dir_sign = h->dir_sign;
+  a.skip = h->skip_now;
   a.cth = v.cth;
   a.ctl = v.ctl;
   a.sig_t = v.sig_t;
@@ -414,7 +425,7 @@ rte_status k1(rte_handle h, const SV<Real>& v, const double* g) {
     a.g_lo = (Real)g[0];
     a.g_hi = (Real)g[1];
     CK(launch_sweep1d<Real>(a, 0, h->st));
-    CK(launch_moment1d<Real>(v.psi_w, h->L.nslot, (int)h->ncell, v.pm, h->st));
+    CK(launch_moment1d<Real>(v.psi_w, h->L.nslot, (int)h->ncell, v.pm, h->st, h->skip_now));
   }
   return RTE_OK;
 }
@@ -468,8 +479,10 @@ int nparts(rte_handle h) { return h->dim == 2 ? h->L.nfam : 1; }
 
 // The sweep source q of the current precision: sigma_s (x - xref) (xref may be nullptr).
 rte_status set_q(rte_handle h, const double* x, const double* xref) {
-  if (h->fp32) CK(launch_scaled_diff<float>(x, xref, h->sig_s, (int)h->ncell, h->q_f, h->st));
-  else CK(launch_scaled_diff<double>(x, xref, h->sig_s, (int)h->ncell, h->q, h->st));
+  if (h->fp32)
+    CK(launch_scaled_diff<float>(x, xref, h->sig_s, (int)h->ncell, h->q_f, h->st, h->skip_now));
+  else
+    CK(launch_scaled_diff<double>(x, xref, h->sig_s, (int)h->ncell, h->q, h->st, h->skip_now));
   return RTE_OK;
 }
 // Pass-A source sigma_s rho + G of the fused sweep.
@@ -480,8 +493,12 @@ rte_status set_qa(rte_handle h, const double* rho) {
 }
 // out (+)= sum of the partial moments, in FP64.
 rte_status sum_pm(rte_handle h, double* out, int accumulate) {
-  if (h->fp32) CK(launch_sum_pm<float>(h->pm_f, nparts(h), (int)h->ncell, out, accumulate, h->st));
-  else CK(launch_sum_pm<double>(h->pm, nparts(h), (int)h->ncell, out, accumulate, h->st));
+  if (h->fp32)
+    CK(launch_sum_pm<float>(h->pm_f, nparts(h), (int)h->ncell, out, accumulate, h->st,
+                            h->skip_now));
+  else
+    CK(launch_sum_pm<double>(h->pm, nparts(h), (int)h->ncell, out, accumulate, h->st,
+                             h->skip_now));
   return RTE_OK;
 }
 rte_status sweep_q(rte_handle h, const double* g) {
@@ -622,8 +639,8 @@ int rec(rte_handle h) {
   return i;
 }
 
-void span(rte_handle h, int kind, int a, int b) {
-  if (a >= 0 && b >= 0) h->spans.push_back({kind, a, b});
+void span(rte_handle h, int kind, int a, int b, int iter = 0) {
+  if (a >= 0 && b >= 0) h->spans.push_back({kind, a, b, iter});
 }
 
 // Adds the recorded spans to the statistics; the caller has synchronised the stream.
@@ -650,86 +667,115 @@ void resolve_spans(rte_handle h) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Algorithm 1 on the current b~ from initial guess rho0.  Leaves rho^n in h->rho.  The host
-// waits once per iteration, for the two norms of the stopping test.
+// Algorithm 1 on the current b~ from initial guess rho0.  Leaves rho^n in h->rho.
+//
+// With options.lookahead the loop runs one iteration ahead of the host: while the host waits
+// for the norms of iteration l, the DSA step of l and the sweep and residual of l + 1 are
+// already queued.  They carry a device skip word that the residual of l sets when l meets the
+// stopping test, so past convergence they return at once and leave every result untouched.
+// The l = 1 step of Phase 3 (the ROM preconditioner) is queued only after the host has seen
+// l = 1 fail.  Measured on GB300 the host's turnaround between iterations (spin wait) is a
+// few microseconds, less than the skipped launches cost, so lookahead is off by default.
 // ---------------------------------------------------------------------------------------
 rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out) {
   const int n = (int)h->ncell;
   const int nb = vec_blocks(n);
+  const int absmode = h->opt.residual_norm == RTE_ABS_INF ? 1 : 0;
   CK(cudaMemcpyAsync(h->rho_prev, h->rho0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemsetAsync(h->d_conv, 0, sizeof(unsigned), h->st));
+  h->skip_now = h->d_conv;
   // FP64: each iteration sweeps sigma_s rho^{l-1}.  FP32 (iterative refinement): the sweeps
   // act on the increments rho^{l-1} - rho_ref in FP32 and their results accumulate into the
   // FP64 y_ir = T Sigma_s rho_ref, so rho^{l-1/2} = y_ir + b~ carries FP64 accuracy in the
   // residual; the first increment is measured from the last swept iterate of the previous step.
-  auto sweep_increment = [&]() -> rte_status {
+  auto sweep_increment = [&](int iter) -> rte_status {
     const int k0 = rec(h);
     if (h->fp32) {
-      CK(launch_scaled_diff_update<float>(h->rho_prev, h->rho_ref, h->sig_s, n, h->q_f, h->st));
+      CK(launch_scaled_diff_update<float>(h->rho_prev, h->rho_ref, h->sig_s, n, h->q_f, h->st,
+                                          h->d_conv));
       TRY(sweep_q(h, nullptr));
-      span(h, SPAN_K1, k0, rec(h));
+      span(h, SPAN_K1, k0, rec(h), iter);
       TRY(sum_pm(h, h->y_ir, 1));
     } else {
       TRY(set_q(h, h->rho_prev, nullptr));
       TRY(sweep_q(h, nullptr));
-      span(h, SPAN_K1, k0, rec(h));
+      span(h, SPAN_K1, k0, rec(h), iter);
     }
     return RTE_OK;
   };
-  bool conv = false;
-  int l = 0;
-  h->pc_applied = false;
-  int mark = rec(h);
-  TRY(sweep_increment());
-  for (l = 1; l <= h->opt.max_iter; ++l) {
+  // rho^{l-1/2}, its norms (pinned copy, parity l & 1) and the device stopping test
+  auto residual = [&](int l) -> rte_status {
+    const int p = l & 1;
+    const int r0 = rec(h);
     if (h->fp32)
       CK(launch_combine_residual(h->y_ir, 1, h->btilde, h->rho_prev, n, h->rho_half, h->partials,
-                                 nb, h->norms, h->st));
+                                 nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa, absmode));
     else
       CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
-                                 h->partials, nb, h->norms, h->st));
-    CK(cudaMemcpyAsync(h->h_norms, h->norms, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
-    int m = rec(h);
-    span(h, SPAN_SWEEP, mark, m);
-    mark = m;
-    if (l == 1)
-      CK(cudaMemcpyAsync(h->rho_half1, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                         h->st));
-    TRY(host_wait(h));
-    const Norms nm = *h->h_norms;
-    const double res = h->opt.residual_norm == RTE_ABS_INF
-                           ? nm.diff_inf
-                           : (nm.half_inf > 0 ? nm.diff_inf / nm.half_inf : nm.diff_inf);
-    conv = h->opt.residual_norm == RTE_ABS_INF ? nm.diff_inf <= h->opt.eps_sisa
-                                               : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
+                                 h->partials, nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa,
+                                 absmode));
+    CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
+    span(h, SPAN_SWEEP, r0, rec(h), l);
+    CK(cudaEventRecord(h->blocking ? h->ev_norm_b[p] : h->ev_norm[p], h->st));
+    return RTE_OK;
+  };
+  // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta.  Its
+  // iteration count stays on the device until the step ends.
+  auto dsa_step = [&](int l) -> rte_status {
+    const int d0 = rec(h);
+    CK(dsa_solve(h->dsa, h->sig_s, h->rho_half, h->rho_prev, h->opt.cg_rtol, h->opt.cg_max_iter,
+                 h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters + l, h->st, h->d_conv));
+    span(h, SPAN_DSA, d0, rec(h), l + 1);
+    return RTE_OK;
+  };
+  bool conv = false;
+  int l = 1;
+  h->pc_applied = false;
+  TRY(sweep_increment(1));
+  TRY(residual(1));
+  CK(cudaMemcpyAsync(h->rho_half1, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                     h->st));
+  for (l = 1;; ++l) {
+    const bool pc_now = l == 1 && use_pc;
+    if (h->opt.lookahead && l < h->opt.max_iter && !pc_now) {   // iteration l + 1, queued ahead
+      TRY(dsa_step(l));
+      TRY(sweep_increment(l + 1));
+      TRY(residual(l + 1));
+    }
+    CK(cudaEventSynchronize(h->blocking ? h->ev_norm_b[l & 1] : h->ev_norm[l & 1]));
+    const Norms nm = h->h_norms[l & 1];
+    const double res = absmode ? nm.diff_inf
+                               : (nm.half_inf > 0 ? nm.diff_inf / nm.half_inf : nm.diff_inf);
+    conv = absmode ? nm.diff_inf <= h->opt.eps_sisa : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
     h->stats.last_residual = res;
-    if (conv) break;
-    if (l == h->opt.max_iter) break;
-    if (l == 1 && use_pc) {
+    if (conv || l == h->opt.max_iter) break;
+    if (!h->opt.lookahead && !pc_now) {
+      TRY(dsa_step(l));
+      TRY(sweep_increment(l + 1));
+      TRY(residual(l + 1));
+    }
+    if (pc_now) {
       // ROM preconditioner, Eq. (dmd-sa): delta = dU C_r^{-1} dU^T (rho^{1/2} - rho^{(0)})
+      const int r0 = rec(h);
       CK(launch_axpby(1.0, h->rho_half, -1.0, h->rho0, n, h->tmp, h->st));
       CK(rom_apply(h->pc, h->tmp, h->delta_pc1, h->st));
       CK(launch_update_rho(h->rho_half, h->delta_pc1, h->sig_s, n, h->rho_prev, h->q, h->st));
+      span(h, SPAN_ROM, r0, rec(h), 2);
       h->pc_applied = true;
-      m = rec(h);
-      span(h, SPAN_ROM, mark, m);
-      mark = m;
-    } else {
-      // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta.  Its
-      // iteration count stays on the device until the step ends.
-      CK(dsa_solve(h->dsa, h->sig_s, h->rho_half, h->rho_prev, h->opt.cg_rtol, h->opt.cg_max_iter,
-                   h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters + l, h->st));
-      m = rec(h);
-      span(h, SPAN_DSA, mark, m);
-      mark = m;
+      TRY(sweep_increment(2));
+      TRY(residual(2));
     }
-    TRY(sweep_increment());
   }
-  if (l > h->opt.max_iter) l = h->opt.max_iter;
+  h->skip_now = nullptr;
+  // drop the statistics of the speculative work that skipped itself
+  h->spans.erase(std::remove_if(h->spans.begin(), h->spans.end(),
+                                [&](const rte_s::Span& s) { return s.iter > l; }),
+                 h->spans.end());
   CK(cudaMemcpyAsync(h->rho, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  // CG counts of this solve: slots 1 .. l-1 written by the DSA calls (the PC step leaves its
-  // slot at zero)
-  CK(cudaMemcpyAsync(h->h_cg, h->cg_iters, sizeof(int) * (l + 1), cudaMemcpyDeviceToHost, h->st));
-  h->cg_slots = l + 1;
+  // CG counts of this solve: slots 1 .. l-1 written by the DSA calls (the PC step and skipped
+  // solves leave their slots at zero)
+  CK(cudaMemcpyAsync(h->h_cg, h->cg_iters, sizeof(int) * (l + 2), cudaMemcpyDeviceToHost, h->st));
+  h->cg_slots = l + 2;
   *iters_out = l;
   *converged_out = conv;
   return RTE_OK;
@@ -1260,7 +1306,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(cudaEventCreateWithFlags(&h->ev_rho, cudaEventDisableTiming));
   CK(cudaEventCreate(&h->ev_r0));
   CK(cudaEventCreate(&h->ev_r1));
-  CK(cudaMallocHost((void**)&h->h_norms, sizeof(Norms)));
+  CK(cudaMallocHost((void**)&h->h_norms, 2 * sizeof(Norms)));
   CK(cudaMallocHost((void**)&h->h_cg, sizeof(int) * (h->opt.max_iter + 2)));
   CK(cudaMallocHost((void**)&h->h_rom_dv, sizeof(double) * 4));
   CK(cudaMallocHost((void**)&h->h_err, 2 * sizeof(unsigned)));
@@ -1294,7 +1340,12 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   }
   CK(dalloc(&h->partials, 3 * 1024));
   CK(dalloc(&h->dotbuf, 4));
-  CK(dalloc(&h->norms, 1));
+  CK(dalloc(&h->norms, 2));
+  CK(cudaMalloc((void**)&h->d_conv, sizeof(unsigned)));
+  CK(cudaMemset(h->d_conv, 0, sizeof(unsigned)));
+  for (auto& e : h->ev_norm) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (auto& e : h->ev_norm_b)
+    CK(cudaEventCreateWithFlags(&e, cudaEventBlockingSync | cudaEventDisableTiming));
   CK(dalloc(&h->cg_iters, (size_t)h->opt.max_iter + 2));
   CK(cudaMemsetAsync(h->cg_iters, 0, sizeof(int) * (h->opt.max_iter + 2), h->st));
   // direction layout and sweep tiles: measured (tune), else the fixed choice
@@ -1337,6 +1388,7 @@ void rte_default_options(rte_options* o) {
   o->cg_rtol = 1e-6;
   o->cg_max_iter = 500;
   o->tune = 1;
+  o->lookahead = 0;
 }
 
 rte_status rte_create(rte_handle* out, const rte_mesh* mesh, const rte_quadrature* quad,

@@ -51,6 +51,7 @@ struct Sweep2DArgs {
   const int* fam_quad;  // [nfam]
   const Real* sig_t;    // [ncell]
   const Real* inv_d;    // [nfam][ncell][dl] 1/(tau+sigma_t+a+b) or nullptr (computed)
+  const unsigned* skip; // set: the launch does nothing (speculative SI-SA work past convergence)
   const Real* cth;      // [nslot] tau + a + b, high part, or nullptr (formed from tau, a, b)
   const Real* ctl;      // [nslot] its low part (FP32: the exact sum is cth + ctl)
   // K1: isotropic source q = Sigma_s rho; K2 pass A: q = Sigma_s rho + G.
@@ -71,6 +72,7 @@ struct Sweep1DArgs {
   const Real* a;
   const Real* w;
   const int* dir_sign;  // [nslot] +1 / -1
+  const unsigned* skip; // as in Sweep2DArgs
   const Real* cth;      // [nslot] tau + a split as hi / lo (FP32), or nullptr
   const Real* ctl;
   const Real* sig_t;
@@ -90,7 +92,8 @@ cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStre
 template <class Real>
 cudaError_t launch_sweep1d(const Sweep1DArgs<Real>& a, int mode, cudaStream_t s);
 template <class Real>
-cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s);
+cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s,
+                            const unsigned* skip = nullptr);
 // inv_d in the family layout [fam][cell][dl]
 template <class Real>
 cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
@@ -100,9 +103,12 @@ cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real t
 struct Norms {             // device-side reduction results of one residual evaluation
   double diff_inf, half_inf, diff_l2sq, pad;
 };
+// conv (optional): skip word of a speculative SI-SA loop; the residual does nothing when it
+// is set and otherwise sets it to the outcome of the stopping test (eps, absolute or relative).
 cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
                                     const double* rho_prev, int ncell, double* rho_half,
-                                    double* partials, int nblocks, Norms* out, cudaStream_t s);
+                                    double* partials, int nblocks, Norms* out, cudaStream_t s,
+                                    unsigned* conv = nullptr, double eps = 0.0, int absmode = 0);
 cudaError_t launch_update_rho(const double* rho_half, const double* delta, const double* sig_s,
                               int ncell, double* rho, double* q, cudaStream_t s);
 cudaError_t launch_scale_copy(const double* x, const double* sig_s, int ncell, double* q,
@@ -120,17 +126,20 @@ cudaError_t launch_rom_gate(const double* e2, const double* n2, double eps_up, i
                             const int* also, int* gate, cudaStream_t s);
 // Sources of the sweeps in their precision (FP32 mode: float).
 template <class Real>
+// Real(sigma_s (x - xref)); skip: a set skip word makes the launch do nothing
 cudaError_t launch_scaled_diff(const double* x, const double* xref, const double* sig_s, int n,
-                               Real* out, cudaStream_t s);        // Real(sigma_s (x - xref))
+                               Real* out, cudaStream_t s, const unsigned* skip = nullptr);
 template <class Real>
+// the same, then xref <- x
 cudaError_t launch_scaled_diff_update(const double* x, double* xref, const double* sig_s, int n,
-                                      Real* out, cudaStream_t s); // same, then xref <- x
+                                      Real* out, cudaStream_t s, const unsigned* skip = nullptr);
 template <class Real>
 cudaError_t launch_scaled_plus(const double* rho, const double* sig_s, const double* src, int n,
                                Real* out, cudaStream_t s);        // Real(sigma_s rho + G)
 template <class Real>
+// out (+)= sum_f pm, in FP64
 cudaError_t launch_sum_pm(const Real* pm, int nfam, int n, double* out, int accumulate,
-                          cudaStream_t s);                        // out (+)= sum_f pm (FP64)
+                          cudaStream_t s, const unsigned* skip = nullptr);
 cudaError_t launch_isotropic_f32(const double* rho, int n, int nslot, int dl, float* f,
                                  cudaStream_t s);
 cudaError_t launch_to_float(const double* x, long n, float* y, cudaStream_t s);
@@ -156,7 +165,7 @@ void dsa_free(DsaOp& op);
 cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
                       const double* residual_b, double rtol, int max_iter, double* delta,
                       const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
-                      cudaStream_t s);
+                      cudaStream_t s, const unsigned* skip = nullptr);
 
 // Allocation-free DSA solve behind rte_dsa_solve_noalloc (cg.cu); *err receives the message.
 rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0, double y1,

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   constexpr int PER_S = (TABLE ? 0 : 1) + (MODE != 2 ? 1 : 0) + (MODE != 0 ? 1 : 0);  // [RW][K]
   constexpr int WARP_REALS = 2 * RW * K * (PER_DL * DL + PER_S);
   static_assert(R <= DL, "rows per lane group must not exceed the lane count");
+  if (A.skip && *A.skip) return;   // before the ticket: the control block stays untouched
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ unsigned s_ticket;
   __shared__ volatile int s_prod[8];    // columns of its bottom row warp w has put in the ring
@@ -592,6 +593,7 @@ __device__ __forceinline__ Cell1D<Real> cell1d(Real ct, Real ctl, Real sig) {
 // operator); each thread then runs its cells' recurrence in the run precision.
 template <class Real, int MODE>
 __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs<Real> A) {
+  if (A.skip && *A.skip) return;
   __shared__ Aff<double> sh[64];
   const int slot = blockIdx.x;
   const int nx = A.nx;
@@ -655,9 +657,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
 }
 
 template <class Real>
-__global__ void moment1d_kernel(const Real* psi_w, int nslot, int ncell, Real* out) {
+__global__ void moment1d_kernel(const Real* psi_w, int nslot, int ncell, Real* out,
+                                const unsigned* skip) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  if (c >= ncell || (skip && *skip)) return;
   Real s = Real(0);
   for (int k = 0; k < nslot; ++k) s += psi_w[(long)k * ncell + c];
   out[c] = s;
@@ -748,9 +751,10 @@ cudaError_t launch_sweep1d(const Sweep1DArgs<Real>& a, int mode, cudaStream_t s)
 }
 
 template <class Real>
-cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s) {
+cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s,
+                            const unsigned* skip) {
   ++g_launches;
-  moment1d_kernel<Real><<<(ncell + 255) / 256, 256, 0, s>>>(psi_w, nslot, ncell, out);
+  moment1d_kernel<Real><<<(ncell + 255) / 256, 256, 0, s>>>(psi_w, nslot, ncell, out, skip);
   return cudaGetLastError();
 }
 
@@ -768,8 +772,10 @@ template cudaError_t launch_sweep2d<double>(const Sweep2DArgs<double>&, int, int
 template cudaError_t launch_sweep2d<float>(const Sweep2DArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_sweep1d<double>(const Sweep1DArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_sweep1d<float>(const Sweep1DArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_moment1d<double>(const double*, int, int, double*, cudaStream_t);
-template cudaError_t launch_moment1d<float>(const float*, int, int, float*, cudaStream_t);
+template cudaError_t launch_moment1d<double>(const double*, int, int, double*, cudaStream_t,
+                                             const unsigned*);
+template cudaError_t launch_moment1d<float>(const float*, int, int, float*, cudaStream_t,
+                                            const unsigned*);
 template cudaError_t launch_inv_d<double>(const double*, const double*, const double*, double, int,
                                           int, int, double*, cudaStream_t);
 template cudaError_t launch_inv_d<float>(const float*, const float*, const float*, float, int, int,

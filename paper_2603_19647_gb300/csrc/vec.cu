@@ -28,7 +28,9 @@ __device__ __forceinline__ double warp_max(double v) {
 __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
                                         const double* __restrict__ btilde,
                                         const double* __restrict__ rho_prev, int n,
-                                        double* __restrict__ rho_half, double* partials) {
+                                        double* __restrict__ rho_half, double* partials,
+                                        const unsigned* skip) {
+  if (skip && *skip) return;   // the solve has converged: speculative work does nothing
   __shared__ double sh[3][VT / 32];
   double dinf = 0.0, hinf = 0.0, d2 = 0.0;
   for (int c = blockIdx.x * VT + threadIdx.x; c < n; c += gridDim.x * VT) {
@@ -66,7 +68,12 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
   }
 }
 
-__global__ void finish_norms_kernel(const double* partials, int nblocks, Norms* out) {
+// Norms of one residual and, when conv is given, the stopping test of Algorithm 1 on them
+// (the same comparison the host makes), which later speculative launches read as their skip
+// word.
+__global__ void finish_norms_kernel(const double* partials, int nblocks, Norms* out,
+                                    unsigned* conv, double eps, int absmode) {
+  if (conv && *conv) return;
   double dinf = 0.0, hinf = 0.0, d2 = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += 32) {
     dinf = fmax(dinf, partials[3 * b]);
@@ -80,6 +87,7 @@ __global__ void finish_norms_kernel(const double* partials, int nblocks, Norms* 
     out->diff_inf = dinf;
     out->half_inf = hinf;
     out->diff_l2sq = d2;
+    if (conv) *conv = (absmode ? dinf <= eps : dinf <= eps * hinf) ? 1u : 0u;
   }
 }
 
@@ -147,9 +155,9 @@ __global__ void dot_finish_kernel(const double* partials, int nblocks, double* o
 // out = Real(sigma_s (x - xref)) (xref may be nullptr); with `update`, xref <- x afterwards.
 template <class Real>
 __global__ void scaled_diff_kernel(const double* x, double* xref, const double* sig_s, int n,
-                                   Real* out, int update) {
+                                   Real* out, int update, const unsigned* skip) {
   const int c = blockIdx.x * VT + threadIdx.x;
-  if (c >= n) return;
+  if (c >= n || (skip && *skip)) return;
   const double xv = x[c];
   const double d = xref ? xv - xref[c] : xv;
   out[c] = (Real)(sig_s[c] * d);
@@ -167,9 +175,10 @@ __global__ void scaled_plus_kernel(const double* rho, const double* sig_s, const
 
 // out (+)= sum over families of pm, accumulated in FP64 in family order
 template <class Real>
-__global__ void sum_pm_kernel(const Real* pm, int nfam, int n, double* out, int accumulate) {
+__global__ void sum_pm_kernel(const Real* pm, int nfam, int n, double* out, int accumulate,
+                              const unsigned* skip) {
   const int c = blockIdx.x * VT + threadIdx.x;
-  if (c >= n) return;
+  if (c >= n || (skip && *skip)) return;
   double s = 0.0;
   for (int f = 0; f < nfam; ++f) s += (double)pm[(long)f * n + c];
   out[c] = accumulate ? out[c] + s : s;
@@ -190,17 +199,17 @@ __global__ void to_float_kernel(const double* x, long n, float* y) {
 
 template <class Real>
 cudaError_t launch_scaled_diff(const double* x, const double* xref, const double* sig_s, int n,
-                               Real* out, cudaStream_t s) {
+                               Real* out, cudaStream_t s, const unsigned* skip) {
   ++g_launches;
   scaled_diff_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(x, const_cast<double*>(xref), sig_s, n,
-                                                            out, 0);
+                                                            out, 0, skip);
   return cudaGetLastError();
 }
 template <class Real>
 cudaError_t launch_scaled_diff_update(const double* x, double* xref, const double* sig_s, int n,
-                                      Real* out, cudaStream_t s) {
+                                      Real* out, cudaStream_t s, const unsigned* skip) {
   ++g_launches;
-  scaled_diff_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(x, xref, sig_s, n, out, 1);
+  scaled_diff_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(x, xref, sig_s, n, out, 1, skip);
   return cudaGetLastError();
 }
 template <class Real>
@@ -212,9 +221,9 @@ cudaError_t launch_scaled_plus(const double* rho, const double* sig_s, const dou
 }
 template <class Real>
 cudaError_t launch_sum_pm(const Real* pm, int nfam, int n, double* out, int accumulate,
-                          cudaStream_t s) {
+                          cudaStream_t s, const unsigned* skip) {
   ++g_launches;
-  sum_pm_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(pm, nfam, n, out, accumulate);
+  sum_pm_kernel<Real><<<(n + VT - 1) / VT, VT, 0, s>>>(pm, nfam, n, out, accumulate, skip);
   return cudaGetLastError();
 }
 cudaError_t launch_isotropic_f32(const double* rho, int n, int nslot, int dl, float* f,
@@ -230,19 +239,21 @@ cudaError_t launch_to_float(const double* x, long n, float* y, cudaStream_t s) {
   return cudaGetLastError();
 }
 template cudaError_t launch_scaled_diff<double>(const double*, const double*, const double*, int,
-                                                double*, cudaStream_t);
+                                                double*, cudaStream_t, const unsigned*);
 template cudaError_t launch_scaled_diff<float>(const double*, const double*, const double*, int,
-                                               float*, cudaStream_t);
+                                               float*, cudaStream_t, const unsigned*);
 template cudaError_t launch_scaled_diff_update<float>(const double*, double*, const double*, int,
-                                                      float*, cudaStream_t);
+                                                      float*, cudaStream_t, const unsigned*);
 template cudaError_t launch_scaled_diff_update<double>(const double*, double*, const double*, int,
-                                                       double*, cudaStream_t);
+                                                       double*, cudaStream_t, const unsigned*);
 template cudaError_t launch_scaled_plus<double>(const double*, const double*, const double*, int,
                                                 double*, cudaStream_t);
 template cudaError_t launch_scaled_plus<float>(const double*, const double*, const double*, int,
                                                float*, cudaStream_t);
-template cudaError_t launch_sum_pm<double>(const double*, int, int, double*, int, cudaStream_t);
-template cudaError_t launch_sum_pm<float>(const float*, int, int, double*, int, cudaStream_t);
+template cudaError_t launch_sum_pm<double>(const double*, int, int, double*, int, cudaStream_t,
+                                          const unsigned*);
+template cudaError_t launch_sum_pm<float>(const float*, int, int, double*, int, cudaStream_t,
+                                         const unsigned*);
 
 int vec_blocks(int n) {
   int b = (n + VT - 1) / VT;
@@ -251,11 +262,13 @@ int vec_blocks(int n) {
 
 cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
                                     const double* rho_prev, int n, double* rho_half,
-                                    double* partials, int nblocks, Norms* out, cudaStream_t s) {
+                                    double* partials, int nblocks, Norms* out, cudaStream_t s,
+                                    unsigned* conv, double eps, int absmode) {
   ++g_launches;
-  combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, partials);
+  combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, partials,
+                                                 conv);
   ++g_launches;
-  finish_norms_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+  finish_norms_kernel<<<1, 32, 0, s>>>(partials, nblocks, out, conv, eps, absmode);
   return cudaGetLastError();
 }
 

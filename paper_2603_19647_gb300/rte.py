@@ -54,7 +54,7 @@ class Options(ctypes.Structure):
                 ("rom", ctypes.c_int), ("residual_norm", ctypes.c_int), ("up_rel", ctypes.c_int),
                 ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int),
                 ("sweep_rows", ctypes.c_int), ("sweep_lanes", ctypes.c_int),
-                ("sweep_warps", ctypes.c_int)]
+                ("sweep_warps", ctypes.c_int), ("lookahead", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
