@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -87,9 +88,16 @@ struct rte_s {
   double *psi_w = nullptr, *psi_w_a = nullptr;
   // FP32 mode (RTE_FP32): sweep data in float; FP64 refinement state
   bool fp32 = false;
+  bool bf16 = false;     // RTE_FP32_BF16F: f stored as BF16 remainders about fref[fcur]
+  __nv_bfloat16 *fb = nullptr, *fb_init = nullptr;
+  float* fref[2] = {nullptr, nullptr};
+  float* fref_init = nullptr;
+  int fcur = 0;
+  unsigned bf_seed = 0;  // counter of BF16 write launches (stochastic-rounding seed)
   float *sig_t_f = nullptr, *src_f = nullptr, *ca_f = nullptr, *cb_f = nullptr, *cw_f = nullptr;
   float *f_f = nullptr, *pm_f = nullptr, *edge_f = nullptr, *psi_w_f = nullptr, *q_f = nullptr;
   float *cth_f = nullptr, *ctl_f = nullptr;   // tau + a + b per slot as an exact hi / lo pair
+  float* sig_tl_f = nullptr;                   // sigma_t - sig_t_f (low part of the pair)
   float *f_init_f = nullptr;
   double *y_ir = nullptr, *rho_ref = nullptr;   // y_ir = T Sigma_s rho_ref, accumulated in FP64
   // device: cell vectors
@@ -309,7 +317,8 @@ void free_all(rte_handle h) {
                   h->resp[1], h->resp[2], h->resp[3], h->partials, h->dotbuf, h->norms,
                   h->cg_iters, h->rho_init, h->f_init, h->sig_t_f, h->src_f, h->ca_f,
                   h->cb_f, h->cw_f, h->f_f, h->pm_f, h->edge_f, h->psi_w_f, h->q_f, h->f_init_f,
-                  h->y_ir, h->rho_ref, h->cth_f, h->ctl_f};
+                  h->y_ir, h->rho_ref, h->cth_f, h->ctl_f, h->fb, h->fb_init, h->fref[0],
+                  h->fref[1], h->fref_init, h->sig_tl_f};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   dsa_free(h->dsa);
@@ -345,16 +354,16 @@ void free_all(rte_handle h) {
 // Device data of the sweeps in one precision.
 template <class Real>
 struct SV {
-  const Real *sig_t, *src, *ca, *cb, *cw, *inv_d, *cth, *ctl;
+  const Real *sig_t, *sig_tl, *src, *ca, *cb, *cw, *inv_d, *cth, *ctl;
   Real *f, *pm, *edge, *psi_w, *q;
 };
 SV<double> sv64(rte_handle h) {
-  return {h->sig_t, h->src, h->ca, h->cb, h->cw, h->inv_d, nullptr, nullptr,
+  return {h->sig_t, nullptr, h->src, h->ca, h->cb, h->cw, h->inv_d, nullptr, nullptr,
           h->f, h->pm, h->edge, h->psi_w, h->q};
 }
 SV<float> sv32(rte_handle h) {
-  return {h->sig_t_f, h->src_f, h->ca_f, h->cb_f, h->cw_f, nullptr, h->cth_f, h->ctl_f,
-          h->f_f, h->pm_f, h->edge_f, h->psi_w_f, h->q_f};
+  return {h->sig_t_f, h->sig_tl_f, h->src_f, h->ca_f, h->cb_f, h->cw_f, nullptr, h->cth_f,
+          h->ctl_f, h->f_f, h->pm_f, h->edge_f, h->psi_w_f, h->q_f};
 }
 
 template <class Real>
@@ -374,6 +383,7 @@ Sweep2DArgs<Real> args2d(rte_handle h, const SV<Real>& v, int mode) {
   a.skip = h->skip_now;
   a.fam_quad = h->fam_quad;
   a.sig_t = v.sig_t;
+  a.sig_tl = v.sig_tl;
   a.inv_d = v.inv_d;
   a.cth = v.cth;
   a.ctl = v.ctl;
@@ -395,6 +405,7 @@ Sweep1DArgs<Real> args1d(rte_handle h, const SV<Real>& v) {
   a.cth = v.cth;
   a.ctl = v.ctl;
   a.sig_t = v.sig_t;
+  a.sig_tl = v.sig_tl;
   a.psi_w = v.psi_w;
   return a;
 }
@@ -441,7 +452,16 @@ rte_status k2(rte_handle h, const SV<Real>& v) {
     a.f = v.f;
     a.pm = v.pm;
     ghosts(h->g, a.gx, a.gy);
-    CK(launch_sweep2d<Real>(a, 1, h->tile[1].R, h->st));
+    int mode = 1;
+    if (h->bf16) {   // reads f^{n-1} about fref[fcur], writes f^n about fref[1 - fcur]
+      a.fb = h->fb;
+      a.fro = h->fref[h->fcur];
+      a.frn = h->fref[1 - h->fcur];
+      a.seed = h->bf_seed++;
+      mode = 3;
+    }
+    CK(launch_sweep2d<Real>(a, mode, h->tile[1].R, h->st));
+    if (h->bf16) h->fcur = 1 - h->fcur;
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.q = v.q;
@@ -464,7 +484,13 @@ rte_status ky(rte_handle h, const SV<Real>& v) {
     a.g2 = v.src;
     a.f = v.f;
     a.pm = v.pm;
-    CK(launch_sweep2d<Real>(a, 2, h->tile[0].R, h->st));
+    int mode = 2;
+    if (h->bf16) {
+      a.fb = h->fb;
+      a.fro = a.frn = h->fref[h->fcur];
+      mode = 4;
+    }
+    CK(launch_sweep2d<Real>(a, mode, h->tile[0].R, h->st));
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.g2 = v.src;
@@ -521,6 +547,7 @@ rte_status sweep_si(rte_handle h, const double* rho_or_null, const double* g, do
 // y = sum_j w_j L_j^-1(G + tau f^n) with zero inflow.
 rte_status sweep_f(rte_handle h, const double* rho, double* y_out) {
   TRY(set_qa(h, rho));
+  if (h->bf16) CK(launch_to_float(rho, h->ncell, h->fref[1 - h->fcur], h->st));
   if (h->fp32) TRY(k2<float>(h, sv32(h)));
   else TRY(k2<double>(h, sv64(h)));
   TRY(sum_pm(h, y_out, 0));
@@ -954,6 +981,21 @@ rte_status one_step(rte_handle h) {
   return RTE_OK;
 }
 
+// IEEE binary32 -> bfloat16 with round-to-nearest-even (NaN kept quiet), and back.
+uint16_t bf16_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+
 bool finite_all(const double* v, long n) {
   for (long i = 0; i < n; ++i)
     if (!std::isfinite(v[i])) return false;
@@ -975,6 +1017,7 @@ rte_status reset_state(rte_handle h) {
   }
   h->stats = rte_stats{};
   h->rom_pend = rte_s::RomPending{};
+  h->bf_seed = 0;
   h->flag_ig = h->flag_pc = false;
   h->y_valid = false;
   h->pending_rom = false;
@@ -1071,9 +1114,17 @@ rte_status alloc_sweep(rte_handle h) {
   if (!h->fp32) {
     CK(dalloc(&h->f, (size_t)n * L.nslot));
     CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
-  } else {
+  } else if (!h->bf16) {
     CK(dalloc(&h->f_f, (size_t)n * L.nslot));
     CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * n * L.nslot, h->st));
+  } else {
+    CK(dalloc(&h->fb, (size_t)n * L.nslot));
+    CK(cudaMemsetAsync(h->fb, 0, sizeof(__nv_bfloat16) * n * L.nslot, h->st));
+    for (auto& r : h->fref) {
+      CK(dalloc(&r, n));
+      CK(cudaMemsetAsync(r, 0, sizeof(float) * n, h->st));
+    }
+    h->fcur = 0;
   }
   if (h->dim == 2) {
     const size_t edge = (size_t)2 * L.nfam * h->nblk_max * h->nx * L.dl;
@@ -1103,6 +1154,7 @@ rte_status alloc_sweep(rte_handle h) {
 }
 
 void free_sweep(rte_handle h) {
+  dfree(h->fb), dfree(h->fref[0]), dfree(h->fref[1]);
   dfree(h->f), dfree(h->f_f), dfree(h->inv_d), dfree(h->pm), dfree(h->pm_f), dfree(h->edge);
   dfree(h->edge_f), dfree(h->ctrl), dfree(h->psi_w), dfree(h->psi_w_f);
 }
@@ -1119,7 +1171,8 @@ void set_tile(rte_handle h, rte_s::Tile& tl, int R, int W) {
 bool tile_fits(rte_handle h, int dl, int R, int W) {
   if (R > dl) return false;
   const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
-  for (int mode = 0; mode < 3; ++mode)
+  const int modes_plain[3] = {0, 1, 2}, modes_bf[3] = {0, 3, 4};
+  for (int mode : h->bf16 ? modes_bf : modes_plain)
     if (sweep2d_smem_bytes(real, dl, R, W, mode, !h->fp32) > 200 * 1024) return false;
   return true;
 }
@@ -1253,9 +1306,13 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0)))
     return fail(h, RTE_EINVAL, "empty domain");
   if (!(c_dt > 0.0) || !std::isfinite(c_dt)) return fail(h, RTE_EINVAL, "c_dt must be > 0");
-  if (h->opt.precision != RTE_FP64 && h->opt.precision != RTE_FP32)
-    return fail(h, RTE_EINVAL, "precision must be RTE_FP64 or RTE_FP32");
-  h->fp32 = h->opt.precision == RTE_FP32;
+  if (h->opt.precision != RTE_FP64 && h->opt.precision != RTE_FP32 &&
+      h->opt.precision != RTE_FP32_BF16F)
+    return fail(h, RTE_EINVAL, "precision must be RTE_FP64, RTE_FP32 or RTE_FP32_BF16F");
+  if (h->opt.precision == RTE_FP32_BF16F && mesh->dim != 2)
+    return fail(h, RTE_EINVAL, "RTE_FP32_BF16F is available for 2D problems");
+  h->fp32 = h->opt.precision != RTE_FP64;
+  h->bf16 = h->opt.precision == RTE_FP32_BF16F;
   if (h->opt.r_max < 1 || h->opt.r_max > 64) return fail(h, RTE_EINVAL, "r_max must be in [1, 64]");
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
@@ -1325,8 +1382,17 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   TRY(upload(h, h->src, source, n));
   if (h->fp32) {
     CK(dalloc(&h->sig_t_f, n));
+    CK(dalloc(&h->sig_tl_f, n));
     CK(dalloc(&h->src_f, n));
-    CK(launch_to_float(h->sig_t, n, h->sig_t_f, h->st));
+    {   // sigma_t as an exact pair hi + lo of FP32 numbers
+      std::vector<float> hi(n), lo(n);
+      for (long c = 0; c < n; ++c) {
+        hi[c] = (float)sigma_t[c];
+        lo[c] = (float)(sigma_t[c] - (double)hi[c]);
+      }
+      CK(cudaMemcpy(h->sig_t_f, hi.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->sig_tl_f, lo.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    }
     CK(launch_to_float(h->src, n, h->src_f, h->st));
     CK(dalloc(&h->q_f, n));
     CK(dalloc(&h->y_ir, n));
@@ -1428,21 +1494,44 @@ rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
       if (!h->f_init) CK(dalloc(&h->f_init, (size_t)n * L.nslot));
       CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * n * L.nslot, cudaMemcpyDeviceToDevice,
                          h->st));
-    } else {
+    } else if (!h->bf16) {
       std::vector<float> ff(fl.begin(), fl.end());
       CK(cudaMemcpyAsync(h->f_f, ff.data(), sizeof(float) * ff.size(), cudaMemcpyHostToDevice, h->st));
       if (!h->f_init_f) CK(dalloc(&h->f_init_f, (size_t)n * L.nslot));
       CK(cudaMemcpyAsync(h->f_init_f, h->f_f, sizeof(float) * n * L.nslot, cudaMemcpyDeviceToDevice,
                          h->st));
       CK(cudaStreamSynchronize(h->st));
+    } else {
+      // reference = the FP32 scalar flux of f0, remainders in BF16
+      std::vector<float> ref(n);
+      for (long c = 0; c < n; ++c) ref[c] = (float)rho[c];
+      std::vector<uint16_t> rb(fl.size());
+      for (size_t i = 0; i < fl.size(); ++i) {
+        const long c = (long)((i / L.dl) % n);
+        rb[i] = bf16_bits((float)(fl[i] - (double)ref[c]));
+      }
+      h->fcur = 0;
+      CK(cudaMemcpy(h->fb, rb.data(), sizeof(uint16_t) * rb.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->fref[0], ref.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+      if (!h->fb_init) CK(dalloc(&h->fb_init, (size_t)n * L.nslot));
+      if (!h->fref_init) CK(dalloc(&h->fref_init, n));
+      CK(cudaMemcpy(h->fb_init, rb.data(), sizeof(uint16_t) * rb.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->fref_init, ref.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
     }
     h->init_kind = 2;
   } else {
     if (!rho0) return fail(h, RTE_EINVAL, "rho0 or f0 is required");
     if (!finite_all(rho0, n)) return fail(h, RTE_EINVAL, "non-finite rho0");
     TRY(upload(h, h->rho, rho0, n));
-    if (!h->fp32) CK(launch_isotropic_f(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
-    else CK(launch_isotropic_f32(h->rho, (int)n, L.nslot, L.dl, h->f_f, h->st));
+    if (!h->fp32) {
+      CK(launch_isotropic_f(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
+    } else if (!h->bf16) {
+      CK(launch_isotropic_f32(h->rho, (int)n, L.nslot, L.dl, h->f_f, h->st));
+    } else {   // isotropic: zero remainders about the reference rho0
+      h->fcur = 0;
+      CK(cudaMemsetAsync(h->fb, 0, sizeof(__nv_bfloat16) * n * L.nslot, h->st));
+      CK(launch_to_float(h->rho, n, h->fref[0], h->st));
+    }
     h->init_kind = 1;
   }
   if (!h->rho_init) CK(dalloc(&h->rho_init, n));
@@ -1463,7 +1552,18 @@ rte_status rte_restart(rte_handle h) {
   if (h->init_kind == 0) return fail(h, RTE_ESTATE, "rte_set_initial has not been called");
   const long n = h->ncell;
   CK(cudaMemcpyAsync(h->rho, h->rho_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  if (h->init_kind == 2 && !h->fp32)
+  if (h->bf16) {
+    h->fcur = 0;
+    if (h->init_kind == 2) {
+      CK(cudaMemcpyAsync(h->fb, h->fb_init, sizeof(__nv_bfloat16) * n * h->L.nslot,
+                         cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpyAsync(h->fref[0], h->fref_init, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                         h->st));
+    } else {
+      CK(cudaMemsetAsync(h->fb, 0, sizeof(__nv_bfloat16) * n * h->L.nslot, h->st));
+      CK(launch_to_float(h->rho, n, h->fref[0], h->st));
+    }
+  } else if (h->init_kind == 2 && !h->fp32)
     CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * n * h->L.nslot, cudaMemcpyDeviceToDevice,
                        h->st));
   else if (h->init_kind == 2)
@@ -1530,11 +1630,21 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
   if (!h->fp32) {
     CK(cudaMemcpyAsync(fl.data(), h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-  } else {
+  } else if (!h->bf16) {
     std::vector<float> ff(fl.size());
     CK(cudaMemcpyAsync(ff.data(), h->f_f, sizeof(float) * ff.size(), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     for (size_t i = 0; i < ff.size(); ++i) fl[i] = ff[i];
+  } else {
+    std::vector<uint16_t> rb(fl.size());
+    std::vector<float> ref(n);
+    CK(cudaMemcpyAsync(rb.data(), h->fb, sizeof(uint16_t) * rb.size(), cudaMemcpyDeviceToHost,
+                       h->st));
+    CK(cudaMemcpyAsync(ref.data(), h->fref[h->fcur], sizeof(float) * n, cudaMemcpyDeviceToHost,
+                       h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (size_t i = 0; i < rb.size(); ++i)
+      fl[i] = (double)(ref[(i / L.dl) % n] + bf16_value(rb[i]));
   }
   for (int d = 0; d < L.nv; ++d) {
     const int s = L.slot_of_dir[d];

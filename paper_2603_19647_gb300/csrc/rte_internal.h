@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA kernels and the host driver of librte.so.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,6 +51,7 @@ struct Sweep2DArgs {
   const Real* w;        // [nslot]
   const int* fam_quad;  // [nfam]
   const Real* sig_t;    // [ncell]
+  const Real* sig_tl;   // [ncell] FP32: sigma_t - sig_t exactly (the low part), or nullptr
   const Real* inv_d;    // [nfam][ncell][dl] 1/(tau+sigma_t+a+b) or nullptr (computed)
   const unsigned* skip; // set: the launch does nothing (speculative SI-SA work past convergence)
   const Real* cth;      // [nslot] tau + a + b, high part, or nullptr (formed from tau, a, b)
@@ -58,6 +60,10 @@ struct Sweep2DArgs {
   const Real* q;        // [ncell]
   const Real* g2;       // K2 pass B isotropic source G [ncell]
   Real* f;              // K2: [nfam][ncell][dl] in / out (f^{n-1} -> f^n)
+  __nv_bfloat16* fb;    // BF16 mode (MODE 3 / 4): f - reference, [nfam][ncell][dl]
+  const float* fro;     // BF16 mode: reference of the stored f^{n-1} [ncell]
+  const float* frn;     // BF16 mode: reference of f^n [ncell] (MODE 4: = fro)
+  unsigned seed;        // BF16 mode: per-launch seed of the stochastic rounding
   Real* pm;             // [nfam][ncell] partial moments (K1: of L^-1 q; K2: of pass B)
   Real gx[4], gy[4];    // per quadrant inflow ghost of pass A (K1: zero)
   Real* edge;           // [nfam][nblk][nx][dl] (K2: two planes, A then B)
@@ -76,6 +82,7 @@ struct Sweep1DArgs {
   const Real* cth;      // [nslot] tau + a split as hi / lo (FP32), or nullptr
   const Real* ctl;
   const Real* sig_t;
+  const Real* sig_tl;   // as in Sweep2DArgs
   const Real* q;        // [ncell]
   const Real* g2;       // K2 pass B source
   Real* f;              // [2][ncell][nslot/2]

@@ -17,6 +17,7 @@
 //
 // 1D: each direction's sweep psi_i = alpha_i psi_{i-1} + beta_i is a linear recurrence,
 // evaluated as a block-wide associative scan of affine maps.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -48,20 +49,22 @@ __device__ __forceinline__ float recip(float x) {
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// 1 / (ch + cl + s) as an unevaluated pair h + l, to about 2^-46 relative, in FP32.
-// ch + cl is tau + a + b of the direction (exact, split on the host) and s is sigma_t of the
-// cell: the sum is formed exactly (Knuth's TwoSum, then a renormalisation), the reciprocal by
-// one Newton correction whose residual 1 - d_h g_h is exact under FMA.  With it the FP32
-// sweeps are the exact Q0 operator of the FP32-rounded coefficients (conservative, no
-// per-step bias), not an operator whose division is off by an ulp.
+// 1 / (ch + cl + s + sl) as an unevaluated pair h + l, to about 2^-46 relative, in FP32.
+// ch + cl is tau + a + b of the direction and s + sl is sigma_t of the cell, both split
+// exactly on the host: the sum is formed exactly (Knuth's TwoSum, then a renormalisation),
+// the reciprocal by one Newton correction whose residual 1 - d_h g_h is exact under FMA.
+// With it the FP32 sweeps are the exact Q0 operator of the problem up to the FP32 rounding
+// of the streaming coefficients a, b (conservative, no per-step bias), not an operator whose
+// division is off by an ulp or whose absorption sigma_t - sigma_s is off by an ulp of
+// sigma_t (which in a strongly scattering cell is a large error in the absorption).
 struct Rcp2 {
   float h, l;
 };
-__device__ __forceinline__ Rcp2 rcp_pair(float ch, float cl, float s) {
+__device__ __forceinline__ Rcp2 rcp_pair(float ch, float cl, float s, float sl) {
   const float sum = ch + s;
   const float bb = sum - ch;
   float e = (ch - (sum - bb)) + (s - bb);
-  e += cl;
+  e += cl + sl;
   const float dh = sum + e;
   const float dl = e - (dh - sum);
   const float gh = recip(dh);
@@ -69,6 +72,24 @@ __device__ __forceinline__ Rcp2 rcp_pair(float ch, float cl, float s) {
   r = fmaf(-dl, gh, r);
   return {gh, r * gh};
 }
+// Unbiased (stochastic) rounding of x to BF16: a uniform 16-bit integer is added below the
+// kept bits before truncation, so E[result] = x; it keeps increments far below one BF16 ulp
+// from being lost step after step.  The random bits come from a counter-based integer hash
+// (the "lowbias32" mixer) of the cell-direction index and a per-launch seed.
+__device__ __forceinline__ unsigned hash32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_stochastic(float x, unsigned idx, unsigned seed) {
+  unsigned u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += hash32(idx ^ hash32(seed)) & 0xffffu;
+  return __ushort_as_bfloat16((unsigned short)(u >> 16));
+}
+
 // t * (h + l): the low part only in FP32 (l = 0 in FP64).
 __device__ __forceinline__ float scale2(float t, float h, float l) { return fmaf(t, h, t * l); }
 __device__ __forceinline__ double scale2(double t, double h, double) { return t * h; }
@@ -147,14 +168,20 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // CTA-wide barrier runs inside the column loop.
 template <class Real, int DL, int R, int K, int MODE, bool TABLE>
 __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A) {
+  // MODE 3 / 4: MODE 1 / 2 with f stored as a BF16 remainder about a per-cell FP32 reference
+  constexpr bool BF = MODE >= 3;
+  constexpr int MB = BF ? MODE - 2 : MODE;
+  static_assert(!BF || sizeof(Real) == 4, "BF16 storage of f goes with FP32 sweeps");
   constexpr int NG = 32 / DL;
   constexpr int RW = NG * R;
   constexpr int RING = 4 * K;
-  constexpr int NP = (MODE == 1) ? 2 : 1;            // planes (recurrences) carried
-  constexpr bool STAGE_F = MODE != 0;
+  constexpr int NP = (MB == 1) ? 2 : 1;              // planes (recurrences) carried
+  constexpr bool STAGE_F = MB != 0;
   constexpr int V = DL * (int)sizeof(Real) / 16;     // 16-byte pieces per cell of a family
+  constexpr int VB = DL * 2 / 16;                    // the same for BF16 values
   constexpr int PER_DL = (TABLE ? 1 : 0) + (STAGE_F ? 1 : 0);              // [RW][K][DL] arrays
-  constexpr int PER_S = (TABLE ? 0 : 1) + (MODE != 2 ? 1 : 0) + (MODE != 0 ? 1 : 0);  // [RW][K]
+  constexpr int PER_S =
+      (TABLE ? 0 : 2) + (MB != 2 ? 1 : 0) + (MB != 0 ? 1 : 0) + (BF ? 2 : 0);  // [RW][K]
   constexpr int WARP_REALS = 2 * RW * K * (PER_DL * DL + PER_S);
   static_assert(R <= DL, "rows per lane group must not exceed the lane count");
   if (A.skip && *A.skip) return;   // before the ticket: the control block stays untouched
@@ -172,8 +199,12 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   Real* tab_s = wbuf;                                            // [2][RW][K][DL]
   Real* f_s = tab_s + (TABLE ? 2 * RW * K * DL : 0);             // [2][RW][K][DL]
   Real* st_s = f_s + (STAGE_F ? 2 * RW * K * DL : 0);            // [2][RW][K]
-  Real* qa_s = st_s + (TABLE ? 0 : 2 * RW * K);
-  Real* g2_s = qa_s + (MODE != 2 ? 2 * RW * K : 0);
+  Real* stl_s = st_s + (TABLE ? 0 : 2 * RW * K);                  // [2][RW][K] its low part
+  Real* qa_s = stl_s + (TABLE ? 0 : 2 * RW * K);
+  Real* g2_s = qa_s + (MB != 2 ? 2 * RW * K : 0);
+  Real* fro_s = g2_s + (MB != 0 ? 2 * RW * K : 0);   // BF16 mode: reference of f^{n-1}
+  Real* frn_s = fro_s + (BF ? 2 * RW * K : 0);        // BF16 mode: reference of f^n
+  __nv_bfloat16* bf_s = reinterpret_cast<__nv_bfloat16*>(f_s);
   Real* rings = reinterpret_cast<Real*>(smraw) + (size_t)W * WARP_REALS;  // [W-1][NP][RING][DL]
   if (tid == 0) {
     s_ticket = atomicAdd(&A.ctrl->ticket, 1u);
@@ -202,7 +233,8 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   const Real gx = A.gx[quad];
   const Real gy = A.gy[quad];
   const Real* tab_fam = TABLE ? A.inv_d + (size_t)fam * ncell * DL : nullptr;
-  Real* f_fam = STAGE_F ? A.f + (size_t)fam * ncell * DL : nullptr;
+  Real* f_fam = (STAGE_F && !BF) ? A.f + (size_t)fam * ncell * DL : nullptr;
+  __nv_bfloat16* fb_fam = BF ? A.fb + (size_t)fam * ncell * DL : nullptr;
   Real* ring_in = warp > 0 ? rings + (size_t)(warp - 1) * NP * RING * DL : nullptr;
   Real* ring_out = warp < W - 1 ? rings + (size_t)warp * NP * RING * DL : nullptr;
 
@@ -225,7 +257,7 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   // Copy this warp's data of chunk c into its buffer c & 1: row rr, step k -> column c K + k - rr.
   auto stage = [&](int c) {
     const int buf = c & 1;
-    if constexpr (TABLE || STAGE_F) {
+    if constexpr (TABLE || (STAGE_F && !BF)) {
       for (int e = lane; e < RW * K * V; e += 32) {
         const int v = e % V, rk = e / V;
         const int rr = rk / K, k = rk % K;
@@ -236,7 +268,19 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
         const int o = ((buf * RW + rr) * K + k) * DL + v * (16 / (int)sizeof(Real));
         const size_t g = (size_t)cell * DL + v * (16 / sizeof(Real));
         if constexpr (TABLE) cp_async_16(tab_s + o, tab_fam + g, ok);
-        if constexpr (STAGE_F) cp_async_16(f_s + o, f_fam + g, ok);
+        if constexpr (STAGE_F && !BF) cp_async_16(f_s + o, f_fam + g, ok);
+      }
+    }
+    if constexpr (BF) {
+      for (int e = lane; e < RW * K * VB; e += 32) {
+        const int v = e % VB, rk = e / VB;
+        const int rr = rk / K, k = rk % K;
+        const int x = c * K + k - rr;
+        const int jj = wrow0 + rr;
+        const bool ok = x >= 0 && x < nx && jj < ny;
+        const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
+        const int o = ((buf * RW + rr) * K + k) * DL + v * 8;
+        cp_async_16(bf_s + o, fb_fam + (size_t)cell * DL + v * 8, ok);
       }
     }
     for (int e = lane; e < RW * K; e += 32) {
@@ -246,9 +290,16 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
       const bool ok = x >= 0 && x < nx && jj < ny;
       const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
       const int o = (buf * RW + rr) * K + k;
-      if constexpr (!TABLE) cp_async(st_s + o, A.sig_t + cell, ok);
-      if constexpr (MODE != 2) cp_async(qa_s + o, A.q + cell, ok);
-      if constexpr (MODE != 0) cp_async(g2_s + o, A.g2 + cell, ok);
+      if constexpr (!TABLE) {
+        cp_async(st_s + o, A.sig_t + cell, ok);
+        cp_async(stl_s + o, A.sig_tl + cell, ok && A.sig_tl != nullptr);
+      }
+      if constexpr (MB != 2) cp_async(qa_s + o, A.q + cell, ok);
+      if constexpr (MB != 0) cp_async(g2_s + o, A.g2 + cell, ok);
+      if constexpr (BF) {
+        cp_async(fro_s + o, A.fro + cell, ok);
+        cp_async(frn_s + o, A.frn + cell, ok);
+      }
     }
     cp_async_commit();
   };
@@ -286,7 +337,7 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
         for (int k = 0; k < K; ++k) {
           const int x = tb + k;
           ebA[k] = (gi == 0 && x < nx) ? ldcg(edge_in + (size_t)x * DL + dl) : Real(0);
-          if constexpr (MODE == 1)
+          if constexpr (MB == 1)
             ebB[k] = (gi == 0 && x < nx) ? ldcg(edge_in + plane + (size_t)x * DL + dl) : Real(0);
           else
             ebB[k] = Real(0);
@@ -323,7 +374,7 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
         }
         const int rs = (t % RING) * DL + dl;
         ebA[k] = ring_in[rs];
-        if constexpr (MODE == 1) ebB[k] = ring_in[RING * DL + rs];
+        if constexpr (MB == 1) ebB[k] = ring_in[RING * DL + rs];
         if (k == K - 1 || t == nx - 1) {
           __syncwarp();
           if (lane == 0) s_cons[warp] = t + 1;   // ring slots of columns <= t may be reused
@@ -346,29 +397,47 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
           if constexpr (TABLE) {
             dinv = tab_s[od];
           } else if constexpr (sizeof(Real) == 4) {
-            const Rcp2 rp = rcp_pair(ct, ctl, st_s[o]);
+            const Rcp2 rp = rcp_pair(ct, ctl, st_s[o], stl_s[o]);
             dinv = rp.h;
             dinvl = rp.l;
           } else {
             dinv = recip(ct + st_s[o]);
           }
           const Real uA = (m == 0) ? upA : psA[m > 0 ? m - 1 : 0];
-          if constexpr (MODE == 0) {
+          if constexpr (MB == 0) {
             const Real v = scale2(qa_s[o] + ca * psA[m] + cb * uA, dinv, dinvl);
             psA[m] = v;
             mb[k * R + m] = v;
-          } else if constexpr (MODE == 2) {
-            const Real v = scale2(g2_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA, dinv, dinvl);
+          } else if constexpr (MB == 2) {
+            Real fo;
+            if constexpr (BF) fo = fro_s[o] + __bfloat162float(bf_s[od]);
+            else fo = f_s[od];
+            const Real v = scale2(g2_s[o] + A.tau * fo + ca * psA[m] + cb * uA, dinv, dinvl);
             psA[m] = v;
             mb[k * R + m] = v;
           } else {
-            const Real va = scale2(qa_s[o] + A.tau * f_s[od] + ca * psA[m] + cb * uA, dinv, dinvl);
+            Real fo;
+            if constexpr (BF) fo = fro_s[o] + __bfloat162float(bf_s[od]);
+            else fo = f_s[od];
+            const Real va = scale2(qa_s[o] + A.tau * fo + ca * psA[m] + cb * uA, dinv, dinvl);
             psA[m] = va;
             const int px = xpos ? x : nx - 1 - x;
             const int py = ypos ? jj : ny - 1 - jj;
-            f_fam[((long)py * nx + px) * DL + dl] = va;
+            // f^n as stored: exactly in FP32 / FP64, as reference + BF16(f^n - reference) in
+            // BF16 mode; pass B sweeps the stored value, so the next step's b~ matches f^n
+            Real vst;
+            if constexpr (BF) {
+              const __nv_bfloat16 rb =
+                  bf16_stochastic(va - frn_s[o], (unsigned)(((long)py * nx + px) * A.nslot + slot),
+                                  A.seed);
+              fb_fam[((long)py * nx + px) * DL + dl] = rb;
+              vst = frn_s[o] + __bfloat162float(rb);
+            } else {
+              f_fam[((long)py * nx + px) * DL + dl] = va;
+              vst = va;
+            }
             const Real uB = (m == 0) ? upB : psB[m > 0 ? m - 1 : 0];
-            const Real vb = scale2(g2_s[o] + A.tau * va + ca * psB[m] + cb * uB, dinv, dinvl);
+            const Real vb = scale2(g2_s[o] + A.tau * vst + ca * psB[m] + cb * uB, dinv, dinvl);
             psB[m] = vb;
             mb[k * R + m] = vb;
           }
@@ -396,14 +465,14 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
           if (gi == NG - 1) {
             const int rs = (xb % RING) * DL + dl;
             ring_out[rs] = psA[R - 1];
-            if constexpr (MODE == 1) ring_out[RING * DL + rs] = psB[R - 1];
+            if constexpr (MB == 1) ring_out[RING * DL + rs] = psB[R - 1];
           }
           __syncwarp();
           __threadfence_block();
           if (lane == 0) s_prod[warp] = xb + 1;
         } else if (has_down && gi == NG - 1) {
           edge_out[(size_t)xb * DL + dl] = psA[R - 1];
-          if constexpr (MODE == 1) edge_out[plane + (size_t)xb * DL + dl] = psB[R - 1];
+          if constexpr (MB == 1) edge_out[plane + (size_t)xb * DL + dl] = psB[R - 1];
         }
       }
     }
@@ -465,9 +534,11 @@ constexpr int KSTEP = 8;   // columns per chunk
 
 inline size_t sweep2d_smem_bytes_impl(size_t real, int dl, int R, int W, int mode, bool table) {
   const int K = 8;
-  const int RW = (32 / dl) * R, np = mode == 1 ? 2 : 1;
-  const int per_dl = (table ? 1 : 0) + (mode != 0 ? 1 : 0);
-  const int per_s = (table ? 0 : 1) + (mode != 2 ? 1 : 0) + (mode != 0 ? 1 : 0);
+  const bool bf = mode >= 3;
+  const int mb = bf ? mode - 2 : mode;
+  const int RW = (32 / dl) * R, np = mb == 1 ? 2 : 1;
+  const int per_dl = (table ? 1 : 0) + (mb != 0 ? 1 : 0);
+  const int per_s = (table ? 0 : 2) + (mb != 2 ? 1 : 0) + (mb != 0 ? 1 : 0) + (bf ? 2 : 0);
   const size_t warp_reals = (size_t)2 * RW * K * (per_dl * dl + per_s);
   return real * (W * warp_reals + (size_t)(W - 1) * np * 4 * K * dl);
 }
@@ -578,10 +649,10 @@ struct Cell1D {
   double d;
 };
 template <class Real>
-__device__ __forceinline__ Cell1D<Real> cell1d(Real ct, Real ctl, Real sig) {
+__device__ __forceinline__ Cell1D<Real> cell1d(Real ct, Real ctl, Real sig, Real sigl) {
   if constexpr (sizeof(Real) == 4) {
-    const Rcp2 rp = rcp_pair(ct, ctl, sig);
-    return {rp.h, rp.l, (double)ct + (double)ctl + (double)sig};
+    const Rcp2 rp = rcp_pair(ct, ctl, sig, sigl);
+    return {rp.h, rp.l, (double)ct + (double)ctl + (double)sig + (double)sigl};
   } else {
     const double d = ct + sig;
     return {Real(1) / d, Real(0), d};
@@ -610,7 +681,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
   Aff<double> mine{1.0, 0.0};
   for (int k = k0; k < k1; ++k) {
     const int c = pos ? k : nx - 1 - k;
-    const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
+    const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c], A.sig_tl ? A.sig_tl[c] : Real(0));
     Real s = (MODE == 2) ? A.g2[c] : A.q[c];
     if (MODE != 0) s += A.tau * A.f[fbase + (long)c * dlh];
     mine = compose(mine, Aff<double>{(double)ca / cc.d, (double)s / cc.d});
@@ -619,7 +690,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
   Real psi = (Real)block_scan_entry(mine, (double)gA, sh);
   for (int k = k0; k < k1; ++k) {
     const int c = pos ? k : nx - 1 - k;
-    const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
+    const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c], A.sig_tl ? A.sig_tl[c] : Real(0));
     Real s = (MODE == 2) ? A.g2[c] : A.q[c];
     if (MODE == 2) {
       s += A.tau * A.f[fbase + (long)c * dlh];
@@ -641,14 +712,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) sweep1d_kernel(const Sweep1DArgs
     Aff<double> mb{1.0, 0.0};
     for (int k = k0; k < k1; ++k) {
       const int c = pos ? k : nx - 1 - k;
-      const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
+      const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c], A.sig_tl ? A.sig_tl[c] : Real(0));
       const Real s = A.g2[c] + A.tau * A.f[fbase + (long)c * dlh];
       mb = compose(mb, Aff<double>{(double)ca / cc.d, (double)s / cc.d});
     }
     Real y = (Real)block_scan_entry(mb, 0.0, sh);
     for (int k = k0; k < k1; ++k) {
       const int c = pos ? k : nx - 1 - k;
-      const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c]);
+      const Cell1D<Real> cc = cell1d(ct, ctl, A.sig_t[c], A.sig_tl ? A.sig_tl[c] : Real(0));
       const Real s = A.g2[c] + A.tau * A.f[fbase + (long)c * dlh];
       y = scale2(s + ca * y, cc.h, cc.l);
       A.psi_w[(long)slot * nx + c] = cw * y;
@@ -680,7 +751,7 @@ __global__ void inv_d_kernel(const Real* sig_t, const Real* a, const Real* b, Re
 
 }  // namespace
 
-// The 2D kernels are instantiated in six translation units (precision x mode) so that the
+// The 2D kernels are instantiated in eight translation units (precision x mode) so that the
 // build compiles them in parallel: RTE_SWEEP_PART selects one, -1 builds everything.
 #ifndef RTE_SWEEP_PART
 #define RTE_SWEEP_PART -1
@@ -717,6 +788,13 @@ RTE_SWEEP_INST(4, float, 1)
 RTE_SWEEP_INST(5, float, 2)
 #endif
 
+#if RTE_SWEEP_PART == -1 || RTE_SWEEP_PART == 7
+RTE_SWEEP_INST(7, float, 3)
+#endif
+#if RTE_SWEEP_PART == -1 || RTE_SWEEP_PART == 8
+RTE_SWEEP_INST(8, float, 4)
+#endif
+
 #if RTE_SWEEP_PART == -1 || RTE_SWEEP_PART == 6
 #if RTE_SWEEP_PART == 6
 RTE_SWEEP_EXTERN(double, 0)
@@ -725,6 +803,8 @@ RTE_SWEEP_EXTERN(double, 2)
 RTE_SWEEP_EXTERN(float, 0)
 RTE_SWEEP_EXTERN(float, 1)
 RTE_SWEEP_EXTERN(float, 2)
+RTE_SWEEP_EXTERN(float, 3)
+RTE_SWEEP_EXTERN(float, 4)
 #endif
 size_t sweep2d_smem_bytes(size_t real, int dl, int R, int W, int mode, bool table) {
   return sweep2d_smem_bytes_impl(real, dl, R, W, mode, table);
@@ -735,7 +815,12 @@ cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStre
   const int dl = a.nslot / a.nfam;
   if (mode == 0) return launch_sweep2d_mode<Real, 0>(a, dl, R, s);
   if (mode == 2) return launch_sweep2d_mode<Real, 2>(a, dl, R, s);
-  return launch_sweep2d_mode<Real, 1>(a, dl, R, s);
+  if (mode == 1) return launch_sweep2d_mode<Real, 1>(a, dl, R, s);
+  if constexpr (sizeof(Real) == 4) {
+    if (mode == 3) return launch_sweep2d_mode<Real, 3>(a, dl, R, s);
+    if (mode == 4) return launch_sweep2d_mode<Real, 4>(a, dl, R, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <class Real>
