@@ -81,3 +81,11 @@ def test_batch_create_rejects_bad_instance(lib):
         rte.rte_batch_create(wls)
     assert ei.value.status == rte.RTE_EINVAL
     assert "instance 1" in str(ei.value)
+
+
+def test_bf16_storage_is_2d_only(lib):
+    from paper_2603_19647_gb300 import inputs
+    wl = inputs.slab_1d(n=16)
+    with pytest.raises(rte.RteError) as ei:
+        rte.create_from_workload(wl, options=rte.default_options(precision=rte.RTE_FP32_BF16F))
+    assert ei.value.status == rte.RTE_EINVAL

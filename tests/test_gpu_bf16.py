@@ -83,10 +83,3 @@ def test_bf16_restart_reproduces():
     h.rte_step(10)
     assert np.array_equal(a, h.rte_get_scalar_flux())
     h.destroy()
-
-
-def test_bf16_rejected_in_1d():
-    wl = inputs.slab_1d(n=16)
-    with pytest.raises(rte.RteError) as ei:
-        rte.create_from_workload(wl, options=rte.default_options(**BF16))
-    assert ei.value.status == rte.RTE_EINVAL
