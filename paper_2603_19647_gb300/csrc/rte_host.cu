@@ -1196,9 +1196,10 @@ rte_status time_sweeps(rte_handle h, int kind, float* ms) {
 }
 
 struct TuneKey {
-  int device, nx, ny, nv, fp32;
+  int device, nx, ny, nv, precision;
   bool operator<(const TuneKey& o) const {
-    return std::tie(device, nx, ny, nv, fp32) < std::tie(o.device, o.nx, o.ny, o.nv, o.fp32);
+    return std::tie(device, nx, ny, nv, precision) <
+           std::tie(o.device, o.nx, o.ny, o.nv, o.precision);
   }
 };
 struct TuneVal {
@@ -1227,7 +1228,7 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     *dl_out = dl;
     return RTE_OK;
   }
-  const TuneKey key{h->device, h->nx, h->ny, (int)h->mu_user.size(), h->fp32 ? 1 : 0};
+  const TuneKey key{h->device, h->nx, h->ny, (int)h->mu_user.size(), h->opt.precision};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
