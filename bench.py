@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reduced-precision and batched workloads measured beside the line")
     ap.add_argument("--n", type=int, default=256, help="grid side (256 = the benchmark workload)")
     return ap.parse_args()
 
@@ -148,6 +150,56 @@ def oracle_sample(wl, budget_s, min_steps=2):
     dt = time.perf_counter() - t0
     updates = sum(s.sweeps for s in o.log) * wl.ncell * p.nv
     return updates / dt, k, dt, transport.num_threads(), o
+
+
+def extra_workloads(rte, inputs, torch):
+    """The other rows of the method on this GPU, each a short, separately timed run (CUDA
+    events on the library's stream): FP32 and FP64 on the 1024^2 log-normal workload (100 of
+    its 500 steps), FP32 and BF16 storage on the 2048^2 diffusive disc (20 of 300 steps), and
+    the 64 batched instances (20 of 100 steps).  Reported beside the headline line."""
+    out = {}
+
+    def march(wl, steps, **o):
+        h = rte.create_from_workload(wl, options=rte.default_options(**o))
+        h.rte_step(2)
+        h.rte_restart()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.rte_step(steps)
+        dt = time.perf_counter() - t0
+        st = h.rte_get_stats()
+        rho = h.rte_get_scalar_flux()
+        h.destroy()
+        return {"ms_per_step": 1e3 * dt / steps, "updates_per_s": st["cell_direction_updates"] / dt,
+                "iterations_per_step": st["total_iterations"] / steps,
+                "si_sweep_ms": st["si_sweep_kernel_ms"] / max(1, st["si_sweep_launches"]),
+                "f_sweep_ms": st["f_sweep_kernel_ms"] / max(1, st["f_sweep_launches"]),
+                "phase_end": st["phase"]}, rho
+
+    import numpy as np
+    ln = inputs.lognormal()
+    r64, rho64 = march(ln, 100, rom=rte.RTE_ROM_AUTO)
+    r32, rho32 = march(ln, 100, rom=rte.RTE_ROM_AUTO, precision=rte.RTE_FP32)
+    p64, _ = march(ln, 100, rom=rte.RTE_ROM_OFF)
+    r32["rel_l2_vs_fp64_gpu"] = float(np.linalg.norm(rho32 - rho64) / np.linalg.norm(rho64))
+    out["lognormal_1024sq_128dirs_100steps"] = {"rom_fp64": r64, "rom_fp32": r32, "sidsa_fp64": p64}
+    disc = inputs.diffusive_disc()
+    d32, rho_d32 = march(disc, 20, precision=rte.RTE_FP32, r_max=60)
+    dbf, rho_dbf = march(disc, 20, precision=rte.RTE_FP32_BF16F, r_max=60)
+    dbf["rel_l2_vs_fp32_gpu"] = float(np.linalg.norm(rho_dbf - rho_d32) / np.linalg.norm(rho_d32))
+    out["diffusive_disc_2048sq_256dirs_20steps"] = {"rom_fp32": d32, "rom_bf16_f": dbf}
+    wls = inputs.batched()
+    b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32))
+    b.rte_batch_step(2)
+    b.rte_batch_restart()
+    t0 = time.perf_counter()
+    b.rte_batch_step(20)
+    dt = time.perf_counter() - t0
+    upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b)))
+    b.destroy()
+    out["batched_64_instances_20steps_fp32_rom"] = {"ms_per_step": 1e3 * dt / 20,
+                                                   "updates_per_s": upd / dt}
+    return out
 
 
 def run_reference(args):
@@ -328,6 +380,8 @@ def run_ours(args):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if not args.no_extras and world == 1:
+        line["other_workloads"] = extra_workloads(rte, inputs, torch)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
