@@ -92,9 +92,12 @@ typedef struct {
   double cg_rtol;    /* DSA conjugate-gradient tolerance ||r|| <= cg_rtol ||b|| (default 1e-6) */
   int cg_max_iter;   /* default 500 */
   int tune;          /* 1 (default): pick sweep tile shapes by timing at create; 0: heuristic */
-  int sweep_rows;    /* 2D sweep: rows per lane group, 1, 2, 4 or 8 (0 = automatic) */
+  int sweep_rows;    /* 2D sweep: rows per lane group, 1, 2, 4 or 8 (0 = automatic); the tile
+                        sequence takes 4 or 8 */
   int sweep_lanes;   /* 2D sweep: directions per lane group, 8, 16 or 32 (0 = automatic) */
   int sweep_warps;   /* 2D sweep: warps per CTA, 1..8 (0 = automatic); reduced to fit shared memory */
+  int sweep_kernel;  /* 2D sweep kernel: 0 measured choice (with tune), 1 strip chain, 2 tile
+                        sequence (FP32 modes; sweep_rows then = rows per tile, 4 or 8) */
   int lookahead;     /* 1: queue SI iteration l+1 before reading the stopping test of l (work
                         past convergence skips itself on the device); 0 (default): wait first */
 } rte_options;
@@ -122,6 +125,7 @@ typedef struct {
   /* 2D sweep tiling in use: directions per lane group, then rows per lane group and warps
    * per CTA of the SI sweep and of the fused f sweep; sweep_tuned = 1 when measured */
   int sweep_lanes, sweep_si_rows, sweep_si_warps, sweep_f_rows, sweep_f_warps, sweep_tuned;
+  int sweep_si_kernel, sweep_f_kernel;   /* 1 strip chain, 2 tile sequence */
 } rte_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -72,6 +72,8 @@ struct rte_s {
   Layout L;
   // 2D sweep tiles: [0] for the SI sweep and the y sweep, [1] for the fused f sweep
   struct Tile {
+    int kind = 1;   // 1: strip chain (sweep.cu, R rows per lane group), 2: tile sequence
+                    // (sweep_tile.cu, FP32 modes, R = TH rows per lane group)
     int R = 1, W = 8, rpb = 32, nblk = 1;
   } tile[2];
   int nblk_max = 1;   // edge buffers and control flags are sized for the larger tile count
@@ -418,6 +420,15 @@ void ghosts(const double g[4], Real gx[4], Real gy[4]) {
   }
 }
 
+// Launch a 2D sweep with the tile of its kind (tl).
+template <class Real>
+cudaError_t launch2d(rte_handle h, const Sweep2DArgs<Real>& a, int mode, const rte_s::Tile& tl) {
+  if constexpr (sizeof(Real) == 4) {
+    if (tl.kind == 2) return launch_sweep2d_tile(a, mode, tl.R, tl.W, h->st);
+  }
+  return launch_sweep2d<Real>(a, mode, tl.R, h->st);
+}
+
 // Partial moments (pm) of sum_j w_j L_j^{-1} q for the isotropic source in v.q, inflow g
 // (nullptr: vacuum): per family in 2D, the full moment in 1D.
 template <class Real>
@@ -429,7 +440,7 @@ rte_status k1(rte_handle h, const SV<Real>& v, const double* g) {
     a.q = v.q;
     a.pm = v.pm;
     ghosts(g, a.gx, a.gy);
-    CK(launch_sweep2d<Real>(a, 0, h->tile[0].R, h->st));
+    CK(launch2d<Real>(h, a, 0, h->tile[0]));
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.q = v.q;
@@ -460,7 +471,7 @@ rte_status k2(rte_handle h, const SV<Real>& v) {
       a.seed = h->bf_seed++;
       mode = 3;
     }
-    CK(launch_sweep2d<Real>(a, mode, h->tile[1].R, h->st));
+    CK(launch2d<Real>(h, a, mode, h->tile[1]));
     if (h->bf16) h->fcur = 1 - h->fcur;
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
@@ -490,7 +501,7 @@ rte_status ky(rte_handle h, const SV<Real>& v) {
       a.fro = a.frn = h->fref[h->fcur];
       mode = 4;
     }
-    CK(launch_sweep2d<Real>(a, mode, h->tile[0].R, h->st));
+    CK(launch2d<Real>(h, a, mode, h->tile[0]));
   } else {
     Sweep1DArgs<Real> a = args1d(h, v);
     a.g2 = v.src;
@@ -1159,39 +1170,45 @@ void free_sweep(rte_handle h) {
   dfree(h->edge_f), dfree(h->ctrl), dfree(h->psi_w), dfree(h->psi_w_f);
 }
 
-void set_tile(rte_handle h, rte_s::Tile& tl, int R, int W) {
+void set_tile(rte_handle h, rte_s::Tile& tl, int kind, int R, int W) {
+  tl.kind = kind;
   tl.R = R;
   tl.W = W;
   tl.rpb = W * (32 / h->L.dl) * R;
   tl.nblk = (h->ny + tl.rpb - 1) / tl.rpb;
 }
 
-// A tile is usable when R <= dl and every sweep kind's staging fits the 200 KiB the
-// launcher allows.
-bool tile_fits(rte_handle h, int dl, int R, int W) {
+// A tile is usable when its kind applies (the tile sequence is FP32 only, with TH = 4 or 8;
+// the strip chain needs R <= dl) and every sweep mode's staging fits the 200 KiB the
+// launchers allow.
+bool tile_fits(rte_handle h, int dl, int kind, int R, int W) {
+  const int modes_plain[3] = {0, 1, 2}, modes_bf[3] = {0, 3, 4};
+  if (kind == 2) {
+    if (!h->fp32 || (R != 4 && R != 8)) return false;
+    for (int mode : h->bf16 ? modes_bf : modes_plain)
+      if (sweep2d_tile_smem_bytes(dl, R, W, mode) > 200 * 1024) return false;
+    return true;
+  }
   if (R > dl) return false;
   const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
-  const int modes_plain[3] = {0, 1, 2}, modes_bf[3] = {0, 3, 4};
   for (int mode : h->bf16 ? modes_bf : modes_plain)
     if (sweep2d_smem_bytes(real, dl, R, W, mode, !h->fp32) > 200 * 1024) return false;
   return true;
 }
 
-// Mean device time of two launches of one sweep kind (0: SI sweep, 1: fused f sweep) after
-// one warm-up launch.
+// Device time of one launch of one sweep mode (0: SI sweep, 1: fused f sweep) after one
+// warm-up launch.
 rte_status time_sweeps(rte_handle h, int kind, float* ms) {
   auto run = [&]() -> rte_status {
     return kind == 0 ? sweep_q(h, nullptr) : sweep_f(h, h->rho, h->y);
   };
   TRY(run());
   CK(cudaEventRecord(h->kev0, h->st));
-  for (int i = 0; i < 2; ++i) TRY(run());
+  TRY(run());
   CK(cudaEventRecord(h->kev1, h->st));
   CK(cudaEventSynchronize(h->kev1));
   TRY(check_sweep_error(h));
-  float t = 0.f;
-  CK(cudaEventElapsedTime(&t, h->kev0, h->kev1));
-  *ms = 0.5f * t;
+  CK(cudaEventElapsedTime(ms, h->kev0, h->kev1));
   return RTE_OK;
 }
 
@@ -1203,28 +1220,37 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int dl, r0, w0, r1, w1;
+  int dl;
+  rte_s::Tile t0, t1;   // kind, R, W of the SI sweep and of the fused sweep
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
 
-// Direction lanes per family (dl) and the tiles (R rows per lane group, W warps per CTA) of
-// the two sweep kinds.  With options.tune every usable (dl, R, W) is timed on this problem's
-// own data (zero flux; the kernels' work does not depend on the values) and the choice with
-// the least 3 t_SI + t_f is kept, once per (device, grid, direction count, precision) and
-// process.  Explicit sweep_* options, or tune = 0, give the fixed choice instead.
+// Direction lanes per family (dl), and for each of the two sweep modes the kernel (strip
+// chain, or for FP32 the tile sequence) with its tile (R rows per lane group, W warps per
+// CTA).  With options.tune every usable combination is timed on this problem's own data (zero
+// flux; the kernels' work does not depend on the values) and the choice with the least
+// 3 t_SI + t_f is kept, once per (device, grid, direction count, precision) and process.
+// Explicit sweep_* options, or tune = 0, give the fixed choice instead.
 rte_status choose_tiles(rte_handle h, int* dl_out) {
   const int dq = (int)h->mu_user.size() / 4;
   const int dl_max = dq >= 32 ? 32 : std::max(8, next_pow2(dq));
-  const bool fixed = h->opt.sweep_lanes || h->opt.sweep_rows || h->opt.sweep_warps || !h->opt.tune;
+  const bool fixed = h->opt.sweep_lanes || h->opt.sweep_rows || h->opt.sweep_warps ||
+                     h->opt.sweep_kernel || !h->opt.tune;
   if (fixed) {
     int dl = h->opt.sweep_lanes ? h->opt.sweep_lanes
                                 : std::min(dl_max, (!h->fp32 && h->ncell >= 512L * 512) ? 32 : 8);
-    int R = std::min(h->opt.sweep_rows ? h->opt.sweep_rows : (h->fp32 ? 2 : 1), dl);
+    const int kind = (h->opt.sweep_kernel == 2 && h->fp32) ? 2 : 1;
+    int R = h->opt.sweep_rows ? h->opt.sweep_rows : (kind == 2 ? 4 : (h->fp32 ? 2 : 1));
+    if (kind == 1) R = std::min(R, dl);
     int W = h->opt.sweep_warps ? h->opt.sweep_warps : 8;
-    while (W > 1 && !tile_fits(h, dl, R, W)) --W;
-    h->tile[0].R = h->tile[1].R = R;
-    h->tile[0].W = h->tile[1].W = W;
+    while (W > 1 && !tile_fits(h, dl, kind, R, W)) --W;
+    if (!tile_fits(h, dl, kind, R, W)) return fail(h, RTE_EINVAL, "the sweep tile does not fit");
+    for (auto& tl : h->tile) {
+      tl.kind = kind;
+      tl.R = R;
+      tl.W = W;
+    }
     *dl_out = dl;
     return RTE_OK;
   }
@@ -1233,29 +1259,36 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      const TuneVal& v = it->second;
-      h->tile[0].R = v.r0, h->tile[0].W = v.w0, h->tile[1].R = v.r1, h->tile[1].W = v.w1;
-      *dl_out = v.dl;
+      h->tile[0] = it->second.t0;
+      h->tile[1] = it->second.t1;
+      *dl_out = it->second.dl;
       h->tuned = true;
       return RTE_OK;
     }
   }
   float best = INFINITY;
-  TuneVal bv{0, 1, 8, 1, 8};
+  TuneVal bv{};
   const int dls[3] = {8, 16, 32};
+  struct Cand {
+    int kind, R, W;
+  };
   for (int dl : dls) {
     if (dl > dl_max) continue;
     TRY(make_layout(h, dl));
-    std::vector<std::pair<int, int>> cand;
-    const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8};
+    std::vector<Cand> cand;
+    const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8}, ths[2] = {4, 8};
     for (int R : rs)
       for (int W : ws)
-        if (tile_fits(h, dl, R, W)) cand.push_back({R, W});
+        if (tile_fits(h, dl, 1, R, W)) cand.push_back({1, R, W});
+    if (h->fp32)
+      for (int th : ths)
+        for (int W : ws)
+          if (tile_fits(h, dl, 2, th, W)) cand.push_back({2, th, W});
     if (cand.empty()) continue;
     int nb = 1;
     for (auto& c : cand) {
       rte_s::Tile tl;
-      set_tile(h, tl, c.first, c.second);
+      set_tile(h, tl, c.kind, c.R, c.W);
       nb = std::max(nb, tl.nblk);
     }
     h->nblk_max = nb;
@@ -1263,10 +1296,10 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     TRY(alloc_sweep(h));
     TRY(set_q(h, h->src, nullptr));
     float t1b = INFINITY, t2b = INFINITY;
-    std::pair<int, int> c1 = cand[0], c2 = cand[0];
+    Cand c1 = cand[0], c2 = cand[0];
     for (auto& c : cand) {
-      set_tile(h, h->tile[0], c.first, c.second);
-      set_tile(h, h->tile[1], c.first, c.second);
+      set_tile(h, h->tile[0], c.kind, c.R, c.W);
+      set_tile(h, h->tile[1], c.kind, c.R, c.W);
       float t1 = 0.f, t2 = 0.f;
       TRY(time_sweeps(h, 0, &t1));
       TRY(time_sweeps(h, 1, &t2));
@@ -1279,7 +1312,9 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     const float score = 3.f * t1b + t2b;
     if (score < best) {
       best = score;
-      bv = TuneVal{dl, c1.first, c1.second, c2.first, c2.second};
+      bv.dl = dl;
+      bv.t0.kind = c1.kind, bv.t0.R = c1.R, bv.t0.W = c1.W;
+      bv.t1.kind = c2.kind, bv.t1.R = c2.R, bv.t1.W = c2.W;
     }
   }
   if (bv.dl == 0) return fail(h, RTE_EINVAL, "no sweep tile fits in shared memory");
@@ -1287,7 +1322,8 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = bv;
   }
-  h->tile[0].R = bv.r0, h->tile[0].W = bv.w0, h->tile[1].R = bv.r1, h->tile[1].W = bv.w1;
+  h->tile[0] = bv.t0;
+  h->tile[1] = bv.t1;
   *dl_out = bv.dl;
   h->tuned = true;
   return RTE_OK;
@@ -1324,6 +1360,8 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
     return fail(h, RTE_EINVAL, "sweep_rows must be 0, 1, 2, 4 or 8");
   if (h->opt.sweep_warps < 0 || h->opt.sweep_warps > 8)
     return fail(h, RTE_EINVAL, "sweep_warps must be in [0, 8]");
+  if (h->opt.sweep_kernel < 0 || h->opt.sweep_kernel > 2)
+    return fail(h, RTE_EINVAL, "sweep_kernel must be 0, 1 or 2");
   if (!(h->opt.eps_sisa >= 0.0)) return fail(h, RTE_EINVAL, "eps_sisa must be >= 0");
   h->dim = mesh->dim;
   h->nx = mesh->nx;
@@ -1420,7 +1458,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   if (h->dim == 2) TRY(choose_tiles(h, &dl));
   TRY(make_layout(h, dl));
   if (h->dim == 2) {
-    for (auto& tl : h->tile) set_tile(h, tl, tl.R, tl.W);
+    for (auto& tl : h->tile) set_tile(h, tl, tl.kind, tl.R, tl.W);
     h->nblk_max = std::max(h->tile[0].nblk, h->tile[1].nblk);
   }
   TRY(setup_slots(h));
@@ -1677,6 +1715,8 @@ rte_status rte_get_stats(rte_handle h, rte_stats* st) {
     st->sweep_f_rows = h->tile[1].R;
     st->sweep_f_warps = h->tile[1].W;
     st->sweep_tuned = h->tuned ? 1 : 0;
+    st->sweep_si_kernel = h->tile[0].kind;
+    st->sweep_f_kernel = h->tile[1].kind;
   }
   return RTE_OK;
 }

@@ -96,6 +96,11 @@ struct Sweep1DArgs {
 size_t sweep2d_smem_bytes(size_t real, int dl, int R, int W, int mode, bool table);
 template <class Real>
 cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStream_t s);
+// FP32 tile-sequence sweep (sweep_tile.cu): TH rows per lane group, W warps per CTA,
+// rows_per_blk = W (32 / dl) TH; the same modes 0-4.
+cudaError_t launch_sweep2d_tile(const Sweep2DArgs<float>& a, int mode, int th, int W,
+                                cudaStream_t s);
+size_t sweep2d_tile_smem_bytes(int dl, int th, int W, int mode);
 template <class Real>
 cudaError_t launch_sweep1d(const Sweep1DArgs<Real>& a, int mode, cudaStream_t s);
 template <class Real>

@@ -1,0 +1,516 @@
+// 2D transport sweep of the FP32 modes in tile sequence (Sec. 2.1 Eq. (DG) with K = 0, in
+// upwind order, Sec. 2.3), with the quadrature moment fused in.
+//
+// Lane = direction (dl lanes per family of one quadrant), as in the strip chain of sweep.cu,
+// but a lane group owns a strip of TH rows and walks it one TW x TH tile at a time: inside a
+// tile every lane solves all TW * TH cells of its direction by itself (the x-upwind value is
+// the cell to the left, the y-upwind value the cell above, both in the lane's registers), so
+// the per-cell work is the cell solve alone and the hand-offs happen once per tile:
+//   * the bottom row of a tile goes to the lane group below by one warp shuffle per column,
+//   * from the last group of a warp to the first group of the next warp through a ring of
+//     RD tiles in shared memory (bounded spins on shared counters),
+//   * from the last warp of a CTA to the first warp of the next CTA of the same family
+//     through global memory behind a release flag per tile (bounded spins).
+// At warp step T lane group g works on tile T - g, so a warp keeps NG = 32 / dl tiles in
+// flight and the strips of a family form one pipeline down the grid.  Each group stages the
+// per-cell data of its next tile (sigma_t as an exact FP32 pair, the sources, f for the
+// fused sweep) into its own double buffer with cp.async while it computes the current one.
+// Out-of-range cells of the last tiles are computed from zero-filled inputs and never
+// stored; they lie downstream of every valid cell.
+//
+// Modes: 0 SI sweep (q, zero inflow unless given), 1 fused f sweep (pass A writes f^n, pass B
+// the moment of L^-1(g2 + tau f^n)), 2 y from the stored f, 3 / 4 = 1 / 2 with f stored as a
+// BF16 remainder about a per-cell FP32 reference (stochastic rounding on write).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "rte_internal.h"
+#include "sweep_common.cuh"
+
+namespace rte {
+
+namespace {
+using namespace sweep_detail;
+
+constexpr int TW = 8;   // columns per tile
+constexpr int RD = 4;   // tiles held by a ring between two warps
+
+template <int DL, int TH, int MODE>
+struct TileCfg {
+  static constexpr bool BF = MODE >= 3;
+  static constexpr int MB = BF ? MODE - 2 : MODE;
+  static constexpr int NG = 32 / DL;
+  static constexpr int NP = MB == 1 ? 2 : 1;
+  static constexpr int CELLS = TH * TW;
+  // per-cell arrays: sigma_t hi, lo, then q (modes 0, 1), g2 (modes 1, 2), BF16 references
+  static constexpr int A_ST = 0, A_STL = 1, A_Q = 2;
+  static constexpr int A_G2 = (MB != 2) ? 3 : 2;
+  static constexpr int A_FRO = A_G2 + (MB != 0 ? 1 : 0);
+  static constexpr int A_FRN = A_FRO + 1;
+  static constexpr int NARR = 2 + (MB != 2 ? 1 : 0) + (MB != 0 ? 1 : 0) + (BF ? 2 : 0);
+  static constexpr int ESZ = BF ? 2 : 4;                       // bytes of one stored f value
+  static constexpr int F_BYTES = (MB != 0) ? CELLS * DL * ESZ : 0;
+  static constexpr int GROUP_BYTES = NARR * CELLS * 4 + F_BYTES;   // one group, one buffer
+  static constexpr int WARP_BYTES = 2 * NG * GROUP_BYTES;
+  static constexpr int RING_FLOATS = NP * RD * TW * DL;
+  static constexpr int FP = (MB != 0) ? DL * ESZ / 16 : 0;     // 16-byte pieces of f per cell
+};
+
+template <int DL, int TH, int MODE>
+__global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<float> A) {
+  using C = TileCfg<DL, TH, MODE>;
+  constexpr int MB = C::MB;
+  constexpr bool BF = C::BF;
+  constexpr int NG = C::NG;
+  if (A.skip && *A.skip) return;   // before the ticket: the control block stays untouched
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned s_ticket;
+  __shared__ volatile int s_prod[8];    // tiles of its last group's bottom rows warp w has put in the ring
+  __shared__ volatile int s_cons[8];    // tiles of the ring above warp w has read
+  __shared__ volatile int s_abandon;
+
+  const int W = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane / DL, dl = lane % DL;
+  if (tid == 0) {
+    s_ticket = atomicAdd(&A.ctrl->ticket, 1u);
+    s_abandon = 0;
+  }
+  if (tid < 8) {
+    s_prod[tid] = 0;
+    s_cons[tid] = 0;
+  }
+  __syncthreads();
+  const unsigned ticket = s_ticket;
+  const int blk = (int)(ticket / (unsigned)A.nfam);
+  const int fam = (int)(ticket % (unsigned)A.nfam);
+  const int quad = A.fam_quad[fam];
+  const bool xpos = (quad & 1) == 0;
+  const bool ypos = quad < 2;
+  const int nx = A.nx, ny = A.ny;
+  const long ncell = (long)nx * ny;
+  const int slot = fam * DL + dl;
+  const float ca = A.a[slot], cb = A.b[slot], cw = A.w[slot];
+  const float ct = A.cth[slot], ctl = A.ctl[slot];
+  const float tau = A.tau;
+  const int strip = warp * NG + g;
+  const int row0 = blk * A.rows_per_blk + strip * TH;     // sweep-order first row of the strip
+  const int ntile = (nx + TW - 1) / TW;
+  const float gx = A.gx[quad], gy = A.gy[quad];
+
+  unsigned char* wbase = smraw + (size_t)warp * C::WARP_BYTES;
+  float* rings = reinterpret_cast<float*>(smraw + (size_t)W * C::WARP_BYTES);
+  const float* ring_in = warp > 0 ? rings + (size_t)(warp - 1) * C::RING_FLOATS : nullptr;
+  float* ring_out = warp < W - 1 ? rings + (size_t)warp * C::RING_FLOATS : nullptr;
+  float* f_fam = (MB == 1 && !BF) ? A.f + (size_t)fam * ncell * DL : nullptr;
+  __nv_bfloat16* fb_fam = (MB == 1 && BF) ? A.fb + (size_t)fam * ncell * DL : nullptr;
+  const unsigned char* fsrc = nullptr;
+  if constexpr (MB != 0) {
+    fsrc = BF ? reinterpret_cast<const unsigned char*>(A.fb + (size_t)fam * ncell * DL)
+              : reinterpret_cast<const unsigned char*>(A.f + (size_t)fam * ncell * DL);
+  }
+  const bool has_up = blk > 0;
+  const bool has_down = blk + 1 < A.nblk;
+  const size_t plane = (size_t)A.nfam * A.nblk * nx * DL;
+  const float* edge_in = A.edge + ((size_t)(fam * A.nblk + (has_up ? blk - 1 : 0)) * nx) * DL;
+  float* edge_out = A.edge + ((size_t)(fam * A.nblk + blk) * nx) * DL;
+  unsigned* flag_in = &A.ctrl->flags[fam * A.nblk + (has_up ? blk - 1 : 0)];
+  unsigned* flag_out = &A.ctrl->flags[fam * A.nblk + blk];
+
+  auto phys = [&](int x, int y) -> long {
+    return (long)(ypos ? y : ny - 1 - y) * nx + (xpos ? x : nx - 1 - x);
+  };
+  auto group_buf = [&](int buf) -> unsigned char* {
+    return wbase + (size_t)(buf * NG + g) * C::GROUP_BYTES;
+  };
+  // cp.async the inputs of tile t of this group's strip into buffer buf.
+  auto stage = [&](int t, int buf) {
+    if (t >= 0 && t < ntile) {
+      float* arr = reinterpret_cast<float*>(group_buf(buf));
+      for (int e = dl; e < C::NARR * C::CELLS; e += DL) {
+        const int a = e / C::CELLS, c = e % C::CELLS;
+        const int x = t * TW + c % TW, y = row0 + c / TW;
+        const bool ok = x < nx && y < ny;
+        const long cell = ok ? phys(x, y) : 0;
+        const float* src = a == C::A_ST ? A.sig_t
+                         : a == C::A_STL ? A.sig_tl
+                         : (MB != 2 && a == C::A_Q) ? A.q
+                         : (MB != 0 && a == C::A_G2) ? A.g2
+                         : (BF && a == C::A_FRO) ? A.fro
+                         : A.frn;
+        cp_async_4(arr + e, src + cell, ok && src != nullptr);
+      }
+      if constexpr (MB != 0) {
+        unsigned char* fdst = group_buf(buf) + C::NARR * C::CELLS * 4;
+        for (int e = dl; e < C::CELLS * C::FP; e += DL) {
+          const int c = e / C::FP, v = e % C::FP;
+          const int x = t * TW + c % TW, y = row0 + c / TW;
+          const bool ok = x < nx && y < ny;
+          const long cell = ok ? phys(x, y) : 0;
+          cp_async_16(fdst + (size_t)e * 16, fsrc + ((size_t)cell * DL * C::ESZ + v * 16), ok);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  float yA[TW], yB[TW];   // row above the next row to solve (after a tile: its bottom row)
+  float xA[TH], xB[TH];   // left column of the next tile (after a tile: its right column)
+#pragma unroll
+  for (int i = 0; i < TW; ++i) yA[i] = yB[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < TH; ++j) {
+    xA[j] = gx;
+    xB[j] = 0.f;
+  }
+
+  const int nstep = ntile + NG - 1;
+  stage(-g, 0);
+  for (int T = 0; T < nstep; ++T) {
+    const int t = T - g;
+    const bool active = t >= 0 && t < ntile;
+    const int buf = T & 1;
+    cp_async_wait0();
+    __syncwarp();
+    stage(t + 1, buf ^ 1);
+    // the row above this tile: from the group above (shuffle); group 0 from the warp above
+    // (ring), the CTA above (global edge) or the inflow ghost
+    float upA[TW], upB[TW];
+#pragma unroll
+    for (int i = 0; i < TW; ++i) {
+      upA[i] = __shfl_up_sync(FULL, yA[i], DL);
+      upB[i] = (MB == 1) ? __shfl_up_sync(FULL, yB[i], DL) : 0.f;
+    }
+    if (warp > 0) {
+      // group 0 works on tile T; wait until the warp above has put that tile in the ring
+      if (T < ntile) {
+        int kp = 0;
+        if (lane == 0) {
+          unsigned spins = 0;
+          while ((kp = s_prod[warp - 1]) <= T && !s_abandon) {
+            if (++spins > SMEM_SPIN_LIMIT) {
+              atomicExch(&A.ctrl->err, 1u);
+              s_abandon = 1;
+              break;
+            }
+          }
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (g == 0) {
+          const float* rs = ring_in + (size_t)(T % RD) * TW * DL + dl;
+#pragma unroll
+          for (int i = 0; i < TW; ++i) {
+            upA[i] = rs[i * DL];
+            if constexpr (MB == 1) upB[i] = rs[(size_t)RD * TW * DL + i * DL];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) s_cons[warp] = T + 1;   // ring slot of tile T may be reused
+      }
+    } else if (g == 0) {
+      if (has_up) {
+        if (T < ntile) {
+          if (dl == 0 && !s_abandon) {
+            unsigned spins = 0;
+            while (ld_acquire(flag_in) < (unsigned)(T + 1)) {
+              if (++spins > SPIN_LIMIT || ld_acquire(&A.ctrl->err) != 0u) {
+                atomicExch(&A.ctrl->err, 1u);
+                s_abandon = 1;
+                break;
+              }
+              if (spins > 256) __nanosleep(64);
+            }
+          }
+          __syncwarp((DL == 32) ? FULL : (((1u << DL) - 1u)));
+          __threadfence();
+#pragma unroll
+          for (int i = 0; i < TW; ++i) {
+            const int x = T * TW + i;
+            upA[i] = x < nx ? ldcg(edge_in + (size_t)x * DL + dl) : 0.f;
+            if constexpr (MB == 1) upB[i] = x < nx ? ldcg(edge_in + plane + (size_t)x * DL + dl) : 0.f;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < TW; ++i) {
+          upA[i] = gy;
+          upB[i] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TW; ++i) {
+      yA[i] = upA[i];
+      yB[i] = upB[i];
+    }
+    if (t == 0) {
+#pragma unroll
+      for (int j = 0; j < TH; ++j) {
+        xA[j] = gx;
+        xB[j] = 0.f;
+      }
+    }
+    // solve the tile: every lane all TW x TH cells of its direction
+    const float* arr = reinterpret_cast<const float*>(group_buf(buf));
+    const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * 4;
+#pragma unroll
+    for (int j = 0; j < TH; ++j) {
+      const int y = row0 + j;
+      float mv[TW];
+#pragma unroll
+      for (int i = 0; i < TW; ++i) {
+        const int c = j * TW + i;
+        const Rcp2 rp = rcp_pair(ct, ctl, arr[C::A_ST * C::CELLS + c], arr[C::A_STL * C::CELLS + c]);
+        const float leftA = (i == 0) ? xA[j] : yA[i - 1];
+        float fo = 0.f;
+        if constexpr (MB != 0) {
+          if constexpr (BF)
+            fo = arr[C::A_FRO * C::CELLS + c] +
+                 __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(fb)[c * DL + dl]);
+          else
+            fo = reinterpret_cast<const float*>(fb)[c * DL + dl];
+        }
+        float srcA;
+        if constexpr (MB == 0) srcA = arr[C::A_Q * C::CELLS + c];
+        else if constexpr (MB == 2) srcA = arr[C::A_G2 * C::CELLS + c] + tau * fo;
+        else srcA = arr[C::A_Q * C::CELLS + c] + tau * fo;
+        // yA[i - 1] is already this row's value: the left neighbour; yA[i] is still the row above
+        const float va = scale2(srcA + ca * leftA + cb * yA[i], rp.h, rp.l);
+        if constexpr (MB == 1) {
+          const int x = t * TW + i;
+          const bool store = active && x < nx && y < ny;
+          float vst;
+          if constexpr (BF) {
+            const long cell = phys(x < nx ? x : 0, y < ny ? y : 0);
+            const __nv_bfloat16 rb = bf16_stochastic(va - arr[C::A_FRN * C::CELLS + c],
+                                                     (unsigned)(cell * A.nslot + slot), A.seed);
+            if (store) fb_fam[(size_t)cell * DL + dl] = rb;
+            vst = arr[C::A_FRN * C::CELLS + c] + __bfloat162float(rb);
+          } else {
+            if (store) f_fam[(size_t)phys(x, y) * DL + dl] = va;
+            vst = va;
+          }
+          const float leftB = (i == 0) ? xB[j] : yB[i - 1];
+          const float vb =
+              scale2(arr[C::A_G2 * C::CELLS + c] + tau * vst + ca * leftB + cb * yB[i], rp.h, rp.l);
+          yB[i] = vb;
+          mv[i] = cw * vb;
+        } else {
+          mv[i] = cw * va;
+        }
+        yA[i] = va;
+      }
+      xA[j] = yA[TW - 1];
+      if constexpr (MB == 1) xB[j] = yB[TW - 1];
+      // quadrature moment of row j over the group's directions: one partial per family and cell
+      TReduce<float, TW, DL / 2>::run(mv, dl);
+      int idx;
+      bool writer;
+      if constexpr (TW >= DL) {
+        idx = dl;
+        writer = true;
+      } else {
+        idx = dl / (DL / TW);
+        writer = (dl & (DL / TW - 1)) == 0;
+      }
+      const int x = t * TW + idx;
+      if (writer && active && x < nx && y < ny) A.pm[fam * ncell + phys(x, y)] = mv[0];
+    }
+    // the bottom row of this tile: to the warp below (ring) or the next CTA (edge)
+    const int tl = T - (NG - 1);   // the last group's tile
+    if (tl >= 0 && tl < ntile) {
+      if (warp < W - 1) {
+        if (tl - RD >= 0) {
+          int kc = 0;
+          if (lane == 0) {
+            unsigned spins = 0;
+            while ((kc = s_cons[warp + 1]) <= tl - RD && !s_abandon) {
+              if (++spins > SMEM_SPIN_LIMIT) {
+                atomicExch(&A.ctrl->err, 1u);
+                s_abandon = 1;
+                break;
+              }
+            }
+          }
+          __syncwarp();
+        }
+        if (g == NG - 1) {
+          float* rs = ring_out + (size_t)(tl % RD) * TW * DL + dl;
+#pragma unroll
+          for (int i = 0; i < TW; ++i) {
+            rs[i * DL] = yA[i];
+            if constexpr (MB == 1) rs[(size_t)RD * TW * DL + i * DL] = yB[i];
+          }
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) s_prod[warp] = tl + 1;
+      } else if (has_down) {
+        if (g == NG - 1) {
+#pragma unroll
+          for (int i = 0; i < TW; ++i) {
+            const int x = tl * TW + i;
+            if (x < nx) {
+              edge_out[(size_t)x * DL + dl] = yA[i];
+              if constexpr (MB == 1) edge_out[plane + (size_t)x * DL + dl] = yB[i];
+            }
+          }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(flag_out, (unsigned)(tl + 1));
+      }
+    }
+  }
+  cp_async_wait0();
+  // Self-reset of the control block by the last CTA to finish.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned total = (unsigned)(A.nfam * A.nblk);
+    if (atomicAdd(&A.ctrl->done, 1u) == total - 1) {
+      for (unsigned i = 0; i < total; ++i) A.ctrl->flags[i] = 0u;
+      A.ctrl->ticket = 0u;
+      A.ctrl->done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+template <int DL, int TH, int MODE>
+size_t tile_smem(int W) {
+  using C = TileCfg<DL, TH, MODE>;
+  return (size_t)W * C::WARP_BYTES + (size_t)(W > 1 ? W - 1 : 0) * C::RING_FLOATS * sizeof(float);
+}
+
+template <int DL, int TH, int MODE>
+cudaError_t launch_tile(const Sweep2DArgs<float>& a, int W, cudaStream_t s) {
+  constexpr int NG = 32 / DL;
+  if (W < 1 || W > 8 || a.rows_per_blk != W * NG * TH) return cudaErrorInvalidValue;
+  const size_t smem = tile_smem<DL, TH, MODE>(W);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static std::atomic<bool> attr_set{false};   // host threads of a batch share it
+  if (!attr_set.load()) {
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_tile_kernel<DL, TH, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ++g_launches;
+  sweep2d_tile_kernel<DL, TH, MODE><<<(unsigned)(a.nfam * a.nblk), 32 * W, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_tile_mode(const Sweep2DArgs<float>& a, int dl, int th, int W, cudaStream_t s) {
+  if (th == 4) {
+    if (dl == 8) return launch_tile<8, 4, MODE>(a, W, s);
+    if (dl == 16) return launch_tile<16, 4, MODE>(a, W, s);
+    if (dl == 32) return launch_tile<32, 4, MODE>(a, W, s);
+  } else if (th == 8) {
+    if (dl == 8) return launch_tile<8, 8, MODE>(a, W, s);
+    if (dl == 16) return launch_tile<16, 8, MODE>(a, W, s);
+    if (dl == 32) return launch_tile<32, 8, MODE>(a, W, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+size_t tile_smem_mode(int dl, int th, int W) {
+  if (th == 4) {
+    if (dl == 8) return tile_smem<8, 4, MODE>(W);
+    if (dl == 16) return tile_smem<16, 4, MODE>(W);
+    if (dl == 32) return tile_smem<32, 4, MODE>(W);
+  } else if (th == 8) {
+    if (dl == 8) return tile_smem<8, 8, MODE>(W);
+    if (dl == 16) return tile_smem<16, 8, MODE>(W);
+    if (dl == 32) return tile_smem<32, 8, MODE>(W);
+  }
+  return ~(size_t)0;
+}
+
+}  // namespace
+
+#ifndef RTE_TILE_PART
+#define RTE_TILE_PART -1
+#endif
+
+// One translation unit per mode, compiled in parallel; the dispatcher sits in part 0.
+template <int MODE>
+cudaError_t launch_tile_part(const Sweep2DArgs<float>& a, int dl, int th, int W, cudaStream_t s);
+template <int MODE>
+size_t tile_smem_part(int dl, int th, int W);
+
+#define RTE_TILE_INST(MODE)                                                                  \
+  template <>                                                                                \
+  cudaError_t launch_tile_part<MODE>(const Sweep2DArgs<float>& a, int dl, int th, int W,     \
+                                     cudaStream_t s) {                                       \
+    return launch_tile_mode<MODE>(a, dl, th, W, s);                                          \
+  }                                                                                          \
+  template <>                                                                                \
+  size_t tile_smem_part<MODE>(int dl, int th, int W) {                                       \
+    return tile_smem_mode<MODE>(dl, th, W);                                                  \
+  }
+#define RTE_TILE_DECL(MODE)                                                                  \
+  template <>                                                                                \
+  cudaError_t launch_tile_part<MODE>(const Sweep2DArgs<float>& a, int dl, int th, int W,     \
+                                     cudaStream_t s);                                        \
+  template <>                                                                                \
+  size_t tile_smem_part<MODE>(int dl, int th, int W);
+
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 0
+RTE_TILE_INST(0)
+#else
+RTE_TILE_DECL(0)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 1
+RTE_TILE_INST(1)
+#else
+RTE_TILE_DECL(1)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 2
+RTE_TILE_INST(2)
+#else
+RTE_TILE_DECL(2)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 3
+RTE_TILE_INST(3)
+#else
+RTE_TILE_DECL(3)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 4
+RTE_TILE_INST(4)
+#else
+RTE_TILE_DECL(4)
+#endif
+
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 0
+cudaError_t launch_sweep2d_tile(const Sweep2DArgs<float>& a, int mode, int th, int W,
+                                cudaStream_t s) {
+  const int dl = a.nslot / a.nfam;
+  switch (mode) {
+    case 0: return launch_tile_part<0>(a, dl, th, W, s);
+    case 1: return launch_tile_part<1>(a, dl, th, W, s);
+    case 2: return launch_tile_part<2>(a, dl, th, W, s);
+    case 3: return launch_tile_part<3>(a, dl, th, W, s);
+    case 4: return launch_tile_part<4>(a, dl, th, W, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t sweep2d_tile_smem_bytes(int dl, int th, int W, int mode) {
+  switch (mode) {
+    case 0: return tile_smem_part<0>(dl, th, W);
+    case 1: return tile_smem_part<1>(dl, th, W);
+    case 2: return tile_smem_part<2>(dl, th, W);
+    case 3: return tile_smem_part<3>(dl, th, W);
+    case 4: return tile_smem_part<4>(dl, th, W);
+    default: return ~(size_t)0;
+  }
+}
+#endif
+
+}  // namespace rte

@@ -54,7 +54,8 @@ class Options(ctypes.Structure):
                 ("rom", ctypes.c_int), ("residual_norm", ctypes.c_int), ("up_rel", ctypes.c_int),
                 ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int),
                 ("sweep_rows", ctypes.c_int), ("sweep_lanes", ctypes.c_int),
-                ("sweep_warps", ctypes.c_int), ("lookahead", ctypes.c_int)]
+                ("sweep_warps", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
+                ("lookahead", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +72,8 @@ class Stats(ctypes.Structure):
                 ("f_sweep_kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
                 ("sweep_lanes", ctypes.c_int), ("sweep_si_rows", ctypes.c_int),
                 ("sweep_si_warps", ctypes.c_int), ("sweep_f_rows", ctypes.c_int),
-                ("sweep_f_warps", ctypes.c_int), ("sweep_tuned", ctypes.c_int)]
+                ("sweep_f_warps", ctypes.c_int), ("sweep_tuned", ctypes.c_int),
+                ("sweep_si_kernel", ctypes.c_int), ("sweep_f_kernel", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -83,3 +83,22 @@ def test_bf16_restart_reproduces():
     h.rte_step(10)
     assert np.array_equal(a, h.rte_get_scalar_flux())
     h.destroy()
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_bf16_both_kernels_fused_sweep(kernel):
+    wl = _disc(37)
+    h, p = make_pair(wl, sweep_kernel=kernel, **BF16)
+    perm, _, _ = match_directions(h, wl.quadrature)
+    rng = np.random.default_rng(kernel)
+    f0 = rng.uniform(0.5, 1.5, (p.nv, wl.ncell))
+    h.rte_set_initial(f0=f0[perm])
+    f0_stored = h.rte_get_angular_flux()[np.argsort(perm)]
+    rho = rng.uniform(0.5, 1.5, wl.ncell)
+    bt = h.rte_op_fsweep(rho)
+    f_exact, _ = tr.final_f(p, rho, f0_stored)
+    ref = np.float32(rho).astype(np.float64)
+    got = h.rte_get_angular_flux()[np.argsort(perm)]
+    assert np.all(np.abs(got - f_exact) <= 2.0 ** -7 * np.abs(f_exact - ref) + 2e-6 * np.abs(f_exact))
+    assert rel_l2(bt, tr.b_tilde(p, got)) < 2e-6
+    h.destroy()
