@@ -253,71 +253,132 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
         xB[j] = 0.f;
       }
     }
-    // solve the tile: every lane all TW x TH cells of its direction
-    const float* arr = reinterpret_cast<const float*>(group_buf(buf));
-    const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * 4;
-#pragma unroll
-    for (int j = 0; j < TH; ++j) {
-      const int y = row0 + j;
-      float mv[TW];
-#pragma unroll
-      for (int i = 0; i < TW; ++i) {
-        const int c = j * TW + i;
-        const Rcp2 rp = rcp_pair(ct, ctl, arr[C::A_ST * C::CELLS + c], arr[C::A_STL * C::CELLS + c]);
-        const float leftA = (i == 0) ? xA[j] : yA[i - 1];
-        float fo = 0.f;
-        if constexpr (MB != 0) {
-          if constexpr (BF)
-            fo = arr[C::A_FRO * C::CELLS + c] +
-                 __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(fb)[c * DL + dl]);
-          else
-            fo = reinterpret_cast<const float*>(fb)[c * DL + dl];
-        }
-        float srcA;
-        if constexpr (MB == 0) srcA = arr[C::A_Q * C::CELLS + c];
-        else if constexpr (MB == 2) srcA = arr[C::A_G2 * C::CELLS + c] + tau * fo;
-        else srcA = arr[C::A_Q * C::CELLS + c] + tau * fo;
-        // yA[i - 1] is already this row's value: the left neighbour; yA[i] is still the row above
-        const float va = scale2(srcA + ca * leftA + cb * yA[i], rp.h, rp.l);
-        if constexpr (MB == 1) {
-          const int x = t * TW + i;
-          const bool store = active && x < nx && y < ny;
-          float vst;
-          if constexpr (BF) {
-            const long cell = phys(x < nx ? x : 0, y < ny ? y : 0);
-            const __nv_bfloat16 rb = bf16_stochastic(va - arr[C::A_FRN * C::CELLS + c],
-                                                     (unsigned)(cell * A.nslot + slot), A.seed);
-            if (store) fb_fam[(size_t)cell * DL + dl] = rb;
-            vst = arr[C::A_FRN * C::CELLS + c] + __bfloat162float(rb);
-          } else {
-            if (store) f_fam[(size_t)phys(x, y) * DL + dl] = va;
-            vst = va;
+    if constexpr (MB == 1) {
+      // fused sweep: row by row (its two recurrences already give two independent chains,
+      // and holding the whole tile of both passes would double the registers)
+      const float* arr = reinterpret_cast<const float*>(group_buf(buf));
+      const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * 4;
+  #pragma unroll
+      for (int j = 0; j < TH; ++j) {
+        const int y = row0 + j;
+        float mv[TW];
+  #pragma unroll
+        for (int i = 0; i < TW; ++i) {
+          const int c = j * TW + i;
+          const Rcp2 rp = rcp_pair(ct, ctl, arr[C::A_ST * C::CELLS + c], arr[C::A_STL * C::CELLS + c]);
+          const float leftA = (i == 0) ? xA[j] : yA[i - 1];
+          float fo = 0.f;
+          if constexpr (MB != 0) {
+            if constexpr (BF)
+              fo = arr[C::A_FRO * C::CELLS + c] +
+                   __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(fb)[c * DL + dl]);
+            else
+              fo = reinterpret_cast<const float*>(fb)[c * DL + dl];
           }
-          const float leftB = (i == 0) ? xB[j] : yB[i - 1];
-          const float vb =
-              scale2(arr[C::A_G2 * C::CELLS + c] + tau * vst + ca * leftB + cb * yB[i], rp.h, rp.l);
-          yB[i] = vb;
-          mv[i] = cw * vb;
-        } else {
-          mv[i] = cw * va;
+          float srcA;
+          if constexpr (MB == 0) srcA = arr[C::A_Q * C::CELLS + c];
+          else if constexpr (MB == 2) srcA = arr[C::A_G2 * C::CELLS + c] + tau * fo;
+          else srcA = arr[C::A_Q * C::CELLS + c] + tau * fo;
+          // yA[i - 1] is already this row's value: the left neighbour; yA[i] is still the row above
+          const float va = scale2(srcA + ca * leftA + cb * yA[i], rp.h, rp.l);
+          if constexpr (MB == 1) {
+            const int x = t * TW + i;
+            const bool store = active && x < nx && y < ny;
+            float vst;
+            if constexpr (BF) {
+              const long cell = phys(x < nx ? x : 0, y < ny ? y : 0);
+              const __nv_bfloat16 rb = bf16_stochastic(va - arr[C::A_FRN * C::CELLS + c],
+                                                       (unsigned)(cell * A.nslot + slot), A.seed);
+              if (store) fb_fam[(size_t)cell * DL + dl] = rb;
+              vst = arr[C::A_FRN * C::CELLS + c] + __bfloat162float(rb);
+            } else {
+              if (store) f_fam[(size_t)phys(x, y) * DL + dl] = va;
+              vst = va;
+            }
+            const float leftB = (i == 0) ? xB[j] : yB[i - 1];
+            const float vb =
+                scale2(arr[C::A_G2 * C::CELLS + c] + tau * vst + ca * leftB + cb * yB[i], rp.h, rp.l);
+            yB[i] = vb;
+            mv[i] = cw * vb;
+          } else {
+            mv[i] = cw * va;
+          }
+          yA[i] = va;
         }
-        yA[i] = va;
+        xA[j] = yA[TW - 1];
+        if constexpr (MB == 1) xB[j] = yB[TW - 1];
+        // quadrature moment of row j over the group's directions: one partial per family and cell
+        TReduce<float, TW, DL / 2>::run(mv, dl);
+        int idx;
+        bool writer;
+        if constexpr (TW >= DL) {
+          idx = dl;
+          writer = true;
+        } else {
+          idx = dl / (DL / TW);
+          writer = (dl & (DL / TW - 1)) == 0;
+        }
+        const int x = t * TW + idx;
+        if (writer && active && x < nx && y < ny) A.pm[fam * ncell + phys(x, y)] = mv[0];
       }
-      xA[j] = yA[TW - 1];
-      if constexpr (MB == 1) xB[j] = yB[TW - 1];
-      // quadrature moment of row j over the group's directions: one partial per family and cell
-      TReduce<float, TW, DL / 2>::run(mv, dl);
-      int idx;
-      bool writer;
-      if constexpr (TW >= DL) {
-        idx = dl;
-        writer = true;
-      } else {
-        idx = dl / (DL / TW);
-        writer = (dl & (DL / TW - 1)) == 0;
+    } else {
+      // single recurrence (SI sweep, y sweep): anti-diagonal by anti-diagonal, so that the up
+      // to TH cells of a diagonal are independent and the dependent FMA chain of the recurrence
+      // overlaps across them; the moment of the whole tile in one transpose-reduce at the end
+      const float* arr = reinterpret_cast<const float*>(group_buf(buf));
+      const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * 4;
+      float vA[TH][TW];
+  #pragma unroll
+      for (int dg = 0; dg < TW + TH - 1; ++dg) {
+  #pragma unroll
+        for (int j = 0; j < TH; ++j) {
+          const int i = dg - j;
+          if (i < 0 || i >= TW) continue;
+          const int c = j * TW + i;
+          const Rcp2 rp = rcp_pair(ct, ctl, arr[C::A_ST * C::CELLS + c], arr[C::A_STL * C::CELLS + c]);
+          const float left = (i == 0) ? xA[j] : vA[j][i > 0 ? i - 1 : 0];
+          const float up = (j == 0) ? yA[i] : vA[j > 0 ? j - 1 : 0][i];
+          float src;
+          if constexpr (MB == 0) {
+            src = arr[C::A_Q * C::CELLS + c];
+          } else {
+            float fo;
+            if constexpr (BF)
+              fo = arr[C::A_FRO * C::CELLS + c] +
+                   __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(fb)[c * DL + dl]);
+            else
+              fo = reinterpret_cast<const float*>(fb)[c * DL + dl];
+            src = arr[C::A_G2 * C::CELLS + c] + tau * fo;
+          }
+          vA[j][i] = scale2(src + ca * left + cb * up, rp.h, rp.l);
+        }
       }
-      const int x = t * TW + idx;
-      if (writer && active && x < nx && y < ny) A.pm[fam * ncell + phys(x, y)] = mv[0];
+  #pragma unroll
+      for (int j = 0; j < TH; ++j) xA[j] = vA[j][TW - 1];
+  #pragma unroll
+      for (int i = 0; i < TW; ++i) yA[i] = vA[TH - 1][i];
+      {
+        constexpr int NV = TH * TW;
+        float mv[NV];
+  #pragma unroll
+        for (int c = 0; c < NV; ++c) mv[c] = cw * vA[c / TW][c % TW];
+        TReduce<float, NV, DL / 2>::run(mv, dl);
+        constexpr int PER = NV >= DL ? NV / DL : 1;
+  #pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          int idx;
+          bool writer;
+          if constexpr (NV >= DL) {
+            idx = dl * PER + q;
+            writer = true;
+          } else {
+            idx = dl / (DL / NV);
+            writer = (dl & (DL / NV - 1)) == 0;
+          }
+          const int x = t * TW + idx % TW, y = row0 + idx / TW;
+          if (writer && active && x < nx && y < ny) A.pm[fam * ncell + phys(x, y)] = mv[q];
+        }
+      }
     }
     // the bottom row of this tile: to the warp below (ring) or the next CTA (edge)
     const int tl = T - (NG - 1);   // the last group's tile
