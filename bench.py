@@ -35,7 +35,8 @@ UNIT = "cell-direction updates/s"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FLOP_PER_UPDATE = 7          # two multiply-adds, one multiply by 1/d, one multiply-add (moment)
 PROFILE = os.path.join(ROOT, "profiles", "sweep_si_fp64_checkerboard.md")
-SWEEP_SRC = os.path.join(ROOT, "paper_2603_19647_gb300", "csrc", "sweep.cu")
+SWEEP_SRC = [os.path.join(ROOT, "paper_2603_19647_gb300", "csrc", f)
+             for f in ("sweep.cu", "sweep_common.cuh")]
 
 
 def parse():
@@ -109,10 +110,10 @@ def profiled_traffic():
     source changed since the capture."""
     try:
         txt = open(PROFILE).read()
-        src_hash = hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()[:16]
+        src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in SWEEP_SRC)).hexdigest()[:16]
         vals = dict(line.split(":", 1) for line in txt.splitlines() if ":" in line and line[:1] != "#")
         vals = {k.strip("-* `"): v.strip(" `") for k, v in vals.items()}
-        if vals.get("sweep_cu_sha256_16") != src_hash:
+        if vals.get("sweep_src_sha256_16") != src_hash:
             return None
         return float(vals["dram_bytes_per_launch_full_size"])
     except (OSError, KeyError, ValueError):
