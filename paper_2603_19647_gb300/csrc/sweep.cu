@@ -356,13 +356,12 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
         }
       }
     }
-    // Quadrature moment of the chunk: weights, then one transpose-reduce over the lane
-    // group's directions for all K x R cells; one partial per family and cell.
+    // Quadrature moment of the chunk: one transpose-reduce over the lane group's directions
+    // for all K x R cells, the weights applied in its first round; one partial per family and
+    // cell.
     {
       constexpr int NV = K * R;
-#pragma unroll
-      for (int i = 0; i < NV; ++i) mb[i] *= cw;
-      TReduce<Real, NV, DL / 2>::run(mb, dl);
+      TReduceW<Real, NV, DL / 2>::run(mb, cw, dl);
       constexpr int PER = NV >= DL ? NV / DL : 1;
 #pragma unroll
       for (int i = 0; i < PER; ++i) {

@@ -105,6 +105,24 @@ struct TReduce {
   }
 };
 
+// TReduce whose first halving round also applies the weight w of the lane's own direction:
+// each lane scales what it sends and what it keeps, so the weights cost N / 2 multiplies and
+// N / 2 fused multiply-adds instead of N multiplies before an unweighted reduce.
+template <class Real, int N, int O>
+struct TReduceW {
+  static __device__ __forceinline__ void run(Real* v, Real w, int dl) {
+    static_assert(N > 1 && O > 0, "at least one halving round");
+    const bool hi = (dl & O) != 0;
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const Real send = w * (hi ? v[i] : v[i + N / 2]);
+      const Real keep = hi ? v[i + N / 2] : v[i];
+      v[i] = fma(keep, w, __shfl_xor_sync(FULL, send, O));
+    }
+    TReduce<Real, N / 2, O / 2>::run(v, dl);
+  }
+};
+
 // cp.async helpers (global -> shared, zero-fill when the source is absent).
 __device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
