@@ -52,7 +52,7 @@ struct Sweep2DArgs {
   const int* fam_quad;  // [nfam]
   const Real* sig_t;    // [ncell]
   const Real* sig_tl;   // [ncell] FP32: sigma_t - sig_t exactly (the low part), or nullptr
-  const Real* inv_d;    // [nfam][ncell][dl] 1/(tau+sigma_t+a+b) or nullptr (computed)
+  const Real* inv_d;    // FP64: [nfam][ncell][dl] w / (tau + sigma_t + a + b); FP32: nullptr
   const unsigned* skip; // set: the launch does nothing (speculative SI-SA work past convergence)
   const Real* cth;      // [nslot] tau + a + b, high part, or nullptr (formed from tau, a, b)
   const Real* ctl;      // [nslot] its low part (FP32: the exact sum is cth + ctl)
@@ -96,20 +96,22 @@ struct Sweep1DArgs {
 size_t sweep2d_smem_bytes(size_t real, int dl, int R, int W, int mode, bool table);
 template <class Real>
 cudaError_t launch_sweep2d(const Sweep2DArgs<Real>& a, int mode, int R, cudaStream_t s);
-// FP32 tile-sequence sweep (sweep_tile.cu): TH rows per lane group, W warps per CTA,
-// rows_per_blk = W (32 / dl) TH; the same modes 0-4.
+// Tile-sequence sweep (sweep_tile.cu): TH rows per lane group, W warps per CTA,
+// rows_per_blk = W (32 / dl) TH; FP32 modes 0-4, FP64 modes 0-2 (FP64 needs inv_d).
 cudaError_t launch_sweep2d_tile(const Sweep2DArgs<float>& a, int mode, int th, int W,
                                 cudaStream_t s);
-size_t sweep2d_tile_smem_bytes(int dl, int th, int W, int mode);
+cudaError_t launch_sweep2d_tile(const Sweep2DArgs<double>& a, int mode, int th, int W,
+                                cudaStream_t s);
+size_t sweep2d_tile_smem_bytes(size_t real, int dl, int th, int W, int mode);
 template <class Real>
 cudaError_t launch_sweep1d(const Sweep1DArgs<Real>& a, int mode, cudaStream_t s);
 template <class Real>
 cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, cudaStream_t s,
                             const unsigned* skip = nullptr);
-// inv_d in the family layout [fam][cell][dl]
+// inv_d = w / (tau + sigma_t + a + b) in the family layout [fam][cell][dl]
 template <class Real>
-cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
-                         int nslot, int dl, Real* inv_d, cudaStream_t s);
+cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, const Real* w, Real tau,
+                         int ncell, int nslot, int dl, Real* inv_d, cudaStream_t s);
 
 // Vector kernels (vec.cu).
 struct Norms {             // device-side reduction results of one residual evaluation
@@ -129,8 +131,9 @@ cudaError_t launch_sum_partials(const double* pm, int nfam, int ncell, const dou
                                 double* out, cudaStream_t s);
 cudaError_t launch_axpby(double alpha, const double* x, double beta, const double* y, int n,
                          double* out, cudaStream_t s);
-cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, int dl, double* f,
-                               cudaStream_t s);
+// f = rho in every slot, times w of the slot when w is given (the 2D FP64 storage w f)
+cudaError_t launch_isotropic_f(const double* rho, int ncell, int nslot, int dl, const double* w,
+                               double* f, cudaStream_t s);
 cudaError_t launch_dot(const double* x, const double* y, int n, double* partials, int nblocks,
                        double* out, cudaStream_t s);
 int vec_blocks(int n);

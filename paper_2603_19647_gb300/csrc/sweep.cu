@@ -108,10 +108,18 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   // tau + a + b of this direction: hi / lo pair in FP32 (exact), one value in FP64
   const Real ct = A.cth ? A.cth[slot] : A.tau + ca + cb;
   const Real ctl = A.ctl ? A.ctl[slot] : Real(0);
+  // With the table (FP64) the lane carries w psi, its direction's weighted flux: the table
+  // holds w / (tau + sigma_t + a + b), so the recurrence keeps its form with a / w, b / w,
+  // tau / w in place of a, b, tau and with inflow ghosts times w, and the quadrature moment
+  // is a plain sum over the directions.  Stored f is then w f.  (Padding slots have w = 0
+  // and stay zero.)
+  const Real iw = TABLE ? (cw != Real(0) ? Real(1) / cw : Real(0)) : Real(1);
+  const Real ka = TABLE ? ca * iw : ca, kb = TABLE ? cb * iw : cb;
+  const Real ktau = TABLE ? A.tau * iw : A.tau;
   const int wrow0 = blk * A.rows_per_blk + warp * RW;   // first sweep-order row of this warp
   const int row0 = wrow0 + gi * R;                       // lane group's row m = 0
-  const Real gx = A.gx[quad];
-  const Real gy = A.gy[quad];
+  const Real gx = TABLE ? A.gx[quad] * cw : A.gx[quad];
+  const Real gy = TABLE ? A.gy[quad] * cw : A.gy[quad];
   const Real* tab_fam = TABLE ? A.inv_d + (size_t)fam * ncell * DL : nullptr;
   Real* f_fam = (STAGE_F && !BF) ? A.f + (size_t)fam * ncell * DL : nullptr;
   __nv_bfloat16* fb_fam = BF ? A.fb + (size_t)fam * ncell * DL : nullptr;
@@ -285,21 +293,21 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
           }
           const Real uA = (m == 0) ? upA : psA[m > 0 ? m - 1 : 0];
           if constexpr (MB == 0) {
-            const Real v = scale2(qa_s[o] + ca * psA[m] + cb * uA, dinv, dinvl);
+            const Real v = scale2(qa_s[o] + ka * psA[m] + kb * uA, dinv, dinvl);
             psA[m] = v;
             mb[k * R + m] = v;
           } else if constexpr (MB == 2) {
             Real fo;
             if constexpr (BF) fo = fro_s[o] + __bfloat162float(bf_s[od]);
             else fo = f_s[od];
-            const Real v = scale2(g2_s[o] + A.tau * fo + ca * psA[m] + cb * uA, dinv, dinvl);
+            const Real v = scale2(g2_s[o] + ktau * fo + ka * psA[m] + kb * uA, dinv, dinvl);
             psA[m] = v;
             mb[k * R + m] = v;
           } else {
             Real fo;
             if constexpr (BF) fo = fro_s[o] + __bfloat162float(bf_s[od]);
             else fo = f_s[od];
-            const Real va = scale2(qa_s[o] + A.tau * fo + ca * psA[m] + cb * uA, dinv, dinvl);
+            const Real va = scale2(qa_s[o] + ktau * fo + ka * psA[m] + kb * uA, dinv, dinvl);
             psA[m] = va;
             const int px = xpos ? x : nx - 1 - x;
             const int py = ypos ? jj : ny - 1 - jj;
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
               vst = va;
             }
             const Real uB = (m == 0) ? upB : psB[m > 0 ? m - 1 : 0];
-            const Real vb = scale2(g2_s[o] + A.tau * vst + ca * psB[m] + cb * uB, dinv, dinvl);
+            const Real vb = scale2(g2_s[o] + ktau * vst + ka * psB[m] + kb * uB, dinv, dinvl);
             psB[m] = vb;
             mb[k * R + m] = vb;
           }
@@ -357,11 +365,14 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
       }
     }
     // Quadrature moment of the chunk: one transpose-reduce over the lane group's directions
-    // for all K x R cells, the weights applied in its first round; one partial per family and
-    // cell.
+    // for all K x R cells (the values already weighted with the table, else the weights
+    // applied in its first round); one partial per family and cell.
     {
       constexpr int NV = K * R;
-      TReduceW<Real, NV, DL / 2>::run(mb, cw, dl);
+      if constexpr (TABLE)
+        TReduce<Real, NV, DL / 2>::run(mb, dl);
+      else
+        TReduceW<Real, NV, DL / 2>::run(mb, cw, dl);
       constexpr int PER = NV >= DL ? NV / DL : 1;
 #pragma unroll
       for (int i = 0; i < PER; ++i) {
@@ -430,16 +441,17 @@ cudaError_t launch_dl_r(const Sweep2DArgs<Real>& a, cudaStream_t s) {
   constexpr int RW = NG * R;
   const int W = a.rows_per_blk / RW;
   if (W < 1 || W > 8 || W * RW != a.rows_per_blk) return cudaErrorInvalidValue;
-  const bool table = a.inv_d != nullptr;
+  // FP64 takes the diagonal from the inverse table, FP32 forms it by the two-part reciprocal
+  constexpr bool table = sizeof(Real) == 8;
+  if (table != (a.inv_d != nullptr)) return cudaErrorInvalidValue;
   const size_t smem = sweep2d_smem_bytes_impl(sizeof(Real), DL, R, W, MODE, table);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  auto kern = table ? sweep2d_kernel<Real, DL, R, KSTEP, MODE, true>
-                    : sweep2d_kernel<Real, DL, R, KSTEP, MODE, false>;
-  static std::atomic<bool> attr_set[2] = {false, false};   // host threads of a batch share it
-  if (!attr_set[table].load()) {
+  auto kern = sweep2d_kernel<Real, DL, R, KSTEP, MODE, table>;
+  static std::atomic<bool> attr_set{false};   // host threads of a batch share it
+  if (!attr_set.load()) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set[table] = true;
+    attr_set = true;
   }
   const dim3 grid((unsigned)(a.nfam * a.nblk));
   ++g_launches;
@@ -617,15 +629,15 @@ __global__ void moment1d_kernel(const Real* psi_w, int nslot, int ncell, Real* o
 }
 
 template <class Real>
-__global__ void inv_d_kernel(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
-                             int nslot, int dl, Real* inv_d) {
+__global__ void inv_d_kernel(const Real* sig_t, const Real* a, const Real* b, const Real* w, Real tau,
+                             int ncell, int nslot, int dl, Real* inv_d) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)ncell * nslot) return;
   // family layout [fam][cell][dl] with dl = 32 / 16 / 8 lanes: i = (fam * ncell + c) * dl + lane
   const long lanei = i % dl, rest = i / dl;
   const long c = rest % ncell, fam = rest / ncell;
   const int s = (int)(fam * dl + lanei);
-  inv_d[i] = Real(1) / (tau + sig_t[c] + a[s] + b[s]);
+  inv_d[i] = w[s] / (tau + sig_t[c] + a[s] + b[s]);
 }
 
 }  // namespace
@@ -723,12 +735,12 @@ cudaError_t launch_moment1d(const Real* psi_w, int nslot, int ncell, Real* out, 
 }
 
 template <class Real>
-cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, Real tau, int ncell,
-                         int nslot, int dl, Real* inv_d, cudaStream_t s) {
+cudaError_t launch_inv_d(const Real* sig_t, const Real* a, const Real* b, const Real* w, Real tau,
+                         int ncell, int nslot, int dl, Real* inv_d, cudaStream_t s) {
   const long n = (long)ncell * nslot;
   ++g_launches;
-  inv_d_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sig_t, a, b, tau, ncell, nslot,
-                                                                 dl, inv_d);
+  inv_d_kernel<Real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sig_t, a, b, w, tau, ncell,
+                                                                 nslot, dl, inv_d);
   return cudaGetLastError();
 }
 
@@ -740,10 +752,9 @@ template cudaError_t launch_moment1d<double>(const double*, int, int, double*, c
                                              const unsigned*);
 template cudaError_t launch_moment1d<float>(const float*, int, int, float*, cudaStream_t,
                                             const unsigned*);
-template cudaError_t launch_inv_d<double>(const double*, const double*, const double*, double, int,
-                                          int, int, double*, cudaStream_t);
-template cudaError_t launch_inv_d<float>(const float*, const float*, const float*, float, int, int,
-                                         int, float*, cudaStream_t);
+template cudaError_t launch_inv_d<double>(const double*, const double*, const double*,
+                                          const double*, double, int, int, int, double*,
+                                          cudaStream_t);
 #endif  // base part
 
 }  // namespace rte

@@ -1,5 +1,5 @@
-// 2D transport sweep of the FP32 modes in tile sequence (Sec. 2.1 Eq. (DG) with K = 0, in
-// upwind order, Sec. 2.3), with the quadrature moment fused in.
+// 2D transport sweep in tile sequence (Sec. 2.1 Eq. (DG) with K = 0, in upwind order,
+// Sec. 2.3), with the quadrature moment fused in; FP32 (modes 0-4) and FP64 (modes 0-2).
 //
 // Lane = direction (dl lanes per family of one quadrant), as in the strip chain of sweep.cu,
 // but a lane group owns a strip of TH rows and walks it one TW x TH tile at a time: inside a
@@ -13,8 +13,10 @@
 //     through global memory behind a release flag per tile (bounded spins).
 // At warp step T lane group g works on tile T - g, so a warp keeps NG = 32 / dl tiles in
 // flight and the strips of a family form one pipeline down the grid.  Each group stages the
-// per-cell data of its next tile (sigma_t as an exact FP32 pair, the sources, f for the
-// fused sweep) into its own double buffer with cp.async while it computes the current one.
+// per-cell data of its next tile (the sources, f for the fused sweep, and the diagonal: in
+// FP32 sigma_t as an exact pair for the two-part reciprocal, in FP64 the per-direction table
+// 1 / (tau + sigma_t + a + b) of the cells) into its own double buffer with cp.async while it
+// computes the current one.
 // Out-of-range cells of the last tiles are computed from zero-filled inputs and never
 // stored; they lie downstream of every valid cell.
 //
@@ -37,30 +39,54 @@ using namespace sweep_detail;
 constexpr int TW = 8;   // columns per tile
 constexpr int RD = 4;   // tiles held by a ring between two warps
 
-template <int DL, int TH, int MODE>
+template <class Real, int DL, int TH, int MODE>
 struct TileCfg {
+  static constexpr bool TBL = sizeof(Real) == 8;   // FP64: diagonal from the inverse table
   static constexpr bool BF = MODE >= 3;
+  static_assert(!(TBL && BF), "BF16 storage is an FP32 mode");
   static constexpr int MB = BF ? MODE - 2 : MODE;
   static constexpr int NG = 32 / DL;
   static constexpr int NP = MB == 1 ? 2 : 1;
   static constexpr int CELLS = TH * TW;
-  // per-cell arrays: sigma_t hi, lo, then q (modes 0, 1), g2 (modes 1, 2), BF16 references
-  static constexpr int A_ST = 0, A_STL = 1, A_Q = 2;
-  static constexpr int A_G2 = (MB != 2) ? 3 : 2;
+  static constexpr int RS = (int)sizeof(Real);
+  // per-cell arrays: (FP32) sigma_t hi, lo, then q (modes 0, 1), g2 (modes 1, 2), BF16
+  // references
+  static constexpr int A_ST = 0, A_STL = 1, A_Q = TBL ? 0 : 2;
+  static constexpr int A_G2 = A_Q + (MB != 2 ? 1 : 0);
   static constexpr int A_FRO = A_G2 + (MB != 0 ? 1 : 0);
   static constexpr int A_FRN = A_FRO + 1;
-  static constexpr int NARR = 2 + (MB != 2 ? 1 : 0) + (MB != 0 ? 1 : 0) + (BF ? 2 : 0);
-  static constexpr int ESZ = BF ? 2 : 4;                       // bytes of one stored f value
+  static constexpr int NARR = (TBL ? 0 : 2) + (MB != 2 ? 1 : 0) + (MB != 0 ? 1 : 0) + (BF ? 2 : 0);
+  static constexpr int ESZ = BF ? 2 : RS;                      // bytes of one stored f value
   static constexpr int F_BYTES = (MB != 0) ? CELLS * DL * ESZ : 0;
-  static constexpr int GROUP_BYTES = NARR * CELLS * 4 + F_BYTES;   // one group, one buffer
+  static constexpr int T_BYTES = TBL ? CELLS * DL * RS : 0;    // inverse-diagonal table
+  static constexpr int GROUP_BYTES = NARR * CELLS * RS + F_BYTES + T_BYTES;   // one buffer
   static constexpr int WARP_BYTES = 2 * NG * GROUP_BYTES;
-  static constexpr int RING_FLOATS = NP * RD * TW * DL;
+  static constexpr int RING_REALS = NP * RD * TW * DL;
   static constexpr int FP = (MB != 0) ? DL * ESZ / 16 : 0;     // 16-byte pieces of f per cell
+  static constexpr int TP = TBL ? DL * RS / 16 : 0;            // the same for the table
+  static_assert((NARR * CELLS * RS) % 16 == 0 && F_BYTES % 16 == 0, "16-byte staging pieces");
 };
 
-template <int DL, int TH, int MODE>
-__global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<float> A) {
-  using C = TileCfg<DL, TH, MODE>;
+// The diagonal 1 / (tau + sigma_t + a + b) of staged cell c for the lane's direction as h + l:
+// FP32 from the exact sigma_t pair (arrays 0 and 1) by the two-part reciprocal, FP64 from the
+// staged inverse table (l = 0).
+template <bool TBL, class Real>
+__device__ __forceinline__ void diag(Real ct, Real ctl, const Real* arr, const Real* tab, int c,
+                                     int dl, int cells, int dln, Real& h, Real& l) {
+  if constexpr (TBL) {
+    h = tab[c * dln + dl];
+    l = Real(0);
+  } else {
+    const Rcp2 rp = rcp_pair(ct, ctl, arr[c], arr[cells + c]);
+    h = rp.h;
+    l = rp.l;
+  }
+}
+
+template <class Real, int DL, int TH, int MODE>
+__global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<Real> A) {
+  using C = TileCfg<Real, DL, TH, MODE>;
+  constexpr bool TBL = C::TBL;
   constexpr int MB = C::MB;
   constexpr bool BF = C::BF;
   constexpr int NG = C::NG;
@@ -92,19 +118,30 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
   const int nx = A.nx, ny = A.ny;
   const long ncell = (long)nx * ny;
   const int slot = fam * DL + dl;
-  const float ca = A.a[slot], cb = A.b[slot], cw = A.w[slot];
-  const float ct = A.cth[slot], ctl = A.ctl[slot];
-  const float tau = A.tau;
+  // FP64 (table): the lane carries w psi of its direction, as in the strip chain: the table
+  // holds w / (tau + sigma_t + a + b), the recurrence takes a / w, b / w, tau / w and ghosts
+  // times w, and the moment is a plain sum (stored f is w f).
+  const Real w0 = A.w[slot];
+  const Real iw = TBL ? (w0 != Real(0) ? Real(1) / w0 : Real(0)) : Real(1);
+  const Real ca = A.a[slot] * iw, cb = A.b[slot] * iw, cw = TBL ? Real(1) : w0;
+  Real ct = Real(0), ctl = Real(0);   // FP32: tau + a + b as an exact pair
+  if constexpr (!TBL) {
+    ct = A.cth[slot];
+    ctl = A.ctl[slot];
+  }
+  const Real tau = A.tau * iw;
   const int strip = warp * NG + g;
   const int row0 = blk * A.rows_per_blk + strip * TH;     // sweep-order first row of the strip
   const int ntile = (nx + TW - 1) / TW;
-  const float gx = A.gx[quad], gy = A.gy[quad];
+  const Real gx = TBL ? A.gx[quad] * w0 : A.gx[quad], gy = TBL ? A.gy[quad] * w0 : A.gy[quad];
 
   unsigned char* wbase = smraw + (size_t)warp * C::WARP_BYTES;
-  float* rings = reinterpret_cast<float*>(smraw + (size_t)W * C::WARP_BYTES);
-  const float* ring_in = warp > 0 ? rings + (size_t)(warp - 1) * C::RING_FLOATS : nullptr;
-  float* ring_out = warp < W - 1 ? rings + (size_t)warp * C::RING_FLOATS : nullptr;
-  float* f_fam = (MB == 1 && !BF) ? A.f + (size_t)fam * ncell * DL : nullptr;
+  Real* rings = reinterpret_cast<Real*>(smraw + (size_t)W * C::WARP_BYTES);
+  const Real* ring_in = warp > 0 ? rings + (size_t)(warp - 1) * C::RING_REALS : nullptr;
+  Real* ring_out = warp < W - 1 ? rings + (size_t)warp * C::RING_REALS : nullptr;
+  Real* f_fam = (MB == 1 && !BF) ? A.f + (size_t)fam * ncell * DL : nullptr;
+  const unsigned char* tab_fam =
+      TBL ? reinterpret_cast<const unsigned char*>(A.inv_d + (size_t)fam * ncell * DL) : nullptr;
   __nv_bfloat16* fb_fam = (MB == 1 && BF) ? A.fb + (size_t)fam * ncell * DL : nullptr;
   const unsigned char* fsrc = nullptr;
   if constexpr (MB != 0) {
@@ -114,8 +151,8 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
   const bool has_up = blk > 0;
   const bool has_down = blk + 1 < A.nblk;
   const size_t plane = (size_t)A.nfam * A.nblk * nx * DL;
-  const float* edge_in = A.edge + ((size_t)(fam * A.nblk + (has_up ? blk - 1 : 0)) * nx) * DL;
-  float* edge_out = A.edge + ((size_t)(fam * A.nblk + blk) * nx) * DL;
+  const Real* edge_in = A.edge + ((size_t)(fam * A.nblk + (has_up ? blk - 1 : 0)) * nx) * DL;
+  Real* edge_out = A.edge + ((size_t)(fam * A.nblk + blk) * nx) * DL;
   unsigned* flag_in = &A.ctrl->flags[fam * A.nblk + (has_up ? blk - 1 : 0)];
   unsigned* flag_out = &A.ctrl->flags[fam * A.nblk + blk];
 
@@ -128,22 +165,42 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
   // cp.async the inputs of tile t of this group's strip into buffer buf.
   auto stage = [&](int t, int buf) {
     if (t >= 0 && t < ntile) {
-      float* arr = reinterpret_cast<float*>(group_buf(buf));
+      Real* arr = reinterpret_cast<Real*>(group_buf(buf));
       for (int e = dl; e < C::NARR * C::CELLS; e += DL) {
         const int a = e / C::CELLS, c = e % C::CELLS;
         const int x = t * TW + c % TW, y = row0 + c / TW;
         const bool ok = x < nx && y < ny;
         const long cell = ok ? phys(x, y) : 0;
-        const float* src = a == C::A_ST ? A.sig_t
-                         : a == C::A_STL ? A.sig_tl
-                         : (MB != 2 && a == C::A_Q) ? A.q
-                         : (MB != 0 && a == C::A_G2) ? A.g2
-                         : (BF && a == C::A_FRO) ? A.fro
-                         : A.frn;
-        cp_async_4(arr + e, src + cell, ok && src != nullptr);
+        const Real* src;
+        if constexpr (BF) {
+          src = a == C::A_ST ? A.sig_t
+              : a == C::A_STL ? A.sig_tl
+              : (MB != 2 && a == C::A_Q) ? A.q
+              : (MB != 0 && a == C::A_G2) ? A.g2
+              : a == C::A_FRO ? A.fro
+              : A.frn;
+        } else if constexpr (TBL) {
+          src = (MB != 2 && a == C::A_Q) ? A.q : A.g2;
+        } else {
+          src = a == C::A_ST ? A.sig_t
+              : a == C::A_STL ? A.sig_tl
+              : (MB != 2 && a == C::A_Q) ? A.q
+              : A.g2;
+        }
+        cp_async(arr + e, src + cell, ok && src != nullptr);
+      }
+      if constexpr (TBL) {
+        unsigned char* tdst = group_buf(buf) + C::NARR * C::CELLS * C::RS + C::F_BYTES;
+        for (int e = dl; e < C::CELLS * C::TP; e += DL) {
+          const int c = e / C::TP, v = e % C::TP;
+          const int x = t * TW + c % TW, y = row0 + c / TW;
+          const bool ok = x < nx && y < ny;
+          const long cell = ok ? phys(x, y) : 0;
+          cp_async_16(tdst + (size_t)e * 16, tab_fam + ((size_t)cell * DL * C::RS + v * 16), ok);
+        }
       }
       if constexpr (MB != 0) {
-        unsigned char* fdst = group_buf(buf) + C::NARR * C::CELLS * 4;
+        unsigned char* fdst = group_buf(buf) + C::NARR * C::CELLS * C::RS;
         for (int e = dl; e < C::CELLS * C::FP; e += DL) {
           const int c = e / C::FP, v = e % C::FP;
           const int x = t * TW + c % TW, y = row0 + c / TW;
@@ -156,14 +213,14 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
     cp_async_commit();
   };
 
-  float yA[TW], yB[TW];   // row above the next row to solve (after a tile: its bottom row)
-  float xA[TH], xB[TH];   // left column of the next tile (after a tile: its right column)
+  Real yA[TW], yB[TW];   // row above the next row to solve (after a tile: its bottom row)
+  Real xA[TH], xB[TH];   // left column of the next tile (after a tile: its right column)
 #pragma unroll
-  for (int i = 0; i < TW; ++i) yA[i] = yB[i] = 0.f;
+  for (int i = 0; i < TW; ++i) yA[i] = yB[i] = Real(0);
 #pragma unroll
   for (int j = 0; j < TH; ++j) {
     xA[j] = gx;
-    xB[j] = 0.f;
+    xB[j] = Real(0);
   }
 
   const int nstep = ntile + NG - 1;
@@ -177,11 +234,11 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
     stage(t + 1, buf ^ 1);
     // the row above this tile: from the group above (shuffle); group 0 from the warp above
     // (ring), the CTA above (global edge) or the inflow ghost
-    float upA[TW], upB[TW];
+    Real upA[TW], upB[TW];
 #pragma unroll
     for (int i = 0; i < TW; ++i) {
       upA[i] = __shfl_up_sync(FULL, yA[i], DL);
-      upB[i] = (MB == 1) ? __shfl_up_sync(FULL, yB[i], DL) : 0.f;
+      upB[i] = (MB == 1) ? __shfl_up_sync(FULL, yB[i], DL) : Real(0);
     }
     if (warp > 0) {
       // group 0 works on tile T; wait until the warp above has put that tile in the ring
@@ -200,7 +257,7 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
         __syncwarp();
         __threadfence_block();
         if (g == 0) {
-          const float* rs = ring_in + (size_t)(T % RD) * TW * DL + dl;
+          const Real* rs = ring_in + (size_t)(T % RD) * TW * DL + dl;
 #pragma unroll
           for (int i = 0; i < TW; ++i) {
             upA[i] = rs[i * DL];
@@ -229,15 +286,16 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
 #pragma unroll
           for (int i = 0; i < TW; ++i) {
             const int x = T * TW + i;
-            upA[i] = x < nx ? ldcg(edge_in + (size_t)x * DL + dl) : 0.f;
-            if constexpr (MB == 1) upB[i] = x < nx ? ldcg(edge_in + plane + (size_t)x * DL + dl) : 0.f;
+            upA[i] = x < nx ? ldcg(edge_in + (size_t)x * DL + dl) : Real(0);
+            if constexpr (MB == 1)
+              upB[i] = x < nx ? ldcg(edge_in + plane + (size_t)x * DL + dl) : Real(0);
           }
         }
       } else {
 #pragma unroll
         for (int i = 0; i < TW; ++i) {
           upA[i] = gy;
-          upB[i] = 0.f;
+          upB[i] = Real(0);
         }
       }
     }
@@ -250,41 +308,43 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
 #pragma unroll
       for (int j = 0; j < TH; ++j) {
         xA[j] = gx;
-        xB[j] = 0.f;
+        xB[j] = Real(0);
       }
     }
     if constexpr (MB == 1) {
       // fused sweep: row by row (its two recurrences already give two independent chains,
       // and holding the whole tile of both passes would double the registers)
-      const float* arr = reinterpret_cast<const float*>(group_buf(buf));
-      const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * 4;
+      const Real* arr = reinterpret_cast<const Real*>(group_buf(buf));
+      const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * C::RS;
+      const Real* tab = reinterpret_cast<const Real*>(fb + C::F_BYTES);
   #pragma unroll
       for (int j = 0; j < TH; ++j) {
         const int y = row0 + j;
-        float mv[TW];
+        Real mv[TW];
   #pragma unroll
         for (int i = 0; i < TW; ++i) {
           const int c = j * TW + i;
-          const Rcp2 rp = rcp_pair(ct, ctl, arr[C::A_ST * C::CELLS + c], arr[C::A_STL * C::CELLS + c]);
-          const float leftA = (i == 0) ? xA[j] : yA[i - 1];
-          float fo = 0.f;
+          Real dh, dlo;
+          diag<TBL>(ct, ctl, arr, tab, c, dl, C::CELLS, DL, dh, dlo);
+          const Real leftA = (i == 0) ? xA[j] : yA[i - 1];
+          Real fo = Real(0);
           if constexpr (MB != 0) {
             if constexpr (BF)
               fo = arr[C::A_FRO * C::CELLS + c] +
                    __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(fb)[c * DL + dl]);
             else
-              fo = reinterpret_cast<const float*>(fb)[c * DL + dl];
+              fo = reinterpret_cast<const Real*>(fb)[c * DL + dl];
           }
-          float srcA;
+          Real srcA;
           if constexpr (MB == 0) srcA = arr[C::A_Q * C::CELLS + c];
           else if constexpr (MB == 2) srcA = arr[C::A_G2 * C::CELLS + c] + tau * fo;
           else srcA = arr[C::A_Q * C::CELLS + c] + tau * fo;
           // yA[i - 1] is already this row's value: the left neighbour; yA[i] is still the row above
-          const float va = scale2(srcA + ca * leftA + cb * yA[i], rp.h, rp.l);
+          const Real va = scale2(srcA + ca * leftA + cb * yA[i], dh, dlo);
           if constexpr (MB == 1) {
             const int x = t * TW + i;
             const bool store = active && x < nx && y < ny;
-            float vst;
+            Real vst;
             if constexpr (BF) {
               const long cell = phys(x < nx ? x : 0, y < ny ? y : 0);
               const __nv_bfloat16 rb = bf16_stochastic(va - arr[C::A_FRN * C::CELLS + c],
@@ -295,9 +355,9 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
               if (store) f_fam[(size_t)phys(x, y) * DL + dl] = va;
               vst = va;
             }
-            const float leftB = (i == 0) ? xB[j] : yB[i - 1];
-            const float vb =
-                scale2(arr[C::A_G2 * C::CELLS + c] + tau * vst + ca * leftB + cb * yB[i], rp.h, rp.l);
+            const Real leftB = (i == 0) ? xB[j] : yB[i - 1];
+            const Real vb =
+                scale2(arr[C::A_G2 * C::CELLS + c] + tau * vst + ca * leftB + cb * yB[i], dh, dlo);
             yB[i] = vb;
             mv[i] = cw * vb;
           } else {
@@ -308,7 +368,7 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
         xA[j] = yA[TW - 1];
         if constexpr (MB == 1) xB[j] = yB[TW - 1];
         // quadrature moment of row j over the group's directions: one partial per family and cell
-        TReduce<float, TW, DL / 2>::run(mv, dl);
+        TReduce<Real, TW, DL / 2>::run(mv, dl);
         int idx;
         bool writer;
         if constexpr (TW >= DL) {
@@ -325,9 +385,10 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
       // single recurrence (SI sweep, y sweep): anti-diagonal by anti-diagonal, so that the up
       // to TH cells of a diagonal are independent and the dependent FMA chain of the recurrence
       // overlaps across them; the moment of the whole tile in one transpose-reduce at the end
-      const float* arr = reinterpret_cast<const float*>(group_buf(buf));
-      const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * 4;
-      float vA[TH][TW];
+      const Real* arr = reinterpret_cast<const Real*>(group_buf(buf));
+      const unsigned char* fb = group_buf(buf) + C::NARR * C::CELLS * C::RS;
+      const Real* tab = reinterpret_cast<const Real*>(fb + C::F_BYTES);
+      Real vA[TH][TW];
   #pragma unroll
       for (int dg = 0; dg < TW + TH - 1; ++dg) {
   #pragma unroll
@@ -335,22 +396,23 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
           const int i = dg - j;
           if (i < 0 || i >= TW) continue;
           const int c = j * TW + i;
-          const Rcp2 rp = rcp_pair(ct, ctl, arr[C::A_ST * C::CELLS + c], arr[C::A_STL * C::CELLS + c]);
-          const float left = (i == 0) ? xA[j] : vA[j][i > 0 ? i - 1 : 0];
-          const float up = (j == 0) ? yA[i] : vA[j > 0 ? j - 1 : 0][i];
-          float src;
+          Real dh, dlo;
+          diag<TBL>(ct, ctl, arr, tab, c, dl, C::CELLS, DL, dh, dlo);
+          const Real left = (i == 0) ? xA[j] : vA[j][i > 0 ? i - 1 : 0];
+          const Real up = (j == 0) ? yA[i] : vA[j > 0 ? j - 1 : 0][i];
+          Real src;
           if constexpr (MB == 0) {
             src = arr[C::A_Q * C::CELLS + c];
           } else {
-            float fo;
+            Real fo;
             if constexpr (BF)
               fo = arr[C::A_FRO * C::CELLS + c] +
                    __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(fb)[c * DL + dl]);
             else
-              fo = reinterpret_cast<const float*>(fb)[c * DL + dl];
+              fo = reinterpret_cast<const Real*>(fb)[c * DL + dl];
             src = arr[C::A_G2 * C::CELLS + c] + tau * fo;
           }
-          vA[j][i] = scale2(src + ca * left + cb * up, rp.h, rp.l);
+          vA[j][i] = scale2(src + ca * left + cb * up, dh, dlo);
         }
       }
   #pragma unroll
@@ -359,10 +421,10 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
       for (int i = 0; i < TW; ++i) yA[i] = vA[TH - 1][i];
       {
         constexpr int NV = TH * TW;
-        float mv[NV];
+        Real mv[NV];
   #pragma unroll
         for (int c = 0; c < NV; ++c) mv[c] = cw * vA[c / TW][c % TW];
-        TReduce<float, NV, DL / 2>::run(mv, dl);
+        TReduce<Real, NV, DL / 2>::run(mv, dl);
         constexpr int PER = NV >= DL ? NV / DL : 1;
   #pragma unroll
         for (int q = 0; q < PER; ++q) {
@@ -399,7 +461,7 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
           __syncwarp();
         }
         if (g == NG - 1) {
-          float* rs = ring_out + (size_t)(tl % RD) * TW * DL + dl;
+          Real* rs = ring_out + (size_t)(tl % RD) * TW * DL + dl;
 #pragma unroll
           for (int i = 0; i < TW; ++i) {
             rs[i * DL] = yA[i];
@@ -441,54 +503,55 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<flo
   }
 }
 
-template <int DL, int TH, int MODE>
+template <class Real, int DL, int TH, int MODE>
 size_t tile_smem(int W) {
-  using C = TileCfg<DL, TH, MODE>;
-  return (size_t)W * C::WARP_BYTES + (size_t)(W > 1 ? W - 1 : 0) * C::RING_FLOATS * sizeof(float);
+  using C = TileCfg<Real, DL, TH, MODE>;
+  return (size_t)W * C::WARP_BYTES + (size_t)(W > 1 ? W - 1 : 0) * C::RING_REALS * sizeof(Real);
 }
 
-template <int DL, int TH, int MODE>
-cudaError_t launch_tile(const Sweep2DArgs<float>& a, int W, cudaStream_t s) {
+template <class Real, int DL, int TH, int MODE>
+cudaError_t launch_tile(const Sweep2DArgs<Real>& a, int W, cudaStream_t s) {
   constexpr int NG = 32 / DL;
   if (W < 1 || W > 8 || a.rows_per_blk != W * NG * TH) return cudaErrorInvalidValue;
-  const size_t smem = tile_smem<DL, TH, MODE>(W);
+  if (sizeof(Real) == 8 && a.inv_d == nullptr) return cudaErrorInvalidValue;
+  const size_t smem = tile_smem<Real, DL, TH, MODE>(W);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static std::atomic<bool> attr_set{false};   // host threads of a batch share it
   if (!attr_set.load()) {
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_tile_kernel<DL, TH, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_tile_kernel<Real, DL, TH, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   ++g_launches;
-  sweep2d_tile_kernel<DL, TH, MODE><<<(unsigned)(a.nfam * a.nblk), 32 * W, smem, s>>>(a);
+  sweep2d_tile_kernel<Real, DL, TH, MODE><<<(unsigned)(a.nfam * a.nblk), 32 * W, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int MODE>
-cudaError_t launch_tile_mode(const Sweep2DArgs<float>& a, int dl, int th, int W, cudaStream_t s) {
+template <class Real, int MODE>
+cudaError_t launch_tile_mode(const Sweep2DArgs<Real>& a, int dl, int th, int W, cudaStream_t s) {
   if (th == 4) {
-    if (dl == 8) return launch_tile<8, 4, MODE>(a, W, s);
-    if (dl == 16) return launch_tile<16, 4, MODE>(a, W, s);
-    if (dl == 32) return launch_tile<32, 4, MODE>(a, W, s);
+    if (dl == 8) return launch_tile<Real, 8, 4, MODE>(a, W, s);
+    if (dl == 16) return launch_tile<Real, 16, 4, MODE>(a, W, s);
+    if (dl == 32) return launch_tile<Real, 32, 4, MODE>(a, W, s);
   } else if (th == 8) {
-    if (dl == 8) return launch_tile<8, 8, MODE>(a, W, s);
-    if (dl == 16) return launch_tile<16, 8, MODE>(a, W, s);
-    if (dl == 32) return launch_tile<32, 8, MODE>(a, W, s);
+    if (dl == 8) return launch_tile<Real, 8, 8, MODE>(a, W, s);
+    if (dl == 16) return launch_tile<Real, 16, 8, MODE>(a, W, s);
+    if (dl == 32) return launch_tile<Real, 32, 8, MODE>(a, W, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int MODE>
+template <class Real, int MODE>
 size_t tile_smem_mode(int dl, int th, int W) {
   if (th == 4) {
-    if (dl == 8) return tile_smem<8, 4, MODE>(W);
-    if (dl == 16) return tile_smem<16, 4, MODE>(W);
-    if (dl == 32) return tile_smem<32, 4, MODE>(W);
+    if (dl == 8) return tile_smem<Real, 8, 4, MODE>(W);
+    if (dl == 16) return tile_smem<Real, 16, 4, MODE>(W);
+    if (dl == 32) return tile_smem<Real, 32, 4, MODE>(W);
   } else if (th == 8) {
-    if (dl == 8) return tile_smem<8, 8, MODE>(W);
-    if (dl == 16) return tile_smem<16, 8, MODE>(W);
-    if (dl == 32) return tile_smem<32, 8, MODE>(W);
+    if (dl == 8) return tile_smem<Real, 8, 8, MODE>(W);
+    if (dl == 16) return tile_smem<Real, 16, 8, MODE>(W);
+    if (dl == 32) return tile_smem<Real, 32, 8, MODE>(W);
   }
   return ~(size_t)0;
 }
@@ -499,53 +562,69 @@ size_t tile_smem_mode(int dl, int th, int W) {
 #define RTE_TILE_PART -1
 #endif
 
-// One translation unit per mode, compiled in parallel; the dispatcher sits in part 0.
-template <int MODE>
-cudaError_t launch_tile_part(const Sweep2DArgs<float>& a, int dl, int th, int W, cudaStream_t s);
-template <int MODE>
+// One translation unit per precision and mode, compiled in parallel (parts 0-4: FP32 modes
+// 0-4, parts 5-7: FP64 modes 0-2); the dispatchers sit in part 0.
+template <class Real, int MODE>
+cudaError_t launch_tile_part(const Sweep2DArgs<Real>& a, int dl, int th, int W, cudaStream_t s);
+template <class Real, int MODE>
 size_t tile_smem_part(int dl, int th, int W);
 
-#define RTE_TILE_INST(MODE)                                                                  \
+#define RTE_TILE_INST(REAL, MODE)                                                            \
   template <>                                                                                \
-  cudaError_t launch_tile_part<MODE>(const Sweep2DArgs<float>& a, int dl, int th, int W,     \
-                                     cudaStream_t s) {                                       \
-    return launch_tile_mode<MODE>(a, dl, th, W, s);                                          \
+  cudaError_t launch_tile_part<REAL, MODE>(const Sweep2DArgs<REAL>& a, int dl, int th, int W, \
+                                           cudaStream_t s) {                                 \
+    return launch_tile_mode<REAL, MODE>(a, dl, th, W, s);                                    \
   }                                                                                          \
   template <>                                                                                \
-  size_t tile_smem_part<MODE>(int dl, int th, int W) {                                       \
-    return tile_smem_mode<MODE>(dl, th, W);                                                  \
+  size_t tile_smem_part<REAL, MODE>(int dl, int th, int W) {                                 \
+    return tile_smem_mode<REAL, MODE>(dl, th, W);                                            \
   }
-#define RTE_TILE_DECL(MODE)                                                                  \
+#define RTE_TILE_DECL(REAL, MODE)                                                            \
   template <>                                                                                \
-  cudaError_t launch_tile_part<MODE>(const Sweep2DArgs<float>& a, int dl, int th, int W,     \
-                                     cudaStream_t s);                                        \
+  cudaError_t launch_tile_part<REAL, MODE>(const Sweep2DArgs<REAL>& a, int dl, int th, int W, \
+                                           cudaStream_t s);                                  \
   template <>                                                                                \
-  size_t tile_smem_part<MODE>(int dl, int th, int W);
+  size_t tile_smem_part<REAL, MODE>(int dl, int th, int W);
 
 #if RTE_TILE_PART == -1 || RTE_TILE_PART == 0
-RTE_TILE_INST(0)
+RTE_TILE_INST(float, 0)
 #else
-RTE_TILE_DECL(0)
+RTE_TILE_DECL(float, 0)
 #endif
 #if RTE_TILE_PART == -1 || RTE_TILE_PART == 1
-RTE_TILE_INST(1)
+RTE_TILE_INST(float, 1)
 #else
-RTE_TILE_DECL(1)
+RTE_TILE_DECL(float, 1)
 #endif
 #if RTE_TILE_PART == -1 || RTE_TILE_PART == 2
-RTE_TILE_INST(2)
+RTE_TILE_INST(float, 2)
 #else
-RTE_TILE_DECL(2)
+RTE_TILE_DECL(float, 2)
 #endif
 #if RTE_TILE_PART == -1 || RTE_TILE_PART == 3
-RTE_TILE_INST(3)
+RTE_TILE_INST(float, 3)
 #else
-RTE_TILE_DECL(3)
+RTE_TILE_DECL(float, 3)
 #endif
 #if RTE_TILE_PART == -1 || RTE_TILE_PART == 4
-RTE_TILE_INST(4)
+RTE_TILE_INST(float, 4)
 #else
-RTE_TILE_DECL(4)
+RTE_TILE_DECL(float, 4)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 5
+RTE_TILE_INST(double, 0)
+#else
+RTE_TILE_DECL(double, 0)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 6
+RTE_TILE_INST(double, 1)
+#else
+RTE_TILE_DECL(double, 1)
+#endif
+#if RTE_TILE_PART == -1 || RTE_TILE_PART == 7
+RTE_TILE_INST(double, 2)
+#else
+RTE_TILE_DECL(double, 2)
 #endif
 
 #if RTE_TILE_PART == -1 || RTE_TILE_PART == 0
@@ -553,22 +632,41 @@ cudaError_t launch_sweep2d_tile(const Sweep2DArgs<float>& a, int mode, int th, i
                                 cudaStream_t s) {
   const int dl = a.nslot / a.nfam;
   switch (mode) {
-    case 0: return launch_tile_part<0>(a, dl, th, W, s);
-    case 1: return launch_tile_part<1>(a, dl, th, W, s);
-    case 2: return launch_tile_part<2>(a, dl, th, W, s);
-    case 3: return launch_tile_part<3>(a, dl, th, W, s);
-    case 4: return launch_tile_part<4>(a, dl, th, W, s);
+    case 0: return launch_tile_part<float, 0>(a, dl, th, W, s);
+    case 1: return launch_tile_part<float, 1>(a, dl, th, W, s);
+    case 2: return launch_tile_part<float, 2>(a, dl, th, W, s);
+    case 3: return launch_tile_part<float, 3>(a, dl, th, W, s);
+    case 4: return launch_tile_part<float, 4>(a, dl, th, W, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-size_t sweep2d_tile_smem_bytes(int dl, int th, int W, int mode) {
+cudaError_t launch_sweep2d_tile(const Sweep2DArgs<double>& a, int mode, int th, int W,
+                                cudaStream_t s) {
+  const int dl = a.nslot / a.nfam;
   switch (mode) {
-    case 0: return tile_smem_part<0>(dl, th, W);
-    case 1: return tile_smem_part<1>(dl, th, W);
-    case 2: return tile_smem_part<2>(dl, th, W);
-    case 3: return tile_smem_part<3>(dl, th, W);
-    case 4: return tile_smem_part<4>(dl, th, W);
+    case 0: return launch_tile_part<double, 0>(a, dl, th, W, s);
+    case 1: return launch_tile_part<double, 1>(a, dl, th, W, s);
+    case 2: return launch_tile_part<double, 2>(a, dl, th, W, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t sweep2d_tile_smem_bytes(size_t real, int dl, int th, int W, int mode) {
+  if (real == sizeof(double)) {
+    switch (mode) {
+      case 0: return tile_smem_part<double, 0>(dl, th, W);
+      case 1: return tile_smem_part<double, 1>(dl, th, W);
+      case 2: return tile_smem_part<double, 2>(dl, th, W);
+      default: return ~(size_t)0;
+    }
+  }
+  switch (mode) {
+    case 0: return tile_smem_part<float, 0>(dl, th, W);
+    case 1: return tile_smem_part<float, 1>(dl, th, W);
+    case 2: return tile_smem_part<float, 2>(dl, th, W);
+    case 3: return tile_smem_part<float, 3>(dl, th, W);
+    case 4: return tile_smem_part<float, 4>(dl, th, W);
     default: return ~(size_t)0;
   }
 }

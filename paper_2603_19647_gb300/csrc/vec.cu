@@ -124,11 +124,13 @@ __global__ void axpby_kernel(double alpha, const double* x, double beta, const d
 }
 
 // f = rho in every direction; f layout [family][cell][lane] with nslot / dl families.
-__global__ void isotropic_f_kernel(const double* rho, int n, int nslot, int dl, double* f) {
+__global__ void isotropic_f_kernel(const double* rho, int n, int nslot, int dl, const double* w,
+                                   double* f) {
   const long i = (long)blockIdx.x * VT + threadIdx.x;
   if (i >= (long)n * nslot) return;
   const long c = (i / dl) % n;
-  f[i] = rho[c];
+  // family layout [fam][cell][dl]: slot = fam * dl + lane
+  f[i] = w ? w[(i / ((long)n * dl)) * dl + i % dl] * rho[c] : rho[c];
 }
 
 __global__ void dot_partial_kernel(const double* x, const double* y, int n, double* partials) {
@@ -300,11 +302,11 @@ cudaError_t launch_axpby(double alpha, const double* x, double beta, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, int dl, double* f,
-                               cudaStream_t s) {
+cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, int dl, const double* w,
+                               double* f, cudaStream_t s) {
   const long tot = (long)n * nslot;
   ++g_launches;
-  isotropic_f_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, dl, f);
+  isotropic_f_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, dl, w, f);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,34 @@ def test_sweep_2d_tilings(lanes, rows, warps, mode):
     h.destroy()
 
 
+@pytest.mark.parametrize("lanes,th,warps", [(8, 4, 1), (8, 8, 2), (16, 4, 3), (32, 4, 4),
+                                             (32, 8, 2), (8, 4, 5), (16, 8, 1)])
+@pytest.mark.parametrize("shape", [(45, 53), (8, 9), (3, 130)])
+def test_sweep_2d_tile_kernel(lanes, th, warps, shape):
+    """The tile-sequence kernel in FP64 (each lane solves whole 8 x TH tiles, the diagonal
+    from the staged inverse table): SI sweep twice, fused f sweep with inflow and b~, on
+    ragged grids (partial tiles in both directions)."""
+    wl, rng = _hetero_2d(*shape, (32, 8), seed=lanes * th + warps + shape[1])
+    h, p = make_pair(wl, sweep_kernel=2, sweep_lanes=lanes, sweep_rows=th, sweep_warps=warps)
+    st = h.rte_get_stats()
+    assert st["sweep_si_kernel"] == 2 and st["sweep_f_kernel"] == 2
+    for _ in range(2):
+        rho = rng.uniform(-1, 1, wl.ncell)
+        assert rel_l2(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)) < 1e-12
+    perm, _, _ = match_directions(h, wl.quadrature)
+    f0 = rng.uniform(0, 1, (p.nv, wl.ncell))
+    h.rte_set_initial(f0=f0[perm])
+    g = np.array([0.3, 0.6, 0.2, 0.9])
+    h.rte_set_inflow(g)
+    p.inflow = g
+    rho = rng.uniform(0, 1, wl.ncell)
+    bt = h.rte_op_fsweep(rho)
+    f_ref, _ = tr.final_f(p, rho, f0)
+    assert rel_l2(h.rte_get_angular_flux(), f_ref[perm]) < 1e-12
+    assert rel_l2(bt, tr.b_tilde(p, f_ref)) < 1e-12
+    h.destroy()
+
+
 @pytest.mark.parametrize("n,nd", [(1, 16), (7, 4), (256, 16), (1000, 8), (4097, 16)])
 def test_sweep_1d(n, nd):
     rng = np.random.default_rng(n)

@@ -94,6 +94,12 @@ def test_checkerboard_downscaled_rom_tight():
     assert max(s.phase for s in orc.log) >= 2
 
 
+def test_checkerboard_tile_kernel_rom_tight():
+    """The same march with the tile-sequence sweep kernel for both sweep modes."""
+    orc = _march(inputs.checkerboard(n=48), 80, 10, rom_on=True, sweep_kernel=2, **TIGHT)
+    assert max(s.phase for s in orc.log) >= 2
+
+
 def test_checkerboard_ragged_small_rule():
     wl = inputs.checkerboard(n=8, quad=(8, 4))
     wl.nx, wl.ny = 27, 19
