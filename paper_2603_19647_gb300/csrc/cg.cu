@@ -2,14 +2,17 @@
 //   C delta = Sigma_s (rho^{l-1/2} - rho^{l-1}),
 // C the cell-centred diffusion discretisation of the correction equation Eq.
 // (discrete_correction_f) (sigma_a~ = tau + sigma_a, D = 1/(3 (tau + sigma_t)), zero inflow):
-// 5-point (1D: 3-point) stencil, harmonic-mean face coefficients 2 D_L D_R/((D_L+D_R) h^2),
-// Marshak vacuum faces 1/(h (2 + h/(2D))).  Solved by conjugate gradients (Sec. 4) in one
-// cooperative launch: every CG iteration is two grid-wide phases,
+// 5-point (1D: 3-point) stencil, harmonic-mean face coefficients 2 D_L D_R/((D_L+D_R) h^2) and
+// Marshak vacuum faces 1/(h (2 + h/(2D))), each floored at 1/(4h) (the half-range current of
+// the upwind sweep).  Solved by conjugate gradients (Sec. 4) in one cooperative launch, with
+// grid-wide phases separated by a bounded software grid barrier; every block sums the block
+// partials in the same fixed order, so the CG scalars are identical everywhere and bitwise
+// reproducible.  The handle's solves on grids of up to 2^18 cells use cg1_kernel, one phase
+// per iteration (the Chronopoulos-Gear arrangement); larger grids and the allocation-free
+// solve use cg_kernel, two phases per iteration:
 //   (1) p <- r + beta p (double-buffered, neighbours recomputed from r and the old p),
 //       Ap = C p, and the block partials of p.Ap;
-//   (2) x += alpha p, r -= alpha Ap and the block partials of r.r,
-// separated by a bounded software grid barrier.  Every block sums the block partials in the
-// same fixed order, so alpha and beta are identical everywhere and bitwise reproducible.
+//   (2) x += alpha p, r -= alpha Ap and the block partials of r.r.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -37,6 +40,7 @@ struct CgArgs {
   double rtol2;
   int max_iter;
   double *r, *p0, *p1, *ap, *x;
+  double *r1, *w1, *s1;   // cg1_kernel: second buffers of r, w = A r (first: ap), s = A p (first: p1)
   double* partial;     // [2 * gridDim.x]
   unsigned* bar;       // [0] arrive count, [1] generation, [2] error
   double* delta;       // output (may alias x)
@@ -193,6 +197,171 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
   if (tid == 0) *a.iters = it;
 }
 
+// Block sums of two values, thread 0 storing them to dst0 / dst1.
+__device__ void block_sum2_store(double u, double v, double* dst0, double* dst1) {
+  __shared__ double sh[2][CT / 32];
+  u = warp_sum(u);
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = u;
+    sh[1][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    u = threadIdx.x < CT / 32 ? sh[0][threadIdx.x] : 0.0;
+    v = threadIdx.x < CT / 32 ? sh[1][threadIdx.x] : 0.0;
+    u = warp_sum(u);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      *dst0 = u;
+      *dst1 = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Sums of two arrays of gridDim.x partials, read by the whole block in one pass and added in a
+// fixed tree order, so every block obtains the same two values.
+__device__ void grid_total2(const double* part0, const double* part1, double& t0, double& t1) {
+  __shared__ double sh[2][CT / 32];
+  __shared__ double tot[2];
+  double u = 0.0, v = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += CT) {
+    u += __ldcg(part0 + b);
+    v += __ldcg(part1 + b);
+  }
+  u = warp_sum(u);
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = u;
+    sh[1][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    u = threadIdx.x < CT / 32 ? sh[0][threadIdx.x] : 0.0;
+    v = threadIdx.x < CT / 32 ? sh[1][threadIdx.x] : 0.0;
+    u = warp_sum(u);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      tot[0] = u;
+      tot[1] = v;
+    }
+  }
+  __syncthreads();
+  t0 = tot[0];
+  t1 = tot[1];
+  __syncthreads();
+}
+
+// The same CG solve in the Chronopoulos-Gear arrangement (s = A p and w = A r carried by
+// recurrences, x, r, p as in the textbook method): in exact arithmetic the iterates, and with
+// the stopping test (r, r) <= rtol^2 (b, b) on the directly summed (r, r) the iteration count,
+// are those of the textbook recurrence, but the two inner products of an iteration, (r, r)
+// and (w, r), come from one reduction, so an iteration is one grid-wide phase and one barrier:
+//   p = r + beta p, s = w + beta s, x += alpha p, r' = r - alpha s, w' = A r', (r', r'), (w', r').
+// A neighbour's r' is recomputed from its r, w and s of the previous phase (double-buffered),
+// with the same fused operations as its owner uses, so every copy is bitwise the owner's.
+// The setup forms only r = b and (b, b); the first step length needs (C r, r), which one more
+// phase computes when the stopping test lets CG iterate at all (a solve of k >= 1 iterations
+// takes k + 2 barriers, a solve that stops at once one).
+__global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
+  if (a.skip && *a.skip) return;   // every block returns before the first barrier
+  unsigned gen = ld_acquire(&a.bar[1]);
+  const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
+  const int nx = a.nx, ny = a.ny, n = a.n;
+  double* partG = a.partial;
+  double* partD = a.partial + gridDim.x;
+  // (C v)_c for v given at c (vc) and at the neighbours by a function of the cell index
+  auto apply = [&](int c, double vc, auto v) {
+    const int i = c % nx;
+    double s = a.diag[c] * vc;
+    if (i + 1 < nx) s -= a.cx[c] * v(c + 1);
+    if (i > 0) s -= a.cx[c - 1] * v(c - 1);
+    if (ny > 1) {
+      if (c + nx < n) s -= a.cy[c] * v(c + nx);
+      if (c - nx >= 0) s -= a.cy[c - nx] * v(c - nx);
+    }
+    return s;
+  };
+  // r = b = sig_s .* residual and (b, b)
+  double g = 0.0, d = 0.0;
+  for (int c = tid; c < n; c += nth) {
+    const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
+    const double b = a.sig_s[c] * rc;
+    a.r[c] = b;
+    g += b * b;
+  }
+  block_sum2_store(g, 0.0, partG + blockIdx.x, partD + blockIdx.x);
+  grid_barrier(a.bar, gen);
+  double gamma, delta;
+  grid_total2(partG, partD, gamma, delta);
+  const double bb = gamma;
+  if (a.max_iter > 0 && gamma > a.rtol2 * bb) {
+    // w = C r and (w, r) for the first step length (only when CG iterates at all)
+    d = 0.0;
+    for (int c = tid; c < n; c += nth) {
+      const double rc = a.r[c];
+      const double w = apply(c, rc, [&](int k) { return __ldcg(a.r + k); });
+      a.ap[c] = w;
+      d += w * rc;
+    }
+    block_sum2_store(0.0, d, partG + blockIdx.x, partD + blockIdx.x);
+    grid_barrier(a.bar, gen);
+    double unused;
+    grid_total2(partG, partD, unused, delta);
+  }
+  double gamma_prev = 0.0, alpha_prev = 0.0;
+  int it = 0;
+  while (it < a.max_iter && gamma > a.rtol2 * bb) {
+    const bool first = it == 0;   // p = r, s = w, x = alpha p (p, s, x start at zero)
+    const double beta = first ? 0.0 : gamma / gamma_prev;
+    const double alpha = first ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
+    const bool odd = (it & 1) != 0;
+    const double* r_o = odd ? a.r1 : a.r;
+    const double* w_o = odd ? a.w1 : a.ap;
+    const double* s_o = odd ? a.s1 : a.p1;
+    double* r_n = odd ? a.r : a.r1;
+    double* w_n = odd ? a.ap : a.w1;
+    double* s_n = odd ? a.p1 : a.s1;
+    auto rnext = [&](int k) {
+      const double sk = first ? __ldcg(w_o + k) : fma(beta, __ldcg(s_o + k), __ldcg(w_o + k));
+      return fma(-alpha, sk, __ldcg(r_o + k));
+    };
+    g = 0.0;
+    d = 0.0;
+    for (int c = tid; c < n; c += nth) {
+      const double rc0 = r_o[c];
+      const double sc = first ? w_o[c] : fma(beta, s_o[c], w_o[c]);
+      const double pc = first ? rc0 : fma(beta, a.p0[c], rc0);
+      a.p0[c] = pc;
+      s_n[c] = sc;
+      a.x[c] = first ? alpha * pc : fma(alpha, pc, a.x[c]);
+      const double rc = fma(-alpha, sc, rc0);
+      const double wc = apply(c, rc, rnext);
+      r_n[c] = rc;
+      w_n[c] = wc;
+      g += rc * rc;
+      d += wc * rc;
+    }
+    block_sum2_store(g, d, partG + blockIdx.x, partD + blockIdx.x);
+    grid_barrier(a.bar, gen);
+    gamma_prev = gamma;
+    alpha_prev = alpha;
+    grid_total2(partG, partD, gamma, delta);
+    ++it;
+  }
+  for (int c = tid; c < n; c += nth) {
+    const double dd = it > 0 ? a.x[c] : 0.0;
+    if (a.delta != a.x || it == 0) a.delta[c] = dd;
+    if (a.rho_out) {
+      const double r = a.rho_half[c] + dd;
+      a.rho_out[c] = r;
+      a.q_out[c] = a.sig_s[c] * r;
+    }
+  }
+  if (tid == 0) *a.iters = it;
+}
+
 }  // namespace
 
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
@@ -233,18 +402,27 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CT, 0);
+  // Small grids, where a CG iteration costs its grid barriers rather than its memory traffic,
+  // take the one-barrier arrangement (cg1_kernel, one block per SM: the barrier's cost grows
+  // with the blocks that arrive); large grids the two-phase one (cg_kernel, up to two blocks
+  // per SM), which moves fewer bytes in solves of few iterations (measured: 256^2 cells 16-20 %
+  // faster per solve with cg1_kernel, 1024^2 cells 20-25 % slower).
+  op.single_phase = n <= (1 << 18);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op.single_phase ? cg1_kernel : cg_kernel,
+                                                CT, 0);
   if (per_sm < 1) per_sm = 1;
-  int want = (n + CT - 1) / CT;
-  int cap = per_sm * sms;
-  if (cap > 2 * sms) cap = 2 * sms;
+  const int want = (n + CT - 1) / CT;
+  int cap = op.single_phase ? sms : 2 * sms;
+  if (cap > per_sm * sms) cap = per_sm * sms;
   op.blocks = want < cap ? want : cap;
   if (op.blocks < 1) op.blocks = 1;
   cudaError_t e;
   const size_t bytes = sizeof(double) * (size_t)n;
-  double** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x};
+  double** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x,
+                     &op.r1, &op.w1, &op.s1};
   for (double** b : bufs) {
     *b = nullptr;
+    if (!op.single_phase && (b == &op.r1 || b == &op.w1 || b == &op.s1)) continue;
     if ((e = cudaMalloc(b, bytes)) != cudaSuccess) return e;
   }
   if ((e = cudaMalloc(&op.partial, sizeof(double) * 2 * op.blocks)) != cudaSuccess) return e;
@@ -260,7 +438,8 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
 }
 
 void dsa_free(DsaOp& op) {
-  double* bufs[] = {op.diag, op.cx, op.cy, op.r, op.p0, op.p1, op.ap, op.x, op.partial, op.scal};
+  double* bufs[] = {op.diag, op.cx, op.cy, op.r,       op.p0,      op.p1,  op.ap,
+                    op.x,    op.r1, op.w1, op.s1, op.partial, op.scal};
   for (double* b : bufs)
     if (b) cudaFree(b);
   op = DsaOp{};
@@ -288,6 +467,9 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   a.p1 = op.p1;
   a.ap = op.ap;
   a.x = op.x;
+  a.r1 = op.r1;
+  a.w1 = op.w1;
+  a.s1 = op.s1;
   a.partial = op.partial;
   a.bar = reinterpret_cast<unsigned*>(op.scal);
   a.delta = delta ? delta : op.x;
@@ -297,7 +479,8 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   a.iters = iters_dev;
   void* args[] = {&a};
   ++g_launches;
-  return cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(op.blocks), dim3(CT), args, 0, s);
+  return cudaLaunchCooperativeKernel(op.single_phase ? (const void*)cg1_kernel : (const void*)cg_kernel,
+                                     dim3(op.blocks), dim3(CT), args, 0, s);
 }
 
 }  // namespace rte

@@ -167,9 +167,11 @@ struct DsaOp {
   double* cy;     // [n] coupling of cell c with c+nx (0 at the north edge / 1D)
   // CG workspace
   double *r, *p0, *p1, *ap, *x;
+  double *r1, *w1, *s1;   // second buffers of the single-barrier CG (r, w = C r, s = C p)
   double* partial;   // [2 * blocks]
   double* scal;      // [8] device scalars
   int blocks;
+  bool single_phase;   // cg1_kernel (one barrier per iteration) instead of cg_kernel
 };
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
                       const double* sig_t_host, const double* sig_s_host, cudaStream_t s);

@@ -147,9 +147,12 @@ def test_fused_f_sweep(case):
 
 
 @pytest.mark.parametrize("rtol", [1e-6, 1e-10])
-@pytest.mark.parametrize("name", ["checkerboard", "slab"])
+@pytest.mark.parametrize("name", ["checkerboard", "slab", "large"])
 def test_dsa_cg(name, rtol):
-    wl = inputs.checkerboard(n=40) if name == "checkerboard" else inputs.slab_1d(n=256)
+    """Both CG arrangements: grids up to 2^18 cells take the one-barrier kernel, larger ones
+    (here 520^2) the two-phase kernel."""
+    wl = (inputs.checkerboard(n=40) if name == "checkerboard"
+          else inputs.checkerboard(n=520) if name == "large" else inputs.slab_1d(n=256))
     h, p = make_pair(wl, cg_rtol=rtol)
     rng = np.random.default_rng(9)
     res = rng.uniform(-1, 1, wl.ncell)
