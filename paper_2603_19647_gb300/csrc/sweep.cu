@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
     for (int k = 0; k < K; ++k) {
       const int t = tb + k;
       Real upA = __shfl_up_sync(FULL, psA[R - 1], DL);
-      Real upB = __shfl_up_sync(FULL, psB[R - 1], DL);
+      Real upB = Real(0);
+      if constexpr (MB == 1) upB = __shfl_up_sync(FULL, psB[R - 1], DL);
       if (warp > 0 && t < nx) {
         // column t of the warp above's bottom row, handed over step by step
         if (known_prod <= t) {
