@@ -720,12 +720,19 @@ void resolve_spans(rte_handle h) {
 // l = 1 fail.  Measured on GB300 the host's turnaround between iterations (spin wait) is a
 // few microseconds, less than the skipped launches cost, so lookahead is off by default.
 // ---------------------------------------------------------------------------------------
-rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out) {
+// init_src: the initial guess when it is not in rho0 yet (it is then copied to rho0 too).
+rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
+                 const double* init_src) {
   const int n = (int)h->ncell;
   const int nb = vec_blocks(n);
   const int absmode = h->opt.residual_norm == RTE_ABS_INF ? 1 : 0;
-  CK(cudaMemcpyAsync(h->rho_prev, h->rho0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  CK(cudaMemsetAsync(h->d_conv, 0, sizeof(unsigned), h->st));
+  // rho^{l-1} = rho^{(0)}, skip word and CG iteration slots cleared, in one launch
+  if (init_src)
+    CK(launch_si_begin(init_src, h->rho0, h->rho_prev, n, h->d_conv, h->cg_iters,
+                       h->opt.max_iter + 2, h->st));
+  else
+    CK(launch_si_begin(h->rho0, h->rho_prev, nullptr, n, h->d_conv, h->cg_iters,
+                       h->opt.max_iter + 2, h->st));
   h->skip_now = h->d_conv;
   // FP64: each iteration sweeps sigma_s rho^{l-1}.  FP32 (iterative refinement): the sweeps
   // act on the increments rho^{l-1} - rho_ref in FP32 and their results accumulate into the
@@ -746,17 +753,21 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
     }
     return RTE_OK;
   };
-  // rho^{l-1/2}, its norms (pinned copy, parity l & 1) and the device stopping test
+  // rho^{l-1/2}, its norms (pinned copy, parity l & 1) and the device stopping test; the
+  // kernel also writes rho^{l-1/2} to rho (the iterate the step returns once converged, work
+  // past convergence skips itself) and, for l = 1, to rho^{n,1/2}
   auto residual = [&](int l) -> rte_status {
     const int p = l & 1;
     const int r0 = rec(h);
+    double* half1 = l == 1 ? h->rho_half1 : nullptr;
     if (h->fp32)
       CK(launch_combine_residual(h->y_ir, 1, h->btilde, h->rho_prev, n, h->rho_half, h->partials,
-                                 nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa, absmode));
+                                 nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa, absmode,
+                                 h->rho, half1));
     else
       CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
                                  h->partials, nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa,
-                                 absmode));
+                                 absmode, h->rho, half1));
     CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
     span(h, SPAN_SWEEP, r0, rec(h), l);
     CK(cudaEventRecord(h->blocking ? h->ev_norm_b[p] : h->ev_norm[p], h->st));
@@ -776,8 +787,6 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
   h->pc_applied = false;
   TRY(sweep_increment(1));
   TRY(residual(1));
-  CK(cudaMemcpyAsync(h->rho_half1, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                     h->st));
   for (l = 1;; ++l) {
     const bool pc_now = l == 1 && use_pc;
     if (h->opt.lookahead && l < h->opt.max_iter && !pc_now) {   // iteration l + 1, queued ahead
@@ -814,7 +823,6 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
   h->spans.erase(std::remove_if(h->spans.begin(), h->spans.end(),
                                 [&](const rte_s::Span& s) { return s.iter > l; }),
                  h->spans.end());
-  CK(cudaMemcpyAsync(h->rho, h->rho_half, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   // CG counts of this solve: slots 1 .. l-1 written by the DSA calls (the PC step and skipped
   // solves leave their slots at zero)
   CK(cudaMemcpyAsync(h->h_cg, h->cg_iters, sizeof(int) * (l + 2), cudaMemcpyDeviceToHost, h->st));
@@ -824,15 +832,13 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out)
   return RTE_OK;
 }
 
-// Sums the CG counts copied at the end of si_sa (after the stream is synchronised) and clears
-// the device slots for the next solve.
+// Sums the CG counts copied at the end of si_sa (after the stream is synchronised); the next
+// solve's first launch clears the device slots.
 rte_status finish_cg_counts(rte_handle h) {
   int cg = 0;
   for (int i = 0; i < h->cg_slots; ++i) cg += h->h_cg[i];
   h->stats.last_cg_iterations = cg;
   h->stats.total_cg_iterations += cg;
-  if (h->cg_slots > 0)
-    CK(cudaMemsetAsync(h->cg_iters, 0, sizeof(int) * h->cg_slots, h->st));
   h->cg_slots = 0;
   return RTE_OK;
 }
@@ -923,7 +929,6 @@ rte_status rom_update_finish(rte_handle h) {
 }
 
 rte_status one_step(rte_handle h) {
-  const int n = (int)h->ncell;
   const bool rom_on = h->opt.rom != RTE_ROM_OFF;
   auto t0 = std::chrono::steady_clock::now();
   if (!h->spans.empty()) {   // left over by a failed call
@@ -941,13 +946,12 @@ rte_status one_step(rte_handle h) {
     h->ig_applied = true;
     m = rec(h);
     span(h, SPAN_ROM, mark, m);
-  } else {
-    CK(cudaMemcpyAsync(h->rho0, h->rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   }
   const bool use_pc = rom_on && h->flag_pc && h->pc.lu_ok;
   int iters = 0;
   bool conv = false;
-  TRY(si_sa(h, use_pc, &iters, &conv));
+  // without the IG the initial guess is rho^{n-1} itself
+  TRY(si_sa(h, use_pc, &iters, &conv, h->ig_applied ? nullptr : h->rho));
   h->last_iters = iters;
   // the phase this step ran in (the ROM update below may end it)
   const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!h->flag_pc ? 2 : 3));

@@ -119,10 +119,15 @@ struct Norms {             // device-side reduction results of one residual eval
 };
 // conv (optional): skip word of a speculative SI-SA loop; the residual does nothing when it
 // is set and otherwise sets it to the outcome of the stopping test (eps, absolute or relative).
+// copy1 / copy2 (optional): further destinations of rho^{l-1/2}.
 cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
                                     const double* rho_prev, int ncell, double* rho_half,
                                     double* partials, int nblocks, Norms* out, cudaStream_t s,
-                                    unsigned* conv = nullptr, double eps = 0.0, int absmode = 0);
+                                    unsigned* conv = nullptr, double eps = 0.0, int absmode = 0,
+                                    double* copy1 = nullptr, double* copy2 = nullptr);
+// Start of an SI-SA solve: src -> dst1 (and dst2 when given), *conv = 0, slots[0..nslots) = 0.
+cudaError_t launch_si_begin(const double* src, double* dst1, double* dst2, int ncell,
+                            unsigned* conv, int* slots, int nslots, cudaStream_t s);
 cudaError_t launch_update_rho(const double* rho_half, const double* delta, const double* sig_s,
                               int ncell, double* rho, double* q, cudaStream_t s);
 cudaError_t launch_scale_copy(const double* x, const double* sig_s, int ncell, double* q,

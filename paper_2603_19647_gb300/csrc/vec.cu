@@ -28,7 +28,8 @@ __device__ __forceinline__ double warp_max(double v) {
 __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
                                         const double* __restrict__ btilde,
                                         const double* __restrict__ rho_prev, int n,
-                                        double* __restrict__ rho_half, double* partials,
+                                        double* __restrict__ rho_half, double* __restrict__ copy1,
+                                        double* __restrict__ copy2, double* partials,
                                         const unsigned* skip) {
   if (skip && *skip) return;   // the solve has converged: speculative work does nothing
   __shared__ double sh[3][VT / 32];
@@ -38,6 +39,8 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
     for (int f = 0; f < nfam; ++f) s += pm[(long)f * n + c];
     s += btilde[c];
     rho_half[c] = s;
+    if (copy1) copy1[c] = s;
+    if (copy2) copy2[c] = s;
     const double d = s - rho_prev[c];
     dinf = fmax(dinf, fabs(d));
     hinf = fmax(hinf, fabs(s));
@@ -262,13 +265,40 @@ int vec_blocks(int n) {
   return b < 1 ? 1 : (b > 1024 ? 1024 : b);
 }
 
+namespace {
+// Start of an SI-SA solve: the initial guess copied into place (dst1, and dst2 when given),
+// the skip word cleared and the CG iteration slots zeroed, in one launch.
+__global__ void si_begin_kernel(const double* __restrict__ src, double* __restrict__ dst1,
+                                double* __restrict__ dst2, int n, unsigned* conv, int* slots,
+                                int nslots) {
+  const int i = blockIdx.x * VT + threadIdx.x;
+  if (i < n) {
+    const double v = src[i];
+    dst1[i] = v;
+    if (dst2) dst2[i] = v;
+  }
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < nslots; k += VT) slots[k] = 0;
+    if (threadIdx.x == 0) *conv = 0u;
+  }
+}
+}  // namespace
+
+cudaError_t launch_si_begin(const double* src, double* dst1, double* dst2, int n, unsigned* conv,
+                            int* slots, int nslots, cudaStream_t s) {
+  ++g_launches;
+  si_begin_kernel<<<(n + VT - 1) / VT, VT, 0, s>>>(src, dst1, dst2, n, conv, slots, nslots);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
                                     const double* rho_prev, int n, double* rho_half,
                                     double* partials, int nblocks, Norms* out, cudaStream_t s,
-                                    unsigned* conv, double eps, int absmode) {
+                                    unsigned* conv, double eps, int absmode, double* copy1,
+                                    double* copy2) {
   ++g_launches;
-  combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, partials,
-                                                 conv);
+  combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, copy1,
+                                                 copy2, partials, conv);
   ++g_launches;
   finish_norms_kernel<<<1, 32, 0, s>>>(partials, nblocks, out, conv, eps, absmode);
   return cudaGetLastError();
