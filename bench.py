@@ -274,9 +274,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def make(rom):
+    def make(rom, precision=rte.RTE_FP64):
         h = rte.create_from_workload(wl, options=rte.default_options(
-            rom=rte.RTE_ROM_AUTO if rom else rte.RTE_ROM_OFF))
+            rom=rte.RTE_ROM_AUTO if rom else rte.RTE_ROM_OFF, precision=precision))
         h.rte_set_stream(stream.cuda_stream)
         return h
 
@@ -328,6 +328,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall_rom = time.perf_counter() - wall0
     ms_plain, agg_plain = timed_marches(h_plain, args.steps)
+    # the reduced-precision arms of the method on the same workload and GPU (FP32 sweeps and
+    # BF16-stored f with the FP64 residual), against the FP64 ROM march's final scalar flux
+    rho64 = h_rom.rte_get_scalar_flux()
+    reduced = {}
+    for name, prec in (("rom_sidsa_fp32", rte.RTE_FP32), ("rom_sidsa_bf16f", rte.RTE_FP32_BF16F)):
+        hr = make(True, prec)
+        hr.rte_restart()
+        hr.rte_step(nsteps)
+        ms_r, _ = timed_marches(hr, args.steps)
+        rho_r = hr.rte_get_scalar_flux()
+        reduced[name] = {"ms": sum(ms_r) / args.steps / nsteps,
+                         "rel_l2_vs_fp64": float(np.linalg.norm(rho_r - rho64) / np.linalg.norm(rho64))}
+        hr.destroy()
 
     total_ms, updates_all = reduce_over_ranks(dist, sum(ms_rom), agg_rom["updates"], "cuda")
     value = updates_all / (total_ms / 1e3)
@@ -391,6 +404,10 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) between steps"},
         "time_per_implicit_step_ms": {"rom_sidsa_fp64": per_step_rom, "sidsa_fp64": per_step_plain},
         "speedup_rom_vs_sidsa": per_step_plain / per_step_rom,
+        "reduced_precision_rom": {k: {"ms_per_implicit_step": v["ms"],
+                                      "speedup_vs_sidsa_fp64": per_step_plain / v["ms"],
+                                      "final_rel_l2_vs_fp64_rom": v["rel_l2_vs_fp64"]}
+                                  for k, v in reduced.items()},
         "sweeps_per_step": {"rom": agg_rom["sweeps"] / (args.steps * nsteps),
                             "sidsa": agg_plain["sweeps"] / (args.steps * nsteps)},
         "rom_ranks_end": {"ig": agg_rom["ig_rank"], "pc": agg_rom["pc_rank"]},
