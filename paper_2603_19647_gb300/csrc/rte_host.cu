@@ -1187,13 +1187,14 @@ void set_tile(rte_handle h, rte_s::Tile& tl, int kind, int R, int W) {
   tl.nblk = (h->ny + tl.rpb - 1) / tl.rpb;
 }
 
-// A tile is usable when its kind applies (the tile sequence takes TH = 4 or 8, the strip
-// chain R <= dl) and every sweep mode's staging fits the 200 KiB the launchers allow.
+// A tile is usable when its kind applies (the tile sequence takes TH = 4 or 8, and 2 in the
+// FP32 modes; the strip chain R <= dl) and every sweep mode's staging fits the 200 KiB the
+// launchers allow.
 bool tile_fits(rte_handle h, int dl, int kind, int R, int W) {
   const int modes_plain[3] = {0, 1, 2}, modes_bf[3] = {0, 3, 4};
   const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
   if (kind == 2) {
-    if (R != 4 && R != 8) return false;
+    if (R != 4 && R != 8 && !(R == 2 && h->fp32)) return false;
     for (int mode : h->bf16 ? modes_bf : modes_plain)
       if (sweep2d_tile_smem_bytes(real, dl, R, W, mode) > 200 * 1024) return false;
     return true;
@@ -1284,7 +1285,7 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     if (dl > dl_max) continue;
     TRY(make_layout(h, dl));
     std::vector<Cand> cand;
-    const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8}, ths[2] = {4, 8};
+    const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8}, ths[3] = {2, 4, 8};
     for (int R : rs)
       for (int W : ws)
         if (tile_fits(h, dl, 1, R, W)) cand.push_back({1, R, W});

@@ -530,6 +530,13 @@ cudaError_t launch_tile(const Sweep2DArgs<Real>& a, int W, cudaStream_t s) {
 
 template <class Real, int MODE>
 cudaError_t launch_tile_mode(const Sweep2DArgs<Real>& a, int dl, int th, int W, cudaStream_t s) {
+  if constexpr (sizeof(Real) == 4) {   // two-row tiles: FP32 only
+    if (th == 2) {
+      if (dl == 8) return launch_tile<Real, 8, 2, MODE>(a, W, s);
+      if (dl == 16) return launch_tile<Real, 16, 2, MODE>(a, W, s);
+      if (dl == 32) return launch_tile<Real, 32, 2, MODE>(a, W, s);
+    }
+  }
   if (th == 4) {
     if (dl == 8) return launch_tile<Real, 8, 4, MODE>(a, W, s);
     if (dl == 16) return launch_tile<Real, 16, 4, MODE>(a, W, s);
@@ -544,6 +551,13 @@ cudaError_t launch_tile_mode(const Sweep2DArgs<Real>& a, int dl, int th, int W, 
 
 template <class Real, int MODE>
 size_t tile_smem_mode(int dl, int th, int W) {
+  if constexpr (sizeof(Real) == 4) {
+    if (th == 2) {
+      if (dl == 8) return tile_smem<Real, 8, 2, MODE>(W);
+      if (dl == 16) return tile_smem<Real, 16, 2, MODE>(W);
+      if (dl == 32) return tile_smem<Real, 32, 2, MODE>(W);
+    }
+  }
   if (th == 4) {
     if (dl == 8) return tile_smem<Real, 8, 4, MODE>(W);
     if (dl == 16) return tile_smem<Real, 16, 4, MODE>(W);

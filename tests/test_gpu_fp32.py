@@ -66,7 +66,8 @@ def test_fp32_tilings_fused_f(lanes, rows, warps):
 
 
 @pytest.mark.parametrize("lanes,th,warps", [(8, 4, 1), (8, 8, 2), (16, 4, 3), (32, 4, 8), (32, 8, 2),
-                                             (8, 4, 8), (16, 8, 5)])
+                                             (8, 4, 8), (16, 8, 5), (8, 2, 3), (32, 2, 4),
+                                             (16, 2, 8)])
 @pytest.mark.parametrize("shape", [(45, 53), (8, 9), (3, 130)])
 def test_fp32_tile_kernel(lanes, th, warps, shape):
     """The tile-sequence kernel (each lane solves whole TW x TH tiles): SI sweep, fused f sweep
