@@ -143,41 +143,74 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
   const int nchunk = (T + K - 1) / K;
 
   // Copy this warp's data of chunk c into its buffer c & 1: row rr, step k -> column c K + k - rr.
+  // Which pieces a lane copies does not depend on the chunk, so each lane's pieces are
+  // described once: the row's first cell, the column offset k - rr, the shared-memory offset in
+  // buffer 0 and the offset within the cell's DL values (16-byte pieces of the per-direction
+  // arrays; single values of the per-cell arrays).
+  struct Piece {
+    long row;
+    int kr, o, vv;
+    bool on;
+  };
+  constexpr int SW = 16 / (int)sizeof(Real);   // values per 16-byte piece
+  constexpr int NPD = (TABLE || (STAGE_F && !BF)) ? (RW * K * V + 31) / 32 : 0;
+  constexpr int NPB = BF ? (RW * K * VB + 31) / 32 : 0;
+  constexpr int NPS = (RW * K + 31) / 32;
+  static_assert(NPD == 0 || (RW * K * V) % 32 == 0, "16-byte pieces fill whole warps");
+  static_assert(NPB == 0 || (RW * K * VB) % 32 == 0, "16-byte pieces fill whole warps");
+  // piece e of per_cell pieces per cell, unit values per piece; stride: values per (row, step)
+  // slot in shared memory (DL for the per-direction arrays, 1 for the per-cell arrays)
+  auto describe = [&](int e, int per_cell, int unit, int stride, int count) {
+    Piece p;
+    const int v = e % per_cell, rk = e / per_cell;
+    const int rr = rk / K, k = rk % K;
+    const int jj = wrow0 + rr;
+    p.on = e < count && jj < ny;
+    p.row = (long)(ypos ? jj : ny - 1 - jj) * nx;
+    p.kr = k - rr;
+    p.o = (rr * K + k) * stride + v * unit;
+    p.vv = v * unit;
+    return p;
+  };
+  Piece pd[NPD > 0 ? NPD : 1], pb[NPB > 0 ? NPB : 1], ps[NPS];
+#pragma unroll
+  for (int i = 0; i < NPD; ++i) pd[i] = describe(lane + 32 * i, V, SW, DL, RW * K * V);
+#pragma unroll
+  for (int i = 0; i < NPB; ++i) pb[i] = describe(lane + 32 * i, VB, 8, DL, RW * K * VB);
+#pragma unroll
+  for (int i = 0; i < NPS; ++i) ps[i] = describe(lane + 32 * i, 1, 1, 1, RW * K);
   auto stage = [&](int c) {
     const int buf = c & 1;
-    if constexpr (TABLE || (STAGE_F && !BF)) {
-      for (int e = lane; e < RW * K * V; e += 32) {
-        const int v = e % V, rk = e / V;
-        const int rr = rk / K, k = rk % K;
-        const int x = c * K + k - rr;
-        const int jj = wrow0 + rr;
-        const bool ok = x >= 0 && x < nx && jj < ny;
-        const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
-        const int o = ((buf * RW + rr) * K + k) * DL + v * (16 / (int)sizeof(Real));
-        const size_t g = (size_t)cell * DL + v * (16 / sizeof(Real));
-        if constexpr (TABLE) cp_async_16(tab_s + o, tab_fam + g, ok);
-        if constexpr (STAGE_F && !BF) cp_async_16(f_s + o, f_fam + g, ok);
-      }
+    const int cK = c * K;
+    auto locate = [&](const Piece& p, bool& ok) -> long {
+      const int x = cK + p.kr;
+      ok = p.on && x >= 0 && x < nx;
+      return ok ? p.row + (xpos ? x : nx - 1 - x) : 0;
+    };
+#pragma unroll
+    for (int i = 0; i < NPD; ++i) {
+      bool ok;
+      const long cell = locate(pd[i], ok);
+      const int o = buf * (RW * K * DL) + pd[i].o;
+      const size_t g = (size_t)cell * DL + pd[i].vv;
+      if constexpr (TABLE) cp_async_16(tab_s + o, tab_fam + g, ok);
+      if constexpr (STAGE_F && !BF) cp_async_16(f_s + o, f_fam + g, ok);
     }
     if constexpr (BF) {
-      for (int e = lane; e < RW * K * VB; e += 32) {
-        const int v = e % VB, rk = e / VB;
-        const int rr = rk / K, k = rk % K;
-        const int x = c * K + k - rr;
-        const int jj = wrow0 + rr;
-        const bool ok = x >= 0 && x < nx && jj < ny;
-        const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
-        const int o = ((buf * RW + rr) * K + k) * DL + v * 8;
-        cp_async_16(bf_s + o, fb_fam + (size_t)cell * DL + v * 8, ok);
+#pragma unroll
+      for (int i = 0; i < NPB; ++i) {
+        bool ok;
+        const long cell = locate(pb[i], ok);
+        const int o = buf * (RW * K * DL) + pb[i].o;
+        cp_async_16(bf_s + o, fb_fam + (size_t)cell * DL + pb[i].vv, ok);
       }
     }
-    for (int e = lane; e < RW * K; e += 32) {
-      const int rr = e / K, k = e % K;
-      const int x = c * K + k - rr;
-      const int jj = wrow0 + rr;
-      const bool ok = x >= 0 && x < nx && jj < ny;
-      const long cell = ok ? (long)(ypos ? jj : ny - 1 - jj) * nx + (xpos ? x : nx - 1 - x) : 0;
-      const int o = (buf * RW + rr) * K + k;
+#pragma unroll
+    for (int i = 0; i < NPS; ++i) {
+      bool ok;
+      const long cell = locate(ps[i], ok);
+      if (lane + 32 * i >= RW * K) continue;
+      const int o = buf * (RW * K) + ps[i].o;
       if constexpr (!TABLE) {
         cp_async(st_s + o, A.sig_t + cell, ok);
         cp_async(stl_s + o, A.sig_tl + cell, ok && A.sig_tl != nullptr);
