@@ -35,6 +35,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int GT = 256;          // rows per GEMV block
 constexpr int MAXR = 65;         // r_max + 1 <= 65
 constexpr int WCAP = 96;         // columns of U0 / W0
+constexpr int COMPACT_SLACK = 24;  // stored columns beyond the rank that trigger a compaction
 constexpr int TALL_ROWS = 64;    // rows per tall x small product block
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -573,7 +574,12 @@ cudaError_t rom_commit(RomDev& R, int* ran, int* grew, double* ratio, cudaStream
   R.wu = (int)h[1];
   R.ww = (int)h[2];
   R.lu_ok = (h[3] != 0.0) ? 1 : 0;
-  if (R.wu >= WCAP - 1 || R.ww >= WCAP - 1) return compact(R, s);
+  // Multiply the factored bases out when the stored columns run out, or once they exceed the
+  // rank by COMPACT_SLACK: every projection and expansion reads all w stored columns, so a
+  // basis whose rank has settled well below WCAP pays for its truncated columns on every use.
+  if (R.wu >= WCAP - 1 || R.ww >= WCAP - 1 || R.wu - R.rank >= COMPACT_SLACK ||
+      R.ww - R.rank >= COMPACT_SLACK)
+    return compact(R, s);
   return cudaSuccess;
 }
 
