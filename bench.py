@@ -209,17 +209,20 @@ def batched_sharded(rte, inputs, torch, dist, rank, world, steps=20):
     own instances; the whole-job figures are the slowest rank's time and all ranks' updates."""
     from paper_2603_19647_gb300.partition import shard
     idx, mine = shard(inputs.batched(), rank, world)
-    b = rte.rte_batch_create(mine, rte.default_options(precision=rte.RTE_FP32))
-    b.rte_batch_step(2)
-    b.rte_batch_restart()
+    b = rte.rte_batch_create(mine, rte.default_options(precision=rte.RTE_FP32)) if mine else None
+    if b:
+        b.rte_batch_step(2)
+        b.rte_batch_restart()
     torch.cuda.synchronize()
     dist.barrier()
     t0 = time.perf_counter()
-    b.rte_batch_step(steps)
+    if b:
+        b.rte_batch_step(steps)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b)))
-    b.destroy()
+    upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b))) if b else 0
+    if b:
+        b.destroy()
     ms, upd_all = reduce_over_ranks(dist, 1e3 * dt, upd, "cuda")
     return {"ms_per_step": ms / steps, "updates_per_s": upd_all / (ms / 1e3),
             "instances_on_rank0": len(idx), "partition": "greedy LPT on N_x N_v (k + 2)"}
