@@ -100,6 +100,30 @@ def test_checkerboard_tile_kernel_rom_tight():
     assert max(s.phase for s in orc.log) >= 2
 
 
+@pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
+def test_lookahead_gives_the_same_march(precision):
+    """options.lookahead queues SI iteration l+1 before the host reads the stopping test of l;
+    the work queued past convergence skips itself on the device, so the march, its iteration
+    counts and its ROM ranks are those of the waiting loop, bit for bit."""
+    wl = inputs.checkerboard(n=48)
+    out = []
+    for la in (0, 1):
+        h, _ = make_pair(wl, rom=rte.RTE_ROM_AUTO, precision=precision, lookahead=la)
+        h.rte_set_initial(rho0=wl.rho0)
+        its = []
+        for _ in range(80):
+            h.rte_step(1)
+            st = h.rte_get_stats()
+            its.append((st["last_iterations"], st["last_cg_iterations"], st["ig_rank"],
+                        st["pc_rank"], st["phase"]))
+        out.append((h.rte_get_scalar_flux(), its, h.rte_get_stats()["total_sweeps"]))
+        h.destroy()
+    (rho0, its0, sw0), (rho1, its1, sw1) = out
+    assert its0 == its1 and sw0 == sw1
+    assert max(t[4] for t in its0) == 3
+    assert np.array_equal(rho0, rho1)
+
+
 def test_checkerboard_ragged_small_rule():
     wl = inputs.checkerboard(n=8, quad=(8, 4))
     wl.nx, wl.ny = 27, 19
