@@ -226,3 +226,22 @@ def test_enoconv_and_manual_rom_states():
     h.rte_step(1)
     assert h.rte_get_stats()["ig_rank"] >= 1
     h.destroy()
+
+def test_caller_stream():
+    """rte_set_stream puts the handle's work on the caller's stream (here a torch stream) and
+    NULL returns it to its own: the march is the same bit for bit either way."""
+    torch = pytest.importorskip("torch")
+    wl = inputs.checkerboard(n=32)
+    res = []
+    for use_stream in (False, True, True):
+        h = rte.create_from_workload(wl)
+        s = torch.cuda.Stream() if use_stream else None
+        if s is not None:
+            h.rte_set_stream(s.cuda_stream)
+        h.rte_step(10)
+        if s is not None:
+            h.rte_set_stream(None)
+        h.rte_step(5)
+        res.append(h.rte_get_scalar_flux())
+        h.destroy()
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])

@@ -29,8 +29,12 @@ def _march(wl, steps, check_every, rom_on, exact=True, **opts):
     o = dict(rom=rte.RTE_ROM_AUTO if rom_on else rte.RTE_ROM_OFF)
     o.update(opts)
     h, p = make_pair(wl, **o)
-    orc = stepper.OracleRTE(p, rom=rom_on, **{k: v for k, v in opts.items()
-                                              if k in stepper.DEFAULTS})
+    oopts = {k: v for k, v in opts.items() if k in stepper.DEFAULTS}
+    if "residual_norm" in oopts:   # the library's enum -> the oracle's names
+        oopts["residual_norm"] = "abs" if oopts["residual_norm"] == rte.RTE_ABS_INF else "rel"
+    if "up_rel" in oopts:
+        oopts["up_rel"] = bool(oopts["up_rel"])
+    orc = stepper.OracleRTE(p, rom=rom_on, **oopts)
     orc.set_initial(wl.rho0)
     eps = opts.get("eps_sisa", stepper.DEFAULTS["eps_sisa"])
     in_p3 = False
@@ -122,6 +126,15 @@ def test_lookahead_gives_the_same_march(precision):
     assert its0 == its1 and sw0 == sw1
     assert max(t[4] for t in its0) == 3
     assert np.array_equal(rho0, rho1)
+
+
+def test_paper_absolute_rules():
+    """The paper's own rules: the absolute stopping test ||rho^{l-1/2} - rho^{l-1}||_inf < eps
+    (RTE_ABS_INF) and the absolute ROM-update threshold (up_rel = 0), against the oracle's
+    march under the same rules."""
+    orc = _march(inputs.checkerboard(n=48), 80, 10, rom_on=True, residual_norm=rte.RTE_ABS_INF,
+                 up_rel=0, **TIGHT)
+    assert max(s.phase for s in orc.log) >= 2
 
 
 def test_checkerboard_ragged_small_rule():
