@@ -336,14 +336,37 @@ __global__ void __launch_bounds__(256) inverse_kernel(Scr sc, double* S, double*
   if (tid == 0) sc.sc[7] = s_ok;
 }
 
-// y = M x for the small row-major M (r x r): one warp per row.
-__global__ void small_mv_kernel(const double* M, int r, const double* x, double* y) {
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5) {
+// The small products of a ROM apply in one block: p = Q^T w0, c = A_r^{-1} p, c0 = Q c (Q
+// row-major, ld MAXR; A_r^{-1} row-major r x r).  Each output is one warp's lane-strided sum,
+// as in small_t_kernel and small_n_kernel.
+__global__ void __launch_bounds__(1024) apply_core_kernel(const double* Q, int wu, int r,
+                                                          const double* inv, const double* w0,
+                                                          double* pc, double* c0) {
+  __shared__ double p[MAXR], c[MAXR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < r; j += nw) {
     double s = 0.0;
-    for (int j = lane; j < r; j += 32) s += M[i * r + j] * x[j];
+    for (int i = lane; i < wu; i += 32) s += Q[i * MAXR + j] * w0[i];
     s = warp_sum(s);
-    if (lane == 0) y[i] = s;
+    if (lane == 0) p[j] = s;
+  }
+  __syncthreads();
+  for (int i = warp; i < r; i += nw) {
+    double s = 0.0;
+    for (int j = lane; j < r; j += 32) s += inv[i * r + j] * p[j];
+    s = warp_sum(s);
+    if (lane == 0) c[i] = s;
+  }
+  __syncthreads();
+  for (int k = warp; k < wu; k += nw) {
+    double s = 0.0;
+    for (int j = lane; j < r; j += 32) s += Q[k * MAXR + j] * c[j];
+    s = warp_sum(s);
+    if (lane == 0) c0[k] = s;
+  }
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    pc[j] = p[j];
+    pc[MAXR + j] = c[j];
   }
 }
 
@@ -593,11 +616,16 @@ cudaError_t rom_append(RomDev& R, const double* x, const double* b, double trunc
 
 cudaError_t rom_apply(RomDev& R, const double* rhs, double* out, cudaStream_t s) {
   if (R.rank <= 0 || !R.lu_ok) return cudaErrorInvalidValue;
+  Scr sc = scr_of(R.core);
   cudaError_t e;
-  if ((e = proj_u(R, rhs, R.proj, s)) != cudaSuccess) return e;
+  // U0^T rhs, then Q^T, A_r^{-1} and Q in one block, then U0 c0
+  if ((e = gemv_t(R.U, R.n, R.wu, rhs, R.partial, sc.w0, s)) != cudaSuccess) return e;
   ++g_launches;
-  small_mv_kernel<<<1, 256, 0, s>>>(R.lu, R.rank, R.proj, R.proj + MAXR);
-  return expand_u(R, R.proj + MAXR, 0.0, nullptr, -1.0, out, s);
+  apply_core_kernel<<<1, 1024, 0, s>>>(R.Q, R.wu, R.rank, R.lu, sc.w0, R.proj, sc.c0);
+  ++g_launches;
+  gemv_n<<<(unsigned)((R.n + 255) / 256), 256, 0, s>>>(R.U, R.n, R.wu, sc.c0, 0.0, nullptr, -1.0,
+                                                       out);
+  return cudaGetLastError();
 }
 
 cudaError_t rom_get(RomDev& R, double* S, double* U, double* Ar, cudaStream_t s) {

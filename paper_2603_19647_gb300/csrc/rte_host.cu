@@ -41,6 +41,7 @@ struct rte_s {
   };
   std::vector<Span> spans;
   unsigned* d_conv = nullptr;             // skip word of the speculative SI-SA loop
+  unsigned* res_ticket = nullptr;         // arrival counter of the fused residual + norms kernel
   const unsigned* skip_now = nullptr;     // skip word the sweep helpers pass on (or none)
   cudaEvent_t ev_norm[2] = {nullptr, nullptr};     // spin-wait
   cudaEvent_t ev_norm_b[2] = {nullptr, nullptr};   // blocking-sync (batched instances)
@@ -344,6 +345,7 @@ void free_all(rte_handle h) {
   if (h->h_cg) cudaFreeHost(h->h_cg);
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->d_conv) cudaFree(h->d_conv);
+  if (h->res_ticket) cudaFree(h->res_ticket);
   for (cudaEvent_t e : h->ev_norm)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_norm_b)
@@ -747,7 +749,9 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
       span(h, SPAN_K1, k0, rec(h), iter);
       TRY(sum_pm(h, h->y_ir, 1));
     } else {
-      TRY(set_q(h, h->rho_prev, nullptr));
+      // after a DSA solve (its kernel) or the PC (the update kernel), q = sigma_s rho^{l-1} is
+      // in place already; the first sweep of a solve forms it from the initial guess
+      if (iter == 1) TRY(set_q(h, h->rho_prev, nullptr));
       TRY(sweep_q(h, nullptr));
       span(h, SPAN_K1, k0, rec(h), iter);
     }
@@ -763,11 +767,11 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
     if (h->fp32)
       CK(launch_combine_residual(h->y_ir, 1, h->btilde, h->rho_prev, n, h->rho_half, h->partials,
                                  nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa, absmode,
-                                 h->rho, half1));
+                                 h->rho, half1, h->res_ticket));
     else
       CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
                                  h->partials, nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa,
-                                 absmode, h->rho, half1));
+                                 absmode, h->rho, half1, h->res_ticket));
     CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
     span(h, SPAN_SWEEP, r0, rec(h), l);
     CK(cudaEventRecord(h->blocking ? h->ev_norm_b[p] : h->ev_norm[p], h->st));
@@ -1460,6 +1464,8 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(dalloc(&h->norms, 2));
   CK(cudaMalloc((void**)&h->d_conv, sizeof(unsigned)));
   CK(cudaMemset(h->d_conv, 0, sizeof(unsigned)));
+  CK(cudaMalloc((void**)&h->res_ticket, sizeof(unsigned)));
+  CK(cudaMemset(h->res_ticket, 0, sizeof(unsigned)));
   for (auto& e : h->ev_norm) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (auto& e : h->ev_norm_b)
     CK(cudaEventCreateWithFlags(&e, cudaEventBlockingSync | cudaEventDisableTiming));

@@ -30,7 +30,8 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
                                         const double* __restrict__ rho_prev, int n,
                                         double* __restrict__ rho_half, double* __restrict__ copy1,
                                         double* __restrict__ copy2, double* partials,
-                                        const unsigned* skip) {
+                                        unsigned* skip, unsigned* ticket, Norms* out, double eps,
+                                        int absmode) {
   if (skip && *skip) return;   // the solve has converged: speculative work does nothing
   __shared__ double sh[3][VT / 32];
   double dinf = 0.0, hinf = 0.0, d2 = 0.0;
@@ -67,6 +68,34 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
       partials[3 * blockIdx.x + 0] = dinf;
       partials[3 * blockIdx.x + 1] = hinf;
       partials[3 * blockIdx.x + 2] = d2;
+    }
+  }
+  if (ticket) {
+    // the last block to finish forms the norms and the stopping test from every block's
+    // partials, in the order finish_norms_kernel uses, and re-arms the ticket
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && w == 0) {
+      __threadfence();
+      double dmax = 0.0, hmax = 0.0, dsum = 0.0;
+      for (int b = l; b < (int)gridDim.x; b += 32) {
+        dmax = fmax(dmax, __ldcg(partials + 3 * b));
+        hmax = fmax(hmax, __ldcg(partials + 3 * b + 1));
+        dsum += __ldcg(partials + 3 * b + 2);
+      }
+      dmax = warp_max(dmax);
+      hmax = warp_max(hmax);
+      dsum = warp_sum(dsum);
+      if (l == 0) {
+        out->diff_inf = dmax;
+        out->half_inf = hmax;
+        out->diff_l2sq = dsum;
+        if (skip) *skip = (absmode ? dmax <= eps : dmax <= eps * hmax) ? 1u : 0u;
+        *ticket = 0u;
+      }
     }
   }
 }
@@ -295,10 +324,11 @@ cudaError_t launch_combine_residual(const double* pm, int nfam, const double* bt
                                     const double* rho_prev, int n, double* rho_half,
                                     double* partials, int nblocks, Norms* out, cudaStream_t s,
                                     unsigned* conv, double eps, int absmode, double* copy1,
-                                    double* copy2) {
+                                    double* copy2, unsigned* ticket) {
   ++g_launches;
   combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, copy1,
-                                                 copy2, partials, conv);
+                                                 copy2, partials, conv, ticket, out, eps, absmode);
+  if (ticket) return cudaGetLastError();
   ++g_launches;
   finish_norms_kernel<<<1, 32, 0, s>>>(partials, nblocks, out, conv, eps, absmode);
   return cudaGetLastError();
