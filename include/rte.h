@@ -24,7 +24,8 @@
  *   - Angular arrays are [n_dirs][ncell], direction order = the order rte_get_quadrature
  *     reports (for RTE_Q_EXPLICIT: the caller's order).
  *   - A handle is not thread-safe; use one handle per host thread.  All device work of a
- *     handle is issued on its own CUDA stream on the device that was current at create.
+ *     handle is issued on its own CUDA streams (or, after rte_set_stream, on the caller's
+ *     stream and the handle's side streams) on the device that was current at create.
  */
 #ifndef RTE_H
 #define RTE_H
@@ -84,7 +85,9 @@ typedef struct {
   int max_iter;      /* N_iter of Algorithm 1 (default 500) */
   int r_max;         /* rank cap of each ROM, <= 64 (default 40) */
   int precision;     /* RTE_FP64 (default) | RTE_FP32: sweeps and f in FP32, the SI residual,
-                        DSA and ROMs in FP64 (iterative refinement of the SI increments) */
+                        DSA and ROMs in FP64 (iterative refinement of the SI increments) |
+                        RTE_FP32_BF16F (2D): as RTE_FP32 with f stored as a per-cell FP32
+                        reference plus BF16 remainders (stochastic rounding) */
   int rom;           /* RTE_ROM_AUTO (default) | RTE_ROM_OFF | RTE_ROM_MANUAL */
   int residual_norm; /* RTE_REL_INF (default): ||.||_inf relative to ||rho^{l-1/2}||_inf;
                         RTE_ABS_INF: the paper's absolute test */
