@@ -1,0 +1,54 @@
+"""Parity at the full size of the 1024^2 log-normal workload (1.34e8 cell-directions), where the
+oracle cannot follow: a property that holds at any size.
+
+Particle balance of the fused f sweep.  f^n solves the discrete transport equation of the step,
+(tau + sigma_t + a_k + b_k) f^n_k = sigma_s rho^n + G + tau f^{n-1}_k + a_k f_up,x + b_k f_up,y,
+so weighting by w_k and summing over directions and cells telescopes the streaming terms to the
+outflow through the boundary (vacuum inflow) and leaves, exactly up to rounding,
+
+    sum_c [tau (F^n - F^{n-1}) + sigma_t F^n - sigma_s rho^n - G]
+        + sum_k w_k (|mu_k| / h_x  sum_rows f^n_k(x-outflow cell)
+                     + |eta_k| / h_y sum_cols f^n_k(y-outflow cell)) = 0,
+
+with F = sum_k w_k f_k.  The check covers the sweep's whole data path at this size (families,
+row blocks, CTA hand-offs, the stored f and its layout) for both precisions."""
+import numpy as np
+import pytest
+
+from paper_2603_19647_gb300 import inputs, rte
+
+pytestmark = pytest.mark.gpu
+
+
+def _balance(wl, quad, f_prev, f_now, rho_now):
+    mu, eta, w = quad
+    nx, ny = wl.nx, wl.ny
+    x0, x1, y0, y1 = wl.domain
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    tau = 1.0 / wl.c_dt
+    F_prev, F_now = w @ f_prev, w @ f_now
+    body = tau * (F_now - F_prev) + wl.sigma_t * F_now - wl.sigma_s * rho_now - wl.source
+    fn = f_now.reshape(len(w), ny, nx)
+    leak = 0.0
+    for k in range(len(w)):
+        col = fn[k, :, -1] if mu[k] > 0 else fn[k, :, 0]
+        row = fn[k, -1, :] if eta[k] > 0 else fn[k, 0, :]
+        leak += w[k] * (abs(mu[k]) / hx * col.sum() + abs(eta[k]) / hy * row.sum())
+    scale = np.sum((tau + wl.sigma_t) * np.abs(F_now))
+    return (body.sum() + leak) / scale
+
+
+@pytest.mark.parametrize("precision,tol", [(rte.RTE_FP64, 1e-12), (rte.RTE_FP32, 2e-6)])
+def test_lognormal_full_size_particle_balance(precision, tol):
+    wl = inputs.lognormal()
+    h = rte.create_from_workload(wl, options=rte.default_options(precision=precision))
+    h.rte_set_initial(rho0=wl.rho0)
+    h.rte_step(2)
+    f_prev = h.rte_get_angular_flux()
+    h.rte_step(1)
+    f_now = h.rte_get_angular_flux()
+    rho_now = h.rte_get_scalar_flux()
+    quad = h.rte_get_quadrature()
+    h.destroy()
+    assert np.all(np.isfinite(f_now))
+    assert abs(_balance(wl, quad, f_prev, f_now, rho_now)) < tol
