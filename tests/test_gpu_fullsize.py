@@ -1,5 +1,10 @@
-"""Parity at the full size of the 1024^2 log-normal workload (1.34e8 cell-directions), where the
-oracle cannot follow: a property that holds at any size.
+"""Parity at the full sizes of the 1024^2 log-normal (1.34e8 cell-directions) and 2048^2
+diffusive-disc (1.07e9) workloads.
+
+One SI sweep T Sigma_s rho (the hot path's dominant kernel, in the tile the autotuner picks for
+that size) against the oracle's sweep of the same rho, every output: the oracle sweeps these
+sizes in seconds.  A whole march at these sizes it cannot follow; there the check is a
+property that holds at any size:
 
 Particle balance of the fused f sweep.  f^n solves the discrete transport equation of the step,
 (tau + sigma_t + a_k + b_k) f^n_k = sigma_s rho^n + G + tau f^{n-1}_k + a_k f_up,x + b_k f_up,y,
@@ -15,9 +20,25 @@ row blocks, CTA hand-offs, the stored f and its layout) for both precisions."""
 import numpy as np
 import pytest
 
+from conftest import oracle_problem
+from gpu_util import rel_l2
+from oracle import transport as tr
 from paper_2603_19647_gb300 import inputs, rte
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,precision,tol", [("lognormal", rte.RTE_FP64, 1e-12),
+                                                ("lognormal", rte.RTE_FP32, 2e-6),
+                                                ("diffusive_disc", rte.RTE_FP32, 2e-6),
+                                                ("diffusive_disc", rte.RTE_FP32_BF16F, 2e-6)])
+def test_si_sweep_full_size(name, precision, tol):
+    wl = inputs.BY_NAME[name]()
+    h = rte.create_from_workload(wl, options=rte.default_options(precision=precision))
+    rho = np.random.default_rng(7).uniform(0.0, 1.0, wl.ncell)
+    got = h.rte_op_sweep(rho)
+    h.destroy()
+    assert rel_l2(got, tr.apply_T_sigma_s(oracle_problem(wl), rho)) < tol
 
 
 def _balance(wl, quad, f_prev, f_now, rho_now):
