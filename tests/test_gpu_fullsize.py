@@ -22,6 +22,7 @@ import pytest
 
 from conftest import oracle_problem
 from gpu_util import match_directions, rel_l2
+from oracle import dsa, rom
 from oracle import transport as tr
 from paper_2603_19647_gb300 import inputs, rte
 
@@ -62,6 +63,41 @@ def test_fused_sweep_full_size(precision, tol):
     f_ref, _ = tr.final_f(p, rho, f0)
     assert rel_l2(f_lib, f_ref[perm]) < tol
     assert rel_l2(bt, tr.b_tilde(p, f_ref)) < tol
+
+
+def test_dsa_full_size():
+    """The DSA solve at 1024^2 (the two-phase CG above 2^18 cells) against the oracle's CG:
+    the same iteration count and the correction within 1e-10."""
+    wl = inputs.lognormal()
+    h = rte.create_from_workload(wl, options=rte.default_options(cg_rtol=1e-8))
+    p = oracle_problem(wl)
+    res = np.random.default_rng(5).uniform(-1.0, 1.0, wl.ncell)
+    got, its = h.rte_op_dsa(res)
+    h.destroy()
+    ref, its_ref = dsa.dsa_correction(p, dsa.dsa_matrix(p), res, 1e-8, 500)
+    assert its == its_ref
+    assert rel_l2(got, ref) < 1e-10
+
+
+def test_rom_full_size():
+    """Incremental SVD appends and the ROM apply on 1024^2-cell snapshots (the tall-skinny
+    products at full length) against the oracle's iSVD."""
+    wl = inputs.lognormal()
+    n = wl.ncell
+    h = rte.create_from_workload(wl, options=rte.default_options(r_max=12))
+    rng = np.random.default_rng(13)
+    X, Y = np.meshgrid(np.linspace(0, 1, wl.nx), np.linspace(0, 1, wl.ny))
+    o = rom.IncrementalSVD(n, 12)
+    for k in range(8):
+        x = (np.exp(-((X - 0.2 - 0.05 * k) ** 2 + (Y - 0.5) ** 2) / 0.02) * (1 + 0.05 * k)).ravel()
+        x = x + 1e-4 * rng.standard_normal(n)
+        b = x + 0.1 * np.roll(x, 3) + 1e-3 * rng.standard_normal(n)
+        assert h.rte_op_rom_append(rte.RTE_ROM_IG, x, b, -1.0) == o.append(x, b, trunc_eps=None)
+    S, _, _ = h.rte_op_rom_get(rte.RTE_ROM_IG)
+    assert np.max(np.abs(S - o.S) / o.S) < 1e-10
+    rhs = b + 0.01 * rng.standard_normal(n)
+    assert rel_l2(h.rte_op_rom_apply(rte.RTE_ROM_IG, rhs), o.solve_apply(rhs)) < 1e-9
+    h.destroy()
 
 
 def _balance(wl, quad, f_prev, f_now, rho_now):
