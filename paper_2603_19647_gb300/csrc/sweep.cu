@@ -280,18 +280,17 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
       if (warp > 0 && t < nx) {
         // column t of the warp above's bottom row, handed over step by step
         if (known_prod <= t) {
-          int kp = 0;
-          if (lane == 0) {
-            unsigned spins = 0;
-            while ((kp = s_prod[warp - 1]) <= t && !s_abandon) {
-              if (++spins > SMEM_SPIN_LIMIT) {
-                atomicExch(&A.ctrl->err, 1u);
-                s_abandon = 1;
-                break;
-              }
+          // every lane polls (one broadcast read per poll), so no shuffle hands the value on
+          int kp;
+          unsigned spins = 0;
+          while ((kp = s_prod[warp - 1]) <= t && !s_abandon) {
+            if (++spins > SMEM_SPIN_LIMIT) {
+              if (lane == 0) atomicExch(&A.ctrl->err, 1u);
+              s_abandon = 1;
+              break;
             }
           }
-          known_prod = __shfl_sync(FULL, kp, 0);
+          known_prod = kp;
           __threadfence_block();
         }
         const int rs = (t % RING) * DL + dl;
