@@ -241,19 +241,19 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
     const int need = min(tb + K, nx);
     if (warp == 0) {
       if (has_up && tb < nx) {
-        if (lane == 0 && !s_abandon) {
+        // every lane acquires the flag itself (one broadcast read per poll), so its edge loads
+        // are ordered after its own acquire: no warp barrier or fence on the CTA's head warp
+        if (!s_abandon) {
           unsigned spins = 0;
           while (ld_acquire(flag_in) < (unsigned)need) {
             if (++spins > SPIN_LIMIT || ld_acquire(&A.ctrl->err) != 0u) {
-              atomicExch(&A.ctrl->err, 1u);
+              if (lane == 0) atomicExch(&A.ctrl->err, 1u);
               s_abandon = 1;
               break;
             }
             if (spins > 256) __nanosleep(64);
           }
         }
-        __syncwarp();
-        __threadfence();
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int x = tb + k;
