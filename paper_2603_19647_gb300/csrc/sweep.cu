@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const Sweep2DArgs<Real> A)
     // publish the bottom-row columns finished in this chunk
     const int done = min(tb + K - (RW - 1), nx);
     if (done > 0 && warp == W - 1 && has_down) {
-      __threadfence();
+      // the warp barrier orders every lane's edge stores before lane 0's release store, whose
+      // release semantics then publish them at GPU scope to the acquiring CTA
       __syncwarp();
       if (lane == 0) st_release(flag_out, (unsigned)done);
     }
