@@ -270,19 +270,19 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<Rea
     } else if (g == 0) {
       if (has_up) {
         if (T < ntile) {
-          if (dl == 0 && !s_abandon) {
+          // every lane of the group acquires the flag itself, so its edge loads are ordered
+          // after its own acquire (no group barrier or fence)
+          if (!s_abandon) {
             unsigned spins = 0;
             while (ld_acquire(flag_in) < (unsigned)(T + 1)) {
               if (++spins > SPIN_LIMIT || ld_acquire(&A.ctrl->err) != 0u) {
-                atomicExch(&A.ctrl->err, 1u);
+                if (dl == 0) atomicExch(&A.ctrl->err, 1u);
                 s_abandon = 1;
                 break;
               }
               if (spins > 256) __nanosleep(64);
             }
           }
-          __syncwarp((DL == 32) ? FULL : (((1u << DL) - 1u)));
-          __threadfence();
 #pragma unroll
           for (int i = 0; i < TW; ++i) {
             const int x = T * TW + i;
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<Rea
             }
           }
         }
-        __threadfence();
+        // the warp barrier orders the group's edge stores before lane 0's release store
         __syncwarp();
         if (lane == 0) st_release(flag_out, (unsigned)(tl + 1));
       }
