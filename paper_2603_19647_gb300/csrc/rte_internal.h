@@ -126,8 +126,8 @@ cudaError_t launch_combine_residual(const double* pm, int nfam, const double* bt
                                     unsigned* conv = nullptr, double eps = 0.0, int absmode = 0,
                                     double* copy1 = nullptr, double* copy2 = nullptr,
                                     unsigned* ticket = nullptr);
-// ticket (optional): a zeroed device word; the residual kernel's last block then also forms
-// the norms and the stopping test (no second launch) and zeroes it again.
+// ticket: a zeroed device word; the residual kernel's last block forms the norms and the
+// stopping test and zeroes it again.
 // Start of an SI-SA solve: src -> dst1 (and dst2 when given), *conv = 0, slots[0..nslots) = 0.
 cudaError_t launch_si_begin(const double* src, double* dst1, double* dst2, int ncell,
                             unsigned* conv, int* slots, int nslots, cudaStream_t s);

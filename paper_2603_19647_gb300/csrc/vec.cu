@@ -70,9 +70,10 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
       partials[3 * blockIdx.x + 2] = d2;
     }
   }
-  if (ticket) {
-    // the last block to finish forms the norms and the stopping test from every block's
-    // partials, in the order finish_norms_kernel uses, and re-arms the ticket
+  {
+    // the last block to finish forms the norms and the stopping test (the host makes the same
+    // comparison; later speculative launches read it as their skip word) from every block's
+    // partials in a fixed order, and re-arms the ticket
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -97,29 +98,6 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
         *ticket = 0u;
       }
     }
-  }
-}
-
-// Norms of one residual and, when conv is given, the stopping test of Algorithm 1 on them
-// (the same comparison the host makes), which later speculative launches read as their skip
-// word.
-__global__ void finish_norms_kernel(const double* partials, int nblocks, Norms* out,
-                                    unsigned* conv, double eps, int absmode) {
-  if (conv && *conv) return;
-  double dinf = 0.0, hinf = 0.0, d2 = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += 32) {
-    dinf = fmax(dinf, partials[3 * b]);
-    hinf = fmax(hinf, partials[3 * b + 1]);
-    d2 += partials[3 * b + 2];
-  }
-  dinf = warp_max(dinf);
-  hinf = warp_max(hinf);
-  d2 = warp_sum(d2);
-  if (threadIdx.x == 0) {
-    out->diff_inf = dinf;
-    out->half_inf = hinf;
-    out->diff_l2sq = d2;
-    if (conv) *conv = (absmode ? dinf <= eps : dinf <= eps * hinf) ? 1u : 0u;
   }
 }
 
@@ -325,12 +303,10 @@ cudaError_t launch_combine_residual(const double* pm, int nfam, const double* bt
                                     double* partials, int nblocks, Norms* out, cudaStream_t s,
                                     unsigned* conv, double eps, int absmode, double* copy1,
                                     double* copy2, unsigned* ticket) {
+  if (!ticket) return cudaErrorInvalidValue;
   ++g_launches;
   combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, copy1,
                                                  copy2, partials, conv, ticket, out, eps, absmode);
-  if (ticket) return cudaGetLastError();
-  ++g_launches;
-  finish_norms_kernel<<<1, 32, 0, s>>>(partials, nblocks, out, conv, eps, absmode);
   return cudaGetLastError();
 }
 
