@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import quadrature as q
-from oracle import rom, stepper
+from oracle import dsa, rom, sisa, stepper
 from oracle import transport as tr
 
 
@@ -100,3 +100,39 @@ def test_rom_march_invariance_and_phases(dim):
     it_rom = np.mean([s.iterations for s in log[-10:]])
     it_plain = np.mean([s.iterations for s in runs[False].log[-10:]])
     assert it_rom < it_plain
+
+
+def test_rom_pc_exact_when_correction_in_span(rng):
+    """Eq. (dmd-sa) with exact data.  With K = T Sigma_s, rho^{1/2} = K rho^{(0)} + b~ and the
+    fixed point rho^n = K rho^n + b~, the step's error e = rho^n - rho^{(0)} gives the ideal
+    first correction delta = rho^n - rho^{1/2} = K e and the right side of the correction
+    equation rho^{1/2} - rho^{(0)} = e - K e.  A PC-ROM built from the pairs (K e_k, e_k - K e_k)
+    represents the correction operator exactly on span{K e_k}; when e lies in span{e_k} the
+    l = 1 correction lands on rho^n and the second sweep meets a 1e-12 test.  DSA from the same
+    guess takes more sweeps, and a planted sign error in the correction is caught."""
+    mu, eta, w = q.cl_hemisphere(8, 4)
+    nx, ny = 6, 5
+    n = nx * ny
+    ss = rng.uniform(0.0, 20.0, n)
+    p = tr.Problem(nx, ny, 0, 1, 0, 0.8, mu, eta, w, ss + rng.uniform(0.05, 1.0, n), ss,
+                   rng.uniform(0, 1, n), 0.05, np.array([0.3, 0.0, 0.5, 0.1]))
+    K = lambda v: tr.apply_T_sigma_s(p, v)
+    bt = tr.b_tilde(p, rng.uniform(0, 1, (p.nv, n)))
+    Kmat = np.stack([K(e) for e in np.eye(n)], axis=1)
+    rho_n = np.linalg.solve(np.eye(n) - Kmat, bt)
+    E = rng.standard_normal((n, 6))
+    pc = rom.IncrementalSVD(n, 40)
+    for k in range(E.shape[1]):
+        assert pc.append(K(E[:, k]), E[:, k] - K(E[:, k]))
+    e = E @ rng.standard_normal(E.shape[1])
+    rho0 = rho_n - e
+    opts = dict(stepper.DEFAULTS, eps_sisa=1e-12, cg_rtol=1e-10)
+    A = dsa.dsa_matrix(p)
+    got, info = sisa.si_sa(p, rho0, bt, opts, A, pc=pc.solve_apply)
+    assert info.iterations == 2
+    assert np.linalg.norm(info.delta_pc_1 - K(e)) <= 1e-10 * np.linalg.norm(K(e))
+    assert np.linalg.norm(got - rho_n) <= 1e-11 * np.linalg.norm(rho_n)
+    _, info_dsa = sisa.si_sa(p, rho0, bt, opts, A)
+    assert info_dsa.iterations > 2
+    _, info_bad = sisa.si_sa(p, rho0, bt, opts, A, pc=lambda r: -pc.solve_apply(r))
+    assert info_bad.iterations > 2
