@@ -24,8 +24,9 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-def _march(wl, steps, check_every, rom_on, exact=True, **opts):
-    """exact=False: exact parity until the first Phase 3 step, tolerance bound afterwards."""
+def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, **opts):
+    """exact=False: exact parity until the first Phase 3 step, tolerance bound afterwards.
+    inflow_at: {step: g} sets the isotropic inflow of both sides before that step."""
     o = dict(rom=rte.RTE_ROM_AUTO if rom_on else rte.RTE_ROM_OFF)
     o.update(opts)
     h, p = make_pair(wl, **o)
@@ -40,6 +41,9 @@ def _march(wl, steps, check_every, rom_on, exact=True, **opts):
     in_p3 = False
     phases_lib, phases_orc = [], []
     for n in range(1, steps + 1):
+        if inflow_at and n in inflow_at:
+            h.rte_set_inflow(inflow_at[n])
+            orc.set_inflow(inflow_at[n])
         h.rte_step(1)
         orc.step(1)
         st = h.rte_get_stats()
@@ -148,6 +152,61 @@ def test_checkerboard_ragged_small_rule():
     wl.inflow = np.array([0.5, 0.0, 0.25, 0.0])
     _march(wl, 40, 5, rom_on=True, **TIGHT)
     _march(wl, 40, 5, rom_on=True, exact=False)
+
+
+def test_degenerate_zero_state_then_inflow():
+    """Nothing to transport for five steps: every iterate, snapshot and stopping test is
+    exactly zero (the relative test accepts 0 <= eps * 0 at l = 1; a zero snapshot does not
+    grow the IG-ROM, whose stop ratio is then 0, so Phase 2 starts with a rank-0 ROM that
+    gives the initial guess 0 = rho^{n-1}); then an inflow switches on and the march follows
+    the oracle's through all three phases."""
+    wl = inputs.checkerboard(n=16, quad=(8, 4))
+    n = wl.ncell
+    wl.source, wl.rho0, wl.inflow = np.zeros(n), np.zeros(n), np.zeros(4)
+    orc = _march(wl, 40, 5, rom_on=True, inflow_at={6: [0.5, 0.0, 0.25, 0.0]}, **TIGHT)
+    assert all(s.iterations == 1 and s.residual == 0.0 for s in orc.log[:5])
+    assert max(s.phase for s in orc.log) == 3
+
+
+def test_degenerate_pure_absorber():
+    """sigma_s = 0: the DSA right side sigma_s (rho^{l-1/2} - rho^{l-1}) vanishes, so CG takes
+    no iteration and every step converges at l = 2; the preconditioner snapshot
+    rho^n - rho^{n,1/2} is exactly zero, so the PC-ROM stays at rank 0 (Phase 3 with a zero
+    correction, the same iterate as the zero DSA correction)."""
+    wl = inputs.checkerboard(n=16, quad=(8, 4))
+    n = wl.ncell
+    wl.sigma_s = np.zeros(n)
+    wl.sigma_t = np.where(np.arange(n) % 3 == 0, 5.0, 0.5)
+    wl.inflow = np.array([0.3, 0.0, 0.6, 0.1])
+    h, _ = make_pair(wl, rom=rte.RTE_ROM_AUTO, **TIGHT)
+    for _ in range(12):
+        h.rte_step(1)
+        st = h.rte_get_stats()
+        assert st["last_cg_iterations"] == 0 and st["last_iterations"] <= 2
+    assert st["phase"] == 3 and st["pc_rank"] == 0
+    h.destroy()
+    orc = _march(wl, 40, 5, rom_on=True, **TIGHT)
+    assert all(s.cg_iterations == 0 for s in orc.log)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 23), (23, 1)])
+def test_degenerate_single_cell_and_strips(shape):
+    """One cell (the ROMs reach their full rank 1 at once) and one-cell-wide strips along
+    either axis, ROM on."""
+    wl = inputs.checkerboard(n=8, quad=(8, 4))
+    wl.nx, wl.ny = shape
+    n = wl.ncell
+    rng = np.random.default_rng(3)
+    ss = rng.uniform(0, 50, n)
+    wl.sigma_s, wl.sigma_t, wl.source = ss, ss + 0.2, rng.uniform(0, 1, n)
+    wl.rho0 = np.zeros(n)
+    wl.inflow = np.array([0.5, 0.0, 0.25, 0.0])
+    _march(wl, 30, 5, rom_on=True, **TIGHT)
+
+
+def test_degenerate_single_cell_slab():
+    wl = inputs.slab_1d(n=1, steps=20)
+    _march(wl, 20, 5, rom_on=True, **TIGHT)
 
 
 @pytest.mark.slow
