@@ -243,20 +243,18 @@ __global__ void __launch_bounds__(256) sweep2d_tile_kernel(const Sweep2DArgs<Rea
     if (warp > 0) {
       // group 0 works on tile T; wait until the warp above has put that tile in the ring
       if (T < ntile) {
-        int kp = 0;
-        if (lane == 0) {
+        if (g == 0) {
+          // every lane of group 0 polls (one broadcast read per poll) and fences for itself,
+          // so no warp barrier hands the value on before the ring reads
           unsigned spins = 0;
-          while ((kp = s_prod[warp - 1]) <= T && !s_abandon) {
+          while (s_prod[warp - 1] <= T && !s_abandon) {
             if (++spins > SMEM_SPIN_LIMIT) {
-              atomicExch(&A.ctrl->err, 1u);
+              if (dl == 0) atomicExch(&A.ctrl->err, 1u);
               s_abandon = 1;
               break;
             }
           }
-        }
-        __syncwarp();
-        __threadfence_block();
-        if (g == 0) {
+          __threadfence_block();
           const Real* rs = ring_in + (size_t)(T % RD) * TW * DL + dl;
 #pragma unroll
           for (int i = 0; i < TW; ++i) {
