@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the reduced-precision and batched workloads measured beside the line")
-    ap.add_argument("--n", type=int, default=256, help="grid side (256 = the benchmark workload)")
+    # not "--n": under torchrun that abbreviates several of the launcher's own options
+    ap.add_argument("--grid", dest="n", type=int, default=256,
+                    help="grid side (256 = the benchmark workload)")
     return ap.parse_args()
 
 
