@@ -71,3 +71,27 @@ def test_batch_restart_and_status():
         assert rte.load().rte_batch_status(b.ptr, i) == rte.RTE_OK
     assert rte.load().rte_batch_status(b.ptr, 3) == rte.RTE_EINVAL
     b.destroy()
+
+
+def test_batch_full_size_sampled():
+    """The 64-instance log-normal batch at full size (sides 128-512, 64 or 128 directions,
+    FP32, ROM on), three steps: sampled instances bit for bit against the same problems
+    stepped alone, and the smallest against the FP64 oracle's march."""
+    wls = inputs.batched(steps=3)
+    opts = rte.default_options(precision=rte.RTE_FP32)
+    b = rte.rte_batch_create(wls, opts)
+    b.rte_batch_step(3)
+    sides = [wl.nx for wl in wls]
+    small = int(np.argmin(sides))
+    for i in sorted({0, len(wls) // 2, len(wls) - 1, small, int(np.argmax(sides))}):
+        h = rte.create_from_workload(wls[i], options=rte.default_options(precision=rte.RTE_FP32))
+        h.rte_step(3)
+        a, s = b.instance(i).rte_get_scalar_flux(), h.rte_get_scalar_flux()
+        assert b.instance(i).rte_get_stats()["total_iterations"] == h.rte_get_stats()["total_iterations"], i
+        assert rel_l2(a, s) < 1e-13, (i, rel_l2(a, s))
+        h.destroy()
+    orc = stepper.OracleRTE(oracle_problem(wls[small]), rom=True)
+    orc.set_initial(wls[small].rho0)
+    orc.step(3)
+    assert rel_l2(b.instance(small).rte_get_scalar_flux(), orc.rho) < 1e-6
+    b.destroy()
