@@ -245,3 +245,29 @@ def test_caller_stream():
         res.append(h.rte_get_scalar_flux())
         h.destroy()
     assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+def test_rom_at_maximum_rank():
+    """r_max = 64, the largest rank the library takes: 90 appends in general position, so the
+    core SVD reaches its largest size (65 x 65), the rank cap drops the smallest triple in
+    each of the last 26, and the factored bases are multiplied out once they hold 24 columns
+    beyond the rank (append 88); singular values, the reduced operator and the apply against
+    the oracle's iSVD."""
+    wl = inputs.checkerboard(n=64, quad=(8, 4))
+    h, p = make_pair(wl, r_max=64)
+    n = wl.ncell
+    rng = np.random.default_rng(17)
+    o = rom.IncrementalSVD(n, 64)
+    for k in range(90):
+        x = rng.standard_normal(n)
+        b = x + 0.1 * np.roll(x, 5) + 0.01 * rng.standard_normal(n)
+        assert h.rte_op_rom_append(rte.RTE_ROM_PC, x, b, -1.0) == o.append(x, b), k
+    S, U, Ar = h.rte_op_rom_get(rte.RTE_ROM_PC)
+    assert S.size == o.rank == 64
+    assert np.max(np.abs(S - o.S) / o.S) < 1e-10
+    sg = np.sign(np.sum(U * o.U.T, axis=1))
+    Ao = o.operator() * sg[:, None] * sg[None, :]
+    assert np.max(np.abs(Ar - Ao)) < 1e-9 * np.max(np.abs(Ao))
+    rhs = rng.standard_normal(n)
+    assert rel_l2(h.rte_op_rom_apply(rte.RTE_ROM_PC, rhs), o.solve_apply(rhs)) < 1e-9
+    h.destroy()
