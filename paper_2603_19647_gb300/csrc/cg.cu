@@ -64,10 +64,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Grid barrier for a cooperative launch (all blocks co-resident).  Bounded: after
-// BARRIER_SPIN_LIMIT polls it records an error and lets the block continue.
-__device__ void grid_barrier(unsigned* bar, unsigned& gen) {
+// BARRIER_SPIN_LIMIT polls it records an error and returns true (for the whole block), and
+// the caller leaves the solve; a wait that ended normally returns false.  A block that left
+// no longer arrives at later barriers, so the other blocks' next waits run out as well and
+// they leave too: a solve whose barrier timed out ends after at most two wait limits.
+__device__ bool grid_barrier(unsigned* bar, unsigned& gen) {
+  __shared__ int s_timeout;
   __syncthreads();
   if (threadIdx.x == 0) {
+    s_timeout = 0;
     __threadfence();
     const unsigned g = gen;
     if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
@@ -79,6 +84,7 @@ __device__ void grid_barrier(unsigned* bar, unsigned& gen) {
       while (ld_acquire(&bar[1]) == g) {
         if (++spins > BARRIER_SPIN_LIMIT) {
           atomicExch(&bar[2], 1u);
+          s_timeout = 1;
           break;
         }
         if (spins > 1024) __nanosleep(32);
@@ -88,6 +94,7 @@ __device__ void grid_barrier(unsigned* bar, unsigned& gen) {
   }
   gen += 1u;
   __syncthreads();
+  return s_timeout != 0;
 }
 
 __device__ double block_sum_store(double v, double* dst) {
@@ -136,14 +143,14 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
     acc += b * b;
   }
   block_sum_store(acc, partB + blockIdx.x);
-  grid_barrier(a.bar, gen);
+  bool dead = grid_barrier(a.bar, gen);   // a barrier wait ran out: leave the solve
   double rr = grid_total(partB);
   const double bb = rr;
   double beta = 0.0;
   int it = 0;
   double* pold = a.p0;
   double* pnew = a.p1;
-  while (it < a.max_iter && rr > a.rtol2 * bb) {
+  while (!dead && it < a.max_iter && rr > a.rtol2 * bb) {
     // (1) p <- r + beta p ; Ap = C p ; p.Ap
     acc = 0.0;
     for (int c = tid; c < a.n; c += nth) {
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
       acc += pc * s;
     }
     block_sum_store(acc, partA + blockIdx.x);
-    grid_barrier(a.bar, gen);
+    if ((dead = grid_barrier(a.bar, gen))) break;
     const double alpha = rr / grid_total(partA);
     // (2) x += alpha p ; r -= alpha Ap ; r.r
     acc = 0.0;
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
       acc += rc * rc;
     }
     block_sum_store(acc, partB + blockIdx.x);
-    grid_barrier(a.bar, gen);
+    if ((dead = grid_barrier(a.bar, gen))) break;
     const double rr_new = grid_total(partB);
     beta = rr_new / rr;
     rr = rr_new;
@@ -292,11 +299,11 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
     g += b * b;
   }
   block_sum2_store(g, 0.0, partG + blockIdx.x, partD + blockIdx.x);
-  grid_barrier(a.bar, gen);
+  bool dead = grid_barrier(a.bar, gen);   // a barrier wait ran out: leave the solve
   double gamma, delta;
   grid_total2(partG, partD, gamma, delta);
   const double bb = gamma;
-  if (a.max_iter > 0 && gamma > a.rtol2 * bb) {
+  if (!dead && a.max_iter > 0 && gamma > a.rtol2 * bb) {
     // w = C r and (w, r) for the first step length (only when CG iterates at all)
     d = 0.0;
     for (int c = tid; c < n; c += nth) {
@@ -306,13 +313,13 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
       d += w * rc;
     }
     block_sum2_store(0.0, d, partG + blockIdx.x, partD + blockIdx.x);
-    grid_barrier(a.bar, gen);
+    dead = grid_barrier(a.bar, gen);
     double unused;
     grid_total2(partG, partD, unused, delta);
   }
   double gamma_prev = 0.0, alpha_prev = 0.0;
   int it = 0;
-  while (it < a.max_iter && gamma > a.rtol2 * bb) {
+  while (!dead && it < a.max_iter && gamma > a.rtol2 * bb) {
     const bool first = it == 0;   // p = r, s = w, x = alpha p (p, s, x start at zero)
     const double beta = first ? 0.0 : gamma / gamma_prev;
     const double alpha = first ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
@@ -344,7 +351,7 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
       d += wc * rc;
     }
     block_sum2_store(g, d, partG + blockIdx.x, partD + blockIdx.x);
-    grid_barrier(a.bar, gen);
+    if ((dead = grid_barrier(a.bar, gen))) break;
     gamma_prev = gamma;
     alpha_prev = alpha;
     grid_total2(partG, partD, gamma, delta);
