@@ -30,6 +30,8 @@
 #ifndef RTE_H
 #define RTE_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -181,6 +183,26 @@ rte_status rte_get_stats(rte_handle h, rte_stats* st);
 const char* rte_last_error(rte_handle h);
 /* Free everything; NULL-safe. */
 void rte_destroy(rte_handle h);
+
+/* ---------------- checkpoint and resume ----------------
+ * The paper has no counterpart: these calls let a long march stop and resume.  rte_save
+ * writes what a step reads from the previous one into a caller-owned host buffer of
+ * rte_save_size bytes: f^n in the handle's storage precision, rho^n, the next step's b~
+ * without inflow, the FP32 refinement pair, both ROMs with their phase flags, the inflow
+ * values and the statistics.  rte_load restores such a blob into a handle created with the
+ * same mesh, quadrature, cross sections, source, c_dt and options; the mesh, the direction
+ * layout, the precision and r_max are checked, the rest is the caller's to keep equal.
+ *   - The loaded march repeats the saved one bit for bit when the sweep configuration is
+ *     also the same.  rte_stats reports it in its sweep_* fields.  It is the same within one
+ *     process, where the measured choice is cached.  Fix it with the sweep_* options to
+ *     resume in another process.
+ *   - rte_restart still returns to the handle's own last rte_set_initial.
+ * Errors: RTE_EINVAL for a buffer smaller than rte_save_size, or for a blob that is of
+ * another problem or layout, truncated or malformed (the handle is then left unchanged);
+ * RTE_ESTATE for rte_save while an RTE_ROM_MANUAL update is pending; RTE_ECUDA. */
+rte_status rte_save_size(rte_handle h, size_t* bytes);
+rte_status rte_save(rte_handle h, void* buf, size_t bytes);
+rte_status rte_load(rte_handle h, const void* buf, size_t bytes);
 
 /* ---------------- operator-level calls (one hot-path step each) ----------------
  * These run exactly one step of the method on the handle's problem with host arrays in

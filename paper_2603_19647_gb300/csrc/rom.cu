@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <utility>
 
 #include "rte_internal.h"
@@ -702,6 +703,71 @@ void rom_free(RomDev& R) {
   if (R.hstate) cudaFreeHost(R.hstate);
   if (R.piv) cudaFree(R.piv);
   R = RomDev{};
+}
+
+// Checkpoint of one ROM: its host counters (rank, stored columns of U0 and W0, lu_ok), then
+// every device array that carries state from one append or apply to the next: the stored
+// columns of U0 and W0, the small factors Q and P, the singular values, A_r^{-1} and the core
+// workspace (which keeps U^T W for the next append).
+namespace {
+constexpr size_t ROM_SMALL_DOUBLES = 2 * (size_t)WCAP * MAXR + MAXR + (size_t)MAXR * MAXR + SCR_DOUBLES;
+}
+
+size_t rom_state_bytes(const RomDev& R) {
+  return 4 * sizeof(int) + sizeof(double) * ((size_t)(R.wu + R.ww) * R.n + ROM_SMALL_DOUBLES);
+}
+
+cudaError_t rom_save(const RomDev& R, unsigned char* out, cudaStream_t s) {
+  const int head[4] = {R.rank, R.wu, R.ww, R.lu_ok};
+  std::memcpy(out, head, sizeof(head));
+  out += sizeof(head);
+  const std::pair<const double*, size_t> parts[] = {
+      {R.U, (size_t)R.wu * R.n}, {R.W, (size_t)R.ww * R.n}, {R.Q, (size_t)WCAP * MAXR},
+      {R.P, (size_t)WCAP * MAXR}, {R.S, (size_t)MAXR},      {R.lu, (size_t)MAXR * MAXR},
+      {R.core, (size_t)SCR_DOUBLES}};
+  for (const auto& pt : parts) {
+    const size_t b = sizeof(double) * pt.second;
+    cudaError_t e = cudaMemcpyAsync(out, pt.first, b, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    out += b;
+  }
+  return cudaStreamSynchronize(s);
+}
+
+size_t rom_checked_bytes(const RomDev& R, const unsigned char* in, size_t avail) {
+  int head[4];
+  if (avail < sizeof(head)) return 0;
+  std::memcpy(head, in, sizeof(head));
+  const int rank = head[0], wu = head[1], ww = head[2];
+  if (rank < 0 || rank > R.r_max || wu < rank || ww < rank || wu > WCAP - 1 || ww > WCAP - 1)
+    return 0;
+  const size_t need =
+      4 * sizeof(int) + sizeof(double) * ((size_t)(wu + ww) * R.n + ROM_SMALL_DOUBLES);
+  return need <= avail ? need : 0;
+}
+
+cudaError_t rom_load(RomDev& R, const unsigned char* in, cudaStream_t s) {
+  int head[4];
+  std::memcpy(head, in, sizeof(head));
+  in += sizeof(head);
+  const int wu = head[1], ww = head[2];
+  const std::pair<double*, size_t> parts[] = {
+      {R.U, (size_t)wu * R.n}, {R.W, (size_t)ww * R.n}, {R.Q, (size_t)WCAP * MAXR},
+      {R.P, (size_t)WCAP * MAXR}, {R.S, (size_t)MAXR},   {R.lu, (size_t)MAXR * MAXR},
+      {R.core, (size_t)SCR_DOUBLES}};
+  for (const auto& pt : parts) {
+    const size_t b = sizeof(double) * pt.second;
+    cudaError_t e = cudaMemcpyAsync(pt.first, in, b, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    in += b;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  R.rank = head[0];
+  R.wu = wu;
+  R.ww = ww;
+  R.lu_ok = head[3] != 0 ? 1 : 0;
+  return cudaSuccess;
 }
 
 }  // namespace rte

@@ -1488,6 +1488,64 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   return reset_state(h);
 }
 
+// ---------------------------------------------------------------------------------------
+// Checkpoint blob (rte_save / rte_load): a header with the problem's sizes, the direction
+// layout and the host-side state, the handle's device state arrays in a fixed order, then
+// the IG-ROM and the PC-ROM.
+// ---------------------------------------------------------------------------------------
+struct CkptHead {
+  char magic[8];
+  uint32_t version;
+  int32_t dim, nx, ny, nslot, dl, nfam, precision, r_max;
+  uint64_t bytes;   // whole blob
+  double g[4];
+  int32_t y_valid, flag_ig, flag_pc, fcur;
+  uint32_t bf_seed, reserved;
+  rte_stats stats;
+};
+const char kCkptMagic[8] = {'R', 'T', 'E', 'C', 'K', 'P', 'T', '\0'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct StatePart {
+  void* dev;
+  size_t bytes;
+};
+// What a step reads from the previous one: f^n (in the precision's storage), rho^n, the next
+// b~ without inflow (y) and, with FP32 sweeps, the refinement pair (rho_ref, y_ir).
+std::vector<StatePart> state_parts(rte_handle h) {
+  const size_t n = (size_t)h->ncell, ns = (size_t)h->L.nslot;
+  std::vector<StatePart> v;
+  if (!h->fp32) {
+    v.push_back({h->f, sizeof(double) * n * ns});
+  } else if (!h->bf16) {
+    v.push_back({h->f_f, sizeof(float) * n * ns});
+  } else {
+    v.push_back({h->fb, sizeof(__nv_bfloat16) * n * ns});
+    v.push_back({h->fref[0], sizeof(float) * n});
+    v.push_back({h->fref[1], sizeof(float) * n});
+  }
+  v.push_back({h->rho, sizeof(double) * n});
+  v.push_back({h->y, sizeof(double) * n});
+  if (h->fp32) {
+    v.push_back({h->rho_ref, sizeof(double) * n});
+    v.push_back({h->y_ir, sizeof(double) * n});
+  }
+  return v;
+}
+
+size_t state_fixed_bytes(rte_handle h) {
+  size_t b = 0;
+  for (const auto& p : state_parts(h)) b += p.bytes;
+  return b;
+}
+
+rte_status sync_streams(rte_handle h) {
+  CK(cudaStreamSynchronize(h->st));
+  if (h->st2) CK(cudaStreamSynchronize(h->st2));
+  if (h->st3) CK(cudaStreamSynchronize(h->st3));
+  return RTE_OK;
+}
+
 }  // namespace
 
 // =========================================================================================
@@ -1725,6 +1783,97 @@ rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta
     if (eta) eta[d] = h->eta_user[d];
     if (w) w[d] = h->w_user[d];
   }
+  return RTE_OK;
+}
+
+rte_status rte_save_size(rte_handle h, size_t* bytes) {
+  if (!h || !bytes) return RTE_EINVAL;
+  *bytes = sizeof(CkptHead) + state_fixed_bytes(h) + rom_state_bytes(h->ig) +
+           rom_state_bytes(h->pc);
+  return RTE_OK;
+}
+
+rte_status rte_save(rte_handle h, void* buf, size_t bytes) {
+  if (!h || !buf) return RTE_EINVAL;
+  if (h->pending_rom)
+    return fail(h, RTE_ESTATE, "RTE_ROM_MANUAL: call rte_rom_update before rte_save");
+  size_t need = 0;
+  TRY(rte_save_size(h, &need));
+  if (bytes < need) return fail(h, RTE_EINVAL, "checkpoint buffer smaller than rte_save_size");
+  TRY(sync_streams(h));
+  CkptHead hd{};
+  std::memcpy(hd.magic, kCkptMagic, sizeof(hd.magic));
+  hd.version = kCkptVersion;
+  hd.dim = h->dim;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.nslot = h->L.nslot;
+  hd.dl = h->L.dl;
+  hd.nfam = h->L.nfam;
+  hd.precision = h->opt.precision;
+  hd.r_max = h->opt.r_max;
+  hd.bytes = need;
+  for (int s = 0; s < 4; ++s) hd.g[s] = h->g[s];
+  hd.y_valid = h->y_valid ? 1 : 0;
+  hd.flag_ig = h->flag_ig ? 1 : 0;
+  hd.flag_pc = h->flag_pc ? 1 : 0;
+  hd.fcur = h->fcur;
+  hd.bf_seed = h->bf_seed;
+  hd.stats = h->stats;
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  std::memcpy(out, &hd, sizeof(hd));
+  out += sizeof(hd);
+  for (const auto& p : state_parts(h)) {
+    CK(cudaMemcpyAsync(out, p.dev, p.bytes, cudaMemcpyDeviceToHost, h->st));
+    out += p.bytes;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  CK(rom_save(h->ig, out, h->st));
+  out += rom_state_bytes(h->ig);
+  CK(rom_save(h->pc, out, h->st));
+  return RTE_OK;
+}
+
+rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
+  if (!h || !buf) return RTE_EINVAL;
+  CkptHead hd;
+  if (bytes < sizeof(hd)) return fail(h, RTE_EINVAL, "checkpoint shorter than its header");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kCkptMagic, sizeof(hd.magic)) != 0 || hd.version != kCkptVersion)
+    return fail(h, RTE_EINVAL, "not a checkpoint of this library version");
+  if (hd.dim != h->dim || hd.nx != h->nx || hd.ny != h->ny || hd.nslot != h->L.nslot ||
+      hd.dl != h->L.dl || hd.nfam != h->L.nfam || hd.precision != h->opt.precision ||
+      hd.r_max != h->opt.r_max)
+    return fail(h, RTE_EINVAL,
+                "checkpoint of another mesh, direction layout, precision or r_max");
+  if (hd.bytes != bytes) return fail(h, RTE_EINVAL, "checkpoint length differs from its header");
+  if (hd.fcur != 0 && hd.fcur != 1) return fail(h, RTE_EINVAL, "malformed checkpoint");
+  // sizes first, so that a malformed blob changes nothing
+  const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof(hd);
+  const size_t left = bytes - sizeof(hd);
+  const size_t fixed = state_fixed_bytes(h);
+  if (left < fixed) return fail(h, RTE_EINVAL, "checkpoint truncated");
+  const size_t b_ig = rom_checked_bytes(h->ig, in + fixed, left - fixed);
+  const size_t b_pc = b_ig ? rom_checked_bytes(h->pc, in + fixed + b_ig, left - fixed - b_ig) : 0;
+  if (!b_ig || !b_pc || fixed + b_ig + b_pc != left)
+    return fail(h, RTE_EINVAL, "malformed ROM part of the checkpoint");
+  TRY(sync_streams(h));
+  for (const auto& p : state_parts(h)) {
+    CK(cudaMemcpyAsync(p.dev, in, p.bytes, cudaMemcpyHostToDevice, h->st));
+    in += p.bytes;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  CK(rom_load(h->ig, in, h->st));
+  CK(rom_load(h->pc, in + b_ig, h->st));
+  for (int s = 0; s < 4; ++s) h->g[s] = hd.g[s];
+  h->y_valid = hd.y_valid != 0;
+  h->flag_ig = hd.flag_ig != 0;
+  h->flag_pc = hd.flag_pc != 0;
+  h->fcur = hd.fcur;
+  h->bf_seed = hd.bf_seed;
+  h->stats = hd.stats;
+  h->pending_rom = false;
+  h->rom_pend = rte_s::RomPending{};
   return RTE_OK;
 }
 

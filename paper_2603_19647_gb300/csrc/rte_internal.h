@@ -242,5 +242,12 @@ cudaError_t rom_commit(RomDev& R, int* ran, int* grew, double* smallest_ratio, c
 // out = U A_r^{-1} U^T rhs.  Returns cudaErrorInvalidValue if the LU is not available.
 cudaError_t rom_apply(RomDev& R, const double* rhs, double* out, cudaStream_t s);
 cudaError_t rom_get(RomDev& R, double* S, double* U, double* Ar, cudaStream_t s);
+// Checkpoint of one ROM's state (host counters and device arrays) in host memory.
+// rom_checked_bytes: bytes of the checkpoint at `in`, 0 when it is malformed or longer than
+// avail; rom_load reads a checkpoint that rom_checked_bytes accepted.
+size_t rom_state_bytes(const RomDev& R);
+cudaError_t rom_save(const RomDev& R, unsigned char* out, cudaStream_t s);
+size_t rom_checked_bytes(const RomDev& R, const unsigned char* in, size_t avail);
+cudaError_t rom_load(RomDev& R, const unsigned char* in, cudaStream_t s);
 
 }  // namespace rte

@@ -106,6 +106,9 @@ _SIGS = {
     "rte_op_rom_apply": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "rte_op_rom_get": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp, _dp, _dp]),
     "rte_op_rom_reset": (ctypes.c_int, [_vp]),
+    "rte_save_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "rte_save": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
+    "rte_load": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
     "rte_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(Problem),
                                         ctypes.POINTER(Options)]),
     "rte_batch_step": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -222,6 +225,19 @@ class Handle:
         mu, eta, w = np.empty(self.nv), np.empty(self.nv), np.empty(self.nv)
         self._check(load().rte_get_quadrature(self.ptr, ctypes.byref(n), _p(mu), _p(eta), _p(w)))
         return mu, eta, w
+
+    def rte_save(self):
+        """rte_save_size + rte_save: the checkpoint as bytes."""
+        n = ctypes.c_size_t(0)
+        self._check(load().rte_save_size(self.ptr, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(load().rte_save(self.ptr, buf, n))
+        return buf.raw
+
+    def rte_load(self, blob):
+        blob = bytes(blob)
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(load().rte_load(self.ptr, buf, ctypes.c_size_t(len(blob))))
 
     def rte_get_stats(self):
         st = Stats()
