@@ -179,6 +179,14 @@ rte_status rte_get_scalar_flux(rte_handle h, double* rho);
 rte_status rte_get_angular_flux(rte_handle h, double* f);
 /* Copy the directions and weights in the library's direction order (host [n_dirs] each). */
 rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta, double* w);
+/* The angular rule a quadrature description gives for dim (1 or 2), host-side only (no
+ * device is needed): *n_dirs receives the direction count; mu, eta, w (host [n_dirs] each,
+ * any may be NULL, e.g. to query the count first) the directions and weights in the order
+ * rte_create and rte_get_quadrature use.  The layout conditions rte_create adds for explicit
+ * rules (equal quadrant counts, no direction on an axis) are not checked here.
+ * Errors: RTE_EINVAL, message from rte_last_error(NULL). */
+rte_status rte_quadrature_rule(const rte_quadrature* quad, int dim, int* n_dirs, double* mu,
+                               double* eta, double* w);
 rte_status rte_get_stats(rte_handle h, rte_stats* st);
 const char* rte_last_error(rte_handle h);
 /* Free everything; NULL-safe. */

@@ -1775,6 +1775,27 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
   return RTE_OK;
 }
 
+rte_status rte_quadrature_rule(const rte_quadrature* quad, int dim, int* n_dirs, double* mu,
+                               double* eta, double* w) {
+  if (!quad || !n_dirs || (dim != 1 && dim != 2)) {
+    g_create_error = "rte_quadrature_rule: NULL argument or dim not 1 or 2";
+    return RTE_EINVAL;
+  }
+  rte_s tmp;   // host fields only: nothing here touches a device
+  const rte_status st = make_rule(&tmp, quad, dim);
+  if (st != RTE_OK) {
+    g_create_error = tmp.err;
+    return st;
+  }
+  *n_dirs = (int)tmp.w_user.size();
+  for (int d = 0; d < *n_dirs; ++d) {
+    if (mu) mu[d] = tmp.mu_user[d];
+    if (eta) eta[d] = tmp.eta_user[d];
+    if (w) w[d] = tmp.w_user[d];
+  }
+  return RTE_OK;
+}
+
 rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta, double* w) {
   if (!h) return RTE_EINVAL;
   if (n_dirs) *n_dirs = h->L.nv;

@@ -106,6 +106,8 @@ _SIGS = {
     "rte_op_rom_apply": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "rte_op_rom_get": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp, _dp, _dp]),
     "rte_op_rom_reset": (ctypes.c_int, [_vp]),
+    "rte_quadrature_rule": (ctypes.c_int, [ctypes.POINTER(Quadrature), ctypes.c_int, _ip, _dp, _dp,
+                                           _dp]),
     "rte_save_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "rte_save": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
     "rte_load": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
@@ -322,6 +324,21 @@ def rte_dsa_solve_noalloc(dim, nx, ny, x0, x1, y0, y1, c_dt, sigma_t_dev, sigma_
     if status != RTE_OK:
         raise RteError(status, lib.rte_last_error(None).decode())
     return its.value
+
+
+def rte_quadrature_rule(quad: Quadrature, dim):
+    """(mu, eta, w) of the rule `quad` describes, computed by the library on the host."""
+    lib = load()
+    n = ctypes.c_int(0)
+    status = lib.rte_quadrature_rule(ctypes.byref(quad), int(dim), ctypes.byref(n), None, None, None)
+    if status != RTE_OK:
+        raise RteError(status, lib.rte_last_error(None).decode())
+    mu, eta, w = np.empty(n.value), np.empty(n.value), np.empty(n.value)
+    status = lib.rte_quadrature_rule(ctypes.byref(quad), int(dim), ctypes.byref(n), _p(mu), _p(eta),
+                                     _p(w))
+    if status != RTE_OK:
+        raise RteError(status, lib.rte_last_error(None).decode())
+    return mu, eta, w
 
 
 def mesh_from(workload):

@@ -89,3 +89,29 @@ def test_bf16_storage_is_2d_only(lib):
     with pytest.raises(rte.RteError) as ei:
         rte.create_from_workload(wl, options=rte.default_options(precision=rte.RTE_FP32_BF16F))
     assert ei.value.status == rte.RTE_EINVAL
+
+
+@pytest.mark.parametrize("desc", [("gl", 2), ("gl", 16), ("gl", 32), ("cl_hemi", 32, 8),
+                                  ("cl_hemi", 16, 8), ("cl_hemi", 32, 16), ("cl_hemi", 4, 2)])
+def test_quadrature_rule_matches_oracle(lib, desc):
+    """The library's host-side angular rules (Gauss-Legendre in 1D, the CL hemisphere rule of
+    App. A in 2D) against the oracle's own, direction by direction (same order)."""
+    from conftest import oracle_quadrature
+    dim = 1 if desc[0] == "gl" else 2
+    mu, eta, w = rte.rte_quadrature_rule(rte.quadrature_from(desc), dim)
+    omu, oeta, ow = oracle_quadrature(desc)
+    assert mu.size == omu.size
+    for d in range(mu.size):
+        k = int(np.argmin((omu - mu[d]) ** 2 + (oeta - eta[d]) ** 2))
+        assert abs(mu[d] - omu[k]) < 1e-14 and abs(eta[d] - oeta[k]) < 1e-14
+        assert abs(w[d] - ow[k]) < 1e-15
+    assert abs(w.sum() - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("desc,dim", [(("gl", 16), 2), (("cl_hemi", 32, 8), 1), (("gl", 3), 1),
+                                      (("cl_hemi", 6, 4), 2), (("cl_hemi", 32, 8), 3)])
+def test_quadrature_rule_rejects_bad_descriptions(lib, desc, dim):
+    with pytest.raises(rte.RteError) as ei:
+        rte.rte_quadrature_rule(rte.quadrature_from(desc), dim)
+    assert ei.value.status == rte.RTE_EINVAL
+    assert len(str(ei.value)) > 12
