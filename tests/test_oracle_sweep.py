@@ -38,6 +38,23 @@ def test_1d_pure_absorber_closed_form(mu):
     assert np.max(np.abs(got - expect) / expect) < 1e-13
 
 
+def test_1d_pure_absorber_continuum_limit():
+    """With tau -> 0 (a very long step) the upwind cell values of a pure absorber approach the
+    steady solution g exp(-sigma x / |mu|) of the transport equation at the cell's outflow face
+    (the upwind cell value is the flux it passes on), with an error of first order in h: the
+    error must halve as h halves (a centred or downwind scheme, or a wrong face, would not)."""
+    mu, g, sig, L = 0.4, 1.3, 2.0, 1.0
+    errs = []
+    for n in (50, 100, 200, 400):
+        p = _problem(n, 1, [mu], [0.0], [1.0], sig, c_dt=1e12, lx=L, g=[g, 0, 0, 0])
+        _, psi = tr.sweep(p, inflow=p.inflow, want_psi=True)
+        x_out = (np.arange(n) + 1.0) * p.hx
+        errs.append(np.max(np.abs(psi[0] - g * np.exp(-sig * x_out / mu))))
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(1.9 < r < 2.1 for r in ratios), ratios
+    assert errs[-1] < 5e-3 * g
+
+
 @pytest.mark.parametrize("sx,sy", [(1, 1), (-1, 1), (1, -1), (-1, -1)])
 def test_2d_pure_absorber_lattice_paths(sx, sy):
     # Inflow g on the x-inflow face only: psi_ij = g sum_{k=1}^{j} C(i-1+j-k, i-1) a^i b^{j-k}
