@@ -191,3 +191,44 @@ def test_paper_two_material_slab_trend():
     # the same solution up to the solver tolerance (Q0 here: 1.7e-9)
     d = np.linalg.norm(runs[True].rho - runs[False].rho)
     assert d < 10 * rep["rom_vs_sidsa_l2_at_t1000"]
+
+
+def test_paper_isotropic_scattering_trend():
+    """The isotropic-scattering problem of Sec. 4.2 at sigma_s = 1 and CFL 1 (data and
+    reported outcomes in tests/golden/isotropic_scattering_2d.json), run by the oracle in Q0
+    with the paper's tolerances and absolute tests.  Trend checks: the ROM phases all occur,
+    Phase 3 needs fewer sweeps per step than SI-DSA (the paper reports Phase 3 at 49 % and
+    Phase 2 at 67 % of SI-DSA's time, time following sweeps), and the two marches agree to
+    the solver tolerance (reported 9.5e-16 in L2 at eps_SISA = 1e-12)."""
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    gold = json.load(open(os.path.join(here, "golden", "isotropic_scattering_2d.json")))
+    pb, tol, rep = gold["problem"], gold["tolerances"], gold["reported"]
+    n = pb["cells_per_side"]
+    a, b = pb["domain"]
+    h = (b - a) / n
+    xc = a + (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xc, xc)
+    G = (10.0 / np.pi * np.exp(-100.0 * (X ** 2 + Y ** 2))).ravel()
+    sig = np.full(n * n, pb["sigma_s"] + pb["sigma_a"])
+    mu, eta, w = q.cl_hemisphere(*pb["cl_rule"])
+    dt = pb["cfl"] * h
+    steps = int(round(pb["t_end"] / dt))
+    opts = dict(tol, residual_norm="abs", up_rel=False, cg_rtol=1e-10)
+    runs = {}
+    for rom in (False, True):
+        p = tr.Problem(n, n, a, b, a, b, mu, eta, w, sig.copy(), np.full(n * n, pb["sigma_s"]),
+                       G, dt, np.zeros(4))
+        r = stepper.OracleRTE(p, rom=rom, **opts)
+        r.set_initial(np.full(n * n, pb["initial"]))
+        r.step(steps)
+        runs[rom] = r
+    plain = np.mean([s.sweeps for s in runs[False].log])
+    log = runs[True].log
+    assert {s.phase for s in log} == {1, 2, 3}
+    p3 = np.mean([s.sweeps for s in log if s.phase == 3])
+    assert p3 / plain < 0.8    # Q0 here: 4.0 against 6.1 sweeps per step
+    d = np.linalg.norm(runs[True].rho - runs[False].rho)
+    # Q0 here: 8.7e-14 on a norm of 5.6; reported: rep["rom_vs_sidsa_l2"]
+    assert d < max(1e-12 * np.linalg.norm(runs[False].rho), rep["rom_vs_sidsa_l2"])
