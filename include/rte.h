@@ -210,7 +210,7 @@ void rte_destroy(rte_handle h);
  * RTE_ESTATE for rte_save while an RTE_ROM_MANUAL update is pending; RTE_ECUDA. */
 rte_status rte_save_size(rte_handle h, size_t* bytes);
 rte_status rte_save(rte_handle h, void* buf, size_t bytes);
-rte_status rte_load(rte_handle h, const void* buf, size_t bytes);
+rte_status rte_load(rte_handle h, const void* buf, size_t bytes);   /* bytes: the blob's length */
 
 /* ---------------- operator-level calls (one hot-path step each) ----------------
  * These run exactly one step of the method on the handle's problem with host arrays in
