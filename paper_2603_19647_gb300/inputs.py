@@ -23,6 +23,8 @@ Workloads (cell centres x_i = x0 + (i + 1/2) h; vacuum boundaries unless stated)
 * ``diffusive_disc`` 2048^2, CL(32,16) hemisphere (256 directions), sigma_s = 1000 in the
                      disc |x-(1/2,1/2)| < 0.3, else 1; sigma_a = 0.01; centred pulse;
                      c dt = 0.001, 300 steps.
+* ``two_material_slab``, ``isotropic_scattering``, ``variable_scattering``: the problems of
+                     Sec. 4.1-4.3 with the paper's data (see each generator).
 
 Every generator takes a size override so the same recipe yields small test cases.
 """
@@ -145,5 +147,54 @@ def diffusive_disc(n=2048, steps=300, c_dt=0.001, quad=(32, 16)):
                     c_dt=c_dt, steps=steps)
 
 
+# The paper's own problems of Sec. 4 (their data only; each run uses the tolerances the paper
+# states for it).  Time is c t with c = 1, so c_dt is the paper's time step.
+
+def two_material_slab(dx=0.1, dt=10.0, steps=100, n_gl=6):
+    """Sec. 4.1: [0, 11]; sigma_s = 0, sigma_a = 1 on [0, 1], sigma_s = 100, sigma_a = 0 on
+    [1, 11]; f = 0 at t = 0; isotropic inflow 5 at x = 0, vacuum at x = 11."""
+    n = int(round(11.0 / dx))
+    x = _centres(n, 0.0, 11.0)
+    ss = np.where(x < 1.0, 0.0, 100.0)
+    sa = np.where(x < 1.0, 1.0, 0.0)
+    return Workload("two_material_slab", n, 1, (0.0, 11.0, 0.0, 1.0), ("gl", n_gl),
+                    sigma_t=ss + sa, sigma_s=ss, source=np.zeros(n), rho0=np.zeros(n),
+                    c_dt=dt, steps=steps, inflow=np.array([5.0, 0.0, 0.0, 0.0]))
+
+
+def isotropic_scattering(n=81, sigma_s=1.0, cfl=1.0, t_end=2.5, quad=(40, 6)):
+    """Sec. 4.2: [-1, 1]^2, sigma_a = 0, G = (10 / pi) exp(-100 (x^2 + y^2)), zero inflow and
+    initial state, dt = CFL dx, up to t = 2.5."""
+    h = 2.0 / n
+    x = _centres(n, -1.0, 1.0)
+    X, Y = np.meshgrid(x, x)
+    G = (10.0 / np.pi * np.exp(-100.0 * (X ** 2 + Y ** 2))).ravel()
+    dt = cfl * h
+    steps = int(np.ceil(t_end / dt - 1e-9))
+    ss = np.full(n * n, float(sigma_s))
+    return Workload("isotropic_scattering", n, n, (-1.0, 1.0, -1.0, 1.0), ("cl_hemi",) + tuple(quad),
+                    sigma_t=ss.copy(), sigma_s=ss, source=G, rho0=np.zeros(n * n), c_dt=dt,
+                    steps=steps, meta=dict(cfl=cfl))
+
+
+def variable_scattering(n=81, cfl=1.0, t_end=2.5, quad=(40, 6), zeta=1e-2):
+    """Sec. 4.3: [-1, 1]^2, sigma_s = 99.9 c^4 (c + sqrt 2)^2 (c - sqrt 2)^2 + 0.1 for
+    c = |x| < 1, else 1; sigma_a = 0; G = 0; zero inflow; isotropic initial state
+    exp(-|x|^2 / (4 zeta^2)) / (4 pi zeta^2); dt = CFL dx, up to t = 2.5."""
+    h = 2.0 / n
+    x = _centres(n, -1.0, 1.0)
+    X, Y = np.meshgrid(x, x)
+    c = np.sqrt(X ** 2 + Y ** 2)
+    r2 = np.sqrt(2.0)
+    ss = np.where(c < 1.0, 99.9 * c ** 4 * (c + r2) ** 2 * (c - r2) ** 2 + 0.1, 1.0).ravel()
+    rho0 = (np.exp(-(X ** 2 + Y ** 2) / (4 * zeta ** 2)) / (4 * np.pi * zeta ** 2)).ravel()
+    dt = cfl * h
+    steps = int(np.ceil(t_end / dt - 1e-9))
+    return Workload("variable_scattering", n, n, (-1.0, 1.0, -1.0, 1.0), ("cl_hemi",) + tuple(quad),
+                    sigma_t=ss.copy(), sigma_s=ss, source=np.zeros(n * n), rho0=rho0, c_dt=dt,
+                    steps=steps, meta=dict(cfl=cfl))
+
+
 BY_NAME = dict(slab_1d=slab_1d, checkerboard=checkerboard, lognormal=lognormal,
-               diffusive_disc=diffusive_disc)
+               diffusive_disc=diffusive_disc, two_material_slab=two_material_slab,
+               isotropic_scattering=isotropic_scattering, variable_scattering=variable_scattering)

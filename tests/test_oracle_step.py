@@ -150,32 +150,43 @@ def test_dsa_contracts_in_thick_heterogeneous_cells():
     assert res[-1] < 1e-10 * res[0]
 
 
-def test_paper_two_material_slab_trend():
-    """The two-material slab of Sec. 4.1 (data and reported outcomes in
-    tests/golden/two_material_slab.json), run by the oracle in Q0 with the paper's own
-    tolerances and its absolute stopping and update tests.  The paper's numbers are for
-    piecewise-linear DG, so the checks are of the trend it reports: SI-DSA needs many
-    iterations in every step (at least 17, above 20 early), the ROM brings Phase 3 steps down
-    to about 2-5, and the two marches end within about 1e-9 of each other in the L2 norm."""
+def _golden(name):
     import json
     import os
     here = os.path.dirname(os.path.abspath(__file__))
-    gold = json.load(open(os.path.join(here, "golden", "two_material_slab.json")))
+    return json.load(open(os.path.join(here, "golden", name)))
+
+
+def _paper_march(wl, rom, tol):
+    """The oracle's march of one of the paper's Sec. 4 problems, with the paper's tolerances
+    and its absolute stopping and update tests."""
+    r = stepper.OracleRTE(oracle_problem(wl), rom=rom, residual_norm="abs", up_rel=False,
+                          cg_rtol=1e-10, **tol)
+    r.set_initial(wl.rho0)
+    r.step(wl.steps)
+    return r
+
+
+def test_paper_two_material_slab_trend():
+    """The two-material slab of Sec. 4.1 (data and reported outcomes in
+    tests/golden/two_material_slab.json).  The paper's numbers are for piecewise-linear DG,
+    so the checks are of the trend it reports: SI-DSA needs many iterations in every step (at
+    least 17, above 20 early), the ROM brings Phase 3 steps down to about 2-5, and the two
+    marches end within about 1e-9 of each other in the L2 norm."""
+    gold = _golden("two_material_slab.json")
     pb, tol, rep = gold["problem"], gold["tolerances"], gold["reported"]
-    n = int(round((pb["domain"][1] - pb["domain"][0]) / pb["dx"]))
-    x = pb["domain"][0] + (np.arange(n) + 0.5) * pb["dx"]
-    ss = np.where(x < 1.0, pb["sigma_s"]["x<1"], pb["sigma_s"]["x>1"])
-    sa = np.where(x < 1.0, pb["sigma_a"]["x<1"], pb["sigma_a"]["x>1"])
-    mu, eta, w = q.gl_slab(pb["gl_points"])
-    opts = dict(tol, residual_norm="abs", up_rel=False, cg_rtol=1e-10)
-    runs = {}
-    for rom in (False, True):
-        p = tr.Problem(n, 1, pb["domain"][0], pb["domain"][1], 0.0, 1.0, mu, eta, w, ss + sa, ss,
-                       np.zeros(n), pb["dt"], np.array([pb["inflow_west"], pb["inflow_east"], 0, 0]))
-        r = stepper.OracleRTE(p, rom=rom, **opts)
-        r.set_initial(np.full(n, pb["initial"]))
-        r.step(pb["steps"])
-        runs[rom] = r
+    wl = inputs.two_material_slab()
+    # the generator holds the problem the fixture states
+    x = pb["domain"][0] + (np.arange(wl.nx) + 0.5) * pb["dx"]
+    assert wl.nx == round((pb["domain"][1] - pb["domain"][0]) / pb["dx"])
+    assert wl.quadrature == ("gl", pb["gl_points"])
+    assert (wl.c_dt, wl.steps) == (pb["dt"], pb["steps"])
+    assert list(wl.inflow[:2]) == [pb["inflow_west"], pb["inflow_east"]]
+    assert np.array_equal(wl.sigma_s, np.where(x < 1, pb["sigma_s"]["x<1"], pb["sigma_s"]["x>1"]))
+    assert np.array_equal(wl.sigma_t - wl.sigma_s,
+                          np.where(x < 1, pb["sigma_a"]["x<1"], pb["sigma_a"]["x>1"]))
+    assert np.all(wl.rho0 == pb["initial"])
+    runs = {rom: _paper_march(wl, rom, tol) for rom in (False, True)}
     plain = [s.iterations for s in runs[False].log]
     rom = runs[True].log
     # SI-DSA: many iterations in every step (Q0 here: 15 at the end, 24 at the start)
@@ -193,37 +204,31 @@ def test_paper_two_material_slab_trend():
     assert d < 10 * rep["rom_vs_sidsa_l2_at_t1000"]
 
 
+def _check_2d_generator(wl, pb):
+    a, b = pb["domain"]
+    n = pb["cells_per_side"]
+    assert (wl.nx, wl.ny) == (n, n) and wl.domain == (a, b, a, b)
+    assert wl.quadrature == ("cl_hemi",) + tuple(pb["cl_rule"])
+    assert wl.c_dt == pb["cfl"] * (b - a) / n
+    assert wl.steps == int(np.ceil(pb["t_end"] / wl.c_dt - 1e-9))
+    assert not np.any(wl.inflow)
+
+
 def test_paper_isotropic_scattering_trend():
     """The isotropic-scattering problem of Sec. 4.2 at sigma_s = 1 and CFL 1 (data and
-    reported outcomes in tests/golden/isotropic_scattering_2d.json), run by the oracle in Q0
-    with the paper's tolerances and absolute tests.  Trend checks: the ROM phases all occur,
-    Phase 3 needs fewer sweeps per step than SI-DSA (the paper reports Phase 3 at 49 % and
-    Phase 2 at 67 % of SI-DSA's time, time following sweeps), and the two marches agree to
-    the solver tolerance (reported 9.5e-16 in L2 at eps_SISA = 1e-12)."""
-    import json
-    import os
-    here = os.path.dirname(os.path.abspath(__file__))
-    gold = json.load(open(os.path.join(here, "golden", "isotropic_scattering_2d.json")))
+    reported outcomes in tests/golden/isotropic_scattering_2d.json).  Trend checks: the ROM
+    phases all occur, Phase 3 needs fewer sweeps per step than SI-DSA (the paper reports
+    Phase 3 at 49 % and Phase 2 at 67 % of SI-DSA's time, time following sweeps), and the two
+    marches agree to the solver tolerance (reported 9.5e-16 in L2 at eps_SISA = 1e-12)."""
+    gold = _golden("isotropic_scattering_2d.json")
     pb, tol, rep = gold["problem"], gold["tolerances"], gold["reported"]
-    n = pb["cells_per_side"]
-    a, b = pb["domain"]
-    h = (b - a) / n
-    xc = a + (np.arange(n) + 0.5) * h
-    X, Y = np.meshgrid(xc, xc)
-    G = (10.0 / np.pi * np.exp(-100.0 * (X ** 2 + Y ** 2))).ravel()
-    sig = np.full(n * n, pb["sigma_s"] + pb["sigma_a"])
-    mu, eta, w = q.cl_hemisphere(*pb["cl_rule"])
-    dt = pb["cfl"] * h
-    steps = int(round(pb["t_end"] / dt))
-    opts = dict(tol, residual_norm="abs", up_rel=False, cg_rtol=1e-10)
-    runs = {}
-    for rom in (False, True):
-        p = tr.Problem(n, n, a, b, a, b, mu, eta, w, sig.copy(), np.full(n * n, pb["sigma_s"]),
-                       G, dt, np.zeros(4))
-        r = stepper.OracleRTE(p, rom=rom, **opts)
-        r.set_initial(np.full(n * n, pb["initial"]))
-        r.step(steps)
-        runs[rom] = r
+    wl = inputs.isotropic_scattering(n=pb["cells_per_side"], sigma_s=pb["sigma_s"], cfl=pb["cfl"])
+    _check_2d_generator(wl, pb)
+    X, Y = np.meshgrid(*[pb["domain"][0] + (np.arange(wl.nx) + 0.5) * 2.0 / wl.nx] * 2)
+    assert np.allclose(wl.source, 10 / np.pi * np.exp(-100 * (X ** 2 + Y ** 2)).ravel(),
+                       rtol=1e-12, atol=0)
+    assert np.all(wl.sigma_s == pb["sigma_s"]) and np.all(wl.sigma_t == wl.sigma_s)
+    runs = {rom: _paper_march(wl, rom, tol) for rom in (False, True)}
     plain = np.mean([s.sweeps for s in runs[False].log])
     log = runs[True].log
     assert {s.phase for s in log} == {1, 2, 3}
@@ -236,44 +241,23 @@ def test_paper_isotropic_scattering_trend():
 
 def test_paper_variable_scattering_trend():
     """The variable-scattering problem of Sec. 4.3 (data and Table 3 in
-    tests/golden/variable_scattering_2d.json), run by the oracle in Q0 with the paper's
-    tolerances and absolute tests.  Table 3 counts sweeps, so the trend checks compare sweep
-    ratios: most steps run in Phase 3 (reported 76 of 102), where the ROM needs well under
-    SI-DSA's sweeps per step (reported 3.58 against 6.67; Q0 here 4.7 against 8.2), and the two
-    marches agree to the solver tolerance (reported 1.3e-11 in L2; Q0 here 1.9e-10 on a norm
-    of 29)."""
-    import json
-    import os
-    here = os.path.dirname(os.path.abspath(__file__))
-    gold = json.load(open(os.path.join(here, "golden", "variable_scattering_2d.json")))
+    tests/golden/variable_scattering_2d.json).  Table 3 counts sweeps, so the trend checks
+    compare sweep ratios: most steps run in Phase 3 (reported 76 of 102), where the ROM needs
+    well under SI-DSA's sweeps per step (reported 3.58 against 6.67; Q0 here 4.7 against 8.2),
+    and the two marches agree to the solver tolerance (reported 1.3e-11 in L2; Q0 here 1.8e-10
+    on a norm of 29)."""
+    gold = _golden("variable_scattering_2d.json")
     pb, tol, rep = gold["problem"], gold["tolerances"], gold["reported"]
-    n = pb["cells_per_side"]
-    a, b = pb["domain"]
-    h = (b - a) / n
-    xc = a + (np.arange(n) + 0.5) * h
-    X, Y = np.meshgrid(xc, xc)
-    c = np.sqrt(X ** 2 + Y ** 2)
-    r2 = np.sqrt(2.0)
-    ss = np.where(c < 1.0, 99.9 * c ** 4 * (c + r2) ** 2 * (c - r2) ** 2 + 0.1, 1.0).ravel()
-    zeta = 1e-2
-    rho0 = (np.exp(-(X ** 2 + Y ** 2) / (4 * zeta ** 2)) / (4 * np.pi * zeta ** 2)).ravel()
-    mu, eta, w = q.cl_hemisphere(*pb["cl_rule"])
-    dt = pb["cfl"] * h
-    steps = int(np.ceil(pb["t_end"] / dt - 1e-9))
-    assert steps == sum(rep["steps_per_phase"])
-    opts = dict(tol, residual_norm="abs", up_rel=False, cg_rtol=1e-10)
-    runs = {}
-    for rom in (False, True):
-        p = tr.Problem(n, n, a, b, a, b, mu, eta, w, ss + pb["sigma_a"], ss.copy(),
-                       np.zeros(n * n), dt, np.zeros(4))
-        r = stepper.OracleRTE(p, rom=rom, **opts)
-        r.set_initial(rho0)
-        r.step(steps)
-        runs[rom] = r
+    wl = inputs.variable_scattering(n=pb["cells_per_side"], cfl=pb["cfl"])
+    _check_2d_generator(wl, pb)
+    assert wl.steps == sum(rep["steps_per_phase"])
+    assert np.all(wl.sigma_t == wl.sigma_s) and not np.any(wl.source)
+    assert abs(wl.sigma_s.min() - 0.1) < 1e-3 and abs(wl.sigma_s.max() - 100.0) < 0.5
+    runs = {rom: _paper_march(wl, rom, tol) for rom in (False, True)}
     plain = [s.sweeps for s in runs[False].log]
     log = runs[True].log
     phases = [s.phase for s in log]
-    assert phases.count(3) >= 0.6 * steps
+    assert phases.count(3) >= 0.6 * wl.steps
     p3_rom = np.mean([s.sweeps for s in log if s.phase == 3])
     p3_plain = np.mean([sw for sw, ph in zip(plain, phases) if ph == 3])
     rs = rep["sweeps_per_step_rom"]["phase3"] / rep["sweeps_per_step_sidsa"]["phase3"]
@@ -289,34 +273,15 @@ def test_paper_isotropic_scattering_cfl_trend():
     (relative time 64 % at CFL 0.5, 47 % at CFL 2).  The oracle in Q0, with sweeps standing in
     for time: the Phase-3 ratio of sweeps per step (ROM over SI-DSA) falls from CFL 0.5 to
     CFL 2 (Q0 here: 0.67 and 0.57) and each is within 0.15 of the reported fraction."""
-    import json
-    import os
-    here = os.path.dirname(os.path.abspath(__file__))
-    gold = json.load(open(os.path.join(here, "golden", "isotropic_scattering_2d.json")))
+    gold = _golden("isotropic_scattering_2d.json")
     pb, tol, rep = gold["problem"], gold["tolerances"], gold["reported"]
     t1 = rep["table1_relative_time_percent"]
-    n = pb["cells_per_side"]
-    a, b = pb["domain"]
-    h = (b - a) / n
-    xc = a + (np.arange(n) + 0.5) * h
-    X, Y = np.meshgrid(xc, xc)
-    G = (10.0 / np.pi * np.exp(-100.0 * (X ** 2 + Y ** 2))).ravel()
-    mu, eta, w = q.cl_hemisphere(*pb["cl_rule"])
-    opts = dict(tol, residual_norm="abs", up_rel=False, cg_rtol=1e-10)
     ratios = []
     for cfl in (0.5, 2.0):
-        dt = cfl * h
-        steps = int(np.ceil(pb["t_end"] / dt - 1e-9))
-        logs = {}
-        for rom in (False, True):
-            p = tr.Problem(n, n, a, b, a, b, mu, eta, w, np.full(n * n, pb["sigma_s"]),
-                           np.full(n * n, pb["sigma_s"]), G, dt, np.zeros(4))
-            r = stepper.OracleRTE(p, rom=rom, **opts)
-            r.set_initial(np.zeros(n * n))
-            r.step(steps)
-            logs[rom] = r.log
+        wl = inputs.isotropic_scattering(n=pb["cells_per_side"], sigma_s=pb["sigma_s"], cfl=cfl)
+        logs = {rom: _paper_march(wl, rom, tol).log for rom in (False, True)}
         p3 = [i for i, s in enumerate(logs[True]) if s.phase == 3]
-        assert len(p3) >= steps // 2
+        assert len(p3) >= wl.steps // 2
         ratio = (np.mean([logs[True][i].sweeps for i in p3]) /
                  np.mean([logs[False][i].sweeps for i in p3]))
         reported = t1["phase3"][t1["cfl"].index(cfl)] / 100.0
