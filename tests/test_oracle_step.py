@@ -288,3 +288,38 @@ def test_paper_isotropic_scattering_cfl_trend():
         assert abs(ratio - reported) < 0.15, (cfl, ratio, reported)
         ratios.append(ratio)
     assert ratios[1] < ratios[0]
+
+
+def test_march_particle_balance_per_step():
+    """Particle balance of every step of a ROM-accelerated march (the identity of the final
+    sweep with the step's converged scalar flux): with rho^ = sum_k w_k f_k,
+      sum_c A [tau (rho^n - rho^{n-1}) + sigma_a rho^n - G] + leakage - inflow
+          = sum_c A sigma_s (rho^n - rho^),
+    where rho^n is the iterate the final sweep scattered.  Since rho^n meets
+    the SI stopping test, that right side is at the solver tolerance: the balance residual of
+    each step must be within a small multiple of eps_SISA of the step's scale."""
+    wl = inputs.checkerboard(n=16, quad=(8, 4))
+    p = oracle_problem(wl)
+    p.inflow = np.array([0.4, 0.0, 0.2, 0.1])
+    eps = 1e-10
+    r = stepper.OracleRTE(p, eps_sisa=eps, rom=True, cg_rtol=1e-10, eps_ig=1e-9, eps_up=1e-9)
+    r.set_initial(wl.rho0)
+    A = p.hx * p.hy
+    sa = p.sigma_t - p.sigma_s
+    for _ in range(25):
+        f_old = r.f.copy()
+        r.step()
+        rho_hat, rho_hat_old = p.w @ r.f, p.w @ f_old
+        F = r.f.reshape(p.nv, p.ny, p.nx)
+        leak = inflow = 0.0
+        for j in range(p.nv):
+            ex, ey = abs(p.mu[j]) * p.hy, abs(p.eta[j]) * p.hx
+            leak += p.w[j] * (ex * np.sum(F[j][:, -1 if p.mu[j] > 0 else 0]) +
+                              ey * np.sum(F[j][-1 if p.eta[j] > 0 else 0, :]))
+            inflow += p.w[j] * (ex * (p.inflow[0] if p.mu[j] > 0 else p.inflow[1]) * p.ny +
+                                ey * (p.inflow[2] if p.eta[j] > 0 else p.inflow[3]) * p.nx)
+        bal = np.sum(A * (p.tau * (rho_hat - rho_hat_old) + sa * rho_hat - p.source)) + leak - inflow
+        scale = np.sum(A * p.tau * np.abs(rho_hat)) + leak + inflow
+        assert abs(bal) < 50 * eps * scale, (r.n, bal / scale)
+        # the scattering term closes it exactly
+        assert abs(bal - np.sum(A * p.sigma_s * (r.rho - rho_hat))) < 1e-12 * scale
