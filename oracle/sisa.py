@@ -41,8 +41,10 @@ def converged(diff, rho_half, eps, mode):
     return dn <= eps * rn, (dn / rn if rn > 0 else dn)
 
 
-def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None):
+def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None, decide=None):
     """Algorithm 1.  pc: callable(rhs) -> delta for the l = 1 SA step, or None for DSA only.
+    decide: optional callable(kind, own, value, threshold) -> bool that may replace the
+    stopping decision ("si_stop"; value = the residual in the test's own units).
 
     Returns (rho^n, SolveInfo).  Raises NoConvergence after opts['max_iter'] sweeps.
     """
@@ -54,6 +56,8 @@ def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None):
         if l == 1:
             info.rho_half_1 = rho_half.copy()
         ok, res = converged(diff, rho_half, opts["eps_sisa"], opts["residual_norm"])
+        if decide is not None:
+            ok = decide("si_stop", ok, res, opts["eps_sisa"])
         info.iterations = l
         info.residual = res
         if ok:

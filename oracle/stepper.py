@@ -20,6 +20,12 @@ Readings where the paper is silent or loose (each listed in the design notes):
 * A step whose first sweep already converged has no first correction, so no PC snapshot
   is taken from it.
 * Step 1's initial guess is rho^0 (the isotropic initial state).
+
+Each decision of the algorithm (the SI stopping test, the end of each construction phase, the
+two update gates) goes through ``decide``, which returns the algorithm's own decision; a
+test may override it to follow another implementation's log where both sides stand within
+rounding of a threshold.  The snapshot pairs and the correction rule are methods of their own
+so that a test can plant a mistake in exactly one of them.
 """
 from dataclasses import dataclass, field
 
@@ -48,13 +54,21 @@ class StepLog:
     residual: float
     ig_error: float = float("nan")
     pc_error: float = float("nan")
+    # record=True: rho^n, rho^{n,1/2} and the initial guess rho^{n,(0)} of the step, and the
+    # singular values of both ROMs after its update
+    rho: np.ndarray = None
+    rho_half_1: np.ndarray = None
+    rho_init: np.ndarray = None
+    ig_s: np.ndarray = None
+    pc_s: np.ndarray = None
 
 
 class OracleRTE:
     """The time march of Algorithm 2 on an oracle.transport.Problem."""
 
-    def __init__(self, problem, **opts):
+    def __init__(self, problem, record=False, **opts):
         self.p = problem
+        self.record = record
         self.o = dict(DEFAULTS)
         self.o.update(opts)
         self.A = _dsa.dsa_matrix(problem)
@@ -86,6 +100,37 @@ class OracleRTE:
         for _ in range(nsteps):
             self._step()
 
+    # ---- the pieces of Algorithm 2 a test may replace one at a time ----
+    def decide(self, kind, own, value, threshold):
+        """A decision of the algorithm: kind is "si_stop", "ig_built", "pc_built", "ig_update"
+        or "pc_update"; own is the algorithm's answer for value against threshold."""
+        return own
+
+    def ig_pair(self, rho_n, btilde_prev, f_new):
+        """IG-ROM snapshot pair: (rho^n, b~^{n-1}), since A~ rho^n = b~^{n-1}."""
+        return rho_n, btilde_prev
+
+    def pc_pair(self, rho_n, rho_half_1, rho_init):
+        """PC-ROM snapshot pair: the first correction rho^n - rho^{n,1/2} and its residual
+        rho^{n,1/2} - rho^{n,(0)} (Sec. 3.2, Phase 2)."""
+        return rho_n - rho_half_1, rho_half_1 - rho_init
+
+    def has_correction(self, info):
+        """A step whose first sweep met the stopping test took no correction."""
+        return info.iterations > 1
+
+    def pc_update_due(self, ig_up, err, threshold):
+        """Phase 3 PC-ROM update: when the IG-ROM was updated in the same step, or when the
+        PC indicator exceeds the threshold (Sec. 3.2, Phase 3)."""
+        return ig_up or self.decide("pc_update", err > threshold, err, threshold)
+
+    def _built(self, kind, svd, grew, eps):
+        """End of a construction phase: s_m / sum s <= eps (Eq. (ig_stop), Eq. (pc_stop)) or
+        the rank cap reached."""
+        ratio = svd.stop_ratio(grew)
+        own = ratio <= eps or svd.rank >= self.o["r_max"]
+        return self.decide(kind, own, ratio, eps)
+
     def _step(self):
         p, o = self.p, self.o
         phase = self.phase()
@@ -100,41 +145,44 @@ class OracleRTE:
         pc = None
         if use_rom and self.flag_pc:
             pc = self.pc.solve_apply
-        rho_n, info = _sisa.si_sa(p, rho0, btilde, o, self.A, pc=pc)
+        rho_n, info = _sisa.si_sa(p, rho0, btilde, o, self.A, pc=pc, decide=self.decide)
         f_new, _ = _tr.final_f(p, rho_n, self.f)
         ig_up = pc_up = False
         ig_err = pc_err = float("nan")
         if use_rom:
             scale = float(np.linalg.norm(rho_n)) if o["up_rel"] else 1.0
             thr = o["eps_up"] * scale
+            x_ig, b_ig = self.ig_pair(rho_n, btilde, f_new)
             if not self.flag_ig:
-                grew = self.ig.append(rho_n, btilde)
+                grew = self.ig.append(x_ig, b_ig)
                 ig_up = True
-                if self.ig.stop_ratio(grew) <= o["eps_ig"] or self.ig.rank >= o["r_max"]:
+                if self._built("ig_built", self.ig, grew, o["eps_ig"]):
                     self.flag_ig = True
             else:
                 ig_err = float(np.linalg.norm(rho_ig - rho_n))
-                if ig_err > thr:
-                    self.ig.append(rho_n, btilde, trunc_eps=o["eps_ig"])
+                if self.decide("ig_update", ig_err > thr, ig_err, thr):
+                    self.ig.append(x_ig, b_ig, trunc_eps=o["eps_ig"])
                     ig_up = True
-                d_rho1 = rho_n - info.rho_half_1
-                d_b1 = info.rho_half_1 - rho_ig
-                has_corr = info.iterations > 1
+                d_rho1, d_b1 = self.pc_pair(rho_n, info.rho_half_1, rho_ig)
+                has_corr = self.has_correction(info)
                 if not self.flag_pc:
                     if has_corr:
                         grew = self.pc.append(d_rho1, d_b1)
                         pc_up = True
-                        if self.pc.stop_ratio(grew) <= o["eps_pc"] or self.pc.rank >= o["r_max"]:
+                        if self._built("pc_built", self.pc, grew, o["eps_pc"]):
                             self.flag_pc = True
                 elif has_corr:
                     pc_err = float(np.linalg.norm(info.delta_pc_1 - d_rho1))
-                    if ig_up or pc_err > thr:
+                    if self.pc_update_due(ig_up, pc_err, thr):
                         self.pc.append(d_rho1, d_b1, trunc_eps=o["eps_pc"])
                         pc_up = True
         self.rho = rho_n
         self.f = f_new
         self.n += 1
         sweeps = info.iterations + 2
-        self.log.append(StepLog(self.n, phase, info.iterations, sweeps, info.cg_iterations,
-                                self.ig.rank, self.pc.rank, ig_up, pc_up, info.residual,
-                                ig_err, pc_err))
+        lg = StepLog(self.n, phase, info.iterations, sweeps, info.cg_iterations, self.ig.rank,
+                     self.pc.rank, ig_up, pc_up, info.residual, ig_err, pc_err)
+        if self.record:
+            lg.rho, lg.rho_half_1, lg.rho_init = rho_n.copy(), info.rho_half_1.copy(), rho0.copy()
+            lg.ig_s, lg.pc_s = self.ig.S.copy(), self.pc.S.copy()
+        self.log.append(lg)
