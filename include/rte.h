@@ -156,7 +156,10 @@ rte_status rte_set_inflow(rte_handle h, const double g[4]);
 
 /* Issue all further device work of h on the caller's CUDA stream (a cudaStream_t of the
  * handle's device, e.g. a torch stream); NULL returns to the handle's own stream.  The
- * handle does not take ownership; the stream must outlive its use by h. */
+ * handle does not take ownership; the stream must outlive its use by h.  The ROM update
+ * runs beside the fused f sweep on two side streams of the lowest priority, and the handle's
+ * own stream has the highest; give the caller's stream a high priority as well, or the ROM
+ * work competes with the sweep for SMs on equal terms. */
 rte_status rte_set_stream(rte_handle h, void* cuda_stream);
 
 /* Return to the state given by the last rte_set_initial (kept on the device): step counter,
@@ -199,7 +202,8 @@ void rte_destroy(rte_handle h);
  * without inflow, the FP32 refinement pair, both ROMs with their phase flags, the inflow
  * values and the statistics.  rte_load restores such a blob into a handle created with the
  * same mesh, quadrature, cross sections, source, c_dt and options; the mesh, the direction
- * layout, the precision and r_max are checked, the rest is the caller's to keep equal.
+ * layout, the precision, r_max, c_dt and a 64-bit digest (FNV-1a) of the cross sections and
+ * the source are checked, the other options are the caller's to keep equal.
  *   - The loaded march repeats the saved one bit for bit when the sweep configuration is
  *     also the same.  rte_stats reports it in its sweep_* fields.  It is the same within one
  *     process, where the measured choice is cached.  Fix it with the sweep_* options to
@@ -249,21 +253,21 @@ rte_status rte_op_rom_reset(rte_handle h);
  * pre-reserved memory budget (where a cudaMalloc can fail) or latency-critical code that
  * must not trigger the device-wide synchronisation of cudaMalloc / cudaFree.
  *
- * It computes the same DSA correction as rte_op_dsa, delta = C^{-1} (sigma_s .* residual)
- * (Eq. (rho_residual), CG from zero until ||r|| <= cg_rtol ||b||), for the mesh
- * [x0,x1] x [y0,y1] with nx * ny cells (dim = 1: ny = 1) and time step c_dt, on the stream
- * `stream` (a cudaStream_t, NULL = the legacy default stream) of the current device.
+ * It computes the same diffusion correction as rte_op_dsa: delta solves C delta =
+ * sigma_s .* residual, where C is the handle's cell-centred diffusion operator for the mesh
+ * [x0,x1] x [y0,y1] with nx * ny cells (dim = 1: ny = 1) and time step c_dt, by conjugate
+ * gradients from zero until ||r|| <= cg_rtol ||b||, on the stream `stream` (a
+ * cudaStream_t, NULL = the legacy default stream) of the current device.
  *   - sigma_t_dev, sigma_s_dev, residual_dev: device [nx*ny] inputs; delta_dev: device
  *     [nx*ny] output; all owned by the caller.  *iterations (host, may be NULL) = CG count.
  *   - All scratch (operator coefficients, CG vectors, reduction and barrier words) lives in
  *     one library-owned device array of fixed size, which every GPU that loads the library
  *     holds until the process exits.  nx * ny above 65536 is rejected with RTE_EINVAL.
- *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.  The first
- *     call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- *     first call before any stream capture.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.  Each call
+ *     looks up the array's device address on the current device (cudaGetSymbolAddress).
  *   - Every call shares the one array and leaves the last call's contents in it; calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on it.
- *   - The call waits for its stream to finish the solve before returning.
+ *   - The call blocks: it waits for its stream to finish the solve before returning.
  * Errors: RTE_EINVAL (sizes, NULL pointers), RTE_ECUDA, RTE_ETIMEOUT; the message is
  * available from rte_last_error(NULL) on the calling thread. */
 rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0,

@@ -16,13 +16,16 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 #include <vector>
 
 #include "rte_internal.h"
 
 namespace rte {
+
+struct DsaRow {
+  double diag, cx, cy;
+};
 
 namespace {
 constexpr int CT = 256;
@@ -371,41 +374,46 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
 
 }  // namespace
 
+// Row c of the diffusion operator C, shared by the handle's set-up (on the host) and the
+// allocation-free solve (on the device) so that both build the same operator bit for bit:
+// D = 1/(3 (sigma_t + tau)); interior face coupling max(2 D_L D_R / ((D_L + D_R) h), 1/4) / h;
+// vacuum (Marshak) face max(1 / (2 + h / (2 D)), 1/4) / h; diagonal sigma_t - sigma_s + tau
+// plus the couplings of the cell's faces, added in a fixed order (x: low face, high face;
+// then y).  cx / cy: the coupling to the +x / +y neighbour (0 on the last column / row).
+__host__ __device__ inline DsaRow dsa_row(int dim, int nx, int ny, int c, double hx, double hy,
+                                          double tau, const double* sig_t, const double* sig_s) {
+  const int i = c % nx, j = c / nx;
+  auto D = [&](int k) { return 1.0 / (3.0 * (sig_t[k] + tau)); };
+  auto face = [](double dl, double dr, double h) {
+    return fmax(2.0 * dl * dr / ((dl + dr) * h), 0.25) / h;
+  };
+  auto marshak = [](double d, double h) { return fmax(1.0 / (2.0 + h / (2.0 * d)), 0.25) / h; };
+  const double dc = D(c);
+  DsaRow row{sig_t[c] - sig_s[c] + tau, 0.0, 0.0};
+  row.diag += i > 0 ? face(D(c - 1), dc, hx) : marshak(dc, hx);
+  if (i + 1 < nx) row.cx = face(dc, D(c + 1), hx);
+  row.diag += i + 1 < nx ? row.cx : marshak(dc, hx);
+  if (dim == 2) {
+    row.diag += j > 0 ? face(D(c - nx), dc, hy) : marshak(dc, hy);
+    if (j + 1 < ny) row.cy = face(dc, D(c + nx), hy);
+    row.diag += j + 1 < ny ? row.cy : marshak(dc, hy);
+  }
+  return row;
+}
+
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
                       const double* sig_t, const double* sig_s, cudaStream_t s) {
   const int n = nx * ny;
   op.nx = nx;
   op.ny = ny;
   op.n = n;
-  std::vector<double> D(n), diag(n), cx(n, 0.0), cy(n, 0.0);
+  std::vector<double> diag(n), cx(n), cy(n);
   for (int c = 0; c < n; ++c) {
-    D[c] = 1.0 / (3.0 * (sig_t[c] + tau));
-    diag[c] = sig_t[c] - sig_s[c] + tau;
+    const DsaRow row = dsa_row(dim, nx, ny, c, hx, hy, tau, sig_t, sig_s);
+    diag[c] = row.diag;
+    cx[c] = row.cx;
+    cy[c] = row.cy;
   }
-  auto face = [](double dl, double dr, double h) { return fmax(2.0 * dl * dr / ((dl + dr) * h), 0.25) / h; };
-  auto marshak = [](double d, double h) { return fmax(1.0 / (2.0 + h / (2.0 * d)), 0.25) / h; };
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      const int c = i + nx * j;
-      if (i + 1 < nx) {
-        const double f = face(D[c], D[c + 1], hx);
-        cx[c] = f;
-        diag[c] += f;
-        diag[c + 1] += f;
-      }
-      if (i == 0) diag[c] += marshak(D[c], hx);
-      if (i == nx - 1) diag[c] += marshak(D[c], hx);
-      if (dim == 2) {
-        if (j + 1 < ny) {
-          const double f = face(D[c], D[c + nx], hy);
-          cy[c] = f;
-          diag[c] += f;
-          diag[c + nx] += f;
-        }
-        if (j == 0) diag[c] += marshak(D[c], hy);
-        if (j == ny - 1) diag[c] += marshak(D[c], hy);
-      }
-    }
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -506,59 +514,27 @@ constexpr int NOALLOC_MAX_BLOCKS = 512;
 constexpr long NOALLOC_DOUBLES = 8L * NOALLOC_MAX_CELLS + 2L * NOALLOC_MAX_BLOCKS + 8;
 static __device__ __align__(256) double g_dsa_noalloc_scratch[NOALLOC_DOUBLES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[MAX_DEVICES] = {};
-
-// Row c of the diffusion operator (same formulas as dsa_setup), one thread per cell.
+// The operator's coefficients on the device, one thread per cell (the row function of the
+// handle's set-up).
 __global__ void dsa_coeff_kernel(int dim, int nx, int ny, double hx, double hy, double tau,
                                  const double* sig_t, const double* sig_s, double* diag,
                                  double* cx, double* cy) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = nx * ny;
-  if (c >= n) return;
-  const int i = c % nx, j = c / nx;
-  auto D = [&](int k) { return 1.0 / (3.0 * (sig_t[k] + tau)); };
-  auto face = [](double dl, double dr, double h) { return fmax(2.0 * dl * dr / ((dl + dr) * h), 0.25) / h; };
-  auto marshak = [](double d, double h) { return fmax(1.0 / (2.0 + h / (2.0 * d)), 0.25) / h; };
-  const double dc = D(c);
-  double dg = sig_t[c] - sig_s[c] + tau;
-  double fx = 0.0, fy = 0.0;
-  if (i + 1 < nx) {
-    fx = face(dc, D(c + 1), hx);
-    dg += fx;
-  }
-  if (i > 0) dg += face(D(c - 1), dc, hx);
-  if (i == 0) dg += marshak(dc, hx);
-  if (i == nx - 1) dg += marshak(dc, hx);
-  if (dim == 2) {
-    if (j + 1 < ny) {
-      fy = face(dc, D(c + nx), hy);
-      dg += fy;
-    }
-    if (j > 0) dg += face(D(c - nx), dc, hy);
-    if (j == 0) dg += marshak(dc, hy);
-    if (j == ny - 1) dg += marshak(dc, hy);
-  }
-  diag[c] = dg;
-  cx[c] = fx;
-  cy[c] = fy;
+  if (c >= nx * ny) return;
+  const DsaRow row = dsa_row(dim, nx, ny, c, hx, hy, tau, sig_t, sig_s);
+  diag[c] = row.diag;
+  cx[c] = row.cx;
+  cy[c] = row.cy;
 }
 
-// Device address of the scratch array on the current device; looked up once per device.
+// Device address of the scratch array on the current device.  It is looked up on every call
+// (cheap, and it allocates nothing): after a cudaDeviceReset the library's module is loaded
+// again, possibly at another address, so a cached address could be stale.
 cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  double* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_dsa_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_dsa_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -616,6 +592,10 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   ++g_launches;
   dsa_coeff_kernel<<<(n + 255) / 256, 256, 0, s>>>(dim, nx, ny, hx, hy, 1.0 / c_dt, sigma_t_dev,
                                                    sigma_s_dev, diag, cx, cy);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    *err = std::string("rte_dsa_solve_noalloc: coefficient kernel: ") + cudaGetErrorString(e);
+    return RTE_ECUDA;
+  }
   CgArgs a{};
   a.nx = nx;
   a.ny = ny;
