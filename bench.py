@@ -137,7 +137,6 @@ def reduce_over_ranks(dist, total_ms, updates, device):
 
 def oracle_sample(wl, budget_s, min_steps=2):
     """Time the CPU oracle's march on the workload for about budget_s seconds."""
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
     from oracle import build as obuild, quadrature, stepper, transport
     obuild.build()
     mu, eta, w = quadrature.cl_hemisphere(*wl.quadrature[1:])
@@ -276,7 +275,8 @@ def run_ours(args):
 
     wl = inputs.checkerboard(n=args.n)
     nsteps = wl.steps
-    stream = torch.cuda.Stream()
+    # a high-priority stream: the library's ROM-update side streams run at the lowest priority
+    stream = torch.cuda.Stream(priority=-1)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def make(rom, precision=rte.RTE_FP64):

@@ -115,6 +115,9 @@ struct rte_s {
   int* cg_iters = nullptr;
   DsaOp dsa{};
   RomDev ig{}, pc{};
+  // FNV-1a digest of the host cross sections and source given to rte_create (checked by
+  // rte_load together with c_dt, so a blob of another problem on the same mesh is refused)
+  uint64_t problem_digest = 0;
   // state
   double g[4] = {0, 0, 0, 0};
   bool resp_ready = false;
@@ -1405,14 +1408,19 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   TRY(validate_impl(h, mesh, quad, sigma_t, sigma_s, source, c_dt, opt));
   const long n = h->ncell;
   CK(cudaGetDevice(&h->device));
-  CK(cudaStreamCreateWithFlags(&h->own_st, cudaStreamNonBlocking));
+  // The step's own stream runs at the highest priority and the two ROM-update streams at the
+  // lowest, so that the block scheduler hands freed SMs to the critical path (the fused f
+  // sweep) before the ROM appends queued beside it.
+  int prio_least = 0, prio_greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+  CK(cudaStreamCreateWithPriority(&h->own_st, cudaStreamNonBlocking, prio_greatest));
   h->st = h->own_st;
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
   CK(cudaEventCreate(&h->kev0));
   CK(cudaEventCreate(&h->kev1));
-  CK(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&h->st3, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithPriority(&h->st2, cudaStreamNonBlocking, prio_least));
+  CK(cudaStreamCreateWithPriority(&h->st3, cudaStreamNonBlocking, prio_least));
   CK(cudaEventCreateWithFlags(&h->ev_gate, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_pc, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_rho, cudaEventDisableTiming));
@@ -1435,6 +1443,14 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   TRY(upload(h, h->sig_t, sigma_t, n));
   TRY(upload(h, h->sig_s, sigma_s, n));
   TRY(upload(h, h->src, source, n));
+  {
+    uint64_t d = 1469598103934665603ull;   // FNV-1a, 64 bit, over the bytes of the three arrays
+    for (const double* a : {sigma_t, sigma_s, source}) {
+      const unsigned char* b = reinterpret_cast<const unsigned char*>(a);
+      for (size_t i = 0; i < sizeof(double) * (size_t)n; ++i) d = (d ^ b[i]) * 1099511628211ull;
+    }
+    h->problem_digest = d;
+  }
   if (h->fp32) {
     CK(dalloc(&h->sig_t_f, n));
     CK(dalloc(&h->sig_tl_f, n));
@@ -1501,10 +1517,12 @@ struct CkptHead {
   double g[4];
   int32_t y_valid, flag_ig, flag_pc, fcur;
   uint32_t bf_seed, reserved;
+  double c_dt;
+  uint64_t problem_digest;   // of sigma_t, sigma_s and the source
   rte_stats stats;
 };
 const char kCkptMagic[8] = {'R', 'T', 'E', 'C', 'K', 'P', 'T', '\0'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 struct StatePart {
   void* dev;
@@ -1840,6 +1858,8 @@ rte_status rte_save(rte_handle h, void* buf, size_t bytes) {
   hd.flag_pc = h->flag_pc ? 1 : 0;
   hd.fcur = h->fcur;
   hd.bf_seed = h->bf_seed;
+  hd.c_dt = h->c_dt;
+  hd.problem_digest = h->problem_digest;
   hd.stats = h->stats;
   unsigned char* out = static_cast<unsigned char*>(buf);
   std::memcpy(out, &hd, sizeof(hd));
@@ -1867,6 +1887,8 @@ rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
       hd.r_max != h->opt.r_max)
     return fail(h, RTE_EINVAL,
                 "checkpoint of another mesh, direction layout, precision or r_max");
+  if (hd.c_dt != h->c_dt || hd.problem_digest != h->problem_digest)
+    return fail(h, RTE_EINVAL, "checkpoint of another time step, cross sections or source");
   if (hd.bytes != bytes) return fail(h, RTE_EINVAL, "checkpoint length differs from its header");
   if (hd.fcur != 0 && hd.fcur != 1) return fail(h, RTE_EINVAL, "malformed checkpoint");
   // sizes first, so that a malformed blob changes nothing

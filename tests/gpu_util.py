@@ -11,6 +11,17 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def max_rel(a, b, floor=1e-3):
+    """Largest element-wise relative error |a - b| / (|b| + floor max|b|): a bad value in one
+    cell (a wrong tile edge, a dropped hand-off) shows here even where it hides in the L2
+    norm of a large array.  The floor keeps values many orders below the field's maximum
+    (deep in an absorber, where FP32 underflows first) from dominating."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    scale = np.abs(b) + floor * (np.max(np.abs(b)) if b.size else 0.0)
+    scale[scale == 0] = 1.0
+    return float(np.max(np.abs(a - b) / scale)) if b.size else 0.0
+
+
 def match_directions(h, quad_desc):
     """Permutation perm such that library direction d equals oracle direction perm[d]."""
     mu, eta, w = h.rte_get_quadrature()

@@ -42,9 +42,15 @@ def test_load_refuses_foreign_or_damaged_blobs():
     blob = a.rte_save()
     a.rte_step(2)
     rho = a.rte_get_scalar_flux()
+    other_dt = inputs.checkerboard(n=32)
+    other_dt.c_dt *= 2
+    other_sigma = inputs.checkerboard(n=32)
+    other_sigma.sigma_s = other_sigma.sigma_s.copy()
+    other_sigma.sigma_s[7] *= 0.5
     others = [rte.create_from_workload(inputs.checkerboard(n=16)),
               rte.create_from_workload(wl, options=rte.default_options(precision=rte.RTE_FP32)),
-              rte.create_from_workload(wl, options=rte.default_options(r_max=20))]
+              rte.create_from_workload(wl, options=rte.default_options(r_max=20)),
+              rte.create_from_workload(other_dt), rte.create_from_workload(other_sigma)]
     for o in others:
         with pytest.raises(rte.RteError) as e:
             o.rte_load(blob)

@@ -11,7 +11,7 @@ relative L2 of the FP64 oracle's march of the same algorithm."""
 import numpy as np
 import pytest
 
-from gpu_util import make_pair, match_directions, rel_l2
+from gpu_util import make_pair, match_directions, max_rel, rel_l2
 from oracle import stepper
 from oracle import transport as tr
 from paper_2603_19647_gb300 import inputs, rte
@@ -20,7 +20,15 @@ pytestmark = pytest.mark.gpu
 
 SWEEP_TOL = 2e-6
 MARCH_TOL = 1e-6
+# element-wise: every output value within 2e-5 of the FP64 value (relative, floored at 1e-3 of
+# the field's maximum): ten times the L2 bound, far below the O(1) error of a wrong value
+ELEM_TOL = 2e-5
 FP32 = dict(precision=rte.RTE_FP32)
+
+
+def _close(got, ref):
+    assert rel_l2(got, ref) < SWEEP_TOL
+    assert max_rel(got, ref) < ELEM_TOL
 
 
 def _hetero_2d(nx, ny, quad, seed):
@@ -42,7 +50,7 @@ def test_fp32_sweep_2d(shape, quad):
     h, p = make_pair(wl, **FP32)
     for _ in range(2):
         rho = rng.uniform(0, 1, wl.ncell)
-        assert rel_l2(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)) < SWEEP_TOL
+        _close(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho))
     h.destroy()
 
 
@@ -51,7 +59,7 @@ def test_fp32_tilings_fused_f(lanes, rows, warps):
     wl, rng = _hetero_2d(45, 53, (32, 8), seed=lanes * rows + warps)
     h, p = make_pair(wl, sweep_lanes=lanes, sweep_rows=rows, sweep_warps=warps, **FP32)
     rho = rng.uniform(0, 1, wl.ncell)
-    assert rel_l2(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)) < SWEEP_TOL
+    _close(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho))
     perm, _, _ = match_directions(h, wl.quadrature)
     f0 = rng.uniform(0, 1, (p.nv, wl.ncell))
     h.rte_set_initial(f0=f0[perm])
@@ -60,8 +68,8 @@ def test_fp32_tilings_fused_f(lanes, rows, warps):
     p.inflow = g
     bt = h.rte_op_fsweep(rho)
     f_ref, _ = tr.final_f(p, rho, f0)
-    assert rel_l2(h.rte_get_angular_flux(), f_ref[perm]) < SWEEP_TOL
-    assert rel_l2(bt, tr.b_tilde(p, f_ref)) < SWEEP_TOL
+    _close(h.rte_get_angular_flux(), f_ref[perm])
+    _close(bt, tr.b_tilde(p, f_ref))
     h.destroy()
 
 
@@ -79,7 +87,7 @@ def test_fp32_tile_kernel(lanes, th, warps, shape):
     assert st["sweep_si_kernel"] == 2 and st["sweep_f_kernel"] == 2
     for _ in range(2):
         rho = rng.uniform(0, 1, wl.ncell)
-        assert rel_l2(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)) < SWEEP_TOL
+        _close(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho))
     perm, _, _ = match_directions(h, wl.quadrature)
     f0 = rng.uniform(0, 1, (p.nv, wl.ncell))
     h.rte_set_initial(f0=f0[perm])
@@ -89,8 +97,8 @@ def test_fp32_tile_kernel(lanes, th, warps, shape):
     rho = rng.uniform(0, 1, wl.ncell)
     bt = h.rte_op_fsweep(rho)
     f_ref, _ = tr.final_f(p, rho, f0)
-    assert rel_l2(h.rte_get_angular_flux(), f_ref[perm]) < SWEEP_TOL
-    assert rel_l2(bt, tr.b_tilde(p, f_ref)) < SWEEP_TOL
+    _close(h.rte_get_angular_flux(), f_ref[perm])
+    _close(bt, tr.b_tilde(p, f_ref))
     h.destroy()
 
 
@@ -108,7 +116,7 @@ def test_fp32_sweep_1d(n, nd):
     wl.sigma_s, wl.sigma_t = ss, ss + rng.uniform(0.01, 1, n)
     h, p = make_pair(wl, **FP32)
     rho = rng.uniform(0, 1, n)
-    assert rel_l2(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)) < SWEEP_TOL
+    _close(h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho))
     h.destroy()
 
 

@@ -21,7 +21,7 @@ import numpy as np
 import pytest
 
 from conftest import oracle_problem
-from gpu_util import match_directions, rel_l2
+from gpu_util import match_directions, max_rel, rel_l2
 from oracle import dsa, rom
 from oracle import transport as tr
 from paper_2603_19647_gb300 import inputs, rte
@@ -39,7 +39,9 @@ def test_si_sweep_full_size(name, precision, tol):
     rho = np.random.default_rng(7).uniform(0.0, 1.0, wl.ncell)
     got = h.rte_op_sweep(rho)
     h.destroy()
-    assert rel_l2(got, tr.apply_T_sigma_s(oracle_problem(wl), rho)) < tol
+    ref = tr.apply_T_sigma_s(oracle_problem(wl), rho)
+    assert rel_l2(got, ref) < tol
+    assert max_rel(got, ref) < 10 * tol   # every cell, not only the norm
 
 
 @pytest.mark.parametrize("precision,tol", [(rte.RTE_FP64, 1e-12), (rte.RTE_FP32, 2e-6)])
@@ -63,6 +65,8 @@ def test_fused_sweep_full_size(precision, tol):
     f_ref, _ = tr.final_f(p, rho, f0)
     assert rel_l2(f_lib, f_ref[perm]) < tol
     assert rel_l2(bt, tr.b_tilde(p, f_ref)) < tol
+    assert max_rel(f_lib, f_ref[perm]) < 10 * tol   # every cell-direction
+    assert max_rel(bt, tr.b_tilde(p, f_ref)) < 10 * tol
 
 
 def test_dsa_full_size():
