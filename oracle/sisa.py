@@ -10,7 +10,9 @@ Readings where the paper leaves a choice:
   (mode "rel"); mode "abs" is the paper's absolute test.  "<=" instead of "<" so
   that an all-zero state counts as converged.
 * The SA step at l = 1 uses the ROM preconditioner when one is given (Sec. 3.2
-  Phase 3, Eq. (dmd-sa)); every other SA step is DSA (Eq. (rho_residual)).
+  Phase 3, Eq. (dmd-sa)); every other SA step is DSA (Eq. (rho_residual)).  With a sequence
+  of preconditioner ROMs (Sec. 3.2, key feature 1: ROMs for the first l - 1 iterations before
+  the one for iteration l), the SA step of iteration l uses the l-th ROM when there is one.
 """
 from dataclasses import dataclass
 
@@ -31,6 +33,11 @@ class SolveInfo:
     rho_half_1: np.ndarray = None   # rho^{n,(1/2)}, kept for the PC snapshot (Sec. 3.2 Phase 2)
     delta_pc_1: np.ndarray = None   # delta_rho_DMD^{n,(1)} when the ROM PC was applied at l = 1
     residual: float = 0.0
+    # per iteration l = 1, 2, ... (index l - 1): rho^{n,(l-1/2)}, rho^{n,(l-1)} and the ROM
+    # correction delta_rho_DMD^{n,(l)} (None where DSA was used)
+    rho_half: list = None
+    rho_prev: list = None
+    delta_pc: list = None
 
 
 def converged(diff, rho_half, eps, mode):
@@ -42,19 +49,25 @@ def converged(diff, rho_half, eps, mode):
 
 
 def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None, decide=None):
-    """Algorithm 1.  pc: callable(rhs) -> delta for the l = 1 SA step, or None for DSA only.
+    """Algorithm 1.  pc: callable(rhs) -> delta for the l = 1 SA step, or a list of such
+    callables for the SA steps l = 1, 2, ..., or None for DSA only.  The ROM correction of
+    iteration l maps the residual rho^{n,(l-1/2)} - rho^{n,(l-1)} to delta (Eq. (dmd-sa)).
     decide: optional callable(kind, own, value, threshold) -> bool that may replace the
     stopping decision ("si_stop"; value = the residual in the test's own units).
 
     Returns (rho^n, SolveInfo).  Raises NoConvergence after opts['max_iter'] sweeps.
     """
-    info = SolveInfo()
+    pcs = [] if pc is None else (list(pc) if isinstance(pc, (list, tuple)) else [pc])
+    info = SolveInfo(rho_half=[], rho_prev=[], delta_pc=[])
     rho_prev = np.array(rho_init, dtype=np.float64, copy=True)
     for l in range(1, opts["max_iter"] + 1):
         rho_half = _tr.apply_T_sigma_s(p, rho_prev) + btilde
         diff = rho_half - rho_prev
         if l == 1:
             info.rho_half_1 = rho_half.copy()
+        if l <= len(pcs) + 1:   # what the ROM snapshots of iteration l need
+            info.rho_half.append(rho_half.copy())
+            info.rho_prev.append(rho_prev.copy())
         ok, res = converged(diff, rho_half, opts["eps_sisa"], opts["residual_norm"])
         if decide is not None:
             ok = decide("si_stop", ok, res, opts["eps_sisa"])
@@ -62,10 +75,14 @@ def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None, decide=None):
         info.residual = res
         if ok:
             return rho_half, info
-        if l == 1 and pc is not None:
-            delta = pc(rho_half - rho_init)
-            info.delta_pc_1 = delta.copy()
+        if l <= len(pcs) and pcs[l - 1] is not None:
+            delta = pcs[l - 1](rho_half - rho_prev)
+            info.delta_pc.append(delta.copy())
+            if l == 1:
+                info.delta_pc_1 = delta.copy()
         else:
+            if l <= len(pcs):
+                info.delta_pc.append(None)
             delta, its = _dsa.dsa_correction(p, A_dsa, diff, opts["cg_rtol"], opts["cg_max_iter"])
             info.cg_iterations += its
         rho_prev = rho_half + delta

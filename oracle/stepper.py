@@ -37,7 +37,8 @@ from . import sisa as _sisa
 from . import transport as _tr
 
 DEFAULTS = dict(eps_sisa=1e-8, eps_ig=1e-6, eps_pc=1e-6, eps_up=1e-6, max_iter=500, r_max=40,
-                rom=True, residual_norm="rel", cg_rtol=1e-6, cg_max_iter=500, up_rel=True)
+                rom=True, residual_norm="rel", cg_rtol=1e-6, cg_max_iter=500, up_rel=True,
+                pc_levels=1)
 
 
 @dataclass
@@ -61,6 +62,9 @@ class StepLog:
     rho_init: np.ndarray = None
     ig_s: np.ndarray = None
     pc_s: np.ndarray = None
+    # every preconditioner ROM (iterations l = 1 .. pc_levels): ranks and updates
+    pc_ranks: tuple = ()
+    pc_ups: tuple = ()
 
 
 class OracleRTE:
@@ -76,10 +80,22 @@ class OracleRTE:
         self.f = np.zeros((problem.nv, problem.ncell))
         self.n = 0
         self.flag_ig = False
-        self.flag_pc = False
         self.ig = _rom.IncrementalSVD(problem.ncell, self.o["r_max"])
-        self.pc = _rom.IncrementalSVD(problem.ncell, self.o["r_max"])
+        # one preconditioner ROM per SI iteration l = 1 .. pc_levels, each with its Flag_PC
+        L = int(self.o["pc_levels"])
+        self.pcs = [_rom.IncrementalSVD(problem.ncell, self.o["r_max"]) for _ in range(L)]
+        self.flags_pc = [False] * L
         self.log = []
+
+    @property
+    def pc(self):
+        """The preconditioner ROM of the first iteration."""
+        return self.pcs[0]
+
+    @property
+    def flag_pc(self):
+        """Every preconditioner ROM is built (Phase 3)."""
+        return all(self.flags_pc)
 
     def set_initial(self, rho0, f0=None):
         """f^0 = rho0 in every direction (isotropic) unless f0 [nv, ncell] is given."""
@@ -110,18 +126,27 @@ class OracleRTE:
         """IG-ROM snapshot pair: (rho^n, b~^{n-1}), since A~ rho^n = b~^{n-1}."""
         return rho_n, btilde_prev
 
-    def pc_pair(self, rho_n, rho_half_1, rho_init):
-        """PC-ROM snapshot pair: the first correction rho^n - rho^{n,1/2} and its residual
-        rho^{n,1/2} - rho^{n,(0)} (Sec. 3.2, Phase 2)."""
-        return rho_n - rho_half_1, rho_half_1 - rho_init
+    def pc_pair(self, rho_n, info, level):
+        """PC-ROM snapshot pair of iteration l = level: the ideal correction
+        rho^n - rho^{n,(l-1/2)} and its residual rho^{n,(l-1/2)} - rho^{n,(l-1)} (Sec. 3.2,
+        Phase 2; for l = 1 the residual is measured from the initial guess rho^{n,(0)})."""
+        rho_half, rho_prev = info.rho_half[level - 1], info.rho_prev[level - 1]
+        return rho_n - rho_half, rho_half - rho_prev
 
-    def has_correction(self, info):
-        """A step whose first sweep met the stopping test took no correction."""
-        return info.iterations > 1
+    def sequential_ready(self, level, built_before):
+        """The ROM of iteration `level` takes snapshots only from steps that applied the ROMs of
+        all earlier iterations (Sec. 3.2, key feature 1)."""
+        return all(built_before[:level - 1])
+
+    def has_correction(self, info, level=1):
+        """A step that met the stopping test at iteration l <= level took no correction at
+        iteration `level`."""
+        return info.iterations > level
 
     def pc_update_due(self, ig_up, err, threshold):
-        """Phase 3 PC-ROM update: when the IG-ROM was updated in the same step, or when the
-        PC indicator exceeds the threshold (Sec. 3.2, Phase 3)."""
+        """Phase 3 PC-ROM update: when the IG-ROM (or, for the ROM of iteration l > 1, any ROM
+        of an earlier iteration) was updated in the same step, or when the PC indicator
+        exceeds the threshold (Sec. 3.2, Phase 3 and key feature 1)."""
         return ig_up or self.decide("pc_update", err > threshold, err, threshold)
 
     def _built(self, kind, svd, grew, eps):
@@ -133,6 +158,7 @@ class OracleRTE:
 
     def _step(self):
         p, o = self.p, self.o
+        L = len(self.pcs)
         phase = self.phase()
         btilde = _tr.b_tilde(p, self.f)
         use_rom = o["rom"]
@@ -142,13 +168,14 @@ class OracleRTE:
             rho0 = rho_ig
         else:
             rho0 = self.rho
-        pc = None
-        if use_rom and self.flag_pc:
-            pc = self.pc.solve_apply
-        rho_n, info = _sisa.si_sa(p, rho0, btilde, o, self.A, pc=pc, decide=self.decide)
+        # the ROM of iteration l applies once it and the ROMs of iterations 1 .. l-1 are built
+        pcs = [self.pcs[k].solve_apply if use_rom and all(self.flags_pc[:k + 1]) else None
+               for k in range(L)]
+        rho_n, info = _sisa.si_sa(p, rho0, btilde, o, self.A, pc=pcs, decide=self.decide)
         f_new, _ = _tr.final_f(p, rho_n, self.f)
-        ig_up = pc_up = False
-        ig_err = pc_err = float("nan")
+        ig_up = False
+        pc_ups, pc_errs = [False] * L, [float("nan")] * L
+        ig_err = float("nan")
         if use_rom:
             scale = float(np.linalg.norm(rho_n)) if o["up_rel"] else 1.0
             thr = o["eps_up"] * scale
@@ -163,26 +190,34 @@ class OracleRTE:
                 if self.decide("ig_update", ig_err > thr, ig_err, thr):
                     self.ig.append(x_ig, b_ig, trunc_eps=o["eps_ig"])
                     ig_up = True
-                d_rho1, d_b1 = self.pc_pair(rho_n, info.rho_half_1, rho_ig)
-                has_corr = self.has_correction(info)
-                if not self.flag_pc:
-                    if has_corr:
-                        grew = self.pc.append(d_rho1, d_b1)
-                        pc_up = True
-                        if self._built("pc_built", self.pc, grew, o["eps_pc"]):
-                            self.flag_pc = True
-                elif has_corr:
-                    pc_err = float(np.linalg.norm(info.delta_pc_1 - d_rho1))
-                    if self.pc_update_due(ig_up, pc_err, thr):
-                        self.pc.append(d_rho1, d_b1, trunc_eps=o["eps_pc"])
-                        pc_up = True
+                earlier_up = ig_up
+                built_before = list(self.flags_pc)   # as this step found them
+                for k in range(L):
+                    if not self.sequential_ready(k + 1, built_before):
+                        break
+                    if not self.has_correction(info, k + 1):
+                        break
+                    svd = self.pcs[k]
+                    d_rho, d_b = self.pc_pair(rho_n, info, k + 1)
+                    if not self.flags_pc[k]:
+                        grew = svd.append(d_rho, d_b)
+                        pc_ups[k] = True
+                        if self._built("pc_built", svd, grew, o["eps_pc"]):
+                            self.flags_pc[k] = True
+                    else:
+                        pc_errs[k] = float(np.linalg.norm(info.delta_pc[k] - d_rho))
+                        if self.pc_update_due(earlier_up, pc_errs[k], thr):
+                            svd.append(d_rho, d_b, trunc_eps=o["eps_pc"])
+                            pc_ups[k] = True
+                    earlier_up = earlier_up or pc_ups[k]
         self.rho = rho_n
         self.f = f_new
         self.n += 1
         sweeps = info.iterations + 2
         lg = StepLog(self.n, phase, info.iterations, sweeps, info.cg_iterations, self.ig.rank,
-                     self.pc.rank, ig_up, pc_up, info.residual, ig_err, pc_err)
+                     self.pcs[0].rank, ig_up, pc_ups[0], info.residual, ig_err, pc_errs[0],
+                     pc_ranks=tuple(v.rank for v in self.pcs), pc_ups=tuple(pc_ups))
         if self.record:
             lg.rho, lg.rho_half_1, lg.rho_init = rho_n.copy(), info.rho_half_1.copy(), rho0.copy()
-            lg.ig_s, lg.pc_s = self.ig.S.copy(), self.pc.S.copy()
+            lg.ig_s, lg.pc_s = self.ig.S.copy(), self.pcs[0].S.copy()
         self.log.append(lg)

@@ -87,8 +87,8 @@ class IGGateNeverOpens(stepper.OracleRTE):
 class ResidualAgainstPreviousRho(stepper.OracleRTE):
     """The PC residual snapshot rho^{n,1/2} - rho^{n-1} instead of rho^{n,1/2} - rho^{n,(0)}."""
 
-    def pc_pair(self, rho_n, rho_half_1, rho_init):
-        return rho_n - rho_half_1, rho_half_1 - self.rho
+    def pc_pair(self, rho_n, info, level):
+        return rho_n - info.rho_half[level - 1], info.rho_half[level - 1] - self.rho
 
 
 class PCGateAlwaysOpen(stepper.OracleRTE):
@@ -315,3 +315,66 @@ def test_construction_phases_end_where_lapack_says():
 @pytest.mark.parametrize("planted", [StopOnFirstRatio, BuildGateNeverCloses])
 def test_construction_pin_catches(planted):
     assert _construction_violations(planted)
+
+
+# ---- a second preconditioner ROM (iteration l = 2; Sec. 3.2, key feature 1) ----
+# A five-mode march with every ROM capped at rank 2 (r_max = 2) and the IG frozen
+# (eps_UP = 0.5 ||rho^n||): the ROM of iteration 1 is exact on a two-dimensional part of the
+# first corrections only, so Phase 3 with it alone takes four iterations.  The map from the
+# first-iteration error to the second-iteration error, e -> (T Sigma_s - P_1 A~) e with P_1 the
+# first ROM's correction, vanishes on that part, so the second-iteration errors span at most
+# the rest (two dimensions here): built sequentially, from steps that already applied the
+# first ROM, the second ROM is exact and every Phase 3 step ends at l = 3.
+LEVELS = dict(eps_sisa=1e-12, cg_rtol=1e-12, eps_ig=1e-6, eps_pc=1e-6, eps_up=0.5, r_max=2)
+
+
+class LevelsConcurrent(stepper.OracleRTE):
+    """The ROM of iteration 2 built at the same time as that of iteration 1, from steps whose
+    first iteration still used DSA."""
+
+    def sequential_ready(self, level, built_before):
+        return True
+
+
+class LevelTwoResidualFromInitialGuess(stepper.OracleRTE):
+    """The second-iteration residual snapshot measured from rho^{n,(0)} instead of rho^{n,(1)}."""
+
+    def pc_pair(self, rho_n, info, level):
+        return rho_n - info.rho_half[level - 1], info.rho_half[level - 1] - info.rho_prev[0]
+
+
+def _levels_violations(cls, levels=2):
+    p = _slab()
+    f0 = _span_start(p, [1.0, 0.7, 0.5, 0.4, 0.3])
+    r = _run(p, f0, 16, cls=cls, pc_levels=levels, **LEVELS)
+    bad = []
+    p3 = [s for s in r.log if s.phase == 3]
+    if len(p3) < 8:
+        return [f"Phase 3 for {len(p3)} steps (phases {[s.phase for s in r.log]})"]
+    want = 3 if levels == 2 else 4
+    for s in p3:
+        if s.iterations != want:
+            bad.append(f"step {s.n}: {s.iterations} iterations, {want} expected")
+        if any(s.pc_ups):
+            bad.append(f"step {s.n}: a preconditioner ROM changed without a reason")
+    if levels == 2:
+        # the second ROM started only once the first was built: its first snapshot comes from
+        # a step after the first ROM's last construction step
+        first_built = next(s.n for s in r.log if s.pc_ranks[0] == 2)
+        first_l2 = next((s.n for s in r.log if s.pc_ranks[1] > 0), None)
+        if first_l2 is None or first_l2 <= first_built:
+            bad.append(f"level 2 began at step {first_l2}, level 1 was built at {first_built}")
+    return bad
+
+
+def test_one_preconditioner_rom_leaves_four_iterations():
+    assert _levels_violations(stepper.OracleRTE, levels=1) == []
+
+
+def test_second_preconditioner_rom_is_exact_when_built_sequentially():
+    assert _levels_violations(stepper.OracleRTE) == []
+
+
+@pytest.mark.parametrize("planted", [LevelsConcurrent, LevelTwoResidualFromInitialGuess])
+def test_second_level_pin_catches(planted):
+    assert _levels_violations(planted)
