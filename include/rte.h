@@ -53,6 +53,7 @@ enum { RTE_FP64 = 0, RTE_FP32 = 1, RTE_FP32_BF16F = 2 };
 enum { RTE_REL_INF = 0, RTE_ABS_INF = 1 };
 enum { RTE_ROM_OFF = 0, RTE_ROM_AUTO = 1, RTE_ROM_MANUAL = 2 };
 enum { RTE_ROM_IG = 0, RTE_ROM_PC = 1 };
+#define RTE_MAX_PC_LEVELS 4   /* preconditioner ROMs: one per SI iteration l = 1 .. 4 at most */
 
 /* Uniform Cartesian mesh.  dim = 1: slab [x0,x1] with nx cells (ny must be 1);
  * dim = 2: [x0,x1] x [y0,y1] with nx*ny rectangles (Sec. 2.1). */
@@ -105,6 +106,14 @@ typedef struct {
                         sequence (sweep_rows then = rows per tile: 2 in the FP32 modes, 4 or 8) */
   int lookahead;     /* 1: queue SI iteration l+1 before reading the stopping test of l (work
                         past convergence skips itself on the device); 0 (default): wait first */
+  int pc_levels;     /* preconditioner ROMs, one for each of the first pc_levels SI iterations
+                        (1 .. RTE_MAX_PC_LEVELS; default 1, Algorithm 2 as printed).  The ROM of
+                        iteration l maps the residual rho^{n,(l-1/2)} - rho^{n,(l-1)} to the
+                        correction rho^n - rho^{n,(l-1/2)}; it is built only from steps that
+                        already applied the ROMs of iterations 1 .. l-1 (Sec. 3.2, key feature
+                        1), Phase 3 begins once all are built, and in Phase 3 each is updated
+                        when the IG-ROM or an earlier iteration's ROM was updated in the same
+                        step, or when its own indicator exceeds eps_up */
 } rte_options;
 
 typedef struct {
@@ -131,6 +140,10 @@ typedef struct {
    * per CTA of the SI sweep and of the fused f sweep; sweep_tuned = 1 when measured */
   int sweep_lanes, sweep_si_rows, sweep_si_warps, sweep_f_rows, sweep_f_warps, sweep_tuned;
   int sweep_si_kernel, sweep_f_kernel;   /* 1 strip chain, 2 tile sequence */
+  /* rank of the preconditioner ROM of each SI iteration l (index l - 1) and whether it was
+   * updated in the last step (the l = 1 entries repeat pc_rank and pc_updated) */
+  int pc_level_rank[RTE_MAX_PC_LEVELS];
+  int pc_level_updated[RTE_MAX_PC_LEVELS];
 } rte_stats;
 
 /* Fill *opt with the defaults listed above. */

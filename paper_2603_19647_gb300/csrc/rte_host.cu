@@ -57,13 +57,14 @@ struct rte_s {
   unsigned* h_err = nullptr;         // pinned copy of the sweeps' error word
   // ROM update queued on the device, finished on the host after the step's last wait
   struct RomPending {
-    bool queued = false, ig = false, pc = false, ig_building = false, pc_building = false;
-    bool ig_err = false, pc_err = false;
+    bool queued = false, ig = false, ig_building = false, ig_err = false;
+    bool pc[RTE_MAX_PC_LEVELS] = {}, pc_building[RTE_MAX_PC_LEVELS] = {},
+         pc_err[RTE_MAX_PC_LEVELS] = {};
   } rom_pend;
-  double* rom_dv = nullptr;        // [4] device scalars of the indicators
+  double* rom_dv = nullptr;        // [2 + levels] device scalars of the indicators
   double* h_rom_dv = nullptr;      // pinned copy
-  int* rom_gate = nullptr;         // [2] device gates (IG, PC)
-  double* rom_partials = nullptr;  // dot partials of the ROM stream
+  int* rom_gate = nullptr;         // [1 + levels] device gates (IG, PC of each iteration)
+  double* rom_partials = nullptr;  // dot partials of the ROM streams, [1 + levels][3 * 1024]
   // problem
   int dim = 2, nx = 0, ny = 0;
   long ncell = 0;
@@ -105,6 +106,15 @@ struct rte_s {
   double *y_ir = nullptr, *rho_ref = nullptr;   // y_ir = T Sigma_s rho_ref, accumulated in FP64
   // device: cell vectors
   double *rho = nullptr, *rho_prev = nullptr, *rho_half = nullptr, *rho_half1 = nullptr;
+  // preconditioner ROMs of iterations l = 2 .. pc_levels (index l - 1; l = 1 uses rho_half1,
+  // rho0, delta_pc1, tmp2, tmp3 and delta): rho^{n,(l-1/2)}, rho^{n,(l-1)}, the ROM correction,
+  // the snapshot pair and the indicator's difference
+  double* lv_half[RTE_MAX_PC_LEVELS] = {};
+  double* lv_prev[RTE_MAX_PC_LEVELS] = {};
+  double* lv_delta[RTE_MAX_PC_LEVELS] = {};
+  double* lv_x[RTE_MAX_PC_LEVELS] = {};
+  double* lv_b[RTE_MAX_PC_LEVELS] = {};
+  double* lv_diff[RTE_MAX_PC_LEVELS] = {};
   double *rho0 = nullptr, *y = nullptr, *btilde = nullptr, *q = nullptr, *delta = nullptr;
   double *tmp = nullptr, *tmp2 = nullptr, *tmp3 = nullptr, *delta_pc1 = nullptr;
   double* resp[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -114,7 +124,10 @@ struct rte_s {
   Norms* norms = nullptr;
   int* cg_iters = nullptr;
   DsaOp dsa{};
-  RomDev ig{}, pc{};
+  RomDev ig{};
+  RomDev pcs[RTE_MAX_PC_LEVELS]{};   // preconditioner ROM of SI iteration l at index l - 1
+  RomDev& pc = pcs[0];
+  int levels = 1;                    // options.pc_levels
   // FNV-1a digest of the host cross sections and source given to rte_create (checked by
   // rte_load together with c_dt, so a blob of another problem on the same mesh is refused)
   uint64_t problem_digest = 0;
@@ -122,10 +135,12 @@ struct rte_s {
   double g[4] = {0, 0, 0, 0};
   bool resp_ready = false;
   bool y_valid = false;
-  bool flag_ig = false, flag_pc = false;
+  bool flag_ig = false;
+  bool flags_pc[RTE_MAX_PC_LEVELS] = {};   // Flag_PC of each iteration's ROM
   bool pending_rom = false;  // RTE_ROM_MANUAL: a step is waiting for rte_rom_update
   // per-step record kept for the ROM update
-  bool ig_applied = false, pc_applied = false;
+  bool ig_applied = false;
+  bool pc_applied[RTE_MAX_PC_LEVELS] = {};
   int last_iters = 0;
   rte_stats stats{};
 };
@@ -336,7 +351,13 @@ void free_all(rte_handle h) {
     if (p) cudaFree(p);
   dsa_free(h->dsa);
   rom_free(h->ig);
-  rom_free(h->pc);
+  for (auto& R : h->pcs) rom_free(R);
+  for (int k = 0; k < RTE_MAX_PC_LEVELS; ++k) {
+    double* lv[] = {h->lv_half[k], h->lv_prev[k], h->lv_delta[k], h->lv_x[k], h->lv_b[k],
+                    h->lv_diff[k]};
+    for (double* q : lv)
+      if (q) cudaFree(q);
+  }
   cudaEvent_t evs[] = {h->ev0,    h->ev1,    h->kev0,    h->kev1, h->ev_rho,
                        h->ev_r0, h->ev_r1, h->ev_gate, h->ev_pc};
   for (cudaEvent_t e : evs)
@@ -726,7 +747,9 @@ void resolve_spans(rte_handle h) {
 // few microseconds, less than the skipped launches cost, so lookahead is off by default.
 // ---------------------------------------------------------------------------------------
 // init_src: the initial guess when it is not in rho0 yet (it is then copied to rho0 too).
-rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
+// pc_active: the SA steps of iterations 1 .. pc_active use the preconditioner ROMs of those
+// iterations (Eq. (dmd-sa)); every other SA step is DSA.
+rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_out,
                  const double* init_src) {
   const int n = (int)h->ncell;
   const int nb = vec_blocks(n);
@@ -744,6 +767,10 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
   // FP64 y_ir = T Sigma_s rho_ref, so rho^{l-1/2} = y_ir + b~ carries FP64 accuracy in the
   // residual; the first increment is measured from the last swept iterate of the previous step.
   auto sweep_increment = [&](int iter) -> rte_status {
+    // rho^{n,(iter-1)} for the snapshot pair of the preconditioner ROM of iteration iter >= 2
+    if (iter >= 2 && iter <= h->levels)
+      CK(cudaMemcpyAsync(h->lv_prev[iter - 1], h->rho_prev, sizeof(double) * n,
+                         cudaMemcpyDeviceToDevice, h->st));
     const int k0 = rec(h);
     if (h->fp32) {
       CK(launch_scaled_diff_update<float>(h->rho_prev, h->rho_ref, h->sig_s, n, h->q_f, h->st,
@@ -766,7 +793,8 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
   auto residual = [&](int l) -> rte_status {
     const int p = l & 1;
     const int r0 = rec(h);
-    double* half1 = l == 1 ? h->rho_half1 : nullptr;
+    // rho^{n,(l-1/2)} kept for the snapshot pairs of the preconditioner ROM of iteration l
+    double* half1 = l == 1 ? h->rho_half1 : (l <= h->levels ? h->lv_half[l - 1] : nullptr);
     if (h->fp32)
       CK(launch_combine_residual(h->y_ir, 1, h->btilde, h->rho_prev, n, h->rho_half, h->partials,
                                  nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa, absmode,
@@ -791,11 +819,11 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
   };
   bool conv = false;
   int l = 1;
-  h->pc_applied = false;
+  for (bool& a : h->pc_applied) a = false;
   TRY(sweep_increment(1));
   TRY(residual(1));
   for (l = 1;; ++l) {
-    const bool pc_now = l == 1 && use_pc;
+    const bool pc_now = l <= pc_active;
     if (h->opt.lookahead && l < h->opt.max_iter && !pc_now) {   // iteration l + 1, queued ahead
       TRY(dsa_step(l));
       TRY(sweep_increment(l + 1));
@@ -814,15 +842,18 @@ rte_status si_sa(rte_handle h, bool use_pc, int* iters_out, bool* converged_out,
       TRY(residual(l + 1));
     }
     if (pc_now) {
-      // ROM preconditioner, Eq. (dmd-sa): delta = dU C_r^{-1} dU^T (rho^{1/2} - rho^{(0)})
+      // ROM preconditioner of iteration l, Eq. (dmd-sa):
+      // delta = dU C_r^{-1} dU^T (rho^{l-1/2} - rho^{l-1})  (rho^{0} = the initial guess)
+      const int k = l - 1;
+      double* dpc = k == 0 ? h->delta_pc1 : h->lv_delta[k];
       const int r0 = rec(h);
-      CK(launch_axpby(1.0, h->rho_half, -1.0, h->rho0, n, h->tmp, h->st));
-      CK(rom_apply(h->pc, h->tmp, h->delta_pc1, h->st));
-      CK(launch_update_rho(h->rho_half, h->delta_pc1, h->sig_s, n, h->rho_prev, h->q, h->st));
-      span(h, SPAN_ROM, r0, rec(h), 2);
-      h->pc_applied = true;
-      TRY(sweep_increment(2));
-      TRY(residual(2));
+      CK(launch_axpby(1.0, h->rho_half, -1.0, h->rho_prev, n, h->tmp, h->st));
+      CK(rom_apply(h->pcs[k], h->tmp, dpc, h->st));
+      CK(launch_update_rho(h->rho_half, dpc, h->sig_s, n, h->rho_prev, h->q, h->st));
+      span(h, SPAN_ROM, r0, rec(h), l + 1);
+      h->pc_applied[k] = true;
+      TRY(sweep_increment(l + 1));
+      TRY(residual(l + 1));
     }
   }
   h->skip_now = nullptr;
@@ -862,8 +893,8 @@ rte_status rom_update_enqueue(rte_handle h) {
   const int nb = vec_blocks(n);
   auto& pd = h->rom_pend;
   pd = rte_s::RomPending{};
-  double* dv = h->rom_dv;   // [0] ||rho^n||^2  [1] IG indicator^2  [2] PC indicator^2
-  double* part_pc = h->rom_partials + 3 * 1024;
+  double* dv = h->rom_dv;   // [0] ||rho^n||^2  [1] IG indicator^2  [2 + k] PC indicator^2 of
+                            // iteration k + 1
   CK(launch_dot(h->rho, h->rho, n, h->rom_partials, nb, dv + 0, h->st));
   if (!h->flag_ig) {
     // Phase 1: the IG-ROM takes every snapshot pair (rho^n, b~^{n-1}), untruncated
@@ -883,31 +914,47 @@ rte_status rom_update_enqueue(rte_handle h) {
     CK(rom_append_async(h->ig, h->rho, h->btilde, h->opt.eps_ig, h->rom_gate + 0, h->st));
     pd.ig = true;
     pd.ig_err = h->ig_applied;
-    const bool has_corr = h->last_iters > 1;
     cudaStream_t s3 = h->st3;
-    // d_rho1 = rho^n - rho^{n,1/2} (tmp2), d_b1 = rho^{n,1/2} - rho^{n,(0)} (tmp3)
-    CK(launch_axpby(1.0, h->rho, -1.0, h->rho_half1, n, h->tmp2, s3));
-    CK(launch_axpby(1.0, h->rho_half1, -1.0, h->rho0, n, h->tmp3, s3));
-    if (!h->flag_pc) {
-      if (has_corr) {   // Phase 2: the PC-ROM takes every correction pair, untruncated
-        CK(rom_append_async(h->pc, h->tmp2, h->tmp3, -1.0, nullptr, s3));
-        pd.pc = pd.pc_building = true;
+    bool built_before[RTE_MAX_PC_LEVELS];
+    for (int k = 0; k < RTE_MAX_PC_LEVELS; ++k) built_before[k] = h->flags_pc[k];
+    const int* also = h->rom_gate + 0;   // an update of the IG-ROM forces one of the PC-ROMs
+    for (int k = 0; k < h->levels; ++k) {
+      // sequential construction: the ROM of iteration k+1 takes snapshots only from steps that
+      // applied the ROMs of iterations 1 .. k; and only from steps that took a correction at
+      // iteration k+1
+      if (k > 0 && !built_before[k - 1]) break;
+      if (!(h->last_iters > k + 1)) break;
+      double* half = k == 0 ? h->rho_half1 : h->lv_half[k];
+      const double* prev = k == 0 ? h->rho0 : h->lv_prev[k];
+      double* x = k == 0 ? h->tmp2 : h->lv_x[k];
+      double* b = k == 0 ? h->tmp3 : h->lv_b[k];
+      // d_rho = rho^n - rho^{n,(k+1/2)} (x), d_b = rho^{n,(k+1/2)} - rho^{n,(k)} (b)
+      CK(launch_axpby(1.0, h->rho, -1.0, half, n, x, s3));
+      CK(launch_axpby(1.0, half, -1.0, prev, n, b, s3));
+      if (!h->flags_pc[k]) {   // construction: every correction pair, untruncated
+        CK(rom_append_async(h->pcs[k], x, b, -1.0, nullptr, s3));
+        pd.pc[k] = pd.pc_building[k] = true;
+      } else {
+        double* diff = k == 0 ? h->delta : h->lv_diff[k];
+        const double* dpc = k == 0 ? h->delta_pc1 : h->lv_delta[k];
+        double* part = h->rom_partials + (size_t)(1 + k) * 3 * 1024;
+        if (h->pc_applied[k]) {
+          CK(launch_axpby(1.0, dpc, -1.0, x, n, diff, s3));
+          CK(launch_dot(diff, diff, n, part, nb, dv + 2 + k, s3));
+        }
+        CK(launch_rom_gate(dv + 2 + k, dv + 0, h->opt.eps_up, h->opt.up_rel, !h->pc_applied[k],
+                           also, h->rom_gate + 1 + k, s3));
+        CK(rom_append_async(h->pcs[k], x, b, h->opt.eps_pc, h->rom_gate + 1 + k, s3));
+        pd.pc[k] = true;
+        pd.pc_err[k] = h->pc_applied[k];
+        also = h->rom_gate + 1 + k;
       }
-    } else if (has_corr) {
-      if (h->pc_applied) {
-        CK(launch_axpby(1.0, h->delta_pc1, -1.0, h->tmp2, n, h->delta, s3));
-        CK(launch_dot(h->delta, h->delta, n, part_pc, nb, dv + 2, s3));
-      }
-      CK(launch_rom_gate(dv + 2, dv + 0, h->opt.eps_up, h->opt.up_rel, !h->pc_applied,
-                         h->rom_gate + 0, h->rom_gate + 1, s3));
-      CK(rom_append_async(h->pc, h->tmp2, h->tmp3, h->opt.eps_pc, h->rom_gate + 1, s3));
-      pd.pc = true;
-      pd.pc_err = h->pc_applied;
     }
     CK(cudaEventRecord(h->ev_pc, s3));
     CK(cudaStreamWaitEvent(h->st, h->ev_pc, 0));
   }
-  CK(cudaMemcpyAsync(h->h_rom_dv, dv, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_rom_dv, dv, sizeof(double) * (2 + h->levels), cudaMemcpyDeviceToHost,
+                     h->st));
   pd.queued = true;
   return RTE_OK;
 }
@@ -916,23 +963,37 @@ rte_status rom_update_finish(rte_handle h) {
   auto& pd = h->rom_pend;
   if (!pd.queued) return RTE_OK;
   pd.queued = false;
-  int ig_ran = 0, pc_ran = 0;
+  int ig_ran = 0;
+  int pc_ran[RTE_MAX_PC_LEVELS] = {};
   double ratio = 0.0;
   if (pd.ig) {
     CK(rom_commit(h->ig, &ig_ran, nullptr, &ratio, h->st));
     if (pd.ig_building && (ratio <= h->opt.eps_ig || h->ig.rank >= h->opt.r_max)) h->flag_ig = true;
   }
-  if (pd.pc) {
-    CK(rom_commit(h->pc, &pc_ran, nullptr, &ratio, h->st));
-    if (pd.pc_building && (ratio <= h->opt.eps_pc || h->pc.rank >= h->opt.r_max)) h->flag_pc = true;
+  for (int k = 0; k < h->levels; ++k) {
+    if (!pd.pc[k]) continue;
+    CK(rom_commit(h->pcs[k], &pc_ran[k], nullptr, &ratio, h->st));
+    if (pd.pc_building[k] && (ratio <= h->opt.eps_pc || h->pcs[k].rank >= h->opt.r_max))
+      h->flags_pc[k] = true;
   }
   h->stats.last_ig_error = pd.ig_err ? std::sqrt(h->h_rom_dv[1]) : NAN;
-  h->stats.last_pc_error = pd.pc_err ? std::sqrt(h->h_rom_dv[2]) : NAN;
+  h->stats.last_pc_error = pd.pc_err[0] ? std::sqrt(h->h_rom_dv[2]) : NAN;
   h->stats.ig_updated = ig_ran;
-  h->stats.pc_updated = pc_ran;
+  h->stats.pc_updated = pc_ran[0];
   h->stats.ig_rank = h->ig.rank;
   h->stats.pc_rank = h->pc.rank;
+  for (int k = 0; k < RTE_MAX_PC_LEVELS; ++k) {
+    h->stats.pc_level_rank[k] = h->pcs[k].rank;
+    h->stats.pc_level_updated[k] = pc_ran[k];
+  }
   return RTE_OK;
+}
+
+// All preconditioner ROMs built: Phase 3.
+bool all_pc_built(rte_handle h) {
+  for (int k = 0; k < h->levels; ++k)
+    if (!h->flags_pc[k]) return false;
+  return true;
 }
 
 rte_status one_step(rte_handle h) {
@@ -954,14 +1015,17 @@ rte_status one_step(rte_handle h) {
     m = rec(h);
     span(h, SPAN_ROM, mark, m);
   }
-  const bool use_pc = rom_on && h->flag_pc && h->pc.lu_ok;
+  // the ROM of iteration l applies once it and the ROMs of iterations 1 .. l-1 are built
+  int pc_active = 0;
+  while (rom_on && pc_active < h->levels && h->flags_pc[pc_active] && h->pcs[pc_active].lu_ok)
+    ++pc_active;
   int iters = 0;
   bool conv = false;
   // without the IG the initial guess is rho^{n-1} itself
-  TRY(si_sa(h, use_pc, &iters, &conv, h->ig_applied ? nullptr : h->rho));
+  TRY(si_sa(h, pc_active, &iters, &conv, h->ig_applied ? nullptr : h->rho));
   h->last_iters = iters;
   // the phase this step ran in (the ROM update below may end it)
-  const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!h->flag_pc ? 2 : 3));
+  const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!all_pc_built(h) ? 2 : 3));
   // rho^n is final: the ROM update may start beside the fused sweep
   CK(cudaEventRecord(h->ev_rho, h->st));
   // f^n and the next step's b~ (without inflow): Eq. (sweep_to_obtain_f), Eq. (implicit_linear_system_rho)
@@ -1045,11 +1109,12 @@ rte_status reset_state(rte_handle h) {
   h->stats = rte_stats{};
   h->rom_pend = rte_s::RomPending{};
   h->bf_seed = 0;
-  h->flag_ig = h->flag_pc = false;
+  h->flag_ig = false;
+  for (bool& f : h->flags_pc) f = false;
   h->y_valid = false;
   h->pending_rom = false;
   rom_reset(h->ig);
-  rom_reset(h->pc);
+  for (int k = 0; k < h->levels; ++k) rom_reset(h->pcs[k]);
   return RTE_OK;
 }
 
@@ -1370,6 +1435,10 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   h->fp32 = h->opt.precision != RTE_FP64;
   h->bf16 = h->opt.precision == RTE_FP32_BF16F;
   if (h->opt.r_max < 1 || h->opt.r_max > 64) return fail(h, RTE_EINVAL, "r_max must be in [1, 64]");
+  if (h->opt.pc_levels == 0) h->opt.pc_levels = 1;   // options zeroed by hand: the default
+  if (h->opt.pc_levels < 1 || h->opt.pc_levels > RTE_MAX_PC_LEVELS)
+    return fail(h, RTE_EINVAL, "pc_levels must be in [1, RTE_MAX_PC_LEVELS]");
+  h->levels = h->opt.pc_levels;
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
       h->opt.sweep_lanes != 32)
@@ -1428,14 +1497,14 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(cudaEventCreate(&h->ev_r1));
   CK(cudaMallocHost((void**)&h->h_norms, 2 * sizeof(Norms)));
   CK(cudaMallocHost((void**)&h->h_cg, sizeof(int) * (h->opt.max_iter + 2)));
-  CK(cudaMallocHost((void**)&h->h_rom_dv, sizeof(double) * 4));
+  CK(cudaMallocHost((void**)&h->h_rom_dv, sizeof(double) * (2 + RTE_MAX_PC_LEVELS)));
   CK(cudaMallocHost((void**)&h->h_err, 2 * sizeof(unsigned)));
   h->h_err[0] = h->h_err[1] = 0;
   CK(cudaEventCreateWithFlags(&h->ev_wait, cudaEventBlockingSync | cudaEventDisableTiming));
-  CK(cudaMalloc((void**)&h->rom_dv, sizeof(double) * 4));
-  CK(cudaMemset(h->rom_dv, 0, sizeof(double) * 4));
-  CK(cudaMalloc((void**)&h->rom_gate, sizeof(int) * 2));
-  CK(dalloc(&h->rom_partials, 2 * 3 * 1024));
+  CK(cudaMalloc((void**)&h->rom_dv, sizeof(double) * (2 + RTE_MAX_PC_LEVELS)));
+  CK(cudaMemset(h->rom_dv, 0, sizeof(double) * (2 + RTE_MAX_PC_LEVELS)));
+  CK(cudaMalloc((void**)&h->rom_gate, sizeof(int) * (1 + RTE_MAX_PC_LEVELS)));
+  CK(dalloc(&h->rom_partials, (size_t)(1 + RTE_MAX_PC_LEVELS) * 3 * 1024));
   // data that does not depend on the direction layout
   CK(dalloc(&h->sig_t, n));
   CK(dalloc(&h->sig_s, n));
@@ -1499,7 +1568,16 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   TRY(alloc_sweep(h));
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st));
   CK(rom_alloc(h->ig, (int)n, h->opt.r_max));
-  CK(rom_alloc(h->pc, (int)n, h->opt.r_max));
+  for (int k = 0; k < h->levels; ++k) {
+    CK(rom_alloc(h->pcs[k], (int)n, h->opt.r_max));
+    if (k == 0) continue;
+    double** lv[] = {&h->lv_half[k], &h->lv_prev[k], &h->lv_delta[k], &h->lv_x[k], &h->lv_b[k],
+                     &h->lv_diff[k]};
+    for (double** q : lv) {
+      CK(dalloc(q, n));
+      CK(cudaMemsetAsync(*q, 0, sizeof(double) * n, h->st));
+    }
+  }
   CK(cudaStreamSynchronize(h->st));
   return reset_state(h);
 }
@@ -1557,6 +1635,12 @@ size_t state_fixed_bytes(rte_handle h) {
   return b;
 }
 
+size_t rom_state_bytes_pcs(rte_handle h) {
+  size_t b = 0;
+  for (int k = 0; k < h->levels; ++k) b += rom_state_bytes(h->pcs[k]);
+  return b;
+}
+
 rte_status sync_streams(rte_handle h) {
   CK(cudaStreamSynchronize(h->st));
   if (h->st2) CK(cudaStreamSynchronize(h->st2));
@@ -1588,6 +1672,7 @@ void rte_default_options(rte_options* o) {
   o->cg_max_iter = 500;
   o->tune = 1;
   o->lookahead = 0;
+  o->pc_levels = 1;
 }
 
 rte_status rte_create(rte_handle* out, const rte_mesh* mesh, const rte_quadrature* quad,
@@ -1828,7 +1913,7 @@ rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta
 rte_status rte_save_size(rte_handle h, size_t* bytes) {
   if (!h || !bytes) return RTE_EINVAL;
   *bytes = sizeof(CkptHead) + state_fixed_bytes(h) + rom_state_bytes(h->ig) +
-           rom_state_bytes(h->pc);
+           rom_state_bytes_pcs(h);
   return RTE_OK;
 }
 
@@ -1855,7 +1940,9 @@ rte_status rte_save(rte_handle h, void* buf, size_t bytes) {
   for (int s = 0; s < 4; ++s) hd.g[s] = h->g[s];
   hd.y_valid = h->y_valid ? 1 : 0;
   hd.flag_ig = h->flag_ig ? 1 : 0;
-  hd.flag_pc = h->flag_pc ? 1 : 0;
+  hd.flag_pc = 0;
+  for (int k = 0; k < h->levels; ++k) hd.flag_pc |= h->flags_pc[k] ? 1 << k : 0;
+  hd.reserved = (uint32_t)h->levels;
   hd.fcur = h->fcur;
   hd.bf_seed = h->bf_seed;
   hd.c_dt = h->c_dt;
@@ -1871,7 +1958,10 @@ rte_status rte_save(rte_handle h, void* buf, size_t bytes) {
   CK(cudaStreamSynchronize(h->st));
   CK(rom_save(h->ig, out, h->st));
   out += rom_state_bytes(h->ig);
-  CK(rom_save(h->pc, out, h->st));
+  for (int k = 0; k < h->levels; ++k) {
+    CK(rom_save(h->pcs[k], out, h->st));
+    out += rom_state_bytes(h->pcs[k]);
+  }
   return RTE_OK;
 }
 
@@ -1884,9 +1974,9 @@ rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
     return fail(h, RTE_EINVAL, "not a checkpoint of this library version");
   if (hd.dim != h->dim || hd.nx != h->nx || hd.ny != h->ny || hd.nslot != h->L.nslot ||
       hd.dl != h->L.dl || hd.nfam != h->L.nfam || hd.precision != h->opt.precision ||
-      hd.r_max != h->opt.r_max)
+      hd.r_max != h->opt.r_max || hd.reserved != (uint32_t)h->levels)
     return fail(h, RTE_EINVAL,
-                "checkpoint of another mesh, direction layout, precision or r_max");
+                "checkpoint of another mesh, direction layout, precision, r_max or pc_levels");
   if (hd.c_dt != h->c_dt || hd.problem_digest != h->problem_digest)
     return fail(h, RTE_EINVAL, "checkpoint of another time step, cross sections or source");
   if (hd.bytes != bytes) return fail(h, RTE_EINVAL, "checkpoint length differs from its header");
@@ -1897,9 +1987,15 @@ rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
   const size_t fixed = state_fixed_bytes(h);
   if (left < fixed) return fail(h, RTE_EINVAL, "checkpoint truncated");
   const size_t b_ig = rom_checked_bytes(h->ig, in + fixed, left - fixed);
-  const size_t b_pc = b_ig ? rom_checked_bytes(h->pc, in + fixed + b_ig, left - fixed - b_ig) : 0;
-  if (!b_ig || !b_pc || fixed + b_ig + b_pc != left)
-    return fail(h, RTE_EINVAL, "malformed ROM part of the checkpoint");
+  size_t b_pc[RTE_MAX_PC_LEVELS] = {};
+  size_t used = fixed + b_ig;
+  bool ok = b_ig != 0;
+  for (int k = 0; k < h->levels && ok; ++k) {
+    b_pc[k] = rom_checked_bytes(h->pcs[k], in + used, left - used);
+    ok = b_pc[k] != 0;
+    used += b_pc[k];
+  }
+  if (!ok || used != left) return fail(h, RTE_EINVAL, "malformed ROM part of the checkpoint");
   TRY(sync_streams(h));
   for (const auto& p : state_parts(h)) {
     CK(cudaMemcpyAsync(p.dev, in, p.bytes, cudaMemcpyHostToDevice, h->st));
@@ -1907,11 +2003,16 @@ rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
   }
   CK(cudaStreamSynchronize(h->st));
   CK(rom_load(h->ig, in, h->st));
-  CK(rom_load(h->pc, in + b_ig, h->st));
+  in += b_ig;
+  for (int k = 0; k < h->levels; ++k) {
+    CK(rom_load(h->pcs[k], in, h->st));
+    in += b_pc[k];
+  }
   for (int s = 0; s < 4; ++s) h->g[s] = hd.g[s];
   h->y_valid = hd.y_valid != 0;
   h->flag_ig = hd.flag_ig != 0;
-  h->flag_pc = hd.flag_pc != 0;
+  for (int k = 0; k < RTE_MAX_PC_LEVELS; ++k)
+    h->flags_pc[k] = k < h->levels && (hd.flag_pc & (1 << k)) != 0;
   h->fcur = hd.fcur;
   h->bf_seed = hd.bf_seed;
   h->stats = hd.stats;
@@ -1925,6 +2026,7 @@ rte_status rte_get_stats(rte_handle h, rte_stats* st) {
   *st = h->stats;
   st->ig_rank = h->ig.rank;
   st->pc_rank = h->pc.rank;
+  for (int k = 0; k < RTE_MAX_PC_LEVELS; ++k) st->pc_level_rank[k] = h->pcs[k].rank;
   if (h->dim == 2) {
     st->sweep_lanes = h->L.dl;
     st->sweep_si_rows = h->tile[0].R;
@@ -2056,8 +2158,9 @@ rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, 
 rte_status rte_op_rom_reset(rte_handle h) {
   if (!h) return RTE_EINVAL;
   rom_reset(h->ig);
-  rom_reset(h->pc);
-  h->flag_ig = h->flag_pc = false;
+  for (int k = 0; k < h->levels; ++k) rom_reset(h->pcs[k]);
+  h->flag_ig = false;
+  for (bool& f : h->flags_pc) f = false;
   return RTE_OK;
 }
 

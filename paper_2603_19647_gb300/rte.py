@@ -28,6 +28,9 @@ class RteError(RuntimeError):
         self.status = status
 
 
+MAX_PC_LEVELS = 4   # RTE_MAX_PC_LEVELS
+
+
 class Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
@@ -55,7 +58,7 @@ class Options(ctypes.Structure):
                 ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int),
                 ("sweep_rows", ctypes.c_int), ("sweep_lanes", ctypes.c_int),
                 ("sweep_warps", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
-                ("lookahead", ctypes.c_int)]
+                ("lookahead", ctypes.c_int), ("pc_levels", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -73,10 +76,15 @@ class Stats(ctypes.Structure):
                 ("sweep_lanes", ctypes.c_int), ("sweep_si_rows", ctypes.c_int),
                 ("sweep_si_warps", ctypes.c_int), ("sweep_f_rows", ctypes.c_int),
                 ("sweep_f_warps", ctypes.c_int), ("sweep_tuned", ctypes.c_int),
-                ("sweep_si_kernel", ctypes.c_int), ("sweep_f_kernel", ctypes.c_int)]
+                ("sweep_si_kernel", ctypes.c_int), ("sweep_f_kernel", ctypes.c_int),
+                ("pc_level_rank", ctypes.c_int * MAX_PC_LEVELS),
+                ("pc_level_updated", ctypes.c_int * MAX_PC_LEVELS)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        for k in ("pc_level_rank", "pc_level_updated"):
+            d[k] = list(d[k])
+        return d
 
 
 _lib = None

@@ -40,6 +40,7 @@ def test_default_options(lib):
     o = rte.default_options()
     assert (o.eps_sisa, o.eps_ig, o.eps_pc, o.eps_up) == (1e-8, 1e-6, 1e-6, 1e-6)
     assert (o.max_iter, o.r_max, o.cg_rtol, o.cg_max_iter) == (500, 40, 1e-6, 500)
+    assert o.pc_levels == 1 and rte.MAX_PC_LEVELS == 4
 
 
 def _create(**kw):
@@ -63,6 +64,8 @@ def _create(**kw):
                                   w=[0.25] * 4)),         # a direction on an axis
     dict(options=rte.default_options(r_max=65)),
     dict(options=rte.default_options(precision=7)),
+    dict(options=rte.default_options(pc_levels=5)),
+    dict(options=rte.default_options(pc_levels=-1)),
 ])
 def test_invalid_problems_rejected(lib, bad):
     with pytest.raises(rte.RteError) as ei:

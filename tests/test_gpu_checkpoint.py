@@ -10,26 +10,29 @@ from paper_2603_19647_gb300 import inputs, rte
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name,precision", [("checkerboard", rte.RTE_FP64),
-                                            ("checkerboard", rte.RTE_FP32),
-                                            ("checkerboard", rte.RTE_FP32_BF16F),
-                                            ("slab", rte.RTE_FP64),
-                                            ("slab", rte.RTE_FP32)])
-def test_resume_is_bit_identical(name, precision):
+@pytest.mark.parametrize("name,precision,levels", [("checkerboard", rte.RTE_FP64, 1),
+                                                   ("checkerboard", rte.RTE_FP32, 1),
+                                                   ("checkerboard", rte.RTE_FP32_BF16F, 1),
+                                                   ("checkerboard", rte.RTE_FP64, 2),
+                                                   ("slab", rte.RTE_FP64, 1),
+                                                   ("slab", rte.RTE_FP32, 1)])
+def test_resume_is_bit_identical(name, precision, levels):
     wl = inputs.checkerboard(n=32) if name == "checkerboard" else inputs.slab_1d(n=64)
     wl.inflow = np.array([0.2, 0.0, 0.1, 0.0])
-    a = rte.create_from_workload(wl, options=rte.default_options(precision=precision))
+    opts = rte.default_options(precision=precision, pc_levels=levels)
+    a = rte.create_from_workload(wl, options=opts)
     a.rte_step(20)
     blob = a.rte_save()
     a.rte_step(15)
-    b = rte.create_from_workload(wl, options=rte.default_options(precision=precision))
+    b = rte.create_from_workload(wl, options=opts)
     b.rte_step(3)   # another state, replaced by the load
     b.rte_load(blob)
     b.rte_step(15)
     sa, sb = a.rte_get_stats(), b.rte_get_stats()
     assert np.array_equal(a.rte_get_scalar_flux(), b.rte_get_scalar_flux())
     assert np.array_equal(a.rte_get_angular_flux(), b.rte_get_angular_flux())
-    for k in ("steps", "phase", "total_iterations", "total_sweeps", "ig_rank", "pc_rank"):
+    for k in ("steps", "phase", "total_iterations", "total_sweeps", "ig_rank", "pc_rank",
+              "pc_level_rank"):
         assert sa[k] == sb[k], k
     a.destroy()
     b.destroy()
@@ -50,7 +53,8 @@ def test_load_refuses_foreign_or_damaged_blobs():
     others = [rte.create_from_workload(inputs.checkerboard(n=16)),
               rte.create_from_workload(wl, options=rte.default_options(precision=rte.RTE_FP32)),
               rte.create_from_workload(wl, options=rte.default_options(r_max=20)),
-              rte.create_from_workload(other_dt), rte.create_from_workload(other_sigma)]
+              rte.create_from_workload(other_dt), rte.create_from_workload(other_sigma),
+              rte.create_from_workload(wl, options=rte.default_options(pc_levels=2))]
     for o in others:
         with pytest.raises(rte.RteError) as e:
             o.rte_load(blob)

@@ -2,15 +2,20 @@
 through the C ABI, in FP64.
 
 Parity of rho^n at a relative L2 error <= 1e-10, with equal iteration counts and ROM ranks,
-holds whenever both sides take the same decisions: ROM-off marches at the working tolerance,
-and ROM-on marches through Phases 1 and 2.  In Phase 3 the preconditioner ROM keeps trailing
-singular triplets at the solver-noise level and its update indicators compare noise-sized
-quantities, so rounding differences can flip a decision (an iteration count, an update);
-both trajectories still satisfy the same stopping test, so they differ by a small multiple
-of the SI-SA tolerance (the paper reports ROM-on vs ROM-off differences of the same kind,
-Sec. 4).  Hence: at a tight tolerance (eps_SISA = 1e-12) rho^n must stay within 1e-10 for the
-whole march; at eps_SISA = 1e-8 within 1e-10 through Phase 2 and within 20 eps_SISA after;
-in both, Phase 3 iteration counts and ranks may differ, N0 and N1 may not."""
+holds whenever the march does not amplify rounding: ROM-off marches, ROM-on marches through
+Phases 1 and 2, tight tolerances (eps_SISA = 1e-12), and Phase 3 at the working tolerance
+eps_SISA = 1e-8 when the preconditioner ROM is truncated at eps_PC = 1e-3.
+
+At the working tolerance with the default eps_PC = 1e-6 the preconditioner ROM keeps singular
+values down to 1e-6 of their sum, and its reduced operator reaches condition numbers of 1e5
+and more (measured on the oracle for the 48^2 checkerboard): the method itself then amplifies
+a rounding difference by that much per step.  The oracle against itself, with its source
+perturbed by 2e-16 relative, drifts to a few 1e-9 in Phase 3 (and flips iteration counts); a
+1e-10 bound is not a property of the method there.  Those marches are held to the method's
+own sensitivity instead: the oracle is run three more times with such perturbations, and the
+library's distance to the unperturbed oracle must stay within 50 times the largest distance
+seen so far among the oracle runs (never below 1e-10).  A real defect (a wrong pairing, a
+wrong gate, a wrong kernel) moves the march by orders of magnitude more."""
 import numpy as np
 import pytest
 
@@ -24,8 +29,32 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, **opts):
-    """exact=False: exact parity until the first Phase 3 step, tolerance bound afterwards.
+ENVELOPE_FACTOR = 50.0
+PERTURBATION = 2e-16
+
+
+def _perturbed_oracles(wl, rom_on, oopts, k=3):
+    """k oracle marches whose source (or, without one, sigma_t) is perturbed by a relative
+    2e-16 (seeded normal numbers): rounding-sized changes of the input."""
+    out = []
+    for seed in range(1, k + 1):
+        p = oracle_problem(wl)
+        rng = np.random.default_rng(seed)
+        if np.any(p.source):
+            p.source = p.source * (1 + PERTURBATION * rng.standard_normal(p.ncell))
+        else:
+            p.sigma_t = p.sigma_t * (1 + PERTURBATION * rng.standard_normal(p.ncell))
+        o = stepper.OracleRTE(p, rom=rom_on, **oopts)
+        o.set_initial(wl.rho0)
+        out.append(o)
+    return out
+
+
+def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, decisions_p3=False,
+           **opts):
+    """exact=False: exact parity until the first Phase 3 step, then within the envelope of the
+    oracle's own rounding sensitivity (module docstring).  decisions_p3: iteration counts and
+    ROM ranks must also agree in Phase 3.
     inflow_at: {step: g} sets the isotropic inflow of both sides before that step."""
     o = dict(rom=rte.RTE_ROM_AUTO if rom_on else rte.RTE_ROM_OFF)
     o.update(opts)
@@ -37,29 +66,36 @@ def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, **opts):
         oopts["up_rel"] = bool(oopts["up_rel"])
     orc = stepper.OracleRTE(p, rom=rom_on, **oopts)
     orc.set_initial(wl.rho0)
-    eps = opts.get("eps_sisa", stepper.DEFAULTS["eps_sisa"])
+    pert = [] if exact else _perturbed_oracles(wl, rom_on, oopts)
+    envelope = 0.0
     in_p3 = False
     phases_lib, phases_orc = [], []
     for n in range(1, steps + 1):
         if inflow_at and n in inflow_at:
             h.rte_set_inflow(inflow_at[n])
-            orc.set_inflow(inflow_at[n])
+            for o in [orc] + pert:
+                o.set_inflow(inflow_at[n])
         h.rte_step(1)
         orc.step(1)
+        for o in pert:
+            o.step(1)
+            envelope = max(envelope, rel_l2(o.rho, orc.rho))
         st = h.rte_get_stats()
         lg = orc.log[-1]
         phases_lib.append(st["phase"])
         phases_orc.append(lg.phase)
         in_p3 = in_p3 or lg.phase == 3 or st["phase"] == 3
-        same_decisions = not in_p3
+        same_decisions = decisions_p3 or not in_p3
         strict = exact or not in_p3
         if same_decisions:
             assert st["last_iterations"] == lg.iterations, n
         if n % check_every == 0 or n == steps or not in_p3:
             err = rel_l2(h.rte_get_scalar_flux(), orc.rho)
-            assert err < (TOL if strict else 20 * eps), (n, err)
+            bound = TOL if strict else max(TOL, ENVELOPE_FACTOR * envelope)
+            assert err < bound, (n, err, envelope)
             if rom_on and same_decisions:
                 assert st["ig_rank"] == orc.ig.rank and st["pc_rank"] == orc.pc.rank, n
+                assert st["pc_level_rank"][:len(orc.pcs)] == [v.rank for v in orc.pcs], n
     if rom_on:   # the same N0 and N1
         for ph in (2, 3):
             a = phases_lib.index(ph) if ph in phases_lib else -1
@@ -108,15 +144,82 @@ def test_checkerboard_tile_kernel_rom_tight():
     assert max(s.phase for s in orc.log) >= 2
 
 
-@pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
-def test_lookahead_gives_the_same_march(precision):
+# Phase 3 at the working tolerance with a well-conditioned preconditioner ROM: the oracle's
+# decisions stand at least 6e-4 (relative) from their thresholds on these marches, so both
+# sides take the same ones and stay within 1e-10 for the whole march.
+WELL_CONDITIONED_PC = dict(eps_pc=1e-3)
+
+
+def test_checkerboard_phase3_working_tolerance_strict():
+    orc = _march(inputs.checkerboard(n=48), 80, 5, rom_on=True, decisions_p3=True,
+                 **WELL_CONDITIONED_PC)
+    assert sum(s.phase == 3 for s in orc.log) >= 60
+
+
+def test_slab_phase3_working_tolerance_strict():
+    orc = _march(inputs.slab_1d(steps=60), 60, 5, rom_on=True, decisions_p3=True,
+                 **WELL_CONDITIONED_PC)
+    assert sum(s.phase == 3 for s in orc.log) >= 40
+
+
+@pytest.mark.parametrize("eps_sisa", [1e-8, 1e-10])
+def test_two_preconditioner_roms_strict(eps_sisa):
+    """A preconditioner ROM for the first and for the second SI iteration (the second built
+    only from steps that applied the first): the same decisions, ranks of both ROMs and 1e-10
+    for the whole march, with updates of the second ROM in Phase 3 (the oracle's decisions
+    stand at least 7e-4 relative from their thresholds)."""
+    orc = _march(inputs.checkerboard(n=48), 80, 5, rom_on=True, decisions_p3=True,
+                 pc_levels=2, eps_sisa=eps_sisa, **WELL_CONDITIONED_PC)
+    assert sum(s.phase == 3 for s in orc.log) >= 60
+    assert sum(s.pc_ups[1] for s in orc.log if s.phase == 3) >= 5
+
+
+def test_two_preconditioner_roms_exact_on_an_invariant_span():
+    """The oracle pin of the sequentially built second preconditioner ROM, run by the library:
+    a five-mode slab march (f0 from eigenvectors of the step's dense system matrix) with every
+    ROM capped at rank 2, where the second ROM is exact and every Phase 3 step ends at l = 3."""
+    from oracle import dense
+    from gpu_util import match_directions
+    wl = inputs.slab_1d(n=16, n_dirs=8, steps=16, c_dt=0.05)
+    rng = np.random.default_rng(5)
+    wl.sigma_s = 0.9 * (0.5 + rng.uniform(0, 1, 16))
+    wl.sigma_t = wl.sigma_s + rng.uniform(0.2, 1.0, 16)
+    p = oracle_problem(wl)
+    lam, V = np.linalg.eig(dense.assemble(p))
+    order = [i for i in np.argsort(np.abs(lam)) if abs(lam[i].imag) < 1e-12]
+    f0 = sum(c * V[:, i].real / np.abs(V[:, i].real).max()
+             for c, i in zip([1.0, 0.7, 0.5, 0.4, 0.3], order)).reshape(p.nv, p.ncell)
+    o = dict(eps_sisa=1e-12, cg_rtol=1e-12, eps_ig=1e-6, eps_pc=1e-6, eps_up=0.5, r_max=2,
+             pc_levels=2)
+    h, _ = make_pair(wl, rom=rte.RTE_ROM_AUTO, **o)
+    perm, _, _ = match_directions(h, wl.quadrature)
+    h.rte_set_initial(f0=f0[perm])
+    orc = stepper.OracleRTE(p, **o)
+    orc.set_initial(np.zeros(p.ncell), f0=f0)
+    for n in range(1, 17):
+        h.rte_step(1)
+        orc.step(1)
+        st, lg = h.rte_get_stats(), orc.log[-1]
+        assert st["phase"] == lg.phase and st["last_iterations"] == lg.iterations, n
+        assert st["pc_level_rank"][:2] == list(lg.pc_ranks), n
+        assert rel_l2(h.rte_get_scalar_flux(), orc.rho) < TOL, n
+        if lg.phase == 3:
+            assert st["last_iterations"] == 3, n
+    h.destroy()
+    assert sum(s.phase == 3 for s in orc.log) >= 8
+
+
+@pytest.mark.parametrize("precision,levels", [(rte.RTE_FP64, 1), (rte.RTE_FP32, 1),
+                                              (rte.RTE_FP64, 2)])
+def test_lookahead_gives_the_same_march(precision, levels):
     """options.lookahead queues SI iteration l+1 before the host reads the stopping test of l;
     the work queued past convergence skips itself on the device, so the march, its iteration
     counts and its ROM ranks are those of the waiting loop, bit for bit."""
     wl = inputs.checkerboard(n=48)
     out = []
     for la in (0, 1):
-        h, _ = make_pair(wl, rom=rte.RTE_ROM_AUTO, precision=precision, lookahead=la)
+        h, _ = make_pair(wl, rom=rte.RTE_ROM_AUTO, precision=precision, lookahead=la,
+                         pc_levels=levels)
         h.rte_set_initial(rho0=wl.rho0)
         its = []
         for _ in range(80):
@@ -214,3 +317,13 @@ def test_checkerboard_full_workload_rom():
     """The benchmark workload (256^2, 128 directions, c dt = 0.005, 200 steps, ROM on)."""
     wl = inputs.checkerboard()
     _march(wl, wl.steps, 25, rom_on=True, exact=False)
+
+
+@pytest.mark.slow
+def test_checkerboard_full_workload_phase3_strict():
+    """The benchmark workload at the working tolerance with the preconditioner ROM truncated at
+    eps_PC = 1e-3: 1e-10 and the same decisions for all 200 steps, 189 of them in Phase 3
+    (the oracle's decisions stand at least 6e-4 relative from their thresholds)."""
+    wl = inputs.checkerboard()
+    orc = _march(wl, wl.steps, 25, rom_on=True, decisions_p3=True, **WELL_CONDITIONED_PC)
+    assert sum(s.phase == 3 for s in orc.log) >= 180
