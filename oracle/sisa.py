@@ -13,12 +13,22 @@ Readings where the paper leaves a choice:
   Phase 3, Eq. (dmd-sa)); every other SA step is DSA (Eq. (rho_residual)).  With a sequence
   of preconditioner ROMs (Sec. 3.2, key feature 1: ROMs for the first l - 1 iterations before
   the one for iteration l), the SA step of iteration l uses the l-th ROM when there is one.
+* opts["sa"] = "mh" replaces DSA by the DMD-across-iterations acceleration the paper combines
+  with its ROMs in Sec. 4 ("hybrid with McClarren-Haut method", compared in Sec. 3.3), which it
+  gives by citation only.  Reading: the SA steps that would be DSA are plain SI steps
+  (delta = 0) collecting this cycle's residuals r_l = rho^{l-1/2} - rho^{l-1}; for plain SI,
+  r_{l+1} = T Sigma_s r_l, so the pairs (r_l, r_l - r_{l+1}) sample I - T Sigma_s.  After
+  K = opts["mh_window"] residuals a DMD reduced model of I - T Sigma_s is built from the K - 1
+  pairs (the incremental SVD and reduced operator of Sec. 3.1) and the iterate jumps to
+  rho^l = rho^{l-1} + C_r^{-1} r_l, the fixed point rho = T Sigma_s rho + b~ restricted to
+  the span of the residuals; the cycle then starts again.
 """
 from dataclasses import dataclass
 
 import numpy as np
 
 from . import dsa as _dsa
+from . import rom as _rom
 from . import transport as _tr
 
 
@@ -38,6 +48,7 @@ class SolveInfo:
     rho_half: list = None
     rho_prev: list = None
     delta_pc: list = None
+    mh_corrections: int = 0      # DMD-across-iterations jumps (opts["sa"] = "mh")
 
 
 def converged(diff, rho_half, eps, mode):
@@ -46,6 +57,24 @@ def converged(diff, rho_half, eps, mode):
         return dn <= eps, dn
     rn = float(np.max(np.abs(rho_half))) if rho_half.size else 0.0
     return dn <= eps * rn, (dn / rn if rn > 0 else dn)
+
+
+def mh_step(cycle, r, window, rho_prev, rho_half):
+    """One SA step of the DMD-across-iterations acceleration (reading in the module docstring):
+    append the residual r to the cycle; a plain SI step (delta = 0) until the cycle holds
+    `window` residuals, then the jump rho^l = rho^{l-1} + C_r^{-1} r of the DMD model of
+    I - T Sigma_s built from the pairs (r_i, r_i - r_{i+1}), returned as delta = rho^l -
+    rho^{l-1/2}, and the cycle is emptied."""
+    cycle.append(r.copy())
+    if len(cycle) < window:
+        return np.zeros_like(r)
+    svd = _rom.IncrementalSVD(r.size, window)
+    for a, b in zip(cycle[:-1], cycle[1:]):
+        svd.append(a, a - b)
+    cycle.clear()
+    if svd.rank == 0:
+        return np.zeros_like(r)
+    return rho_prev + svd.solve_apply(r) - rho_half
 
 
 def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None, decide=None):
@@ -60,6 +89,9 @@ def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None, decide=None):
     pcs = [] if pc is None else (list(pc) if isinstance(pc, (list, tuple)) else [pc])
     info = SolveInfo(rho_half=[], rho_prev=[], delta_pc=[])
     rho_prev = np.array(rho_init, dtype=np.float64, copy=True)
+    mh = opts.get("sa", "dsa") == "mh"
+    window = int(opts.get("mh_window", 4))
+    cycle = []   # residuals of the current DMD-across-iterations cycle
     for l in range(1, opts["max_iter"] + 1):
         rho_half = _tr.apply_T_sigma_s(p, rho_prev) + btilde
         diff = rho_half - rho_prev
@@ -83,7 +115,12 @@ def si_sa(p, rho_init, btilde, opts, A_dsa, pc=None, decide=None):
         else:
             if l <= len(pcs):
                 info.delta_pc.append(None)
-            delta, its = _dsa.dsa_correction(p, A_dsa, diff, opts["cg_rtol"], opts["cg_max_iter"])
-            info.cg_iterations += its
+            if mh:
+                delta = mh_step(cycle, diff, window, rho_prev, rho_half)
+                info.mh_corrections += 0 if cycle else 1
+            else:
+                delta, its = _dsa.dsa_correction(p, A_dsa, diff, opts["cg_rtol"],
+                                                 opts["cg_max_iter"])
+                info.cg_iterations += its
         rho_prev = rho_half + delta
     raise NoConvergence(f"SI-SA did not converge in {opts['max_iter']} iterations")

@@ -38,7 +38,7 @@ from . import transport as _tr
 
 DEFAULTS = dict(eps_sisa=1e-8, eps_ig=1e-6, eps_pc=1e-6, eps_up=1e-6, max_iter=500, r_max=40,
                 rom=True, residual_norm="rel", cg_rtol=1e-6, cg_max_iter=500, up_rel=True,
-                pc_levels=1)
+                pc_levels=1, sa="dsa", mh_window=4)
 
 
 @dataclass
