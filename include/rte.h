@@ -54,6 +54,7 @@ enum { RTE_REL_INF = 0, RTE_ABS_INF = 1 };
 enum { RTE_ROM_OFF = 0, RTE_ROM_AUTO = 1, RTE_ROM_MANUAL = 2 };
 enum { RTE_ROM_IG = 0, RTE_ROM_PC = 1 };
 #define RTE_MAX_PC_LEVELS 4   /* preconditioner ROMs: one per SI iteration l = 1 .. 4 at most */
+enum { RTE_SA_DSA = 0, RTE_SA_DMD_ITER = 1 };
 
 /* Uniform Cartesian mesh.  dim = 1: slab [x0,x1] with nx cells (ny must be 1);
  * dim = 2: [x0,x1] x [y0,y1] with nx*ny rectangles (Sec. 2.1). */
@@ -114,6 +115,14 @@ typedef struct {
                         1), Phase 3 begins once all are built, and in Phase 3 each is updated
                         when the IG-ROM or an earlier iteration's ROM was updated in the same
                         step, or when its own indicator exceeds eps_up */
+  int sa_kind;       /* the SA steps that are not ROM corrections: RTE_SA_DSA (default, Eq.
+                        (rho_residual)) | RTE_SA_DMD_ITER: the DMD-across-iterations
+                        acceleration the paper combines with its ROMs in place of DSA (Sec. 4,
+                        compared in Sec. 3.3): plain SI steps collect mh_window residuals
+                        r_l = rho^{l-1/2} - rho^{l-1}, then the iterate jumps to
+                        rho^{l-1} + C_r^{-1} r_l with C_r the DMD reduced operator of
+                        I - T Sigma_s from the pairs (r_l, r_l - r_{l+1}); lookahead is off */
+  int mh_window;     /* residuals per DMD-across-iterations cycle, 2 .. 16 (default 4) */
 } rte_options;
 
 typedef struct {
@@ -144,6 +153,7 @@ typedef struct {
    * updated in the last step (the l = 1 entries repeat pc_rank and pc_updated) */
   int pc_level_rank[RTE_MAX_PC_LEVELS];
   int pc_level_updated[RTE_MAX_PC_LEVELS];
+  long long total_mh_jumps;     /* DMD-across-iterations jumps (sa_kind = RTE_SA_DMD_ITER) */
 } rte_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -65,6 +65,7 @@ class StepLog:
     # every preconditioner ROM (iterations l = 1 .. pc_levels): ranks and updates
     pc_ranks: tuple = ()
     pc_ups: tuple = ()
+    mh_jumps: int = 0   # DMD-across-iterations jumps of the step (sa = "mh")
 
 
 class OracleRTE:
@@ -216,7 +217,8 @@ class OracleRTE:
         sweeps = info.iterations + 2
         lg = StepLog(self.n, phase, info.iterations, sweeps, info.cg_iterations, self.ig.rank,
                      self.pcs[0].rank, ig_up, pc_ups[0], info.residual, ig_err, pc_errs[0],
-                     pc_ranks=tuple(v.rank for v in self.pcs), pc_ups=tuple(pc_ups))
+                     pc_ranks=tuple(v.rank for v in self.pcs), pc_ups=tuple(pc_ups),
+                     mh_jumps=info.mh_corrections)
         if self.record:
             lg.rho, lg.rho_half_1, lg.rho_init = rho_n.copy(), info.rho_half_1.copy(), rho0.copy()
             lg.ig_s, lg.pc_s = self.ig.S.copy(), self.pcs[0].S.copy()

@@ -128,6 +128,10 @@ struct rte_s {
   RomDev pcs[RTE_MAX_PC_LEVELS]{};   // preconditioner ROM of SI iteration l at index l - 1
   RomDev& pc = pcs[0];
   int levels = 1;                    // options.pc_levels
+  // DMD-across-iterations SA steps (options.sa_kind): the cycle's model of I - T Sigma_s, the
+  // last two residuals, their difference and a zero vector (the plain SI step)
+  RomDev mh{};
+  double *mh_r[2] = {nullptr, nullptr}, *mh_b = nullptr, *mh_zero = nullptr;
   // FNV-1a digest of the host cross sections and source given to rte_create (checked by
   // rte_load together with c_dt, so a blob of another problem on the same mesh is refused)
   uint64_t problem_digest = 0;
@@ -352,6 +356,9 @@ void free_all(rte_handle h) {
   dsa_free(h->dsa);
   rom_free(h->ig);
   for (auto& R : h->pcs) rom_free(R);
+  rom_free(h->mh);
+  for (double* q : {h->mh_r[0], h->mh_r[1], h->mh_b, h->mh_zero})
+    if (q) cudaFree(q);
   for (int k = 0; k < RTE_MAX_PC_LEVELS; ++k) {
     double* lv[] = {h->lv_half[k], h->lv_prev[k], h->lv_delta[k], h->lv_x[k], h->lv_b[k],
                     h->lv_diff[k]};
@@ -817,6 +824,39 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
     span(h, SPAN_DSA, d0, rec(h), l + 1);
     return RTE_OK;
   };
+  // DMD-across-iterations SA step (options.sa_kind): a plain SI step that collects the
+  // residual r_l = rho^{l-1/2} - rho^{l-1}; after mh_window residuals the iterate jumps to
+  // rho^{l-1} + C_r^{-1} r_l, C_r the DMD model of I - T Sigma_s from the pairs
+  // (r_i, r_i - r_{i+1}) of the cycle (appended as they come, with one host wait each).
+  int cyc = 0;
+  auto mh_step = [&](int l) -> rte_status {
+    const int d0 = rec(h);
+    double* r = h->mh_r[cyc & 1];
+    CK(launch_axpby(1.0, h->rho_half, -1.0, h->rho_prev, n, r, h->st));
+    if (cyc > 0) {
+      double* rp = h->mh_r[(cyc - 1) & 1];
+      CK(launch_axpby(1.0, rp, -1.0, r, n, h->mh_b, h->st));
+      CK(rom_append(h->mh, rp, h->mh_b, -1.0, nullptr, nullptr, h->st));
+    }
+    if (++cyc == h->opt.mh_window) {
+      cyc = 0;
+      if (h->mh.rank > 0 && h->mh.lu_ok) {
+        CK(rom_apply(h->mh, r, h->tmp, h->st));
+        CK(launch_update_rho(h->rho_prev, h->tmp, h->sig_s, n, h->rho_prev, h->q, h->st));
+        h->stats.total_mh_jumps += 1;
+      } else {
+        CK(launch_update_rho(h->rho_half, h->mh_zero, h->sig_s, n, h->rho_prev, h->q, h->st));
+      }
+      rom_reset(h->mh);
+    } else {
+      CK(launch_update_rho(h->rho_half, h->mh_zero, h->sig_s, n, h->rho_prev, h->q, h->st));
+    }
+    span(h, SPAN_DSA, d0, rec(h), l + 1);
+    return RTE_OK;
+  };
+  const bool mh = h->opt.sa_kind == RTE_SA_DMD_ITER;
+  if (mh) rom_reset(h->mh);
+  auto sa_step = [&](int l) -> rte_status { return mh ? mh_step(l) : dsa_step(l); };
   bool conv = false;
   int l = 1;
   for (bool& a : h->pc_applied) a = false;
@@ -824,7 +864,7 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
   TRY(residual(1));
   for (l = 1;; ++l) {
     const bool pc_now = l <= pc_active;
-    if (h->opt.lookahead && l < h->opt.max_iter && !pc_now) {   // iteration l + 1, queued ahead
+    if (h->opt.lookahead && !mh && l < h->opt.max_iter && !pc_now) {   // l + 1, queued ahead
       TRY(dsa_step(l));
       TRY(sweep_increment(l + 1));
       TRY(residual(l + 1));
@@ -836,8 +876,8 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
     conv = absmode ? nm.diff_inf <= h->opt.eps_sisa : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
     h->stats.last_residual = res;
     if (conv || l == h->opt.max_iter) break;
-    if (!h->opt.lookahead && !pc_now) {
-      TRY(dsa_step(l));
+    if ((!h->opt.lookahead || mh) && !pc_now) {
+      TRY(sa_step(l));
       TRY(sweep_increment(l + 1));
       TRY(residual(l + 1));
     }
@@ -1439,6 +1479,11 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.pc_levels < 1 || h->opt.pc_levels > RTE_MAX_PC_LEVELS)
     return fail(h, RTE_EINVAL, "pc_levels must be in [1, RTE_MAX_PC_LEVELS]");
   h->levels = h->opt.pc_levels;
+  if (h->opt.sa_kind != RTE_SA_DSA && h->opt.sa_kind != RTE_SA_DMD_ITER)
+    return fail(h, RTE_EINVAL, "sa_kind must be RTE_SA_DSA or RTE_SA_DMD_ITER");
+  if (h->opt.mh_window == 0) h->opt.mh_window = 4;   // options zeroed by hand: the default
+  if (h->opt.mh_window < 2 || h->opt.mh_window > 16)
+    return fail(h, RTE_EINVAL, "mh_window must be in [2, 16]");
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
       h->opt.sweep_lanes != 32)
@@ -1568,6 +1613,13 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   TRY(alloc_sweep(h));
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st));
   CK(rom_alloc(h->ig, (int)n, h->opt.r_max));
+  if (h->opt.sa_kind == RTE_SA_DMD_ITER) {
+    CK(rom_alloc(h->mh, (int)n, h->opt.mh_window));
+    for (double** q : {&h->mh_r[0], &h->mh_r[1], &h->mh_b, &h->mh_zero}) {
+      CK(dalloc(q, n));
+      CK(cudaMemsetAsync(*q, 0, sizeof(double) * n, h->st));
+    }
+  }
   for (int k = 0; k < h->levels; ++k) {
     CK(rom_alloc(h->pcs[k], (int)n, h->opt.r_max));
     if (k == 0) continue;
@@ -1673,6 +1725,8 @@ void rte_default_options(rte_options* o) {
   o->tune = 1;
   o->lookahead = 0;
   o->pc_levels = 1;
+  o->sa_kind = RTE_SA_DSA;
+  o->mh_window = 4;
 }
 
 rte_status rte_create(rte_handle* out, const rte_mesh* mesh, const rte_quadrature* quad,

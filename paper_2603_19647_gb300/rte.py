@@ -18,6 +18,7 @@ RTE_FP64, RTE_FP32, RTE_FP32_BF16F = range(3)
 RTE_REL_INF, RTE_ABS_INF = range(2)
 RTE_ROM_OFF, RTE_ROM_AUTO, RTE_ROM_MANUAL = range(3)
 RTE_ROM_IG, RTE_ROM_PC = range(2)
+RTE_SA_DSA, RTE_SA_DMD_ITER = range(2)
 STATUS_NAMES = {0: "RTE_OK", 1: "RTE_EINVAL", 2: "RTE_ENOMEM", 3: "RTE_ENOCONV", 4: "RTE_ECUDA",
                 5: "RTE_ETIMEOUT", 6: "RTE_ESTATE"}
 
@@ -58,7 +59,8 @@ class Options(ctypes.Structure):
                 ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("tune", ctypes.c_int),
                 ("sweep_rows", ctypes.c_int), ("sweep_lanes", ctypes.c_int),
                 ("sweep_warps", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
-                ("lookahead", ctypes.c_int), ("pc_levels", ctypes.c_int)]
+                ("lookahead", ctypes.c_int), ("pc_levels", ctypes.c_int),
+                ("sa_kind", ctypes.c_int), ("mh_window", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -78,7 +80,8 @@ class Stats(ctypes.Structure):
                 ("sweep_f_warps", ctypes.c_int), ("sweep_tuned", ctypes.c_int),
                 ("sweep_si_kernel", ctypes.c_int), ("sweep_f_kernel", ctypes.c_int),
                 ("pc_level_rank", ctypes.c_int * MAX_PC_LEVELS),
-                ("pc_level_updated", ctypes.c_int * MAX_PC_LEVELS)]
+                ("pc_level_updated", ctypes.c_int * MAX_PC_LEVELS),
+                ("total_mh_jumps", ctypes.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

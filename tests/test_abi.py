@@ -41,6 +41,7 @@ def test_default_options(lib):
     assert (o.eps_sisa, o.eps_ig, o.eps_pc, o.eps_up) == (1e-8, 1e-6, 1e-6, 1e-6)
     assert (o.max_iter, o.r_max, o.cg_rtol, o.cg_max_iter) == (500, 40, 1e-6, 500)
     assert o.pc_levels == 1 and rte.MAX_PC_LEVELS == 4
+    assert o.sa_kind == rte.RTE_SA_DSA and o.mh_window == 4
 
 
 def _create(**kw):
@@ -65,6 +66,9 @@ def _create(**kw):
     dict(options=rte.default_options(r_max=65)),
     dict(options=rte.default_options(precision=7)),
     dict(options=rte.default_options(pc_levels=5)),
+    dict(options=rte.default_options(sa_kind=2)),
+    dict(options=rte.default_options(mh_window=1)),
+    dict(options=rte.default_options(mh_window=17)),
     dict(options=rte.default_options(pc_levels=-1)),
 ])
 def test_invalid_problems_rejected(lib, bad):

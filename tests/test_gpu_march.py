@@ -64,6 +64,8 @@ def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, decisions
         oopts["residual_norm"] = "abs" if oopts["residual_norm"] == rte.RTE_ABS_INF else "rel"
     if "up_rel" in oopts:
         oopts["up_rel"] = bool(oopts["up_rel"])
+    if "sa_kind" in opts:
+        oopts["sa"] = "mh" if opts["sa_kind"] == rte.RTE_SA_DMD_ITER else "dsa"
     orc = stepper.OracleRTE(p, rom=rom_on, **oopts)
     orc.set_initial(wl.rho0)
     pert = [] if exact else _perturbed_oracles(wl, rom_on, oopts)
@@ -89,6 +91,8 @@ def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, decisions
         strict = exact or not in_p3
         if same_decisions:
             assert st["last_iterations"] == lg.iterations, n
+            if "sa_kind" in opts:
+                assert st["total_mh_jumps"] == sum(s.mh_jumps for s in orc.log), n
         if n % check_every == 0 or n == steps or not in_p3:
             err = rel_l2(h.rte_get_scalar_flux(), orc.rho)
             bound = TOL if strict else max(TOL, ENVELOPE_FACTOR * envelope)
@@ -172,6 +176,35 @@ def test_two_preconditioner_roms_strict(eps_sisa):
                  pc_levels=2, eps_sisa=eps_sisa, **WELL_CONDITIONED_PC)
     assert sum(s.phase == 3 for s in orc.log) >= 60
     assert sum(s.pc_ups[1] for s in orc.log if s.phase == 3) >= 5
+
+
+@pytest.mark.parametrize("case", ["rom_working_tolerance", "rom_off", "slab", "two_levels_fp32"])
+def test_dmd_across_iterations_in_place_of_dsa(case):
+    """The DMD-across-iterations SA steps (options.sa_kind) against the oracle's, in the
+    ROM-accelerated march (Phases 1-3, the hybrid of the paper's Sec. 4) and in plain SI with
+    them alone: the same decisions, the same number of jumps and 1e-10 throughout (FP32 sweeps:
+    within 1e-6 of the FP64 oracle)."""
+    wl = inputs.slab_1d(steps=60) if case == "slab" else inputs.checkerboard(n=48)
+    steps = 60 if case == "slab" else 80
+    extra = dict(pc_levels=2, precision=rte.RTE_FP32) if case == "two_levels_fp32" else {}
+    rom_on = case != "rom_off"
+    if case == "two_levels_fp32":
+        h, p = make_pair(wl, rom=rte.RTE_ROM_AUTO, sa_kind=rte.RTE_SA_DMD_ITER, eps_pc=1e-3,
+                         **extra)
+        orc = stepper.OracleRTE(p, sa="mh", eps_pc=1e-3, pc_levels=2)
+        orc.set_initial(wl.rho0)
+        for n in range(1, steps + 1):
+            h.rte_step(1)
+            orc.step(1)
+            if n % 10 == 0:
+                assert rel_l2(h.rte_get_scalar_flux(), orc.rho) < 1e-6, n
+        h.destroy()
+        return
+    orc = _march(wl, steps, 5, rom_on=rom_on, decisions_p3=True, sa_kind=rte.RTE_SA_DMD_ITER,
+                 **WELL_CONDITIONED_PC)
+    assert sum(s.cg_iterations for s in orc.log) == 0
+    if rom_on:
+        assert sum(s.phase == 3 for s in orc.log) >= 40
 
 
 def test_two_preconditioner_roms_exact_on_an_invariant_span():
