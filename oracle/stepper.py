@@ -20,6 +20,13 @@ Readings where the paper is silent or loose (each listed in the design notes):
 * A step whose first sweep already converged has no first correction, so no PC snapshot
   is taken from it.
 * Step 1's initial guess is rho^0 (the isotropic initial state).
+* scheme = "bdf2" marches with the second-order backward difference formula the paper names as
+  an alternative to backward Euler (Sec. 2.1): (3 f^n - 4 f^{n-1} + f^{n-2}) / (2 c dt) replaces
+  (f^n - f^{n-1}) / (c dt), i.e. the step's system is that of backward Euler with
+  tau' = 3 / (2 c dt) and the history h^n = (4 f^{n-1} - f^{n-2}) / 3 in place of f^{n-1}.
+  The first step is a backward-Euler step of dt (its local error O(dt^2) keeps the march
+  second order), and it gives the ROMs no snapshot: they learn the BDF2 step's system
+  A~ rho^n = b~^{n-1} (b~ built from h), on which Algorithm 2 runs unchanged from step 2.
 
 Each decision of the algorithm (the SI stopping test, the end of each construction phase, the
 two update gates) goes through ``decide``, which returns the algorithm's own decision; a
@@ -27,6 +34,7 @@ test may override it to follow another implementation's log where both sides sta
 rounding of a threshold.  The snapshot pairs and the correction rule are methods of their own
 so that a test can plant a mistake in exactly one of them.
 """
+import dataclasses
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -38,7 +46,7 @@ from . import transport as _tr
 
 DEFAULTS = dict(eps_sisa=1e-8, eps_ig=1e-6, eps_pc=1e-6, eps_up=1e-6, max_iter=500, r_max=40,
                 rom=True, residual_norm="rel", cg_rtol=1e-6, cg_max_iter=500, up_rel=True,
-                pc_levels=1, sa="dsa", mh_window=4)
+                pc_levels=1, sa="dsa", mh_window=4, scheme="be")
 
 
 @dataclass
@@ -76,9 +84,16 @@ class OracleRTE:
         self.record = record
         self.o = dict(DEFAULTS)
         self.o.update(opts)
-        self.A = _dsa.dsa_matrix(problem)
+        if self.o["scheme"] not in ("be", "bdf2"):
+            raise ValueError("scheme must be 'be' or 'bdf2'")
+        # the step's system: backward Euler's with tau' = 3 / (2 c dt) for BDF2
+        self.q = (problem if self.o["scheme"] == "be"
+                  else dataclasses.replace(problem, c_dt=problem.c_dt * 2.0 / 3.0))
+        self.A = _dsa.dsa_matrix(self.q)
+        self.A_start = self.A if self.o["scheme"] == "be" else _dsa.dsa_matrix(problem)
         self.rho = np.zeros(problem.ncell)
         self.f = np.zeros((problem.nv, problem.ncell))
+        self.f_prev = self.f.copy()
         self.n = 0
         self.flag_ig = False
         self.ig = _rom.IncrementalSVD(problem.ncell, self.o["r_max"])
@@ -106,9 +121,22 @@ class OracleRTE:
         else:
             self.f = np.array(f0, dtype=np.float64).reshape(self.p.nv, self.p.ncell).copy()
             self.rho = self.p.w @ self.f
+        self.f_prev = self.f.copy()   # BDF2: f^{-1} = f^0
 
     def set_inflow(self, g):
         self.p.inflow = np.asarray(g, dtype=np.float64).ravel().copy()
+        self.q.inflow = self.p.inflow
+
+    def starting_step(self):
+        """BDF2's first step, a backward-Euler step."""
+        return self.o["scheme"] == "bdf2" and self.n == 0
+
+    def history(self):
+        """What the step's sweeps scale by tau: f^{n-1} (backward Euler and BDF2's first step)
+        or h^n = (4 f^{n-1} - f^{n-2}) / 3 (BDF2)."""
+        if self.o["scheme"] == "be" or self.starting_step():
+            return self.f
+        return (4.0 * self.f - self.f_prev) / 3.0
 
     def phase(self):
         return 1 if not self.flag_ig else (2 if not self.flag_pc else 3)
@@ -158,11 +186,14 @@ class OracleRTE:
         return self.decide(kind, own, ratio, eps)
 
     def _step(self):
-        p, o = self.p, self.o
+        start = self.starting_step()
+        p, o = (self.p if start else self.q), self.o
+        A = self.A_start if start else self.A
         L = len(self.pcs)
         phase = self.phase()
-        btilde = _tr.b_tilde(p, self.f)
-        use_rom = o["rom"]
+        hist = self.history()
+        btilde = _tr.b_tilde(p, hist)
+        use_rom = o["rom"] and not start
         rho_ig = None
         if use_rom and self.flag_ig:
             rho_ig = self.ig.solve_apply(btilde)
@@ -172,8 +203,8 @@ class OracleRTE:
         # the ROM of iteration l applies once it and the ROMs of iterations 1 .. l-1 are built
         pcs = [self.pcs[k].solve_apply if use_rom and all(self.flags_pc[:k + 1]) else None
                for k in range(L)]
-        rho_n, info = _sisa.si_sa(p, rho0, btilde, o, self.A, pc=pcs, decide=self.decide)
-        f_new, _ = _tr.final_f(p, rho_n, self.f)
+        rho_n, info = _sisa.si_sa(p, rho0, btilde, o, A, pc=pcs, decide=self.decide)
+        f_new, _ = _tr.final_f(p, rho_n, hist)
         ig_up = False
         pc_ups, pc_errs = [False] * L, [float("nan")] * L
         ig_err = float("nan")
@@ -212,6 +243,7 @@ class OracleRTE:
                             pc_ups[k] = True
                     earlier_up = earlier_up or pc_ups[k]
         self.rho = rho_n
+        self.f_prev = self.f
         self.f = f_new
         self.n += 1
         sweeps = info.iterations + 2
