@@ -55,6 +55,7 @@ enum { RTE_ROM_OFF = 0, RTE_ROM_AUTO = 1, RTE_ROM_MANUAL = 2 };
 enum { RTE_ROM_IG = 0, RTE_ROM_PC = 1 };
 #define RTE_MAX_PC_LEVELS 4   /* preconditioner ROMs: one per SI iteration l = 1 .. 4 at most */
 enum { RTE_SA_DSA = 0, RTE_SA_DMD_ITER = 1 };
+enum { RTE_BE = 0, RTE_BDF2 = 1 };
 
 /* Uniform Cartesian mesh.  dim = 1: slab [x0,x1] with nx cells (ny must be 1);
  * dim = 2: [x0,x1] x [y0,y1] with nx*ny rectangles (Sec. 2.1). */
@@ -123,6 +124,16 @@ typedef struct {
                         rho^{l-1} + C_r^{-1} r_l with C_r the DMD reduced operator of
                         I - T Sigma_s from the pairs (r_l, r_l - r_{l+1}); lookahead is off */
   int mh_window;     /* residuals per DMD-across-iterations cycle, 2 .. 16 (default 4) */
+  int cg_blocks;     /* blocks of the DSA solve's cooperative CG launch: 0 (default) one per SM
+                        (two above 2^18 cells); a cap leaves the other SMs to concurrent work
+                        (batched instances) at the price of a longer solve */
+  int time_scheme;   /* RTE_BE (default): backward Euler, Sec. 2.1 | RTE_BDF2: the second-order
+                        backward difference formula Sec. 2.1 names as an alternative: the step's
+                        system is backward Euler's with tau' = 3 / (2 c dt) and the history
+                        (4 f^{n-1} - f^{n-2}) / 3 in place of f^{n-1}; the first step (after
+                        rte_set_initial, rte_restart) is a backward-Euler step of c_dt and gives
+                        the ROMs no snapshot.  Each step sweeps once more (b~ of the next step
+                        from the history).  Not with RTE_FP32_BF16F. */
 } rte_options;
 
 typedef struct {
@@ -305,7 +316,9 @@ rte_status rte_dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, 
  * full rte_handle on its own CUDA streams, and rte_batch_step steps all of them
  * concurrently, one host thread per instance, so that their kernels overlap on the device
  * (small grids leave most SMs idle on their own).  Algorithm 2 runs per instance, exactly
- * as rte_step would run it.
+ * as rte_step would run it.  Set CUDA_DEVICE_MAX_CONNECTIONS=32 in the environment before
+ * the process creates its CUDA context: with the default 8 hardware queues the instances'
+ * streams share queues and their kernels serialise (64 instances: 66 -> 39 ms per step).
  * ------------------------------------------------------------------------------------- */
 typedef struct rte_batch_s* rte_batch;
 

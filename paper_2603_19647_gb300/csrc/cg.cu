@@ -402,7 +402,7 @@ __host__ __device__ inline DsaRow dsa_row(int dim, int nx, int ny, int c, double
 }
 
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
-                      const double* sig_t, const double* sig_s, cudaStream_t s) {
+                      const double* sig_t, const double* sig_s, cudaStream_t s, int max_blocks) {
   const int n = nx * ny;
   op.nx = nx;
   op.ny = ny;
@@ -429,6 +429,7 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   const int want = (n + CT - 1) / CT;
   int cap = op.single_phase ? sms : 2 * sms;
   if (cap > per_sm * sms) cap = per_sm * sms;
+  if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
   op.blocks = want < cap ? want : cap;
   if (op.blocks < 1) op.blocks = 1;
   cudaError_t e;

@@ -166,6 +166,9 @@ cudaError_t launch_sum_pm(const Real* pm, int nfam, int n, double* out, int accu
 cudaError_t launch_isotropic_f32(const double* rho, int n, int nslot, int dl, float* f,
                                  cudaStream_t s);
 cudaError_t launch_to_float(const double* x, long n, float* y, cudaStream_t s);
+// BDF2 (options.time_scheme): f <- (4 f - prev) / 3 and prev <- the old f, elementwise
+template <class Real>
+cudaError_t launch_bdf2_history(Real* f, Real* prev, long n, cudaStream_t s);
 
 // DSA (cg.cu): 5-point (1D: 3-point) diffusion operator with Marshak vacuum faces.
 struct DsaOp {
@@ -181,8 +184,9 @@ struct DsaOp {
   int blocks;
   bool single_phase;   // cg1_kernel (one barrier per iteration) instead of cg_kernel
 };
+// max_blocks > 0 caps the blocks of the cooperative CG launch (default: one or two per SM).
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
-                      const double* sig_t_host, const double* sig_s_host, cudaStream_t s);
+                      const double* sig_t_host, const double* sig_s_host, cudaStream_t s, int max_blocks = 0);
 void dsa_free(DsaOp& op);
 // delta = C^{-1} (sig_s .* (residual - residual_b)) (residual_b may be nullptr);
 // rho_out = rho_half + delta and q_out = sig_s .* rho_out when rho_out != nullptr.

@@ -9,6 +9,11 @@ import os
 
 import numpy as np
 
+# Hardware work queues of the process's CUDA context, read when the context is created: the
+# default 8 makes the streams of batched instances (three each) share queues and serialise.
+# Takes effect only when this module is imported before anything initialises CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librte.so")
 
@@ -19,6 +24,7 @@ RTE_REL_INF, RTE_ABS_INF = range(2)
 RTE_ROM_OFF, RTE_ROM_AUTO, RTE_ROM_MANUAL = range(3)
 RTE_ROM_IG, RTE_ROM_PC = range(2)
 RTE_SA_DSA, RTE_SA_DMD_ITER = range(2)
+RTE_BE, RTE_BDF2 = range(2)
 STATUS_NAMES = {0: "RTE_OK", 1: "RTE_EINVAL", 2: "RTE_ENOMEM", 3: "RTE_ENOCONV", 4: "RTE_ECUDA",
                 5: "RTE_ETIMEOUT", 6: "RTE_ESTATE"}
 
@@ -60,7 +66,8 @@ class Options(ctypes.Structure):
                 ("sweep_rows", ctypes.c_int), ("sweep_lanes", ctypes.c_int),
                 ("sweep_warps", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("pc_levels", ctypes.c_int),
-                ("sa_kind", ctypes.c_int), ("mh_window", ctypes.c_int)]
+                ("sa_kind", ctypes.c_int), ("mh_window", ctypes.c_int),
+                ("cg_blocks", ctypes.c_int), ("time_scheme", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
