@@ -135,6 +135,12 @@ struct rte_s {
   // FNV-1a digest of the host cross sections and source given to rte_create (checked by
   // rte_load together with c_dt, so a blob of another problem on the same mesh is refused)
   uint64_t problem_digest = 0;
+  std::vector<double> sig_t_host, sig_s_host;   // for the DSA operator when tau changes
+  // BDF2 (options.time_scheme): f^{n-1} in the storage of f (f itself holds the history
+  // h^{n+1} = (4 f^n - f^{n-1}) / 3 between steps)
+  bool bdf2 = false;
+  double* f_prev = nullptr;
+  float* f_prev_f = nullptr;
   // state
   double g[4] = {0, 0, 0, 0};
   bool resp_ready = false;
@@ -174,6 +180,8 @@ rte_status cuda_fail(rte_handle h, cudaError_t e, const char* what) {
     rte_status s_ = (call);          \
     if (s_ != RTE_OK) return s_;     \
   } while (0)
+
+rte_status set_tau(rte_handle h, double tau);   // the step's tau (backward Euler / BDF2)
 
 // ---------------------------------------------------------------------------------------
 // Angular rules (Sec. 2.1, App. A).  Gauss-Legendre nodes by Newton's method on the
@@ -350,7 +358,7 @@ void free_all(rte_handle h) {
                   h->cg_iters, h->rho_init, h->f_init, h->sig_t_f, h->src_f, h->ca_f,
                   h->cb_f, h->cw_f, h->f_f, h->pm_f, h->edge_f, h->psi_w_f, h->q_f, h->f_init_f,
                   h->y_ir, h->rho_ref, h->cth_f, h->ctl_f, h->fb, h->fb_init, h->fref[0],
-                  h->fref[1], h->fref_init, h->sig_tl_f};
+                  h->fref[1], h->fref_init, h->sig_tl_f, h->f_prev, h->f_prev_f};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   dsa_free(h->dsa);
@@ -1068,6 +1076,15 @@ rte_status one_step(rte_handle h) {
   const int phase = !rom_on ? 0 : (!h->flag_ig ? 1 : (!all_pc_built(h) ? 2 : 3));
   // rho^n is final: the ROM update may start beside the fused sweep
   CK(cudaEventRecord(h->ev_rho, h->st));
+  // BDF2: the first step is a backward-Euler step; f^0 is kept for the first history
+  const bool bdf2_start = h->bdf2 && h->stats.steps == 0;
+  const size_t fcount = (size_t)h->ncell * h->L.nslot;
+  if (bdf2_start) {
+    if (h->fp32)
+      CK(cudaMemcpyAsync(h->f_prev_f, h->f_f, sizeof(float) * fcount, cudaMemcpyDeviceToDevice, h->st));
+    else
+      CK(cudaMemcpyAsync(h->f_prev, h->f, sizeof(double) * fcount, cudaMemcpyDeviceToDevice, h->st));
+  }
   // f^n and the next step's b~ (without inflow): Eq. (sweep_to_obtain_f), Eq. (implicit_linear_system_rho)
   mark = rec(h);
   TRY(sweep_f(h, h->rho, h->y));
@@ -1075,9 +1092,17 @@ rte_status one_step(rte_handle h) {
   span(h, SPAN_K2, mark, m);
   span(h, SPAN_SWEEP, mark, m);
   h->y_valid = true;
+  if (h->bdf2) {
+    // the buffer of f now holds the next step's history (4 f^n - f^{n-1}) / 3, that of f^{n-1}
+    // holds f^n; the next step sweeps its b~ from the history (pass B above used f^n)
+    if (h->fp32) CK(launch_bdf2_history<float>(h->f_f, h->f_prev_f, (long)fcount, h->st));
+    else CK(launch_bdf2_history<double>(h->f, h->f_prev, (long)fcount, h->st));
+    h->y_valid = false;
+  }
   bool rom_ran = false;
   rte_status rom_status = RTE_OK;
-  if (rom_on && conv && h->opt.rom == RTE_ROM_AUTO) {
+  // BDF2's backward-Euler first step gives the ROMs no snapshot
+  if (rom_on && conv && h->opt.rom == RTE_ROM_AUTO && !bdf2_start) {
     CK(cudaStreamWaitEvent(h->st2, h->ev_rho, 0));
     cudaStream_t main = h->st;
     h->st = h->st2;
@@ -1103,10 +1128,13 @@ rte_status one_step(rte_handle h) {
   h->stats.steps += 1;
   h->stats.last_iterations = iters;
   h->stats.total_iterations += iters;
-  h->stats.total_sweeps += iters + 2;
-  h->stats.cell_direction_updates += (long long)(iters + 2) * h->ncell * h->L.nv;
+  // BDF2: one sweep more per step (the next step's b~ from the history)
+  const int sweeps = iters + 2 + (h->bdf2 ? 1 : 0);
+  h->stats.total_sweeps += sweeps;
+  h->stats.cell_direction_updates += (long long)sweeps * h->ncell * h->L.nv;
+  if (bdf2_start) TRY(set_tau(h, 1.5 / h->c_dt));   // BDF2 from the second step on
   if (!conv) return fail(h, RTE_ENOCONV, "SI-SA reached max_iter without meeting eps_sisa");
-  if (rom_on && h->opt.rom == RTE_ROM_MANUAL) h->pending_rom = true;
+  if (rom_on && h->opt.rom == RTE_ROM_MANUAL && !bdf2_start) h->pending_rom = true;
   auto t1 = std::chrono::steady_clock::now();
   h->stats.time_total_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
   return RTE_OK;
@@ -1139,7 +1167,52 @@ rte_status upload(rte_handle h, double* dst, const double* src, long n) {
   return RTE_OK;
 }
 
+// FP32 tau + a + b of each slot as an exact hi / lo pair (tau and a, b rounded to FP32 once).
+void fp32_ct_pairs(rte_handle h, std::vector<float>& cth, std::vector<float>& ctl) {
+  const Layout& L = h->L;
+  const double tau32 = (double)(float)h->tau;
+  cth.resize(L.nslot);
+  ctl.resize(L.nslot);
+  for (int s = 0; s < L.nslot; ++s) {
+    const double a = (double)(float)(std::fabs(L.mu[s]) / h->hx);
+    const double b = h->dim == 2 ? (double)(float)(std::fabs(L.eta[s]) / h->hy) : 0.0;
+    const double ct = tau32 + a + b;
+    cth[s] = (float)ct;
+    ctl[s] = (float)(ct - (double)cth[s]);
+  }
+}
+
+// The step's tau = 1 / (c dt) (backward Euler) or 3 / (2 c dt) (BDF2): the FP64 inverse table,
+// the FP32 tau + a + b pairs, the DSA operator and the inflow responses follow it.
+rte_status set_tau(rte_handle h, double tau) {
+  if (h->tau == tau) return RTE_OK;
+  h->tau = tau;
+  const Layout& L = h->L;
+  if (!h->fp32 && h->dim == 2 && h->inv_d)
+    CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)h->ncell, L.nslot, L.dl,
+                            h->inv_d, h->st));
+  if (h->fp32 && h->cth_f) {
+    std::vector<float> cth, ctl;
+    fp32_ct_pairs(h, cth, ctl);
+    CK(cudaMemcpyAsync(h->cth_f, cth.data(), sizeof(float) * L.nslot, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->ctl_f, ctl.data(), sizeof(float) * L.nslot, cudaMemcpyHostToDevice, h->st));
+  }
+  if (h->fp32) {   // the refinement pair y_ir = T Sigma_s rho_ref belongs to the old tau
+    CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ncell, h->st));
+    CK(cudaMemsetAsync(h->rho_ref, 0, sizeof(double) * h->ncell, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  dsa_free(h->dsa);
+  CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, h->sig_t_host.data(),
+               h->sig_s_host.data(), h->st, h->opt.cg_blocks));
+  h->resp_ready = false;
+  h->y_valid = false;
+  return RTE_OK;
+}
+
 rte_status reset_state(rte_handle h) {
+  // BDF2 starts with a backward-Euler step
+  if (h->bdf2) TRY(set_tau(h, 1.0 / h->c_dt));
   if (h->fp32) {
     // refinement state: y_ir = T Sigma_s rho_ref with rho_ref = 0
     CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ncell, h->st));
@@ -1203,16 +1276,13 @@ rte_status setup_slots(rte_handle h) {
     // exactly as a hi / lo pair, and the weights nudged by whole ulps so that their exact
     // sum is 1 again.  The FP32 sweeps then apply the exact Q0 operator of these rounded
     // coefficients, which conserves particles like the FP64 one.
-    std::vector<float> a32(L.nslot), b32(L.nslot), cth(L.nslot), ctl(L.nslot), w32(L.nslot);
-    const double tau32 = (double)(float)h->tau;
+    std::vector<float> a32(L.nslot), b32(L.nslot), cth, ctl, w32(L.nslot);
     for (int s = 0; s < L.nslot; ++s) {
       a32[s] = (float)a[s];
       b32[s] = (float)b[s];
-      const double ct = tau32 + (double)a32[s] + (double)b32[s];
-      cth[s] = (float)ct;
-      ctl[s] = (float)(ct - (double)cth[s]);
       w32[s] = (float)L.w[s];
     }
+    fp32_ct_pairs(h, cth, ctl);
     balance_weights(w32);
     CK(dalloc(&h->ca_f, L.nslot));
     CK(dalloc(&h->cb_f, L.nslot));
@@ -1479,6 +1549,12 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.pc_levels < 1 || h->opt.pc_levels > RTE_MAX_PC_LEVELS)
     return fail(h, RTE_EINVAL, "pc_levels must be in [1, RTE_MAX_PC_LEVELS]");
   h->levels = h->opt.pc_levels;
+  if (h->opt.cg_blocks < 0) return fail(h, RTE_EINVAL, "cg_blocks must be >= 0");
+  if (h->opt.time_scheme != RTE_BE && h->opt.time_scheme != RTE_BDF2)
+    return fail(h, RTE_EINVAL, "time_scheme must be RTE_BE or RTE_BDF2");
+  if (h->opt.time_scheme == RTE_BDF2 && h->opt.precision == RTE_FP32_BF16F)
+    return fail(h, RTE_EINVAL, "RTE_BDF2 is not available with RTE_FP32_BF16F");
+  h->bdf2 = h->opt.time_scheme == RTE_BDF2;
   if (h->opt.sa_kind != RTE_SA_DSA && h->opt.sa_kind != RTE_SA_DMD_ITER)
     return fail(h, RTE_EINVAL, "sa_kind must be RTE_SA_DSA or RTE_SA_DMD_ITER");
   if (h->opt.mh_window == 0) h->opt.mh_window = 4;   // options zeroed by hand: the default
@@ -1611,7 +1687,20 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   }
   TRY(setup_slots(h));
   TRY(alloc_sweep(h));
-  CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st));
+  h->sig_t_host.assign(sigma_t, sigma_t + n);
+  h->sig_s_host.assign(sigma_s, sigma_s + n);
+  if (h->bdf2) {
+    const size_t fc = (size_t)n * h->L.nslot;
+    if (h->fp32) {
+      CK(dalloc(&h->f_prev_f, fc));
+      CK(cudaMemsetAsync(h->f_prev_f, 0, sizeof(float) * fc, h->st));
+    } else {
+      CK(dalloc(&h->f_prev, fc));
+      CK(cudaMemsetAsync(h->f_prev, 0, sizeof(double) * fc, h->st));
+    }
+  }
+  CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st,
+               h->opt.cg_blocks));
   CK(rom_alloc(h->ig, (int)n, h->opt.r_max));
   if (h->opt.sa_kind == RTE_SA_DMD_ITER) {
     CK(rom_alloc(h->mh, (int)n, h->opt.mh_window));
@@ -1671,6 +1760,10 @@ std::vector<StatePart> state_parts(rte_handle h) {
     v.push_back({h->fb, sizeof(__nv_bfloat16) * n * ns});
     v.push_back({h->fref[0], sizeof(float) * n});
     v.push_back({h->fref[1], sizeof(float) * n});
+  }
+  if (h->bdf2) {
+    if (h->fp32) v.push_back({h->f_prev_f, sizeof(float) * n * ns});
+    else v.push_back({h->f_prev, sizeof(double) * n * ns});
   }
   v.push_back({h->rho, sizeof(double) * n});
   v.push_back({h->y, sizeof(double) * n});
@@ -1901,8 +1994,11 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
   const Layout& L = h->L;
   const long n = h->ncell;
   std::vector<double> fl((size_t)n * L.nslot);
+  // BDF2 after a step: f^n sits in the buffer of f^{n-1} (that of f holds the history)
+  const bool prev = h->bdf2 && h->stats.steps > 0;
   if (!h->fp32) {
-    CK(cudaMemcpyAsync(fl.data(), h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(fl.data(), prev ? h->f_prev : h->f, sizeof(double) * fl.size(),
+                       cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (f_weights(h))
       for (size_t i = 0; i < fl.size(); ++i) {
@@ -1911,7 +2007,8 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
       }
   } else if (!h->bf16) {
     std::vector<float> ff(fl.size());
-    CK(cudaMemcpyAsync(ff.data(), h->f_f, sizeof(float) * ff.size(), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(ff.data(), prev ? h->f_prev_f : h->f_f, sizeof(float) * ff.size(),
+                       cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     for (size_t i = 0; i < ff.size(); ++i) fl[i] = ff[i];
   } else {
@@ -2051,6 +2148,9 @@ rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
   }
   if (!ok || used != left) return fail(h, RTE_EINVAL, "malformed ROM part of the checkpoint");
   TRY(sync_streams(h));
+  // BDF2: the step's tau is backward Euler's before the first step, BDF2's after it (set
+  // before the state is copied: a change of tau clears the FP32 refinement pair)
+  if (h->bdf2) TRY(set_tau(h, hd.stats.steps > 0 ? 1.5 / h->c_dt : 1.0 / h->c_dt));
   for (const auto& p : state_parts(h)) {
     CK(cudaMemcpyAsync(p.dev, in, p.bytes, cudaMemcpyHostToDevice, h->st));
     in += p.bytes;

@@ -245,6 +245,28 @@ cudaError_t launch_isotropic_f32(const double* rho, int n, int nslot, int dl, fl
   isotropic_f32_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, dl, f);
   return cudaGetLastError();
 }
+namespace {
+// BDF2 history after a step: f holds f^n, prev holds f^{n-1}; afterwards f holds the next
+// step's history h^{n+1} = (4 f^n - f^{n-1}) / 3 and prev holds f^n.
+template <class Real>
+__global__ void bdf2_history_kernel(Real* f, Real* prev, long n) {
+  const long i = (long)blockIdx.x * VT + threadIdx.x;
+  if (i >= n) return;
+  const Real t = f[i];
+  f[i] = (Real(4) * t - prev[i]) * (Real(1) / Real(3));
+  prev[i] = t;
+}
+}  // namespace
+
+template <class Real>
+cudaError_t launch_bdf2_history(Real* f, Real* prev, long n, cudaStream_t s) {
+  ++g_launches;
+  bdf2_history_kernel<Real><<<(unsigned)((n + VT - 1) / VT), VT, 0, s>>>(f, prev, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_bdf2_history<double>(double*, double*, long, cudaStream_t);
+template cudaError_t launch_bdf2_history<float>(float*, float*, long, cudaStream_t);
+
 cudaError_t launch_to_float(const double* x, long n, float* y, cudaStream_t s) {
   ++g_launches;
   to_float_kernel<<<(unsigned)((n + VT - 1) / VT), VT, 0, s>>>(x, n, y);

@@ -360,3 +360,64 @@ def test_checkerboard_full_workload_phase3_strict():
     wl = inputs.checkerboard()
     orc = _march(wl, wl.steps, 25, rom_on=True, decisions_p3=True, **WELL_CONDITIONED_PC)
     assert sum(s.phase == 3 for s in orc.log) >= 180
+
+
+@pytest.mark.parametrize("case", ["checkerboard_rom", "slab_rom", "checkerboard_plain"])
+def test_bdf2_march(case):
+    """BDF2 (options.time_scheme): a backward-Euler first step, then the BDF2 step's system with
+    its history; against the oracle's BDF2 march with the same decisions and 1e-10 (ROM on:
+    the preconditioner ROM truncated at eps_PC = 1e-3, §2 item 13 of the design notes)."""
+    wl = inputs.slab_1d(steps=60) if case == "slab_rom" else inputs.checkerboard(n=48)
+    steps = 60 if case == "slab_rom" else 80
+    rom_on = case != "checkerboard_plain"
+    o = dict(time_scheme=rte.RTE_BDF2, **WELL_CONDITIONED_PC)
+    h, p = make_pair(wl, rom=rte.RTE_ROM_AUTO if rom_on else rte.RTE_ROM_OFF, **o)
+    orc = stepper.OracleRTE(p, rom=rom_on, scheme="bdf2", **WELL_CONDITIONED_PC)
+    h.rte_set_initial(rho0=wl.rho0)
+    orc.set_initial(wl.rho0)
+    for n in range(1, steps + 1):
+        h.rte_step(1)
+        orc.step(1)
+        st, lg = h.rte_get_stats(), orc.log[-1]
+        assert st["last_iterations"] == lg.iterations, n
+        assert st["phase"] == (lg.phase if rom_on else 0), n
+        assert rel_l2(h.rte_get_scalar_flux(), orc.rho) < TOL, n
+    if rom_on:
+        assert max(s.phase for s in orc.log) == 3
+    h.destroy()
+
+
+@pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
+def test_bdf2_angular_flux_restart_and_checkpoint(precision):
+    """The angular flux of a BDF2 march is f^n (not the stored history) and matches the
+    oracle's; rte_restart begins again with a backward-Euler step (the march repeats bit for
+    bit); a checkpoint taken mid-march resumes bit for bit."""
+    from gpu_util import match_directions
+    wl = inputs.checkerboard(n=32)
+    wl.inflow = np.array([0.3, 0.0, 0.1, 0.0])
+    opts = dict(time_scheme=rte.RTE_BDF2, precision=precision)
+    h, p = make_pair(wl, **opts)
+    orc = stepper.OracleRTE(p, scheme="bdf2")
+    h.rte_set_initial(rho0=wl.rho0)
+    orc.set_initial(wl.rho0)
+    h.rte_step(12)
+    orc.step(12)
+    perm, _, _ = match_directions(h, wl.quadrature)
+    tol = TOL if precision == rte.RTE_FP64 else 1e-6
+    assert rel_l2(h.rte_get_angular_flux(), orc.f[perm]) < tol
+    rho12 = h.rte_get_scalar_flux()
+    blob = h.rte_save()
+    h.rte_step(6)
+    rho18 = h.rte_get_scalar_flux()
+    h.rte_restart()
+    h.rte_step(12)
+    assert np.array_equal(h.rte_get_scalar_flux(), rho12)
+    for pre_steps in (3, 0):   # a handle past its first step, and a fresh one
+        b, _ = make_pair(wl, **opts)
+        b.rte_set_initial(rho0=wl.rho0)
+        b.rte_step(pre_steps)
+        b.rte_load(blob)
+        b.rte_step(6)
+        assert np.array_equal(b.rte_get_scalar_flux(), rho18), pre_steps
+        b.destroy()
+    h.destroy()
