@@ -124,3 +124,12 @@ def test_quadrature_rule_rejects_bad_descriptions(lib, desc, dim):
         rte.rte_quadrature_rule(rte.quadrature_from(desc), dim)
     assert ei.value.status == rte.RTE_EINVAL
     assert len(str(ei.value)) > 12
+
+
+def test_march_cli_help():
+    """The command-line march parses its options before touching the GPU."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-m", "paper_2603_19647_gb300.march", "--help"],
+                       cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0 and "--precision" in r.stdout
