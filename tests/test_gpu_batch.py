@@ -17,6 +17,17 @@ def _small_batch(count=6, steps=24, seed=4):
     return inputs.batched(count=count, seed=seed, n_range=(128, 512), steps=steps, scale=0.1)
 
 
+def _alone_options(inst, precision):
+    """Options that give a handle stepped alone the same sweep tiles as batch instance `inst`
+    (FP32 batches take a fixed tile; FP64 instances tune exactly as a handle alone does)."""
+    if precision == rte.RTE_FP64:
+        return rte.default_options(precision=precision)
+    st = inst.rte_get_stats()
+    return rte.default_options(precision=precision, sweep_kernel=st["sweep_si_kernel"],
+                               sweep_lanes=st["sweep_lanes"], sweep_rows=st["sweep_si_rows"],
+                               sweep_warps=st["sweep_si_warps"])
+
+
 @pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
 def test_batch_matches_single_instances(precision):
     wls = _small_batch()
@@ -25,7 +36,7 @@ def test_batch_matches_single_instances(precision):
     b.rte_batch_step(12)
     b.rte_batch_step(12)
     for i, wl in enumerate(wls):
-        h = rte.create_from_workload(wl, options=rte.default_options(precision=precision))
+        h = rte.create_from_workload(wl, options=_alone_options(b.instance(i), precision))
         h.rte_step(24)
         a, s = b.instance(i).rte_get_scalar_flux(), h.rte_get_scalar_flux()
         st_b, st_h = b.instance(i).rte_get_stats(), h.rte_get_stats()
@@ -84,7 +95,7 @@ def test_batch_full_size_sampled():
     sides = [wl.nx for wl in wls]
     small = int(np.argmin(sides))
     for i in sorted({0, len(wls) // 2, len(wls) - 1, small, int(np.argmax(sides))}):
-        h = rte.create_from_workload(wls[i], options=rte.default_options(precision=rte.RTE_FP32))
+        h = rte.create_from_workload(wls[i], options=_alone_options(b.instance(i), rte.RTE_FP32))
         h.rte_step(3)
         a, s = b.instance(i).rte_get_scalar_flux(), h.rte_get_scalar_flux()
         assert b.instance(i).rte_get_stats()["total_iterations"] == h.rte_get_stats()["total_iterations"], i
@@ -94,4 +105,21 @@ def test_batch_full_size_sampled():
     orc.set_initial(wls[small].rho0)
     orc.step(3)
     assert rel_l2(b.instance(small).rte_get_scalar_flux(), orc.rho) < 1e-6
+    b.destroy()
+
+
+def test_batch_fp32_takes_the_concurrent_tile():
+    """FP32 batches whose options leave the sweep to the library take the tile sequence with
+    32 directions per lane group, 4-row tiles and 8 warps per CTA (fewer if shared memory is
+    short); FP64 batches and explicit choices are left alone."""
+    wls = _small_batch(count=2, steps=2)
+    b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32))
+    for i in range(2):
+        st = b.instance(i).rte_get_stats()
+        assert (st["sweep_si_kernel"], st["sweep_lanes"], st["sweep_si_rows"]) == (2, 32, 4)
+        assert st["sweep_tuned"] == 0
+    b.destroy()
+    b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32, sweep_rows=8,
+                                                      sweep_kernel=2))
+    assert b.instance(0).rte_get_stats()["sweep_si_rows"] == 8
     b.destroy()
