@@ -11,8 +11,9 @@ Modules (each function cites the passage of Liu & Peng, "On-the-fly ROM-based
 acceleration of SI-DSA for implicit time marching of the RTE", it follows):
 
 * ``quadrature``  Gauss-Legendre slab rule and Chebyshev-Legendre rule (Sec. 2.1, App. A).
-* ``transport``   Q0 upwind sweep + moment (Sec. 2.1 Eq. (DG), Sec. 2.2, Sec. 2.3), via a plain C loop nest.
-* ``dsa``         diffusion correction operator and conjugate gradients (Sec. 2.3 Eq. (rho_residual)).
+* ``transport``   Q0 and Q1 upwind DG sweeps + moment (Sec. 2.1 Eq. (DG), Sec. 2.2, Sec. 2.3), via plain C loop nests.
+* ``dsa``         diffusion correction operators (Q0 cell-centred; Q1 interior penalty) and conjugate
+                  gradients (Sec. 2.3 Eq. (rho_residual)).
 * ``sisa``        memory-efficient SI-SA, Algorithm 1.
 * ``rom``         incremental SVD (App. B) and the DMD reduced operators (Sec. 3.1, 3.2).
 * ``stepper``     the on-the-fly ROM-accelerated time march, Algorithm 2.

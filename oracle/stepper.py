@@ -91,15 +91,15 @@ class OracleRTE:
                   else dataclasses.replace(problem, c_dt=problem.c_dt * 2.0 / 3.0))
         self.A = _dsa.dsa_matrix(self.q)
         self.A_start = self.A if self.o["scheme"] == "be" else _dsa.dsa_matrix(problem)
-        self.rho = np.zeros(problem.ncell)
-        self.f = np.zeros((problem.nv, problem.ncell))
+        self.rho = np.zeros(problem.ndof)
+        self.f = np.zeros((problem.nv, problem.ndof))
         self.f_prev = self.f.copy()
         self.n = 0
         self.flag_ig = False
-        self.ig = _rom.IncrementalSVD(problem.ncell, self.o["r_max"])
+        self.ig = _rom.IncrementalSVD(problem.ndof, self.o["r_max"])
         # one preconditioner ROM per SI iteration l = 1 .. pc_levels, each with its Flag_PC
         L = int(self.o["pc_levels"])
-        self.pcs = [_rom.IncrementalSVD(problem.ncell, self.o["r_max"]) for _ in range(L)]
+        self.pcs = [_rom.IncrementalSVD(problem.ndof, self.o["r_max"]) for _ in range(L)]
         self.flags_pc = [False] * L
         self.log = []
 
@@ -114,12 +114,12 @@ class OracleRTE:
         return all(self.flags_pc)
 
     def set_initial(self, rho0, f0=None):
-        """f^0 = rho0 in every direction (isotropic) unless f0 [nv, ncell] is given."""
+        """f^0 = rho0 in every direction (isotropic) unless f0 [nv, ndof] is given."""
         self.rho = np.array(rho0, dtype=np.float64).ravel().copy()
         if f0 is None:
             self.f = np.tile(self.rho, (self.p.nv, 1))
         else:
-            self.f = np.array(f0, dtype=np.float64).reshape(self.p.nv, self.p.ncell).copy()
+            self.f = np.array(f0, dtype=np.float64).reshape(self.p.nv, self.p.ndof).copy()
             self.rho = self.p.w @ self.f
         self.f_prev = self.f.copy()   # BDF2: f^{-1} = f^0
 
