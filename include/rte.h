@@ -6,7 +6,9 @@
  * linear RTE with isotropic scattering and isotropic inflow (Sec. 2, Eq. (rte)) with
  *   - S_N directions (Sec. 2.1; Gauss-Legendre in 1D, Chebyshev-Legendre CL rule of App. A),
  *   - backward Euler in time (Sec. 2.1, Eq. (time_discrete)), tau = 1/(c dt),
- *   - upwind DG in space, lowest order Q0 member of Eq. (dg_space): one value per cell,
+ *   - upwind DG in space, Eq. (DG): the Q0 member of Eq. (dg_space) (one value per cell), or
+ *     with options.degree = 1 the Q1 member the paper computes with (bilinear functions on
+ *     each rectangle, 2D) and an interior-penalty DSA on the same space,
  *   - memory-efficient SI with DSA (Sec. 2.3, Algorithm 1),
  *   - on-the-fly DMD / incremental-SVD reduced models for the initial guess and the
  *     first-iteration preconditioner (Sec. 3, Algorithm 2, App. B).
@@ -21,7 +23,13 @@
  *     copied during the call; the caller keeps ownership of every pointer it passes.
  *   - Cell arrays have ncell = nx*ny entries, cell index c = i + nx*j (x fastest), FP64,
  *     whatever the internal precision.
- *   - Angular arrays are [n_dirs][ncell], direction order = the order rte_get_quadrature
+ *   - Arrays over the degrees of freedom (the source, rho0, scalar fluxes, residuals and ROM
+ *     snapshots) have ndof entries: ndof = ncell for degree 0; for degree 1, ndof = 4 ncell,
+ *     mode-major: mode k of cell c at k*ncell + c, where mode k = a + 2b is the coefficient of
+ *     p_a(xi) p_b(zeta), p_0 = 1, p_1 = sqrt(3) t, in the cell's local coordinates
+ *     xi, zeta in [-1, 1] (orthonormal under the cell average: mode 0 is the cell average).
+ *     sigma_t and sigma_s are per cell in both.
+ *   - Angular arrays are [n_dirs][ndof], direction order = the order rte_get_quadrature
  *     reports (for RTE_Q_EXPLICIT: the caller's order).
  *   - A handle is not thread-safe; use one handle per host thread.  All device work of a
  *     handle is issued on its own CUDA streams (or, after rte_set_stream, on the caller's
@@ -134,6 +142,13 @@ typedef struct {
                         rte_set_initial, rte_restart) is a backward-Euler step of c_dt and gives
                         the ROMs no snapshot.  Each step sweeps once more (b~ of the next step
                         from the history).  Not with RTE_FP32_BF16F. */
+  int degree;        /* K of the DG space Eq. (dg_space): 0 (default) one value per cell, or 1
+                        (2D, RTE_FP64): bilinear functions per rectangle with the upwind flux
+                        of Eq. (DG), four unknowns per cell-direction solved together in the
+                        sweeps, and a DSA by the symmetric interior-penalty discretisation of
+                        the diffusion correction on the same space (penalty
+                        max(2 (D_L + D_R) / h, 1/4) per face, Marshak condition taken weakly).
+                        The paper's own fully consistent DSA is given by citation only. */
 } rte_options;
 
 typedef struct {
@@ -159,7 +174,7 @@ typedef struct {
   /* 2D sweep tiling in use: directions per lane group, then rows per lane group and warps
    * per CTA of the SI sweep and of the fused f sweep; sweep_tuned = 1 when measured */
   int sweep_lanes, sweep_si_rows, sweep_si_warps, sweep_f_rows, sweep_f_warps, sweep_tuned;
-  int sweep_si_kernel, sweep_f_kernel;   /* 1 strip chain, 2 tile sequence */
+  int sweep_si_kernel, sweep_f_kernel;   /* 1 strip chain, 2 tile sequence, 3 Q1 strip chain */
   /* rank of the preconditioner ROM of each SI iteration l (index l - 1) and whether it was
    * updated in the last step (the l = 1 entries repeat pc_rank and pc_updated) */
   int pc_level_rank[RTE_MAX_PC_LEVELS];
@@ -171,7 +186,8 @@ typedef struct {
 void rte_default_options(rte_options* opt);
 
 /* Create a problem (Sec. 2 Eq. (rte), data of Eq. (kinetic_dg_discrete)).
- * sigma_t, sigma_s, source: host [ncell]; requires finite values, sigma_s >= 0,
+ * sigma_t, sigma_s: host [ncell]; source: host [ndof] (its modes for degree 1); requires
+ * finite values, sigma_s >= 0,
  * sigma_t >= sigma_s (Sec. 2), c_dt > 0, quadrature weights summing to 1 within 1e-12.
  * opt may be NULL (defaults).  Initial state: f^0 = 0, vacuum inflow.
  * On success *out owns all device memory; on failure *out = NULL. */
@@ -180,7 +196,7 @@ rte_status rte_create(rte_handle* out, const rte_mesh* mesh, const rte_quadratur
                       double c_dt, const rte_options* opt);
 
 /* Initial state: f^0_j = rho0 for every direction j (isotropic) when f0 == NULL, else
- * f^0 = f0 [n_dirs][ncell] and rho0 is ignored (may be NULL).  Resets the step counter,
+ * f^0 = f0 [n_dirs][ndof] and rho0 [ndof] is ignored (may be NULL).  Resets the step counter,
  * statistics and both ROMs. */
 rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0);
 
@@ -210,9 +226,9 @@ rte_status rte_step(rte_handle h, int nsteps);
  * since the last call. */
 rte_status rte_rom_update(rte_handle h);
 
-/* Copy rho^n (host [ncell]). */
+/* Copy rho^n (host [ndof]). */
 rte_status rte_get_scalar_flux(rte_handle h, double* rho);
-/* Copy f^n (host [n_dirs][ncell]). */
+/* Copy f^n (host [n_dirs][ndof]). */
 rte_status rte_get_angular_flux(rte_handle h, double* f);
 /* Copy the directions and weights in the library's direction order (host [n_dirs] each). */
 rte_status rte_get_quadrature(rte_handle h, int* n_dirs, double* mu, double* eta, double* w);
@@ -275,7 +291,7 @@ rte_status rte_op_rom_append(rte_handle h, int which, const double* x, const dou
                              double trunc_eps, int* grew);
 /* out = U c with A_r c = U^T rhs (Eq. (dmd-ig) / Eq. (dmd-sa)) for ROM `which`. */
 rte_status rte_op_rom_apply(rte_handle h, int which, const double* rhs, double* out);
-/* Rank, singular values (descending, [rank]) and optionally U ([rank][ncell]) and the
+/* Rank, singular values (descending, [rank]) and optionally U ([rank][ndof]) and the
  * reduced operator A_r = U^T W S^{-1} ([rank][rank], row-major); NULL skips an output. */
 rte_status rte_op_rom_get(rte_handle h, int which, int* rank, double* S, double* U, double* Ar);
 /* Drop both ROMs and the phase flags. */
@@ -327,8 +343,8 @@ typedef struct {
   rte_quadrature quad;
   const double* sigma_t;   /* host [ncell] */
   const double* sigma_s;   /* host [ncell] */
-  const double* source;    /* host [ncell] */
-  const double* rho0;      /* host [ncell]: isotropic initial flux f0 = rho0, or NULL (zero) */
+  const double* source;    /* host [ndof] */
+  const double* rho0;      /* host [ndof]: isotropic initial flux f0 = rho0, or NULL (zero) */
   double c_dt;
 } rte_problem;
 

@@ -13,6 +13,17 @@
 //   (1) p <- r + beta p (double-buffered, neighbours recomputed from r and the old p),
 //       Ap = C p, and the block partials of p.Ap;
 //   (2) x += alpha p, r -= alpha Ap and the block partials of r.r.
+//
+// Q1 scheme (bilinear modes per cell, mode-major vectors): C is the symmetric interior-penalty
+// DG discretisation of the same correction equation on the same bilinear space, with the
+// penalty of the modified-interior-penalty DSA (Wang and Ragusa, 2010), the Marshak condition
+// -D d(delta)/dn = delta / 2 taken weakly, and every term divided by the cell area:
+//   a(u, v) = sum_T int_T (D grad u . grad v + sigma_a~ u v)
+//           + sum_{interior F} int_F (kappa_F [u][v] - {D du/dn}[v] - [u]{D dv/dn})
+//           + sum_{boundary F} int_F u v / 2,     kappa_F = max(2 (D_L + D_R) / h_perp, 1/4).
+// On a tensor-product basis every term acts on the x modes or on the y modes alone, so the
+// operator of a cell is Xd (x) I + I (x) Yd on its own modes plus one 2 x 2 block per
+// neighbour: 14 coefficients per cell, set up on the host.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -37,6 +48,8 @@ struct CgArgs {
   const double* diag;
   const double* cx;
   const double* cy;
+  const double* blk;   // Q1: [14][ncell] Xd00 Xd01 Xd11 Yd00 Yd01 Yd11 Ex00 Ex01 Ex10 Ex11 Ny..
+  int ncell;           // Q1: cells (n = 4 ncell)
   const double* sig_s;
   const double* residual;
   const double* residual_b;   // optional: residual = residual - residual_b
@@ -129,6 +142,55 @@ __device__ double grid_total(const double* part) {
   return v;
 }
 
+// (C v) at vector index c for v given at c (vc) and elsewhere by a function of the index.
+// DEG 0: the 5-point (1D: 3-point) stencil.  DEG 1: index c = mode k ncell + cell, k = a + 2 b;
+// the cell's own block Xd (x) I + I (x) Yd, the +x neighbour's block Ex (x) I, the -x
+// neighbour's Ex^T (x) I (its own Ex), and likewise Ny for the y neighbours.
+template <int DEG, class V>
+__device__ __forceinline__ double op_apply(const CgArgs& a, int c, double vc, V v) {
+  if constexpr (DEG == 0) {
+    const int i = c % a.nx;
+    double s = a.diag[c] * vc;
+    if (i + 1 < a.nx) s -= a.cx[c] * v(c + 1);
+    if (i > 0) s -= a.cx[c - 1] * v(c - 1);
+    if (a.ny > 1) {
+      if (c + a.nx < a.n) s -= a.cy[c] * v(c + a.nx);
+      if (c - a.nx >= 0) s -= a.cy[c - a.nx] * v(c - a.nx);
+    }
+    return s;
+  } else {
+    const int nc = a.ncell, nx = a.nx;
+    const int k = c / nc, cell = c - k * nc;
+    const int am = k & 1, bm = k >> 1;
+    const int i = cell % nx, j = cell / nx;
+    const double* B = a.blk;
+    auto co = [&](int e, int cc) { return __ldg(B + (size_t)e * nc + cc); };
+    // own cell: x part (modes (a', b)) and y part (modes (a, b'))
+    const int ko = am ^ 1, kx = ko + 2 * bm, ky = am + 2 * (bm ^ 1);
+    const double xd_aa = co(am ? 2 : 0, cell), xd_ab = co(1, cell);
+    const double yd_bb = co(bm ? 5 : 3, cell), yd_ab = co(4, cell);
+    double s = (xd_aa + yd_bb) * vc + xd_ab * v(kx * nc + cell) + yd_ab * v(ky * nc + cell);
+    if (i + 1 < nx) {   // Ex[a][c'] v(c', b) of the +x neighbour
+      const int nb = cell + 1;
+      s += co(6 + 2 * am, cell) * v(2 * bm * nc + nb) + co(7 + 2 * am, cell) * v((1 + 2 * bm) * nc + nb);
+    }
+    if (i > 0) {        // Ex_{-x}[c'][a] v(c', b) of the -x neighbour
+      const int nb = cell - 1;
+      s += co(6 + am, nb) * v(2 * bm * nc + nb) + co(8 + am, nb) * v((1 + 2 * bm) * nc + nb);
+    }
+    if (j + 1 < a.ny) { // Ny[b][d] v(a, d) of the +y neighbour
+      const int nb = cell + nx;
+      s += co(10 + 2 * bm, cell) * v(am * nc + nb) + co(11 + 2 * bm, cell) * v((am + 2) * nc + nb);
+    }
+    if (j > 0) {        // Ny_{-y}[d][b] v(a, d) of the -y neighbour
+      const int nb = cell - nx;
+      s += co(10 + bm, nb) * v(am * nc + nb) + co(12 + bm, nb) * v((am + 2) * nc + nb);
+    }
+    return s;
+  }
+}
+
+template <int DEG>
 __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
@@ -157,19 +219,12 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
     // (1) p <- r + beta p ; Ap = C p ; p.Ap
     acc = 0.0;
     for (int c = tid; c < a.n; c += nth) {
-      const int i = c % a.nx;
       // Neighbours belong to other blocks: read them through L2 (__ldcg), never a stale L1 line.
       auto pval = [&](int k) {
         return (it == 0) ? __ldcg(pold + k) : __ldcg(a.r + k) + beta * __ldcg(pold + k);
       };
       const double pc = pval(c);
-      double s = a.diag[c] * pc;
-      if (i + 1 < a.nx) s -= a.cx[c] * pval(c + 1);
-      if (i > 0) s -= a.cx[c - 1] * pval(c - 1);
-      if (a.ny > 1) {
-        if (c + a.nx < a.n) s -= a.cy[c] * pval(c + a.nx);
-        if (c - a.nx >= 0) s -= a.cy[c - a.nx] * pval(c - a.nx);
-      }
+      const double s = op_apply<DEG>(a, c, pc, pval);
       pnew[c] = pc;
       a.ap[c] = s;
       acc += pc * s;
@@ -274,25 +329,16 @@ __device__ void grid_total2(const double* part0, const double* part1, double& t0
 // The setup forms only r = b and (b, b); the first step length needs (C r, r), which one more
 // phase computes when the stopping test lets CG iterate at all (a solve of k >= 1 iterations
 // takes k + 2 barriers, a solve that stops at once one).
+template <int DEG>
 __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
   const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
-  const int nx = a.nx, ny = a.ny, n = a.n;
+  const int n = a.n;
   double* partG = a.partial;
   double* partD = a.partial + gridDim.x;
-  // (C v)_c for v given at c (vc) and at the neighbours by a function of the cell index
-  auto apply = [&](int c, double vc, auto v) {
-    const int i = c % nx;
-    double s = a.diag[c] * vc;
-    if (i + 1 < nx) s -= a.cx[c] * v(c + 1);
-    if (i > 0) s -= a.cx[c - 1] * v(c - 1);
-    if (ny > 1) {
-      if (c + nx < n) s -= a.cy[c] * v(c + nx);
-      if (c - nx >= 0) s -= a.cy[c - nx] * v(c - nx);
-    }
-    return s;
-  };
+  // (C v)_c for v given at c (vc) and elsewhere by a function of the vector index
+  auto apply = [&](int c, double vc, auto v) { return op_apply<DEG>(a, c, vc, v); };
   // r = b = sig_s .* residual and (b, b)
   double g = 0.0, d = 0.0;
   for (int c = tid; c < n; c += nth) {
@@ -401,18 +447,108 @@ __host__ __device__ inline DsaRow dsa_row(int dim, int nx, int ny, int c, double
   return row;
 }
 
+namespace {
+// Coefficients of the Q1 interior-penalty operator, [14][ncell] (see the file comment).  Per
+// axis, on the reference interval with the orthonormal p_0 = 1, p_1 = sqrt(3) t: traces
+// P(+1) = (1, sqrt 3) and P(-1) = (1, -sqrt 3), derivative (2/h) (0, sqrt 3), stiffness
+// (4/h^2) diag(0, 3); a face term divided by the cell area carries 1/h.  For the face between
+// L (trace P(+1)) and R (trace P(-1)), test function on the rows and trial on the columns:
+//   LL = kappa P+ P+^T - D_L (P+ g^T + g P+^T) / 2
+//   LR = -kappa P+ P-^T - D_R P+ g^T / 2 + D_L g P-^T / 2
+//   RR = kappa P- P-^T + D_R (P- g^T + g P-^T) / 2
+// and a boundary face adds P P^T / 2 with the cell's own trace there.
+void dsa_q1_blocks(int nx, int ny, double hx, double hy, double tau, const double* sig_t,
+                   const double* sig_s, std::vector<double>& blk) {
+  const long nc = (long)nx * ny;
+  blk.assign((size_t)14 * nc, 0.0);
+  const double r3 = std::sqrt(3.0);
+  const double tp[2] = {1.0, r3}, tm[2] = {1.0, -r3};
+  auto D = [&](long k) { return 1.0 / (3.0 * (sig_t[k] + tau)); };
+  using M2 = double[2][2];
+  auto outer = [](const double* u, const double* v, double f, M2& out) {
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) out[a][b] += f * u[a] * v[b];
+  };
+  // the face's blocks, scaled by 1/h
+  auto face = [&](double h, double dl, double dr, M2& LL, M2& LR, M2& RR) {
+    const double g[2] = {0.0, 2.0 * r3 / h};
+    const double kap = std::fmax(2.0 * (dl + dr) / h, 0.25);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) LL[a][b] = LR[a][b] = RR[a][b] = 0.0;
+    outer(tp, tp, kap / h, LL);
+    outer(tp, g, -0.5 * dl / h, LL);
+    outer(g, tp, -0.5 * dl / h, LL);
+    outer(tp, tm, -kap / h, LR);
+    outer(tp, g, -0.5 * dr / h, LR);
+    outer(g, tm, 0.5 * dl / h, LR);
+    outer(tm, tm, kap / h, RR);
+    outer(tm, g, 0.5 * dr / h, RR);
+    outer(g, tm, 0.5 * dr / h, RR);
+  };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const long c = i + (long)nx * j;
+      const double dc = D(c);
+      for (int axis = 0; axis < 2; ++axis) {
+        const double h = axis == 0 ? hx : hy;
+        const bool lo_in = axis == 0 ? i > 0 : j > 0;
+        const bool hi_in = axis == 0 ? i + 1 < nx : j + 1 < ny;
+        const long lo = axis == 0 ? c - 1 : c - nx, hi = axis == 0 ? c + 1 : c + nx;
+        M2 d = {{0.0, 0.0}, {0.0, 0.0}}, LL, LR, RR;
+        d[1][1] = dc * 12.0 / (h * h);   // stiffness (4/h^2) diag(0, 3)
+        if (lo_in) {   // the cell is R of the low face
+          face(h, D(lo), dc, LL, LR, RR);
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) d[a][b] += RR[a][b];
+        } else {
+          outer(tm, tm, 0.5 / h, d);
+        }
+        if (hi_in) {   // the cell is L of the high face
+          face(h, dc, D(hi), LL, LR, RR);
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) d[a][b] += LL[a][b];
+          const int e0 = axis == 0 ? 6 : 10;
+          blk[(size_t)(e0 + 0) * nc + c] = LR[0][0];
+          blk[(size_t)(e0 + 1) * nc + c] = LR[0][1];
+          blk[(size_t)(e0 + 2) * nc + c] = LR[1][0];
+          blk[(size_t)(e0 + 3) * nc + c] = LR[1][1];
+        } else {
+          outer(tp, tp, 0.5 / h, d);
+        }
+        if (axis == 0) {
+          d[0][0] += sig_t[c] - sig_s[c] + tau;
+          d[1][1] += sig_t[c] - sig_s[c] + tau;
+        }
+        const int e0 = axis == 0 ? 0 : 3;
+        blk[(size_t)(e0 + 0) * nc + c] = d[0][0];
+        blk[(size_t)(e0 + 1) * nc + c] = d[0][1];
+        blk[(size_t)(e0 + 2) * nc + c] = d[1][1];
+      }
+    }
+}
+}  // namespace
+
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
-                      const double* sig_t, const double* sig_s, cudaStream_t s, int max_blocks) {
-  const int n = nx * ny;
+                      const double* sig_t, const double* sig_s, cudaStream_t s, int max_blocks,
+                      int degree) {
+  const int ncell = nx * ny;
+  const int n = degree == 1 ? 4 * ncell : ncell;
   op.nx = nx;
   op.ny = ny;
   op.n = n;
-  std::vector<double> diag(n), cx(n), cy(n);
-  for (int c = 0; c < n; ++c) {
-    const DsaRow row = dsa_row(dim, nx, ny, c, hx, hy, tau, sig_t, sig_s);
-    diag[c] = row.diag;
-    cx[c] = row.cx;
-    cy[c] = row.cy;
+  op.ncell = ncell;
+  op.deg = degree;
+  std::vector<double> diag, cx, cy, blk;
+  if (degree == 1) {
+    dsa_q1_blocks(nx, ny, hx, hy, tau, sig_t, sig_s, blk);
+  } else {
+    diag.resize(n), cx.resize(n), cy.resize(n);
+    for (int c = 0; c < n; ++c) {
+      const DsaRow row = dsa_row(dim, nx, ny, c, hx, hy, tau, sig_t, sig_s);
+      diag[c] = row.diag;
+      cx[c] = row.cx;
+      cy[c] = row.cy;
+    }
   }
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -423,8 +559,9 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   // per SM), which moves fewer bytes in solves of few iterations (measured: 256^2 cells 16-20 %
   // faster per solve with cg1_kernel, 1024^2 cells 20-25 % slower).
   op.single_phase = n <= (1 << 18);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op.single_phase ? cg1_kernel : cg_kernel,
-                                                CT, 0);
+  const void* kern = degree == 1 ? (op.single_phase ? (const void*)cg1_kernel<1> : (const void*)cg_kernel<1>)
+                                 : (op.single_phase ? (const void*)cg1_kernel<0> : (const void*)cg_kernel<0>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CT, 0);
   if (per_sm < 1) per_sm = 1;
   const int want = (n + CT - 1) / CT;
   int cap = op.single_phase ? sms : 2 * sms;
@@ -436,14 +573,23 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   const size_t bytes = sizeof(double) * (size_t)n;
   double** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x,
                      &op.r1, &op.w1, &op.s1};
+  op.blk = nullptr;
   for (double** b : bufs) {
     *b = nullptr;
     if (!op.single_phase && (b == &op.r1 || b == &op.w1 || b == &op.s1)) continue;
+    if (degree == 1 && (b == &op.diag || b == &op.cx || b == &op.cy)) continue;
     if ((e = cudaMalloc(b, bytes)) != cudaSuccess) return e;
   }
   if ((e = cudaMalloc(&op.partial, sizeof(double) * 2 * op.blocks)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&op.scal, 64)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(op.scal, 0, 64, s)) != cudaSuccess) return e;
+  if (degree == 1) {
+    if ((e = cudaMalloc(&op.blk, sizeof(double) * blk.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(op.blk, blk.data(), sizeof(double) * blk.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return e;
+    return cudaStreamSynchronize(s);
+  }
   if ((e = cudaMemcpyAsync(op.diag, diag.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return e;
   if ((e = cudaMemcpyAsync(op.cx, cx.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -455,7 +601,7 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
 
 void dsa_free(DsaOp& op) {
   double* bufs[] = {op.diag, op.cx, op.cy, op.r,       op.p0,      op.p1,  op.ap,
-                    op.x,    op.r1, op.w1, op.s1, op.partial, op.scal};
+                    op.x,    op.r1, op.w1, op.s1, op.partial, op.scal, op.blk};
   for (double* b : bufs)
     if (b) cudaFree(b);
   op = DsaOp{};
@@ -473,6 +619,8 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   a.diag = op.diag;
   a.cx = op.cx;
   a.cy = op.cy;
+  a.blk = op.blk;
+  a.ncell = op.ncell;
   a.sig_s = sig_s;
   a.residual = residual;
   a.residual_b = residual_b;
@@ -495,8 +643,10 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   a.iters = iters_dev;
   void* args[] = {&a};
   ++g_launches;
-  return cudaLaunchCooperativeKernel(op.single_phase ? (const void*)cg1_kernel : (const void*)cg_kernel,
-                                     dim3(op.blocks), dim3(CT), args, 0, s);
+  const void* kern = op.deg == 1
+                         ? (op.single_phase ? (const void*)cg1_kernel<1> : (const void*)cg_kernel<1>)
+                         : (op.single_phase ? (const void*)cg1_kernel<0> : (const void*)cg_kernel<0>);
+  return cudaLaunchCooperativeKernel(kern, dim3(op.blocks), dim3(CT), args, 0, s);
 }
 
 }  // namespace rte
@@ -577,7 +727,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<0>, CT, 0);
   int blocks = (n + CT - 1) / CT;
   int cap = (per_sm < 1 ? 1 : per_sm) * sms;
   if (cap > 2 * sms) cap = 2 * sms;
@@ -623,7 +773,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   a.iters = iters_dev;
   void* args[] = {&a};
   ++g_launches;
-  e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(CT), args, 0, s);
+  e = cudaLaunchCooperativeKernel((const void*)cg_kernel<0>, dim3(blocks), dim3(CT), args, 0, s);
   if (e != cudaSuccess) {
     *err = std::string("rte_dsa_solve_noalloc: ") + cudaGetErrorString(e);
     return RTE_ECUDA;

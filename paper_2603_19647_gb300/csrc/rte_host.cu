@@ -68,6 +68,10 @@ struct rte_s {
   // problem
   int dim = 2, nx = 0, ny = 0;
   long ncell = 0;
+  // DG degree (options.degree): nb unknowns per cell and direction (Q0: 1, Q1: 4), ndof =
+  // nb ncell per direction and in every rho-like vector (mode-major for Q1)
+  int deg = 0, nb = 1;
+  long ndof = 0;
   double hx = 1, hy = 1, c_dt = 1, tau = 1;
   rte_options opt{};
   std::vector<double> mu_user, eta_user, w_user;  // library direction order
@@ -75,7 +79,8 @@ struct rte_s {
   // 2D sweep tiles: [0] for the SI sweep and the y sweep, [1] for the fused f sweep
   struct Tile {
     int kind = 1;   // 1: strip chain (sweep.cu, R rows per lane group), 2: tile sequence
-                    // (sweep_tile.cu, FP32 modes, R = TH rows per lane group)
+                    // (sweep_tile.cu, FP32 modes, R = TH rows per lane group), 3: Q1 strip
+                    // chain (sweep_q1.cu, one warp per CTA)
     int R = 1, W = 8, rpb = 32, nblk = 1;
   } tile[2];
   int nblk_max = 1;   // edge buffers and control flags are sized for the larger tile count
@@ -281,7 +286,9 @@ int slot_of_f_index(const Layout& L, long ncell, long i) {
 
 // The 2D FP64 sweeps carry w psi per direction (their table holds w / (tau + sigma_t + a + b)),
 // so the stored angular flux there is w f: the per-slot weights to apply, else nullptr.
-const double* f_weights(rte_handle h) { return (h->dim == 2 && !h->fp32) ? h->cw : nullptr; }
+const double* f_weights(rte_handle h) {
+  return (h->dim == 2 && !h->fp32 && h->deg == 0) ? h->cw : nullptr;
+}
 
 int next_pow2(int v) {
   int p = 1;
@@ -471,6 +478,8 @@ void ghosts(const double g[4], Real gx[4], Real gy[4]) {
 // Launch a 2D sweep with the tile of its kind (tl).
 template <class Real>
 cudaError_t launch2d(rte_handle h, const Sweep2DArgs<Real>& a, int mode, const rte_s::Tile& tl) {
+  if constexpr (sizeof(Real) == 8)
+    if (tl.kind == 3) return launch_sweep_q1(a, mode, h->L.dl, tl.R, h->st);
   if (tl.kind == 2) return launch_sweep2d_tile(a, mode, tl.R, tl.W, h->st);
   return launch_sweep2d<Real>(a, mode, tl.R, h->st);
 }
@@ -563,24 +572,24 @@ int nparts(rte_handle h) { return h->dim == 2 ? h->L.nfam : 1; }
 // The sweep source q of the current precision: sigma_s (x - xref) (xref may be nullptr).
 rte_status set_q(rte_handle h, const double* x, const double* xref) {
   if (h->fp32)
-    CK(launch_scaled_diff<float>(x, xref, h->sig_s, (int)h->ncell, h->q_f, h->st, h->skip_now));
+    CK(launch_scaled_diff<float>(x, xref, h->sig_s, (int)h->ndof, h->q_f, h->st, h->skip_now));
   else
-    CK(launch_scaled_diff<double>(x, xref, h->sig_s, (int)h->ncell, h->q, h->st, h->skip_now));
+    CK(launch_scaled_diff<double>(x, xref, h->sig_s, (int)h->ndof, h->q, h->st, h->skip_now));
   return RTE_OK;
 }
 // Pass-A source sigma_s rho + G of the fused sweep.
 rte_status set_qa(rte_handle h, const double* rho) {
-  if (h->fp32) CK(launch_scaled_plus<float>(rho, h->sig_s, h->src, (int)h->ncell, h->q_f, h->st));
-  else CK(launch_scaled_plus<double>(rho, h->sig_s, h->src, (int)h->ncell, h->q, h->st));
+  if (h->fp32) CK(launch_scaled_plus<float>(rho, h->sig_s, h->src, (int)h->ndof, h->q_f, h->st));
+  else CK(launch_scaled_plus<double>(rho, h->sig_s, h->src, (int)h->ndof, h->q, h->st));
   return RTE_OK;
 }
 // out (+)= sum of the partial moments, in FP64.
 rte_status sum_pm(rte_handle h, double* out, int accumulate) {
   if (h->fp32)
-    CK(launch_sum_pm<float>(h->pm_f, nparts(h), (int)h->ncell, out, accumulate, h->st,
+    CK(launch_sum_pm<float>(h->pm_f, nparts(h), (int)h->ndof, out, accumulate, h->st,
                             h->skip_now));
   else
-    CK(launch_sum_pm<double>(h->pm, nparts(h), (int)h->ncell, out, accumulate, h->st,
+    CK(launch_sum_pm<double>(h->pm, nparts(h), (int)h->ndof, out, accumulate, h->st,
                              h->skip_now));
   return RTE_OK;
 }
@@ -592,8 +601,8 @@ rte_status sweep_q(rte_handle h, const double* g) {
 rte_status sweep_si(rte_handle h, const double* rho_or_null, const double* g, double* out) {
   if (rho_or_null) TRY(set_q(h, rho_or_null, nullptr));
   else {
-    if (h->fp32) CK(cudaMemsetAsync(h->q_f, 0, sizeof(float) * h->ncell, h->st));
-    else CK(cudaMemsetAsync(h->q, 0, sizeof(double) * h->ncell, h->st));
+    if (h->fp32) CK(cudaMemsetAsync(h->q_f, 0, sizeof(float) * h->ndof, h->st));
+    else CK(cudaMemsetAsync(h->q, 0, sizeof(double) * h->ndof, h->st));
   }
   TRY(sweep_q(h, g));
   TRY(sum_pm(h, out, 0));
@@ -679,7 +688,7 @@ rte_status ensure_responses(rte_handle h) {
   if (h->resp_ready) return RTE_OK;
   const int sides = h->dim == 2 ? 4 : 2;
   for (int s = 0; s < sides; ++s) {
-    if (!h->resp[s]) CK(dalloc(&h->resp[s], h->ncell));
+    if (!h->resp[s]) CK(dalloc(&h->resp[s], h->ndof));
     double g[4] = {0, 0, 0, 0};
     g[s] = 1.0;
     TRY(sweep_si(h, nullptr, g, h->resp[s]));
@@ -693,7 +702,7 @@ rte_status make_btilde(rte_handle h) {
     TRY(sweep_y(h, h->y));
     h->y_valid = true;
   }
-  CK(cudaMemcpyAsync(h->btilde, h->y, sizeof(double) * h->ncell, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->btilde, h->y, sizeof(double) * h->ndof, cudaMemcpyDeviceToDevice, h->st));
   const int sides = h->dim == 2 ? 4 : 2;
   bool any = false;
   for (int s = 0; s < sides; ++s) any = any || h->g[s] != 0.0;
@@ -701,7 +710,7 @@ rte_status make_btilde(rte_handle h) {
     TRY(ensure_responses(h));
     for (int s = 0; s < sides; ++s)
       if (h->g[s] != 0.0)
-        CK(launch_axpby(1.0, h->btilde, h->g[s], h->resp[s], (int)h->ncell, h->btilde, h->st));
+        CK(launch_axpby(1.0, h->btilde, h->g[s], h->resp[s], (int)h->ndof, h->btilde, h->st));
   }
   return RTE_OK;
 }
@@ -766,7 +775,7 @@ void resolve_spans(rte_handle h) {
 // iterations (Eq. (dmd-sa)); every other SA step is DSA.
 rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_out,
                  const double* init_src) {
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   const int nb = vec_blocks(n);
   const int absmode = h->opt.residual_norm == RTE_ABS_INF ? 1 : 0;
   // rho^{l-1} = rho^{(0)}, skip word and CG iteration slots cleared, in one launch
@@ -937,7 +946,7 @@ rte_status finish_cg_counts(rte_handle h) {
 // runs the first half on a second stream beside the fused f sweep, which neither reads nor
 // writes what it uses.
 rte_status rom_update_enqueue(rte_handle h) {
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   const int nb = vec_blocks(n);
   auto& pd = h->rom_pend;
   pd = rte_s::RomPending{};
@@ -1078,7 +1087,7 @@ rte_status one_step(rte_handle h) {
   CK(cudaEventRecord(h->ev_rho, h->st));
   // BDF2: the first step is a backward-Euler step; f^0 is kept for the first history
   const bool bdf2_start = h->bdf2 && h->stats.steps == 0;
-  const size_t fcount = (size_t)h->ncell * h->L.nslot;
+  const size_t fcount = (size_t)h->ndof * h->L.nslot;
   if (bdf2_start) {
     if (h->fp32)
       CK(cudaMemcpyAsync(h->f_prev_f, h->f_f, sizeof(float) * fcount, cudaMemcpyDeviceToDevice, h->st));
@@ -1198,13 +1207,13 @@ rte_status set_tau(rte_handle h, double tau) {
     CK(cudaMemcpyAsync(h->ctl_f, ctl.data(), sizeof(float) * L.nslot, cudaMemcpyHostToDevice, h->st));
   }
   if (h->fp32) {   // the refinement pair y_ir = T Sigma_s rho_ref belongs to the old tau
-    CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ncell, h->st));
-    CK(cudaMemsetAsync(h->rho_ref, 0, sizeof(double) * h->ncell, h->st));
+    CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ndof, h->st));
+    CK(cudaMemsetAsync(h->rho_ref, 0, sizeof(double) * h->ndof, h->st));
   }
   CK(cudaStreamSynchronize(h->st));
   dsa_free(h->dsa);
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, h->sig_t_host.data(),
-               h->sig_s_host.data(), h->st, h->opt.cg_blocks));
+               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg));
   h->resp_ready = false;
   h->y_valid = false;
   return RTE_OK;
@@ -1215,8 +1224,8 @@ rte_status reset_state(rte_handle h) {
   if (h->bdf2) TRY(set_tau(h, 1.0 / h->c_dt));
   if (h->fp32) {
     // refinement state: y_ir = T Sigma_s rho_ref with rho_ref = 0
-    CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ncell, h->st));
-    CK(cudaMemsetAsync(h->rho_ref, 0, sizeof(double) * h->ncell, h->st));
+    CK(cudaMemsetAsync(h->y_ir, 0, sizeof(double) * h->ndof, h->st));
+    CK(cudaMemsetAsync(h->rho_ref, 0, sizeof(double) * h->ndof, h->st));
     CK(cudaStreamSynchronize(h->st));
   }
   h->stats = rte_stats{};
@@ -1312,10 +1321,10 @@ void free_slots(rte_handle h) {
 // current layout; the edge buffers and flags are sized for nblk_max row blocks.
 rte_status alloc_sweep(rte_handle h) {
   const Layout& L = h->L;
-  const long n = h->ncell;
+  const long n = h->ncell, nd = h->ndof;
   if (!h->fp32) {
-    CK(dalloc(&h->f, (size_t)n * L.nslot));
-    CK(cudaMemsetAsync(h->f, 0, sizeof(double) * n * L.nslot, h->st));
+    CK(dalloc(&h->f, (size_t)nd * L.nslot));
+    CK(cudaMemsetAsync(h->f, 0, sizeof(double) * nd * L.nslot, h->st));
   } else if (!h->bf16) {
     CK(dalloc(&h->f_f, (size_t)n * L.nslot));
     CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * n * L.nslot, h->st));
@@ -1329,12 +1338,15 @@ rte_status alloc_sweep(rte_handle h) {
     h->fcur = 0;
   }
   if (h->dim == 2) {
-    const size_t edge = (size_t)2 * L.nfam * h->nblk_max * h->nx * L.dl;
+    // two passes (the fused sweep), times the face modes a row hands on (Q1: two)
+    const size_t edge = (size_t)2 * L.nfam * h->nblk_max * h->nx * L.dl * (h->deg == 1 ? 2 : 1);
     if (!h->fp32) {
-      CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
-      CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)n, L.nslot, L.dl, h->inv_d,
-                              h->st));
-      CK(dalloc(&h->pm, (size_t)L.nfam * n));
+      if (h->deg == 0) {   // the Q1 sweeps form their cell solves without a table
+        CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
+        CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)n, L.nslot, L.dl,
+                                h->inv_d, h->st));
+      }
+      CK(dalloc(&h->pm, (size_t)L.nfam * nd));
       CK(dalloc(&h->edge, edge));
     } else {
       CK(dalloc(&h->pm_f, (size_t)L.nfam * n));
@@ -1373,6 +1385,8 @@ void set_tile(rte_handle h, rte_s::Tile& tl, int kind, int R, int W) {
 // FP32 modes; the strip chain R <= dl) and every sweep mode's staging fits the 200 KiB the
 // launchers allow.
 bool tile_fits(rte_handle h, int dl, int kind, int R, int W) {
+  if (h->deg == 1) return kind == 3 && W == 1 && (R == 1 || R == 2 || R == 4);
+  if (kind == 3) return false;
   const int modes_plain[3] = {0, 1, 2}, modes_bf[3] = {0, 3, 4};
   const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
   if (kind == 2) {
@@ -1404,10 +1418,10 @@ rte_status time_sweeps(rte_handle h, int kind, float* ms) {
 }
 
 struct TuneKey {
-  int device, nx, ny, nv, precision;
+  int device, nx, ny, nv, precision, degree;
   bool operator<(const TuneKey& o) const {
-    return std::tie(device, nx, ny, nv, precision) <
-           std::tie(o.device, o.nx, o.ny, o.nv, o.precision);
+    return std::tie(device, nx, ny, nv, precision, degree) <
+           std::tie(o.device, o.nx, o.ny, o.nv, o.precision, o.degree);
   }
 };
 struct TuneVal {
@@ -1428,6 +1442,18 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
   const int dl_max = dq >= 32 ? 32 : std::max(8, next_pow2(dq));
   const bool fixed = h->opt.sweep_lanes || h->opt.sweep_rows || h->opt.sweep_warps ||
                      h->opt.sweep_kernel || !h->opt.tune;
+  if (fixed && h->deg == 1) {   // the Q1 strip chain: one warp per CTA
+    const int dl = h->opt.sweep_lanes ? h->opt.sweep_lanes : std::min(dl_max, 8);
+    const int R = h->opt.sweep_rows ? h->opt.sweep_rows : 2;
+    if (!tile_fits(h, dl, 3, R, 1)) return fail(h, RTE_EINVAL, "the Q1 sweep takes sweep_rows 1, 2 or 4");
+    for (auto& tl : h->tile) {
+      tl.kind = 3;
+      tl.R = R;
+      tl.W = 1;
+    }
+    *dl_out = dl;
+    return RTE_OK;
+  }
   if (fixed) {
     int dl = h->opt.sweep_lanes ? h->opt.sweep_lanes
                                 : std::min(dl_max, (!h->fp32 && h->ncell >= 512L * 512) ? 32 : 8);
@@ -1445,7 +1471,7 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     *dl_out = dl;
     return RTE_OK;
   }
-  const TuneKey key{h->device, h->nx, h->ny, (int)h->mu_user.size(), h->opt.precision};
+  const TuneKey key{h->device, h->nx, h->ny, (int)h->mu_user.size(), h->opt.precision, h->deg};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1468,9 +1494,11 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     TRY(make_layout(h, dl));
     std::vector<Cand> cand;
     const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8}, ths[3] = {2, 4, 8};
-    for (int R : rs)
+    for (int R : rs) {
+      if (tile_fits(h, dl, 3, R, 1)) cand.push_back({3, R, 1});
       for (int W : ws)
         if (tile_fits(h, dl, 1, R, W)) cand.push_back({1, R, W});
+    }
     // The FP64 tile sequence is left out of the search: on 256^2 and 1024^2 grids with 128
     // directions it measured 1.6-1.8x slower than the strip chain in both sweep modes (the
     // FP64 pipe, not the hand-offs, bounds those sweeps); it stays selectable by sweep_kernel.
@@ -1572,17 +1600,23 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.sweep_kernel < 0 || h->opt.sweep_kernel > 2)
     return fail(h, RTE_EINVAL, "sweep_kernel must be 0, 1 or 2");
   if (!(h->opt.eps_sisa >= 0.0)) return fail(h, RTE_EINVAL, "eps_sisa must be >= 0");
+  if (h->opt.degree != 0 && h->opt.degree != 1) return fail(h, RTE_EINVAL, "degree must be 0 or 1");
+  if (h->opt.degree == 1 && (mesh->dim != 2 || h->opt.precision != RTE_FP64))
+    return fail(h, RTE_EINVAL, "degree 1 (Q1) is available for 2D problems in RTE_FP64");
+  h->deg = h->opt.degree;
+  h->nb = h->deg == 1 ? 4 : 1;
   h->dim = mesh->dim;
   h->nx = mesh->nx;
   h->ny = mesh->ny;
   h->ncell = (long)mesh->nx * mesh->ny;
-  if (h->ncell > (1L << 31) / 2) return fail(h, RTE_EINVAL, "too many cells");
+  h->ndof = h->nb * h->ncell;
+  if (h->ndof > (1L << 31) / 2) return fail(h, RTE_EINVAL, "too many cells");
   h->hx = (mesh->x1 - mesh->x0) / mesh->nx;
   h->hy = mesh->dim == 2 ? (mesh->y1 - mesh->y0) / mesh->ny : 1.0;
   h->c_dt = c_dt;
   h->tau = 1.0 / c_dt;
   const long n = h->ncell;
-  if (!finite_all(sigma_t, n) || !finite_all(sigma_s, n) || !finite_all(source, n))
+  if (!finite_all(sigma_t, n) || !finite_all(sigma_s, n) || !finite_all(source, h->ndof))
     return fail(h, RTE_EINVAL, "non-finite cross section or source");
   for (long i = 0; i < n; ++i)
     if (sigma_s[i] < 0.0 || sigma_t[i] < sigma_s[i])
@@ -1596,7 +1630,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
                        const double* sigma_t, const double* sigma_s, const double* source,
                        double c_dt, const rte_options* opt) {
   TRY(validate_impl(h, mesh, quad, sigma_t, sigma_s, source, c_dt, opt));
-  const long n = h->ncell;
+  const long n = h->ncell, nd = h->ndof;
   CK(cudaGetDevice(&h->device));
   // The step's own stream runs at the highest priority and the two ROM-update streams at the
   // lowest, so that the block scheduler hands freed SMs to the critical path (the fused f
@@ -1628,16 +1662,21 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   CK(dalloc(&h->rom_partials, (size_t)(1 + RTE_MAX_PC_LEVELS) * 3 * 1024));
   // data that does not depend on the direction layout
   CK(dalloc(&h->sig_t, n));
-  CK(dalloc(&h->sig_s, n));
-  CK(dalloc(&h->src, n));
+  CK(dalloc(&h->sig_s, nd));
+  CK(dalloc(&h->src, nd));
   TRY(upload(h, h->sig_t, sigma_t, n));
-  TRY(upload(h, h->sig_s, sigma_s, n));
-  TRY(upload(h, h->src, source, n));
+  // sigma_s on every unknown of a cell (mode-major: the same value for each Q1 mode), so that
+  // the vector kernels scale rho-like vectors by it elementwise
+  for (int k = 0; k < h->nb; ++k) TRY(upload(h, h->sig_s + k * n, sigma_s, n));
+  TRY(upload(h, h->src, source, nd));
   {
     uint64_t d = 1469598103934665603ull;   // FNV-1a, 64 bit, over the bytes of the three arrays
+    const long lens[3] = {n, n, nd};
+    int ai = 0;
     for (const double* a : {sigma_t, sigma_s, source}) {
       const unsigned char* b = reinterpret_cast<const unsigned char*>(a);
-      for (size_t i = 0; i < sizeof(double) * (size_t)n; ++i) d = (d ^ b[i]) * 1099511628211ull;
+      for (size_t i = 0; i < sizeof(double) * (size_t)lens[ai]; ++i) d = (d ^ b[i]) * 1099511628211ull;
+      ++ai;
     }
     h->problem_digest = d;
   }
@@ -1655,15 +1694,15 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
       CK(cudaMemcpy(h->sig_tl_f, lo.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
     }
     CK(launch_to_float(h->src, n, h->src_f, h->st));
-    CK(dalloc(&h->q_f, n));
-    CK(dalloc(&h->y_ir, n));
-    CK(dalloc(&h->rho_ref, n));
+    CK(dalloc(&h->q_f, nd));
+    CK(dalloc(&h->y_ir, nd));
+    CK(dalloc(&h->rho_ref, nd));
   }
   double** vecs[] = {&h->rho, &h->rho_prev, &h->rho_half, &h->rho_half1, &h->rho0, &h->y,
                      &h->btilde, &h->q, &h->delta, &h->tmp, &h->tmp2, &h->tmp3, &h->delta_pc1};
   for (double** v : vecs) {
-    CK(dalloc(v, n));
-    CK(cudaMemsetAsync(*v, 0, sizeof(double) * n, h->st));
+    CK(dalloc(v, nd));
+    CK(cudaMemsetAsync(*v, 0, sizeof(double) * nd, h->st));
   }
   CK(dalloc(&h->partials, 3 * 1024));
   CK(dalloc(&h->dotbuf, 4));
@@ -1690,7 +1729,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   h->sig_t_host.assign(sigma_t, sigma_t + n);
   h->sig_s_host.assign(sigma_s, sigma_s + n);
   if (h->bdf2) {
-    const size_t fc = (size_t)n * h->L.nslot;
+    const size_t fc = (size_t)nd * h->L.nslot;
     if (h->fp32) {
       CK(dalloc(&h->f_prev_f, fc));
       CK(cudaMemsetAsync(h->f_prev_f, 0, sizeof(float) * fc, h->st));
@@ -1700,23 +1739,23 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
     }
   }
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st,
-               h->opt.cg_blocks));
-  CK(rom_alloc(h->ig, (int)n, h->opt.r_max));
+               h->opt.cg_blocks, h->deg));
+  CK(rom_alloc(h->ig, (int)nd, h->opt.r_max));
   if (h->opt.sa_kind == RTE_SA_DMD_ITER) {
-    CK(rom_alloc(h->mh, (int)n, h->opt.mh_window));
+    CK(rom_alloc(h->mh, (int)nd, h->opt.mh_window));
     for (double** q : {&h->mh_r[0], &h->mh_r[1], &h->mh_b, &h->mh_zero}) {
-      CK(dalloc(q, n));
-      CK(cudaMemsetAsync(*q, 0, sizeof(double) * n, h->st));
+      CK(dalloc(q, nd));
+      CK(cudaMemsetAsync(*q, 0, sizeof(double) * nd, h->st));
     }
   }
   for (int k = 0; k < h->levels; ++k) {
-    CK(rom_alloc(h->pcs[k], (int)n, h->opt.r_max));
+    CK(rom_alloc(h->pcs[k], (int)nd, h->opt.r_max));
     if (k == 0) continue;
     double** lv[] = {&h->lv_half[k], &h->lv_prev[k], &h->lv_delta[k], &h->lv_x[k], &h->lv_b[k],
                      &h->lv_diff[k]};
     for (double** q : lv) {
-      CK(dalloc(q, n));
-      CK(cudaMemsetAsync(*q, 0, sizeof(double) * n, h->st));
+      CK(dalloc(q, nd));
+      CK(cudaMemsetAsync(*q, 0, sizeof(double) * nd, h->st));
     }
   }
   CK(cudaStreamSynchronize(h->st));
@@ -1750,10 +1789,10 @@ struct StatePart {
 // What a step reads from the previous one: f^n (in the precision's storage), rho^n, the next
 // b~ without inflow (y) and, with FP32 sweeps, the refinement pair (rho_ref, y_ir).
 std::vector<StatePart> state_parts(rte_handle h) {
-  const size_t n = (size_t)h->ncell, ns = (size_t)h->L.nslot;
+  const size_t n = (size_t)h->ncell, nd = (size_t)h->ndof, ns = (size_t)h->L.nslot;
   std::vector<StatePart> v;
   if (!h->fp32) {
-    v.push_back({h->f, sizeof(double) * n * ns});
+    v.push_back({h->f, sizeof(double) * nd * ns});
   } else if (!h->bf16) {
     v.push_back({h->f_f, sizeof(float) * n * ns});
   } else {
@@ -1763,13 +1802,13 @@ std::vector<StatePart> state_parts(rte_handle h) {
   }
   if (h->bdf2) {
     if (h->fp32) v.push_back({h->f_prev_f, sizeof(float) * n * ns});
-    else v.push_back({h->f_prev, sizeof(double) * n * ns});
+    else v.push_back({h->f_prev, sizeof(double) * nd * ns});
   }
-  v.push_back({h->rho, sizeof(double) * n});
-  v.push_back({h->y, sizeof(double) * n});
+  v.push_back({h->rho, sizeof(double) * nd});
+  v.push_back({h->y, sizeof(double) * nd});
   if (h->fp32) {
-    v.push_back({h->rho_ref, sizeof(double) * n});
-    v.push_back({h->y_ir, sizeof(double) * n});
+    v.push_back({h->rho_ref, sizeof(double) * nd});
+    v.push_back({h->y_ir, sizeof(double) * nd});
   }
   return v;
 }
@@ -1784,6 +1823,37 @@ size_t rom_state_bytes_pcs(rte_handle h) {
   size_t b = 0;
   for (int k = 0; k < h->levels; ++k) b += rom_state_bytes(h->pcs[k]);
   return b;
+}
+
+// rte_set_initial for the Q1 scheme: rho0 [ndof] copied to every direction, or f0
+// [n_dirs][ndof] in the device layout [fam][cell][k][dl] with rho = sum_j w_j f0_j.
+rte_status set_initial_q1(rte_handle h, const double* rho0, const double* f0) {
+  const Layout& L = h->L;
+  const long n = h->ncell, nd = h->ndof;
+  if (f0) {
+    if (!finite_all(f0, nd * L.nv)) return fail(h, RTE_EINVAL, "non-finite f0");
+    std::vector<double> fl((size_t)nd * L.nslot, 0.0), rho(nd, 0.0);
+    for (int d = 0; d < L.nv; ++d) {
+      const int sl = L.slot_of_dir[d];
+      for (int k = 0; k < 4; ++k)
+        for (long c = 0; c < n; ++c) fl[f_index(L, 4 * n, 4 * c + k, sl)] = f0[(size_t)d * nd + k * n + c];
+    }
+    for (int d = 0; d < L.nv; ++d)
+      for (long i = 0; i < nd; ++i) rho[i] += h->w_user[d] * f0[(size_t)d * nd + i];
+    TRY(upload(h, h->rho, rho.data(), nd));
+    TRY(upload(h, h->f, fl.data(), (long)fl.size()));
+    if (!h->f_init) CK(dalloc(&h->f_init, fl.size()));
+    CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToDevice,
+                       h->st));
+    h->init_kind = 2;
+  } else {
+    if (!rho0) return fail(h, RTE_EINVAL, "rho0 or f0 is required");
+    if (!finite_all(rho0, nd)) return fail(h, RTE_EINVAL, "non-finite rho0");
+    TRY(upload(h, h->rho, rho0, nd));
+    CK(launch_isotropic_f_q1(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
+    h->init_kind = 1;
+  }
+  return RTE_OK;
 }
 
 rte_status sync_streams(rte_handle h) {
@@ -1844,7 +1914,8 @@ rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
   if (!h) return RTE_EINVAL;
   const long n = h->ncell;
   const Layout& L = h->L;
-  if (f0) {
+  if (h->deg == 1) TRY(set_initial_q1(h, rho0, f0));
+  else if (f0) {
     if (!finite_all(f0, n * L.nv)) return fail(h, RTE_EINVAL, "non-finite f0");
     std::vector<double> fl((size_t)n * L.nslot, 0.0), rho(n, 0.0);
     for (int d = 0; d < L.nv; ++d) {
@@ -1901,8 +1972,9 @@ rte_status rte_set_initial(rte_handle h, const double* rho0, const double* f0) {
     }
     h->init_kind = 1;
   }
-  if (!h->rho_init) CK(dalloc(&h->rho_init, n));
-  CK(cudaMemcpyAsync(h->rho_init, h->rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  if (!h->rho_init) CK(dalloc(&h->rho_init, h->ndof));
+  CK(cudaMemcpyAsync(h->rho_init, h->rho, sizeof(double) * h->ndof, cudaMemcpyDeviceToDevice,
+                     h->st));
   CK(cudaStreamSynchronize(h->st));
   return reset_state(h);
 }
@@ -1918,8 +1990,15 @@ rte_status rte_restart(rte_handle h) {
   if (!h) return RTE_EINVAL;
   if (h->init_kind == 0) return fail(h, RTE_ESTATE, "rte_set_initial has not been called");
   const long n = h->ncell;
-  CK(cudaMemcpyAsync(h->rho, h->rho_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  if (h->bf16) {
+  CK(cudaMemcpyAsync(h->rho, h->rho_init, sizeof(double) * h->ndof, cudaMemcpyDeviceToDevice,
+                     h->st));
+  if (h->deg == 1) {
+    if (h->init_kind == 2)
+      CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * h->ndof * h->L.nslot,
+                         cudaMemcpyDeviceToDevice, h->st));
+    else
+      CK(launch_isotropic_f_q1(h->rho, (int)n, h->L.nslot, h->L.dl, h->f, h->st));
+  } else if (h->bf16) {
     h->fcur = 0;
     if (h->init_kind == 2) {
       CK(cudaMemcpyAsync(h->fb, h->fb_init, sizeof(__nv_bfloat16) * n * h->L.nslot,
@@ -1984,7 +2063,7 @@ rte_status rte_rom_update(rte_handle h) {
 
 rte_status rte_get_scalar_flux(rte_handle h, double* rho) {
   if (!h || !rho) return RTE_EINVAL;
-  CK(cudaMemcpyAsync(rho, h->rho, sizeof(double) * h->ncell, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(rho, h->rho, sizeof(double) * h->ndof, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return RTE_OK;
 }
@@ -1993,6 +2072,21 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
   if (!h || !f) return RTE_EINVAL;
   const Layout& L = h->L;
   const long n = h->ncell;
+  if (h->deg == 1) {
+    // device [fam][cell][k][dl] -> caller [dir][k ncell + cell]
+    std::vector<double> fl((size_t)h->ndof * L.nslot);
+    const bool prev = h->bdf2 && h->stats.steps > 0;
+    CK(cudaMemcpyAsync(fl.data(), prev ? h->f_prev : h->f, sizeof(double) * fl.size(),
+                       cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int d = 0; d < L.nv; ++d) {
+      const int sl = L.slot_of_dir[d];
+      for (int k = 0; k < 4; ++k)
+        for (long c = 0; c < n; ++c)
+          f[(size_t)d * h->ndof + k * n + c] = fl[f_index(L, 4 * n, 4 * c + k, sl)];
+    }
+    return RTE_OK;
+  }
   std::vector<double> fl((size_t)n * L.nslot);
   // BDF2 after a step: f^n sits in the buffer of f^{n-1} (that of f holds the history)
   const bool prev = h->bdf2 && h->stats.steps > 0;
@@ -2093,7 +2187,7 @@ rte_status rte_save(rte_handle h, void* buf, size_t bytes) {
   hd.flag_ig = h->flag_ig ? 1 : 0;
   hd.flag_pc = 0;
   for (int k = 0; k < h->levels; ++k) hd.flag_pc |= h->flags_pc[k] ? 1 << k : 0;
-  hd.reserved = (uint32_t)h->levels;
+  hd.reserved = (uint32_t)(h->levels | (h->deg << 8));   // pc_levels and the DG degree
   hd.fcur = h->fcur;
   hd.bf_seed = h->bf_seed;
   hd.c_dt = h->c_dt;
@@ -2125,9 +2219,9 @@ rte_status rte_load(rte_handle h, const void* buf, size_t bytes) {
     return fail(h, RTE_EINVAL, "not a checkpoint of this library version");
   if (hd.dim != h->dim || hd.nx != h->nx || hd.ny != h->ny || hd.nslot != h->L.nslot ||
       hd.dl != h->L.dl || hd.nfam != h->L.nfam || hd.precision != h->opt.precision ||
-      hd.r_max != h->opt.r_max || hd.reserved != (uint32_t)h->levels)
+      hd.r_max != h->opt.r_max || hd.reserved != (uint32_t)(h->levels | (h->deg << 8)))
     return fail(h, RTE_EINVAL,
-                "checkpoint of another mesh, direction layout, precision, r_max or pc_levels");
+                "checkpoint of another mesh, direction layout, precision, r_max, pc_levels or degree");
   if (hd.c_dt != h->c_dt || hd.problem_digest != h->problem_digest)
     return fail(h, RTE_EINVAL, "checkpoint of another time step, cross sections or source");
   if (hd.bytes != bytes) return fail(h, RTE_EINVAL, "checkpoint length differs from its header");
@@ -2206,7 +2300,7 @@ void rte_destroy(rte_handle h) {
 
 rte_status rte_op_sweep(rte_handle h, const double* rho, double* out) {
   if (!h || !rho || !out) return RTE_EINVAL;
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   TRY(upload(h, h->tmp, rho, n));
   TRY(set_q(h, h->tmp, nullptr));
   cudaEventRecord(h->kev0, h->st);
@@ -2227,7 +2321,7 @@ rte_status rte_op_sweep(rte_handle h, const double* rho, double* out) {
 
 rte_status rte_op_fsweep(rte_handle h, const double* rho, double* btilde) {
   if (!h || !rho) return RTE_EINVAL;
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   TRY(upload(h, h->tmp, rho, n));
   cudaEventRecord(h->kev0, h->st);
   TRY(sweep_f(h, h->tmp, h->y));
@@ -2250,7 +2344,7 @@ rte_status rte_op_fsweep(rte_handle h, const double* rho, double* btilde) {
 
 rte_status rte_op_dsa(rte_handle h, const double* residual, double* delta, int* iterations) {
   if (!h || !residual || !delta) return RTE_EINVAL;
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   TRY(upload(h, h->tmp, residual, n));
   CK(dsa_solve(h->dsa, h->sig_s, h->tmp, nullptr, h->opt.cg_rtol, h->opt.cg_max_iter, h->delta,
                nullptr, nullptr, nullptr, h->cg_iters, h->st));
@@ -2265,7 +2359,7 @@ rte_status rte_op_dsa(rte_handle h, const double* residual, double* delta, int* 
 rte_status rte_op_rom_append(rte_handle h, int which, const double* x, const double* b,
                              double trunc_eps, int* grew) {
   if (!h || !x || !b || (which != RTE_ROM_IG && which != RTE_ROM_PC)) return RTE_EINVAL;
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   TRY(upload(h, h->tmp2, x, n));
   TRY(upload(h, h->tmp3, b, n));
   RomDev& R = which == RTE_ROM_IG ? h->ig : h->pc;
@@ -2280,7 +2374,7 @@ rte_status rte_op_rom_apply(rte_handle h, int which, const double* rhs, double* 
   if (!h || !rhs || !out || (which != RTE_ROM_IG && which != RTE_ROM_PC)) return RTE_EINVAL;
   RomDev& R = which == RTE_ROM_IG ? h->ig : h->pc;
   if (R.rank <= 0 || !R.lu_ok) return fail(h, RTE_ESTATE, "ROM is empty or its operator is singular");
-  const int n = (int)h->ncell;
+  const int n = (int)h->ndof;
   TRY(upload(h, h->tmp2, rhs, n));
   CK(rom_apply(R, h->tmp2, h->tmp3, h->st));
   CK(cudaMemcpyAsync(out, h->tmp3, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
@@ -2379,7 +2473,7 @@ rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* proble
       if (p.rho0) {
         s = rte_set_initial(b->h[i], p.rho0, nullptr);
       } else {
-        std::vector<double> z((size_t)b->h[i]->ncell, 0.0);
+        std::vector<double> z((size_t)b->h[i]->ndof, 0.0);
         s = rte_set_initial(b->h[i], z.data(), nullptr);
       }
       if (s != RTE_OK) g_create_error = b->h[i]->err;

@@ -91,6 +91,14 @@ struct Sweep1DArgs {
   Real g_lo, g_hi;      // inflow at x0 (for mu > 0) and x1 (for mu < 0), pass A
 };
 
+// Q1 sweeps (sweep_q1.cu), FP64, mode 0 / 1 / 2 as in the Q0 strip chain; one warp per CTA,
+// rows_per_blk = (32 / dl) R.  q, g2: [4][ncell]; f: [nfam][ncell][4][dl]; pm: [nfam][4][ncell];
+// edge: per pass [nfam][nblk][nx][2][dl] (mode 1: two passes).
+cudaError_t launch_sweep_q1(const Sweep2DArgs<double>& a, int mode, int dl, int R, cudaStream_t s);
+// f[fam][cell][k][dl] = rho[k ncell + cell] in every slot (isotropic Q1 angular flux)
+cudaError_t launch_isotropic_f_q1(const double* rho, int ncell, int nslot, int dl, double* f,
+                                  cudaStream_t s);
+
 // Launchers (sweep.cu).
 // Dynamic shared memory of one 2D sweep CTA (the launcher rejects more than 200 KiB).
 size_t sweep2d_smem_bytes(size_t real, int dl, int R, int W, int mode, bool table);
@@ -172,10 +180,12 @@ cudaError_t launch_bdf2_history(Real* f, Real* prev, long n, cudaStream_t s);
 
 // DSA (cg.cu): 5-point (1D: 3-point) diffusion operator with Marshak vacuum faces.
 struct DsaOp {
-  int nx, ny, n;
-  double* diag;   // [n]
-  double* cx;     // [n] coupling of cell c with c+1 (0 at the east edge)
-  double* cy;     // [n] coupling of cell c with c+nx (0 at the north edge / 1D)
+  int nx, ny, n;  // n: unknowns (Q0: cells; Q1: 4 modes per cell, mode-major)
+  int ncell, deg;
+  double* diag;   // Q0 [n]
+  double* cx;     // Q0 [n] coupling of cell c with c+1 (0 at the east edge)
+  double* cy;     // Q0 [n] coupling of cell c with c+nx (0 at the north edge / 1D)
+  double* blk;    // Q1 [14][ncell] block coefficients
   // CG workspace
   double *r, *p0, *p1, *ap, *x;
   double *r1, *w1, *s1;   // second buffers of the single-barrier CG (r, w = C r, s = C p)
@@ -185,8 +195,10 @@ struct DsaOp {
   bool single_phase;   // cg1_kernel (one barrier per iteration) instead of cg_kernel
 };
 // max_blocks > 0 caps the blocks of the cooperative CG launch (default: one or two per SM).
+// degree 1: the Q1 interior-penalty operator (2D) on mode-major vectors of 4 nx ny values.
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
-                      const double* sig_t_host, const double* sig_s_host, cudaStream_t s, int max_blocks = 0);
+                      const double* sig_t_host, const double* sig_s_host, cudaStream_t s,
+                      int max_blocks = 0, int degree = 0);
 void dsa_free(DsaOp& op);
 // delta = C^{-1} (sig_s .* (residual - residual_b)) (residual_b may be nullptr);
 // rho_out = rho_half + delta and q_out = sig_s .* rho_out when rho_out != nullptr.

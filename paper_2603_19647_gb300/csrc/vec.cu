@@ -143,6 +143,14 @@ __global__ void isotropic_f_kernel(const double* rho, int n, int nslot, int dl, 
   f[i] = w ? w[(i / ((long)n * dl)) * dl + i % dl] * rho[c] : rho[c];
 }
 
+// Q1: f[fam][cell][k][dl] = rho[k ncell + cell] (mode-major rho) in every slot.
+__global__ void isotropic_f_q1_kernel(const double* rho, int ncell, int nslot, int dl, double* f) {
+  const long i = (long)blockIdx.x * VT + threadIdx.x;
+  if (i >= 4L * ncell * nslot) return;
+  const long k = (i / dl) % 4, c = (i / (4L * dl)) % ncell;
+  f[i] = rho[k * ncell + c];
+}
+
 __global__ void dot_partial_kernel(const double* x, const double* y, int n, double* partials) {
   __shared__ double sh[VT / 32];
   double s = 0.0;
@@ -365,6 +373,14 @@ cudaError_t launch_isotropic_f(const double* rho, int n, int nslot, int dl, cons
   const long tot = (long)n * nslot;
   ++g_launches;
   isotropic_f_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, n, nslot, dl, w, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_isotropic_f_q1(const double* rho, int ncell, int nslot, int dl, double* f,
+                                  cudaStream_t s) {
+  const long tot = 4L * ncell * nslot;
+  ++g_launches;
+  isotropic_f_q1_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, ncell, nslot, dl, f);
   return cudaGetLastError();
 }
 

@@ -67,7 +67,8 @@ class Options(ctypes.Structure):
                 ("sweep_warps", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("pc_levels", ctypes.c_int),
                 ("sa_kind", ctypes.c_int), ("mh_window", ctypes.c_int),
-                ("cg_blocks", ctypes.c_int), ("time_scheme", ctypes.c_int)]
+                ("cg_blocks", ctypes.c_int), ("time_scheme", ctypes.c_int),
+                ("degree", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -181,12 +182,15 @@ def default_options(**kw):
 
 
 class Handle:
-    """One problem instance (an ``rte_handle``).  Methods mirror the C calls one to one."""
+    """One problem instance (an ``rte_handle``).  Methods mirror the C calls one to one.
+    Vectors over the degrees of freedom have ndof entries (ncell, or 4 ncell mode-major for the
+    Q1 scheme, ``options.degree = 1``)."""
 
-    def __init__(self, ptr, ncell, nv):
+    def __init__(self, ptr, ncell, nv, ndof=None):
         self.ptr = ptr
         self.ncell = ncell
         self.nv = nv
+        self.ndof = ncell if ndof is None else ndof
 
     def _check(self, status):
         if status != RTE_OK:
@@ -208,8 +212,8 @@ class Handle:
             pass
 
     def rte_set_initial(self, rho0=None, f0=None):
-        rho0 = None if rho0 is None else _f64(rho0, self.ncell)
-        f0 = None if f0 is None else _f64(f0, self.ncell * self.nv)
+        rho0 = None if rho0 is None else _f64(rho0, self.ndof)
+        f0 = None if f0 is None else _f64(f0, self.ndof * self.nv)
         self._check(load().rte_set_initial(self.ptr, _p(rho0), _p(f0)))
 
     def rte_set_inflow(self, g):
@@ -231,12 +235,12 @@ class Handle:
         self._check(load().rte_rom_update(self.ptr))
 
     def rte_get_scalar_flux(self):
-        out = np.empty(self.ncell)
+        out = np.empty(self.ndof)
         self._check(load().rte_get_scalar_flux(self.ptr, _p(out)))
         return out
 
     def rte_get_angular_flux(self):
-        out = np.empty((self.nv, self.ncell))
+        out = np.empty((self.nv, self.ndof))
         self._check(load().rte_get_angular_flux(self.ptr, _p(out)))
         return out
 
@@ -266,35 +270,35 @@ class Handle:
 
     # operator-level calls ------------------------------------------------------------
     def rte_op_sweep(self, rho):
-        rho = _f64(rho, self.ncell)
-        out = np.empty(self.ncell)
+        rho = _f64(rho, self.ndof)
+        out = np.empty(self.ndof)
         self._check(load().rte_op_sweep(self.ptr, _p(rho), _p(out)))
         return out
 
     def rte_op_fsweep(self, rho):
-        rho = _f64(rho, self.ncell)
-        out = np.empty(self.ncell)
+        rho = _f64(rho, self.ndof)
+        out = np.empty(self.ndof)
         self._check(load().rte_op_fsweep(self.ptr, _p(rho), _p(out)))
         return out
 
     def rte_op_dsa(self, residual):
-        r = _f64(residual, self.ncell)
-        out = np.empty(self.ncell)
+        r = _f64(residual, self.ndof)
+        out = np.empty(self.ndof)
         its = ctypes.c_int(0)
         self._check(load().rte_op_dsa(self.ptr, _p(r), _p(out), ctypes.byref(its)))
         return out, its.value
 
     def rte_op_rom_append(self, which, x, b, trunc_eps=-1.0):
-        x = _f64(x, self.ncell)
-        b = _f64(b, self.ncell)
+        x = _f64(x, self.ndof)
+        b = _f64(b, self.ndof)
         grew = ctypes.c_int(0)
         self._check(load().rte_op_rom_append(self.ptr, int(which), _p(x), _p(b), float(trunc_eps),
                                              ctypes.byref(grew)))
         return bool(grew.value)
 
     def rte_op_rom_apply(self, which, rhs):
-        rhs = _f64(rhs, self.ncell)
-        out = np.empty(self.ncell)
+        rhs = _f64(rhs, self.ndof)
+        out = np.empty(self.ndof)
         self._check(load().rte_op_rom_apply(self.ptr, int(which), _p(rhs), _p(out)))
         return out
 
@@ -302,7 +306,7 @@ class Handle:
         r = ctypes.c_int(0)
         self._check(load().rte_op_rom_get(self.ptr, int(which), ctypes.byref(r), None, None, None))
         r = r.value
-        S, U, Ar = np.empty(r), np.empty((r, self.ncell)), np.empty((r, r))
+        S, U, Ar = np.empty(r), np.empty((r, self.ndof)), np.empty((r, r))
         if r:
             self._check(load().rte_op_rom_get(self.ptr, int(which), None, _p(S), _p(U), _p(Ar)))
         return S, U, Ar
@@ -311,12 +315,29 @@ class Handle:
         self._check(load().rte_op_rom_reset(self.ptr))
 
 
+def _ndof(n, options):
+    return 4 * n if options is not None and options.degree == 1 else n
+
+
+def as_modes(x, n, nd):
+    """A per-cell array as the degrees of freedom of a piecewise-constant field: unchanged for
+    Q0; for Q1 the cell values are mode 0 (the cell average) and the other modes are zero."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    if x.size == nd or nd == n:
+        return x
+    out = np.zeros(nd)
+    out[:n] = x
+    return out
+
+
 def rte_create(mesh: Mesh, quad: Quadrature, sigma_t, sigma_s, source, c_dt, options=None):
     """rte_create; returns a Handle.  mesh / quad: ctypes structs (see ``mesh_from`` and
-    ``quadrature_from``); arrays are per cell, x fastest."""
+    ``quadrature_from``); sigma_t, sigma_s per cell, x fastest; source per degree of freedom
+    (a per-cell source is taken as piecewise constant, see ``as_modes``)."""
     lib = load()
     n = mesh.nx * mesh.ny
-    st, ss, G = _f64(sigma_t, n), _f64(sigma_s, n), _f64(source, n)
+    nd = _ndof(n, options)
+    st, ss, G = _f64(sigma_t, n), _f64(sigma_s, n), _f64(as_modes(source, n, nd), nd)
     h = _vp()
     opt = ctypes.byref(options) if options is not None else None
     status = lib.rte_create(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), _p(st), _p(ss),
@@ -325,7 +346,7 @@ def rte_create(mesh: Mesh, quad: Quadrature, sigma_t, sigma_s, source, c_dt, opt
         raise RteError(status, lib.rte_last_error(None).decode())
     nv = ctypes.c_int(0)
     lib.rte_get_quadrature(h, ctypes.byref(nv), None, None, None)
-    return Handle(h, n, nv.value)
+    return Handle(h, n, nv.value, nd)
 
 
 def rte_dsa_solve_noalloc(dim, nx, ny, x0, x1, y0, y1, c_dt, sigma_t_dev, sigma_s_dev,
@@ -383,7 +404,7 @@ def create_from_workload(wl, options=None, quad=None):
     """rte_create + rte_set_initial for an inputs.Workload (inflow set when nonzero)."""
     h = rte_create(mesh_from(wl), quad if quad is not None else quadrature_from(wl.quadrature),
                    wl.sigma_t, wl.sigma_s, wl.source, wl.c_dt, options)
-    h.rte_set_initial(wl.rho0)
+    h.rte_set_initial(as_modes(wl.rho0, h.ncell, h.ndof))
     if np.any(wl.inflow):
         h.rte_set_inflow(wl.inflow)
     return h
@@ -437,7 +458,9 @@ def rte_batch_create(workloads, options=None):
     keep = []
     for i, wl in enumerate(workloads):
         nc = wl.nx * wl.ny
-        arrs = [_f64(wl.sigma_t, nc), _f64(wl.sigma_s, nc), _f64(wl.source, nc), _f64(wl.rho0, nc)]
+        nd = _ndof(nc, options)
+        arrs = [_f64(wl.sigma_t, nc), _f64(wl.sigma_s, nc), as_modes(wl.source, nc, nd),
+                as_modes(wl.rho0, nc, nd)]
         q = quadrature_from(wl.quadrature)
         keep.append((arrs, q))
         probs[i] = Problem(mesh_from(wl), q, _p(arrs[0]), _p(arrs[1]), _p(arrs[2]), _p(arrs[3]),
@@ -452,7 +475,7 @@ def rte_batch_create(workloads, options=None):
         hp = lib.rte_batch_instance(b, i)
         nv = ctypes.c_int(0)
         lib.rte_get_quadrature(hp, ctypes.byref(nv), None, None, None)
-        h = Handle(_vp(hp), wl.nx * wl.ny, nv.value)
+        h = Handle(_vp(hp), wl.nx * wl.ny, nv.value, _ndof(wl.nx * wl.ny, options))
         h._owned_by_batch = True
         handles.append(h)
     return Batch(b, handles, keep)

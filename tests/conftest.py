@@ -22,13 +22,21 @@ def oracle_quadrature(quad):
     return q.cl_hemisphere(quad[1], quad[2])
 
 
-def oracle_problem(wl, quad=None):
+def cell_modes(x, degree):
+    """A per-cell array as the unknowns of a piecewise-constant field: itself for Q0; for Q1
+    the cell values in mode 0 (the cell average) and zero in the three linear modes."""
+    x = np.asarray(x, dtype=float).ravel()
+    return x.copy() if degree == 0 else np.concatenate([x, np.zeros(3 * x.size)])
+
+
+def oracle_problem(wl, quad=None, degree=0):
     """oracle.transport.Problem from an inputs.Workload (both sides get the same arrays)."""
     from oracle.transport import Problem
     mu, eta, w = quad if quad is not None else oracle_quadrature(wl.quadrature)
     x0, x1, y0, y1 = wl.domain
     return Problem(wl.nx, wl.ny, x0, x1, y0, y1, mu, eta, w, wl.sigma_t.copy(),
-                   wl.sigma_s.copy(), wl.source.copy(), wl.c_dt, np.array(wl.inflow, dtype=float))
+                   wl.sigma_s.copy(), cell_modes(wl.source, degree), wl.c_dt,
+                   np.array(wl.inflow, dtype=float), degree=degree)
 
 
 @pytest.fixture

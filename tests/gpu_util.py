@@ -39,8 +39,8 @@ def lib_options(**kw):
 
 
 def make_pair(wl, **opts):
-    """Library handle and oracle problem for the same workload."""
+    """Library handle and oracle problem for the same workload (options.degree on both)."""
     o = lib_options(**opts)
     h = rte.create_from_workload(wl, options=o)
-    p = oracle_problem(wl)
+    p = oracle_problem(wl, degree=opts.get("degree", 0))
     return h, p

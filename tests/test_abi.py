@@ -42,6 +42,7 @@ def test_default_options(lib):
     assert (o.max_iter, o.r_max, o.cg_rtol, o.cg_max_iter) == (500, 40, 1e-6, 500)
     assert o.pc_levels == 1 and rte.MAX_PC_LEVELS == 4
     assert o.sa_kind == rte.RTE_SA_DSA and o.mh_window == 4
+    assert o.degree == 0
 
 
 def _create(**kw):
@@ -72,6 +73,9 @@ def _create(**kw):
     dict(options=rte.default_options(time_scheme=2)),
     dict(options=rte.default_options(time_scheme=rte.RTE_BDF2, precision=rte.RTE_FP32_BF16F)),
     dict(options=rte.default_options(pc_levels=-1)),
+    dict(options=rte.default_options(degree=2)),
+    dict(options=rte.default_options(degree=1, precision=rte.RTE_FP32)),
+    dict(options=rte.default_options(degree=1), source=np.r_[np.zeros(63), np.inf]),
 ])
 def test_invalid_problems_rejected(lib, bad):
     with pytest.raises(rte.RteError) as ei:
@@ -97,6 +101,14 @@ def test_bf16_storage_is_2d_only(lib):
     wl = inputs.slab_1d(n=16)
     with pytest.raises(rte.RteError) as ei:
         rte.create_from_workload(wl, options=rte.default_options(precision=rte.RTE_FP32_BF16F))
+    assert ei.value.status == rte.RTE_EINVAL
+
+
+def test_q1_is_2d_only(lib):
+    from paper_2603_19647_gb300 import inputs
+    wl = inputs.slab_1d(n=16)
+    with pytest.raises(rte.RteError) as ei:
+        rte.create_from_workload(wl, options=rte.default_options(degree=1))
     assert ei.value.status == rte.RTE_EINVAL
 
 

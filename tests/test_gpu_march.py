@@ -19,7 +19,7 @@ wrong gate, a wrong kernel) moves the march by orders of magnitude more."""
 import numpy as np
 import pytest
 
-from conftest import oracle_problem
+from conftest import cell_modes, oracle_problem
 from gpu_util import make_pair, rel_l2
 from oracle import stepper
 from paper_2603_19647_gb300 import inputs, rte
@@ -33,19 +33,19 @@ ENVELOPE_FACTOR = 50.0
 PERTURBATION = 2e-16
 
 
-def _perturbed_oracles(wl, rom_on, oopts, k=3):
+def _perturbed_oracles(wl, rom_on, oopts, k=3, degree=0):
     """k oracle marches whose source (or, without one, sigma_t) is perturbed by a relative
     2e-16 (seeded normal numbers): rounding-sized changes of the input."""
     out = []
     for seed in range(1, k + 1):
-        p = oracle_problem(wl)
+        p = oracle_problem(wl, degree=degree)
         rng = np.random.default_rng(seed)
         if np.any(p.source):
-            p.source = p.source * (1 + PERTURBATION * rng.standard_normal(p.ncell))
+            p.source = p.source * (1 + PERTURBATION * rng.standard_normal(p.ndof))
         else:
             p.sigma_t = p.sigma_t * (1 + PERTURBATION * rng.standard_normal(p.ncell))
         o = stepper.OracleRTE(p, rom=rom_on, **oopts)
-        o.set_initial(wl.rho0)
+        o.set_initial(cell_modes(wl.rho0, degree))
         out.append(o)
     return out
 
@@ -66,9 +66,12 @@ def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, decisions
         oopts["up_rel"] = bool(oopts["up_rel"])
     if "sa_kind" in opts:
         oopts["sa"] = "mh" if opts["sa_kind"] == rte.RTE_SA_DMD_ITER else "dsa"
+    if "time_scheme" in opts:
+        oopts["scheme"] = "bdf2" if opts["time_scheme"] == rte.RTE_BDF2 else "be"
+    deg = opts.get("degree", 0)
     orc = stepper.OracleRTE(p, rom=rom_on, **oopts)
-    orc.set_initial(wl.rho0)
-    pert = [] if exact else _perturbed_oracles(wl, rom_on, oopts)
+    orc.set_initial(cell_modes(wl.rho0, deg))
+    pert = [] if exact else _perturbed_oracles(wl, rom_on, oopts, degree=deg)
     envelope = 0.0
     in_p3 = False
     phases_lib, phases_orc = [], []
