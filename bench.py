@@ -39,6 +39,9 @@ UNIT = "cell-direction updates/s"
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA (4 flop) per clock x 2.07 GHz = 1.2586 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FLOP_PER_UPDATE = 7          # two multiply-adds, one multiply by 1/d, one multiply-add (moment)
+# Q1 SI sweep: the closed-form bilinear cell solve (106 FP64 flops, multiply-add = 2) and the
+# weighted moment of its four modes (8)
+Q1_FLOPS_PER_UPDATE = 114
 PROFILE = os.path.join(ROOT, "profiles", "sweep_si_fp64_checkerboard.md")
 SWEEP_SRC = [os.path.join(ROOT, "paper_2603_19647_gb300", "csrc", f)
              for f in ("sweep.cu", "sweep_common.cuh")]
@@ -218,6 +221,20 @@ def extra_workloads(rte, inputs, torch):
         r["speedup_vs_sidsa_fp64"] = q64["ms_per_step"] / r["ms_per_step"]
     out[f"diffusive_disc_2048sq_256dirs_{disc.steps}steps"] = {
         "rom_fp64": d64, "rom_fp32": d32, "rom_bf16_f": dbf, "sidsa_fp64": q64}
+    # the paper's own discretisation: Q1 upwind DG (options.degree = 1) on the headline
+    # checkerboard, ROM-accelerated and plain SI-DSA, full length
+    cb = inputs.checkerboard()
+    k64, _ = march(cb, cb.steps, cb.steps, rom=rte.RTE_ROM_AUTO, degree=1)
+    k0, _ = march(cb, cb.steps, cb.steps, rom=rte.RTE_ROM_OFF, degree=1)
+    k64["speedup_vs_sidsa_fp64"] = k0["ms_per_step"] / k64["ms_per_step"]
+    # roofline of the Q1 SI sweep: FP64 flops per cell-direction of its closed-form cell solve
+    # (106, FMA = 2) and the weighted moment (8), against the nominal FP64 peak
+    flops = Q1_FLOPS_PER_UPDATE * cb.ncell * 128
+    for r in (k64, k0):
+        r["si_sweep_roofline"] = {"bound": "fp64", "achieved": flops / (r["si_sweep_ms"] * 1e-3) / 1e12,
+                                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": flops / (r["si_sweep_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    out[f"checkerboard_256sq_128dirs_q1_{cb.steps}steps"] = {"rom_fp64": k64, "sidsa_fp64": k0}
     wls = inputs.batched()
     b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32))
     b.rte_batch_step(2)

@@ -25,7 +25,7 @@
 // is one warp that takes the top row of its strip from the CTA above through global memory,
 // published in chunks of K columns behind a release flag.  CTAs take tickets in
 // row-block-major order, so a CTA only waits for CTAs that already started.  A cell solve is
-// about sixty FP64 operations: the kernel is bound by the FP64 pipe, not by memory, and reads
+// about a hundred FP64 flops: the kernel is bound by the FP64 pipe, not by memory, and reads
 // its per-cell data straight from global memory.  All waits are bounded.
 #include <cuda_runtime.h>
 
@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<double> 
           double s[4], fA[4], ox[2], oy[2];
 #pragma unroll
           for (int md = 0; md < 4; ++md) {
-            if constexpr (MODE == 2) s[md] = fma(tau, fo[md], A.g2[md * ncell + cell]);
+            if constexpr (MODE == 0) s[md] = A.q[md * ncell + cell];
+            else if constexpr (MODE == 2) s[md] = fma(tau, fo[md], A.g2[md * ncell + cell]);
             else s[md] = fma(tau, fo[md], A.q[md * ncell + cell]);
           }
           q1_cell(cc, ax, ay, ux, uy, s, xA[m], tyA, fA, ox, oy);

@@ -27,6 +27,10 @@ def main(argv=None):
     ap.add_argument("--sa", choices=["dsa", "dmd"], default="dsa")
     ap.add_argument("--scheme", choices=["be", "bdf2"], default="be")
     ap.add_argument("--r-max", type=int, default=40)
+    ap.add_argument("--degree", type=int, choices=[0, 1], default=0,
+                    help="DG degree: 0 (one value per cell) or 1 (bilinear, 2D FP64)")
+    ap.add_argument("--lanes", type=int, default=0, help="sweep_lanes (0: the library's choice)")
+    ap.add_argument("--rows", type=int, default=0, help="sweep_rows (0: the library's choice)")
     a = ap.parse_args(argv)
     wl = inputs.BY_NAME[a.workload]()
     steps = a.steps if a.steps is not None else wl.steps
@@ -35,7 +39,8 @@ def main(argv=None):
         rom=rte.RTE_ROM_AUTO if a.rom == "on" else rte.RTE_ROM_OFF,
         pc_levels=a.pc_levels, r_max=a.r_max,
         sa_kind=rte.RTE_SA_DMD_ITER if a.sa == "dmd" else rte.RTE_SA_DSA,
-        time_scheme=rte.RTE_BDF2 if a.scheme == "bdf2" else rte.RTE_BE)
+        time_scheme=rte.RTE_BDF2 if a.scheme == "bdf2" else rte.RTE_BE,
+        degree=a.degree, sweep_lanes=a.lanes, sweep_rows=a.rows)
     h = rte.create_from_workload(wl, options=opts)
     t0 = time.perf_counter()
     h.rte_step(steps)
