@@ -143,7 +143,8 @@ typedef struct {
                         the ROMs no snapshot.  Each step sweeps once more (b~ of the next step
                         from the history).  Not with RTE_FP32_BF16F. */
   int degree;        /* K of the DG space Eq. (dg_space): 0 (default) one value per cell, or 1
-                        (2D, RTE_FP64): bilinear functions per rectangle with the upwind flux
+                        (2D; RTE_FP64, or RTE_FP32 with FP32 sweeps and f refined by the FP64
+                        residual as for degree 0): bilinear functions per rectangle with the upwind flux
                         of Eq. (DG), four unknowns per cell-direction solved together in the
                         sweeps, and a DSA by the symmetric interior-penalty discretisation of
                         the diffusion correction on the same space (penalty

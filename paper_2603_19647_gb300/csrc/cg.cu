@@ -49,6 +49,7 @@ struct CgArgs {
   const double* cx;
   const double* cy;
   const double* blk;   // Q1: [14][ncell] Xd00 Xd01 Xd11 Yd00 Yd01 Yd11 Ex00 Ex01 Ex10 Ex11 Ny..
+  const double* dinv;  // Q1: [n] inverse diagonal of C (the Jacobi preconditioner)
   int ncell;           // Q1: cells (n = 4 ncell)
   const double* sig_s;
   const double* residual;
@@ -142,55 +143,79 @@ __device__ double grid_total(const double* part) {
   return v;
 }
 
-// (C v) at vector index c for v given at c (vc) and elsewhere by a function of the index.
-// DEG 0: the 5-point (1D: 3-point) stencil.  DEG 1: index c = mode k ncell + cell, k = a + 2 b;
-// the cell's own block Xd (x) I + I (x) Yd, the +x neighbour's block Ex (x) I, the -x
-// neighbour's Ex^T (x) I (its own Ex), and likewise Ny for the y neighbours.
-template <int DEG, class V>
+// (C v) at cell index c of the 5-point (1D: 3-point) stencil, for v given at c (vc) and at the
+// neighbours by a function of the index.
+template <class V>
 __device__ __forceinline__ double op_apply(const CgArgs& a, int c, double vc, V v) {
-  if constexpr (DEG == 0) {
-    const int i = c % a.nx;
-    double s = a.diag[c] * vc;
-    if (i + 1 < a.nx) s -= a.cx[c] * v(c + 1);
-    if (i > 0) s -= a.cx[c - 1] * v(c - 1);
-    if (a.ny > 1) {
-      if (c + a.nx < a.n) s -= a.cy[c] * v(c + a.nx);
-      if (c - a.nx >= 0) s -= a.cy[c - a.nx] * v(c - a.nx);
-    }
-    return s;
-  } else {
-    const int nc = a.ncell, nx = a.nx;
-    const int k = c / nc, cell = c - k * nc;
-    const int am = k & 1, bm = k >> 1;
-    const int i = cell % nx, j = cell / nx;
-    const double* B = a.blk;
-    auto co = [&](int e, int cc) { return __ldg(B + (size_t)e * nc + cc); };
-    // own cell: x part (modes (a', b)) and y part (modes (a, b'))
-    const int ko = am ^ 1, kx = ko + 2 * bm, ky = am + 2 * (bm ^ 1);
-    const double xd_aa = co(am ? 2 : 0, cell), xd_ab = co(1, cell);
-    const double yd_bb = co(bm ? 5 : 3, cell), yd_ab = co(4, cell);
-    double s = (xd_aa + yd_bb) * vc + xd_ab * v(kx * nc + cell) + yd_ab * v(ky * nc + cell);
-    if (i + 1 < nx) {   // Ex[a][c'] v(c', b) of the +x neighbour
-      const int nb = cell + 1;
-      s += co(6 + 2 * am, cell) * v(2 * bm * nc + nb) + co(7 + 2 * am, cell) * v((1 + 2 * bm) * nc + nb);
-    }
-    if (i > 0) {        // Ex_{-x}[c'][a] v(c', b) of the -x neighbour
-      const int nb = cell - 1;
-      s += co(6 + am, nb) * v(2 * bm * nc + nb) + co(8 + am, nb) * v((1 + 2 * bm) * nc + nb);
-    }
-    if (j + 1 < a.ny) { // Ny[b][d] v(a, d) of the +y neighbour
-      const int nb = cell + nx;
-      s += co(10 + 2 * bm, cell) * v(am * nc + nb) + co(11 + 2 * bm, cell) * v((am + 2) * nc + nb);
-    }
-    if (j > 0) {        // Ny_{-y}[d][b] v(a, d) of the -y neighbour
-      const int nb = cell - nx;
-      s += co(10 + bm, nb) * v(am * nc + nb) + co(12 + bm, nb) * v((am + 2) * nc + nb);
-    }
-    return s;
+  const int i = c % a.nx;
+  double s = a.diag[c] * vc;
+  if (i + 1 < a.nx) s -= a.cx[c] * v(c + 1);
+  if (i > 0) s -= a.cx[c - 1] * v(c - 1);
+  if (a.ny > 1) {
+    if (c + a.nx < a.n) s -= a.cy[c] * v(c + a.nx);
+    if (c - a.nx >= 0) s -= a.cy[c - a.nx] * v(c - a.nx);
+  }
+  return s;
+}
+
+// Q1: (C v) for the four modes of one cell (mode k = a + 2b at index k ncell + cell), given
+// the cell's own modes u and the neighbours' by a function of the vector index, each
+// neighbour value taken once.  With U[a][b] = u[a + 2b]:
+//   Y = Xd U + U Yd^T + Ex U_{+x} + Ex_{-x}^T U_{-x} + U_{+y} Ny^T + U_{-y} Ny_{-y}
+// (Xd, Yd symmetric; Ex, Ny the cell's own blocks to its +x and +y neighbours, Ex_{-x} and
+// Ny_{-y} those of the -x and -y neighbours, i.e. the transposes of the blocks seen from here).
+template <class V>
+__device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const double u[4], V v,
+                                              double y[4]) {
+  const int nc = a.ncell, nx = a.nx;
+  const int i = cell % nx, j = cell / nx;
+  const double* B = a.blk;
+  auto co = [&](int e, int cc) { return __ldg(B + (size_t)e * nc + cc); };
+  const double x00 = co(0, cell), x01 = co(1, cell), x11 = co(2, cell);
+  const double y00 = co(3, cell), y01 = co(4, cell), y11 = co(5, cell);
+  // own block: y[a + 2b] = sum_c Xd[a][c] u[c + 2b] + sum_d Yd[b][d] u[a + 2d]
+  y[0] = x00 * u[0] + x01 * u[1] + y00 * u[0] + y01 * u[2];
+  y[1] = x01 * u[0] + x11 * u[1] + y00 * u[1] + y01 * u[3];
+  y[2] = x00 * u[2] + x01 * u[3] + y01 * u[0] + y11 * u[2];
+  y[3] = x01 * u[2] + x11 * u[3] + y01 * u[1] + y11 * u[3];
+  if (i + 1 < nx) {   // sum_c Ex[a][c] v(c + 2b) of the +x neighbour
+    const int nb = cell + 1;
+    const double e00 = co(6, cell), e01 = co(7, cell), e10 = co(8, cell), e11 = co(9, cell);
+    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    y[0] += e00 * w0 + e01 * w1;
+    y[1] += e10 * w0 + e11 * w1;
+    y[2] += e00 * w2 + e01 * w3;
+    y[3] += e10 * w2 + e11 * w3;
+  }
+  if (i > 0) {        // sum_c Ex_{-x}[c][a] v(c + 2b) of the -x neighbour
+    const int nb = cell - 1;
+    const double e00 = co(6, nb), e01 = co(7, nb), e10 = co(8, nb), e11 = co(9, nb);
+    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    y[0] += e00 * w0 + e10 * w1;
+    y[1] += e01 * w0 + e11 * w1;
+    y[2] += e00 * w2 + e10 * w3;
+    y[3] += e01 * w2 + e11 * w3;
+  }
+  if (j + 1 < a.ny) { // sum_d Ny[b][d] v(a + 2d) of the +y neighbour
+    const int nb = cell + nx;
+    const double n00 = co(10, cell), n01 = co(11, cell), n10 = co(12, cell), n11 = co(13, cell);
+    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    y[0] += n00 * w0 + n01 * w2;
+    y[1] += n00 * w1 + n01 * w3;
+    y[2] += n10 * w0 + n11 * w2;
+    y[3] += n10 * w1 + n11 * w3;
+  }
+  if (j > 0) {        // sum_d Ny_{-y}[d][b] v(a + 2d) of the -y neighbour
+    const int nb = cell - nx;
+    const double n00 = co(10, nb), n01 = co(11, nb), n10 = co(12, nb), n11 = co(13, nb);
+    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    y[0] += n00 * w0 + n10 * w2;
+    y[1] += n00 * w1 + n10 * w3;
+    y[2] += n01 * w0 + n11 * w2;
+    y[3] += n01 * w1 + n11 * w3;
   }
 }
 
-template <int DEG>
 __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
@@ -224,7 +249,7 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
         return (it == 0) ? __ldcg(pold + k) : __ldcg(a.r + k) + beta * __ldcg(pold + k);
       };
       const double pc = pval(c);
-      const double s = op_apply<DEG>(a, c, pc, pval);
+      const double s = op_apply(a, c, pc, pval);
       pnew[c] = pc;
       a.ap[c] = s;
       acc += pc * s;
@@ -245,6 +270,100 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
     const double rr_new = grid_total(partB);
     beta = rr_new / rr;
     rr = rr_new;
+    double* t = pold;
+    pold = pnew;
+    pnew = t;
+    ++it;
+  }
+  for (int c = tid; c < a.n; c += nth) {
+    const double d = a.x[c];
+    if (a.delta != a.x) a.delta[c] = d;
+    if (a.rho_out) {
+      const double r = a.rho_half[c] + d;
+      a.rho_out[c] = r;
+      a.q_out[c] = a.sig_s[c] * r;
+    }
+  }
+  if (tid == 0) *a.iters = it;
+}
+
+// Forward declarations of the two-value block and grid sums (defined below).
+__device__ void block_sum2_store(double u, double v, double* dst0, double* dst1);
+__device__ void grid_total2(const double* part0, const double* part1, double& t0, double& t1);
+
+// Q1 solves: conjugate gradients preconditioned by the diagonal of C (Jacobi; Sec. 4
+// preconditions its DSA solves), two grid-wide phases per iteration as cg_kernel:
+//   (1) p <- z + beta p with z = D^-1 r (neighbours' p recomputed from r and the old p),
+//       Ap = C p and the block partials of p.Ap, one cell (four unknowns) per thread;
+//   (2) x += alpha p, r -= alpha Ap and the block partials of r.r (the stopping test) and of
+//       r.z (the next beta).
+// Three partial arrays: phase 1 writes the first while every block may still be reading the
+// second and third of the previous phase, and the reverse.
+__global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs a) {
+  if (a.skip && *a.skip) return;   // every block returns before the first barrier
+  unsigned gen = ld_acquire(&a.bar[1]);
+  const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
+  double* partA = a.partial;
+  double* partR = a.partial + gridDim.x;
+  double* partZ = a.partial + 2 * gridDim.x;
+  // r = b = sig_s .* residual, x = 0, p = z = D^-1 b; (b, b) and (b, z)
+  double accr = 0.0, accz = 0.0;
+  for (int c = tid; c < a.n; c += nth) {
+    const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
+    const double b = a.sig_s[c] * rc;
+    const double z = b * a.dinv[c];
+    a.r[c] = b;
+    a.x[c] = 0.0;
+    a.p0[c] = z;
+    accr += b * b;
+    accz += b * z;
+  }
+  block_sum2_store(accr, accz, partR + blockIdx.x, partZ + blockIdx.x);
+  bool dead = grid_barrier(a.bar, gen);
+  double rr, rz;
+  grid_total2(partR, partZ, rr, rz);
+  const double bb = rr;
+  double beta = 0.0;
+  int it = 0;
+  double* pold = a.p0;
+  double* pnew = a.p1;
+  while (!dead && it < a.max_iter && rr > a.rtol2 * bb) {
+    double acc = 0.0;
+    const int nc = a.ncell;
+    for (int cell = tid; cell < nc; cell += nth) {   // one cell (its four modes) per thread
+      auto pval = [&](int k) {
+        return (it == 0) ? __ldcg(pold + k)
+                         : fma(beta, __ldcg(pold + k), __ldcg(a.r + k) * __ldg(a.dinv + k));
+      };
+      double pc[4], y[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pc[k] = pval(k * nc + cell);
+      q1_apply_cell(a, cell, pc, pval, y);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        pnew[k * nc + cell] = pc[k];
+        a.ap[k * nc + cell] = y[k];
+        acc += pc[k] * y[k];
+      }
+    }
+    block_sum_store(acc, partA + blockIdx.x);
+    if ((dead = grid_barrier(a.bar, gen))) break;
+    const double alpha = rz / grid_total(partA);
+    accr = 0.0;
+    accz = 0.0;
+    for (int c = tid; c < a.n; c += nth) {
+      a.x[c] += alpha * pnew[c];
+      const double rc = a.r[c] - alpha * a.ap[c];
+      a.r[c] = rc;
+      accr += rc * rc;
+      accz += rc * (rc * a.dinv[c]);
+    }
+    block_sum2_store(accr, accz, partR + blockIdx.x, partZ + blockIdx.x);
+    if ((dead = grid_barrier(a.bar, gen))) break;
+    double rz_new;
+    grid_total2(partR, partZ, rr, rz_new);
+    beta = rz_new / rz;
+    rz = rz_new;
     double* t = pold;
     pold = pnew;
     pnew = t;
@@ -329,7 +448,6 @@ __device__ void grid_total2(const double* part0, const double* part1, double& t0
 // The setup forms only r = b and (b, b); the first step length needs (C r, r), which one more
 // phase computes when the stopping test lets CG iterate at all (a solve of k >= 1 iterations
 // takes k + 2 barriers, a solve that stops at once one).
-template <int DEG>
 __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
@@ -338,7 +456,7 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
   double* partG = a.partial;
   double* partD = a.partial + gridDim.x;
   // (C v)_c for v given at c (vc) and elsewhere by a function of the vector index
-  auto apply = [&](int c, double vc, auto v) { return op_apply<DEG>(a, c, vc, v); };
+  auto apply = [&](int c, double vc, auto v) { return op_apply(a, c, vc, v); };
   // r = b = sig_s .* residual and (b, b)
   double g = 0.0, d = 0.0;
   for (int c = tid; c < n; c += nth) {
@@ -558,9 +676,12 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   // with the blocks that arrive); large grids the two-phase one (cg_kernel, up to two blocks
   // per SM), which moves fewer bytes in solves of few iterations (measured: 256^2 cells 16-20 %
   // faster per solve with cg1_kernel, 1024^2 cells 20-25 % slower).
-  op.single_phase = n <= (1 << 18);
-  const void* kern = degree == 1 ? (op.single_phase ? (const void*)cg1_kernel<1> : (const void*)cg_kernel<1>)
-                                 : (op.single_phase ? (const void*)cg1_kernel<0> : (const void*)cg_kernel<0>);
+  // Q1: the Jacobi-preconditioned two-phase solve (measured with plain CG at 256^2 cells, the
+  // two-phase arrangement took 20 % less time per solve than the one-barrier one, whose
+  // recomputation of a neighbour's r' costs three loads and the Q1 operator reads ten)
+  op.single_phase = degree == 0 && n <= (1 << 18);
+  const void* kern = degree == 1 ? (const void*)pcg_q1_kernel
+                                 : (op.single_phase ? (const void*)cg1_kernel : (const void*)cg_kernel);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CT, 0);
   if (per_sm < 1) per_sm = 1;
   const int want = (n + CT - 1) / CT;
@@ -574,18 +695,31 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   double** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x,
                      &op.r1, &op.w1, &op.s1};
   op.blk = nullptr;
+  op.dinv = nullptr;
   for (double** b : bufs) {
     *b = nullptr;
     if (!op.single_phase && (b == &op.r1 || b == &op.w1 || b == &op.s1)) continue;
     if (degree == 1 && (b == &op.diag || b == &op.cx || b == &op.cy)) continue;
     if ((e = cudaMalloc(b, bytes)) != cudaSuccess) return e;
   }
-  if ((e = cudaMalloc(&op.partial, sizeof(double) * 2 * op.blocks)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&op.partial, sizeof(double) * 3 * op.blocks)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&op.scal, 64)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(op.scal, 0, 64, s)) != cudaSuccess) return e;
   if (degree == 1) {
+    // inverse diagonal of C: mode k = a + 2b of a cell has Xd[a][a] + Yd[b][b]
+    std::vector<double> dinv(n);
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < ncell; ++c) {
+        const double d = blk[(size_t)((k & 1) ? 2 : 0) * ncell + c] +
+                         blk[(size_t)((k >> 1) ? 5 : 3) * ncell + c];
+        dinv[(size_t)k * ncell + c] = 1.0 / d;
+      }
     if ((e = cudaMalloc(&op.blk, sizeof(double) * blk.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&op.dinv, sizeof(double) * dinv.size())) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(op.blk, blk.data(), sizeof(double) * blk.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(op.dinv, dinv.data(), sizeof(double) * dinv.size(),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return e;
     return cudaStreamSynchronize(s);
@@ -601,7 +735,7 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
 
 void dsa_free(DsaOp& op) {
   double* bufs[] = {op.diag, op.cx, op.cy, op.r,       op.p0,      op.p1,  op.ap,
-                    op.x,    op.r1, op.w1, op.s1, op.partial, op.scal, op.blk};
+                    op.x,    op.r1, op.w1, op.s1, op.partial, op.scal, op.blk, op.dinv};
   for (double* b : bufs)
     if (b) cudaFree(b);
   op = DsaOp{};
@@ -620,6 +754,7 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   a.cx = op.cx;
   a.cy = op.cy;
   a.blk = op.blk;
+  a.dinv = op.dinv;
   a.ncell = op.ncell;
   a.sig_s = sig_s;
   a.residual = residual;
@@ -644,8 +779,8 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   void* args[] = {&a};
   ++g_launches;
   const void* kern = op.deg == 1
-                         ? (op.single_phase ? (const void*)cg1_kernel<1> : (const void*)cg_kernel<1>)
-                         : (op.single_phase ? (const void*)cg1_kernel<0> : (const void*)cg_kernel<0>);
+                         ? (const void*)pcg_q1_kernel
+                         : (op.single_phase ? (const void*)cg1_kernel : (const void*)cg_kernel);
   return cudaLaunchCooperativeKernel(kern, dim3(op.blocks), dim3(CT), args, 0, s);
 }
 
@@ -727,7 +862,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<0>, CT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CT, 0);
   int blocks = (n + CT - 1) / CT;
   int cap = (per_sm < 1 ? 1 : per_sm) * sms;
   if (cap > 2 * sms) cap = 2 * sms;
@@ -773,7 +908,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   a.iters = iters_dev;
   void* args[] = {&a};
   ++g_launches;
-  e = cudaLaunchCooperativeKernel((const void*)cg_kernel<0>, dim3(blocks), dim3(CT), args, 0, s);
+  e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(CT), args, 0, s);
   if (e != cudaSuccess) {
     *err = std::string("rte_dsa_solve_noalloc: ") + cudaGetErrorString(e);
     return RTE_ECUDA;

@@ -478,8 +478,7 @@ void ghosts(const double g[4], Real gx[4], Real gy[4]) {
 // Launch a 2D sweep with the tile of its kind (tl).
 template <class Real>
 cudaError_t launch2d(rte_handle h, const Sweep2DArgs<Real>& a, int mode, const rte_s::Tile& tl) {
-  if constexpr (sizeof(Real) == 8)
-    if (tl.kind == 3) return launch_sweep_q1(a, mode, h->L.dl, tl.R, h->st);
+  if (tl.kind == 3) return launch_sweep_q1(a, mode, h->L.dl, tl.R, h->st);
   if (tl.kind == 2) return launch_sweep2d_tile(a, mode, tl.R, tl.W, h->st);
   return launch_sweep2d<Real>(a, mode, tl.R, h->st);
 }
@@ -1326,8 +1325,8 @@ rte_status alloc_sweep(rte_handle h) {
     CK(dalloc(&h->f, (size_t)nd * L.nslot));
     CK(cudaMemsetAsync(h->f, 0, sizeof(double) * nd * L.nslot, h->st));
   } else if (!h->bf16) {
-    CK(dalloc(&h->f_f, (size_t)n * L.nslot));
-    CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * n * L.nslot, h->st));
+    CK(dalloc(&h->f_f, (size_t)nd * L.nslot));
+    CK(cudaMemsetAsync(h->f_f, 0, sizeof(float) * nd * L.nslot, h->st));
   } else {
     CK(dalloc(&h->fb, (size_t)n * L.nslot));
     CK(cudaMemsetAsync(h->fb, 0, sizeof(__nv_bfloat16) * n * L.nslot, h->st));
@@ -1349,7 +1348,7 @@ rte_status alloc_sweep(rte_handle h) {
       CK(dalloc(&h->pm, (size_t)L.nfam * nd));
       CK(dalloc(&h->edge, edge));
     } else {
-      CK(dalloc(&h->pm_f, (size_t)L.nfam * n));
+      CK(dalloc(&h->pm_f, (size_t)L.nfam * nd));
       CK(dalloc(&h->edge_f, edge));
     }
     const size_t cb_bytes = sizeof(SweepCtrl) + sizeof(unsigned) * L.nfam * h->nblk_max;
@@ -1601,8 +1600,8 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
     return fail(h, RTE_EINVAL, "sweep_kernel must be 0, 1 or 2");
   if (!(h->opt.eps_sisa >= 0.0)) return fail(h, RTE_EINVAL, "eps_sisa must be >= 0");
   if (h->opt.degree != 0 && h->opt.degree != 1) return fail(h, RTE_EINVAL, "degree must be 0 or 1");
-  if (h->opt.degree == 1 && (mesh->dim != 2 || h->opt.precision != RTE_FP64))
-    return fail(h, RTE_EINVAL, "degree 1 (Q1) is available for 2D problems in RTE_FP64");
+  if (h->opt.degree == 1 && (mesh->dim != 2 || h->opt.precision == RTE_FP32_BF16F))
+    return fail(h, RTE_EINVAL, "degree 1 (Q1) is available for 2D problems in RTE_FP64 or RTE_FP32");
   h->deg = h->opt.degree;
   h->nb = h->deg == 1 ? 4 : 1;
   h->dim = mesh->dim;
@@ -1683,7 +1682,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   if (h->fp32) {
     CK(dalloc(&h->sig_t_f, n));
     CK(dalloc(&h->sig_tl_f, n));
-    CK(dalloc(&h->src_f, n));
+    CK(dalloc(&h->src_f, nd));
     {   // sigma_t as an exact pair hi + lo of FP32 numbers
       std::vector<float> hi(n), lo(n);
       for (long c = 0; c < n; ++c) {
@@ -1693,7 +1692,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
       CK(cudaMemcpy(h->sig_t_f, hi.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(h->sig_tl_f, lo.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
     }
-    CK(launch_to_float(h->src, n, h->src_f, h->st));
+    CK(launch_to_float(h->src, nd, h->src_f, h->st));
     CK(dalloc(&h->q_f, nd));
     CK(dalloc(&h->y_ir, nd));
     CK(dalloc(&h->rho_ref, nd));
@@ -1794,7 +1793,7 @@ std::vector<StatePart> state_parts(rte_handle h) {
   if (!h->fp32) {
     v.push_back({h->f, sizeof(double) * nd * ns});
   } else if (!h->bf16) {
-    v.push_back({h->f_f, sizeof(float) * n * ns});
+    v.push_back({h->f_f, sizeof(float) * nd * ns});
   } else {
     v.push_back({h->fb, sizeof(__nv_bfloat16) * n * ns});
     v.push_back({h->fref[0], sizeof(float) * n});
@@ -1841,16 +1840,27 @@ rte_status set_initial_q1(rte_handle h, const double* rho0, const double* f0) {
     for (int d = 0; d < L.nv; ++d)
       for (long i = 0; i < nd; ++i) rho[i] += h->w_user[d] * f0[(size_t)d * nd + i];
     TRY(upload(h, h->rho, rho.data(), nd));
-    TRY(upload(h, h->f, fl.data(), (long)fl.size()));
-    if (!h->f_init) CK(dalloc(&h->f_init, fl.size()));
-    CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToDevice,
-                       h->st));
+    if (!h->fp32) {
+      TRY(upload(h, h->f, fl.data(), (long)fl.size()));
+      if (!h->f_init) CK(dalloc(&h->f_init, fl.size()));
+      CK(cudaMemcpyAsync(h->f_init, h->f, sizeof(double) * fl.size(), cudaMemcpyDeviceToDevice,
+                         h->st));
+    } else {
+      std::vector<float> ff(fl.begin(), fl.end());
+      CK(cudaMemcpyAsync(h->f_f, ff.data(), sizeof(float) * ff.size(), cudaMemcpyHostToDevice,
+                         h->st));
+      if (!h->f_init_f) CK(dalloc(&h->f_init_f, ff.size()));
+      CK(cudaMemcpyAsync(h->f_init_f, h->f_f, sizeof(float) * ff.size(), cudaMemcpyDeviceToDevice,
+                         h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
     h->init_kind = 2;
   } else {
     if (!rho0) return fail(h, RTE_EINVAL, "rho0 or f0 is required");
     if (!finite_all(rho0, nd)) return fail(h, RTE_EINVAL, "non-finite rho0");
     TRY(upload(h, h->rho, rho0, nd));
-    CK(launch_isotropic_f_q1(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
+    if (!h->fp32) CK(launch_isotropic_f_q1(h->rho, (int)n, L.nslot, L.dl, h->f, h->st));
+    else CK(launch_isotropic_f32_q1(h->rho, (int)n, L.nslot, L.dl, h->f_f, h->st));
     h->init_kind = 1;
   }
   return RTE_OK;
@@ -1993,11 +2003,15 @@ rte_status rte_restart(rte_handle h) {
   CK(cudaMemcpyAsync(h->rho, h->rho_init, sizeof(double) * h->ndof, cudaMemcpyDeviceToDevice,
                      h->st));
   if (h->deg == 1) {
-    if (h->init_kind == 2)
-      CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * h->ndof * h->L.nslot,
-                         cudaMemcpyDeviceToDevice, h->st));
-    else
+    const size_t fc = (size_t)h->ndof * h->L.nslot;
+    if (h->init_kind == 2 && !h->fp32)
+      CK(cudaMemcpyAsync(h->f, h->f_init, sizeof(double) * fc, cudaMemcpyDeviceToDevice, h->st));
+    else if (h->init_kind == 2)
+      CK(cudaMemcpyAsync(h->f_f, h->f_init_f, sizeof(float) * fc, cudaMemcpyDeviceToDevice, h->st));
+    else if (!h->fp32)
       CK(launch_isotropic_f_q1(h->rho, (int)n, h->L.nslot, h->L.dl, h->f, h->st));
+    else
+      CK(launch_isotropic_f32_q1(h->rho, (int)n, h->L.nslot, h->L.dl, h->f_f, h->st));
   } else if (h->bf16) {
     h->fcur = 0;
     if (h->init_kind == 2) {
@@ -2076,9 +2090,17 @@ rte_status rte_get_angular_flux(rte_handle h, double* f) {
     // device [fam][cell][k][dl] -> caller [dir][k ncell + cell]
     std::vector<double> fl((size_t)h->ndof * L.nslot);
     const bool prev = h->bdf2 && h->stats.steps > 0;
-    CK(cudaMemcpyAsync(fl.data(), prev ? h->f_prev : h->f, sizeof(double) * fl.size(),
-                       cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    if (!h->fp32) {
+      CK(cudaMemcpyAsync(fl.data(), prev ? h->f_prev : h->f, sizeof(double) * fl.size(),
+                         cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    } else {
+      std::vector<float> ff(fl.size());
+      CK(cudaMemcpyAsync(ff.data(), prev ? h->f_prev_f : h->f_f, sizeof(float) * ff.size(),
+                         cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      for (size_t i = 0; i < ff.size(); ++i) fl[i] = ff[i];
+    }
     for (int d = 0; d < L.nv; ++d) {
       const int sl = L.slot_of_dir[d];
       for (int k = 0; k < 4; ++k)

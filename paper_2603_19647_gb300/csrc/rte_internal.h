@@ -91,10 +91,14 @@ struct Sweep1DArgs {
   Real g_lo, g_hi;      // inflow at x0 (for mu > 0) and x1 (for mu < 0), pass A
 };
 
-// Q1 sweeps (sweep_q1.cu), FP64, mode 0 / 1 / 2 as in the Q0 strip chain; one warp per CTA,
+// Q1 sweeps (sweep_q1.cu), FP64 or FP32, mode 0 / 1 / 2 as in the Q0 strip chain; one warp per CTA,
 // rows_per_blk = (32 / dl) R.  q, g2: [4][ncell]; f: [nfam][ncell][4][dl]; pm: [nfam][4][ncell];
 // edge: per pass [nfam][nblk][nx][2][dl] (mode 1: two passes).
 cudaError_t launch_sweep_q1(const Sweep2DArgs<double>& a, int mode, int dl, int R, cudaStream_t s);
+cudaError_t launch_sweep_q1(const Sweep2DArgs<float>& a, int mode, int dl, int R, cudaStream_t s);
+// FP32: f[fam][cell][k][dl] = float(rho[k ncell + cell])
+cudaError_t launch_isotropic_f32_q1(const double* rho, int ncell, int nslot, int dl, float* f,
+                                    cudaStream_t s);
 // f[fam][cell][k][dl] = rho[k ncell + cell] in every slot (isotropic Q1 angular flux)
 cudaError_t launch_isotropic_f_q1(const double* rho, int ncell, int nslot, int dl, double* f,
                                   cudaStream_t s);
@@ -186,6 +190,7 @@ struct DsaOp {
   double* cx;     // Q0 [n] coupling of cell c with c+1 (0 at the east edge)
   double* cy;     // Q0 [n] coupling of cell c with c+nx (0 at the north edge / 1D)
   double* blk;    // Q1 [14][ncell] block coefficients
+  double* dinv;   // Q1 [n] inverse diagonal (the Jacobi preconditioner)
   // CG workspace
   double *r, *p0, *p1, *ap, *x;
   double *r1, *w1, *s1;   // second buffers of the single-barrier CG (r, w = C r, s = C p)

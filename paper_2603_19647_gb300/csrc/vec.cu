@@ -151,6 +151,13 @@ __global__ void isotropic_f_q1_kernel(const double* rho, int ncell, int nslot, i
   f[i] = rho[k * ncell + c];
 }
 
+__global__ void isotropic_f32_q1_kernel(const double* rho, int ncell, int nslot, int dl, float* f) {
+  const long i = (long)blockIdx.x * VT + threadIdx.x;
+  if (i >= 4L * ncell * nslot) return;
+  const long k = (i / dl) % 4, c = (i / (4L * dl)) % ncell;
+  f[i] = (float)rho[k * ncell + c];
+}
+
 __global__ void dot_partial_kernel(const double* x, const double* y, int n, double* partials) {
   __shared__ double sh[VT / 32];
   double s = 0.0;
@@ -381,6 +388,14 @@ cudaError_t launch_isotropic_f_q1(const double* rho, int ncell, int nslot, int d
   const long tot = 4L * ncell * nslot;
   ++g_launches;
   isotropic_f_q1_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, ncell, nslot, dl, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_isotropic_f32_q1(const double* rho, int ncell, int nslot, int dl, float* f,
+                                    cudaStream_t s) {
+  const long tot = 4L * ncell * nslot;
+  ++g_launches;
+  isotropic_f32_q1_kernel<<<(unsigned)((tot + VT - 1) / VT), VT, 0, s>>>(rho, ncell, nslot, dl, f);
   return cudaGetLastError();
 }
 

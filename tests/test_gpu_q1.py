@@ -1,5 +1,5 @@
 """GPU parity of the Q1 upwind DG path (Sec. 2.1 Eq. (DG) with K = 1, options.degree = 1)
-against the oracle's Q1 scheme, through the C ABI, in FP64.
+against the oracle's Q1 scheme, through the C ABI, in FP64 (and the FP32 mode at the end).
 
 Bounds as for the Q0 path: relative L2 <= 1e-12 (and element-wise 1e-11 against the field's
 scale) for single sweeps, 1e-10 where an iterative solve sits in between; whole marches with
@@ -105,8 +105,8 @@ def test_q1_dsa(shape):
     h.destroy()
 
 
-def test_q1_dsa_large_grid_two_phase_cg():
-    """Above 2^18 unknowns the two-phase CG kernel runs (four modes per cell: 260^2 cells)."""
+def test_q1_dsa_large_grid():
+    """The Jacobi-preconditioned CG on 260^2 cells (270 400 unknowns, two blocks per SM)."""
     wl, rng = _hetero(260, 260, (8, 4), seed=5)
     h, p = make_pair(wl, cg_rtol=1e-8, cg_max_iter=3000, **Q1)
     res = rng.normal(size=4 * wl.ncell)
@@ -185,4 +185,55 @@ def test_q1_full_size_sweeps():
     f_ref, _ = tr.final_f(p, rho, np.tile(cell_modes(wl.rho0, 1), (p.nv, 1)))
     assert rel_l2(h.rte_get_angular_flux(), f_ref[perm]) < 1e-12
     assert rel_l2(bt, tr.b_tilde(p, f_ref)) < 1e-12
+    h.destroy()
+
+
+# ---- FP32 sweeps with the FP64 residual (options.precision = RTE_FP32) ---------------------
+
+FP32 = dict(degree=1, precision=rte.RTE_FP32)
+
+
+@pytest.mark.parametrize("lanes,rows", [(8, 1), (8, 4), (16, 2), (32, 1)])
+def test_q1_fp32_sweeps(lanes, rows):
+    """FP32 cell solves: the SI sweep and the fused sweep within 2e-6 (relative L2) of the FP64
+    oracle, and element by element within 2e-5 relative for every value above 1 % of the field's
+    largest (the linear modes of f run down to zero, where FP32's error relative to the field,
+    about 1e-7, is what remains)."""
+    wl, rng = _hetero(45, 53, (32, 8), seed=7 * lanes + rows)
+    h, p = make_pair(wl, sweep_lanes=lanes, sweep_rows=rows, **FP32)
+    rho = rng.uniform(0, 1, 4 * wl.ncell)
+    got, ref = h.rte_op_sweep(rho), tr.apply_T_sigma_s(p, rho)
+    assert rel_l2(got, ref) < 2e-6 and max_rel(got, ref) < 2e-5, (rel_l2(got, ref), max_rel(got, ref))
+    perm, _, _ = match_directions(h, wl.quadrature)
+    f0 = rng.uniform(0, 1, (p.nv, 4 * wl.ncell))
+    h.rte_set_initial(f0=f0[perm])
+    g = np.array([0.3, 0.6, 0.2, 0.9])
+    h.rte_set_inflow(g)
+    p.inflow = g
+    bt = h.rte_op_fsweep(rho)
+    f_ref, _ = tr.final_f(p, rho, f0)
+    f_got = h.rte_get_angular_flux()
+    assert rel_l2(f_got, f_ref[perm]) < 2e-6 and max_rel(f_got, f_ref[perm], floor=1e-2) < 2e-5
+    bt_ref = tr.b_tilde(p, f_ref)
+    assert rel_l2(bt, bt_ref) < 2e-6 and max_rel(bt, bt_ref, floor=1e-2) < 2e-5
+    h.destroy()
+
+
+@pytest.mark.parametrize("rom_on", [False, True])
+def test_q1_fp32_march_within_1e6_of_fp64_oracle(rom_on):
+    """The FP32 march (FP32 sweeps and f, FP64 residual, DSA and ROMs) stays within 1e-6 of the
+    FP64 oracle's march at every step, through Phase 3 with the ROMs on."""
+    wl = _q1_workload(n=32, steps=60)
+    o = dict(rom=rte.RTE_ROM_AUTO if rom_on else rte.RTE_ROM_OFF, **FP32)
+    h, p = make_pair(wl, **o)
+    orc = stepper.OracleRTE(p, rom=rom_on)
+    orc.set_initial(cell_modes(wl.rho0, 1))
+    worst = 0.0
+    for n in range(1, 61):
+        h.rte_step(1)
+        orc.step(1)
+        worst = max(worst, rel_l2(h.rte_get_scalar_flux(), orc.rho))
+    assert worst < 1e-6, worst
+    if rom_on:
+        assert h.rte_get_stats()["phase"] == 3
     h.destroy()
