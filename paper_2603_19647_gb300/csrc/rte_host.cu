@@ -434,6 +434,7 @@ Sweep2DArgs<Real> args2d(rte_handle h, const SV<Real>& v, int mode) {
   a.nblk = tl.nblk;
   a.rows_per_blk = tl.rpb;
   a.tau = (Real)h->tau;
+  a.tau_lo = (Real)(h->tau - (double)a.tau);
   a.a = v.ca;
   a.b = v.cb;
   a.w = v.cw;

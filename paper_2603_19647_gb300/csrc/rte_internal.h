@@ -46,6 +46,7 @@ template <class Real>
 struct Sweep2DArgs {
   int nx, ny, nfam, nslot, nblk, rows_per_blk;
   Real tau;
+  Real tau_lo;          // Q1 FP32: tau - (float)tau (the exact pair tau + tau_lo), else 0
   const Real* a;        // [nslot] |mu|/hx
   const Real* b;        // [nslot] |eta|/hy
   const Real* w;        // [nslot]

@@ -44,57 +44,120 @@ using namespace sweep_detail;
 constexpr int KQ1 = 4;   // columns per published edge chunk
 constexpr double SQRT3 = 1.7320508075688772;
 
+// sqrt(3) in FP32 as an exact pair: SQRT3_HI + SQRT3_LO (to about 2^-48)
+constexpr float SQRT3_HI = 1.73205077648162841796875f;
+constexpr float SQRT3_LO = 3.1087250107475484e-08f;
+
 // a * b + c rounded once, in the sweep's precision
 __device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// One cell solve (see the file comment).  s: source modes; tx: face modes (y mode b) of the
-// upwind value on the inflow x face; ty: face modes (x mode a) on the inflow y face.
-// Returns the cell's modes in f and its outflow traces in ox (per y mode), oy (per x mode).
+// The c-dependent factors of one cell solve (see the file comment): Q0 = q0 I + ax Bx, the
+// second column's q1, beta = uy ay, S = s0 I + s1 Bx, and the inverses' scales kS, kQ.
 template <class Real>
-__device__ __forceinline__ void q1_cell(Real c, Real ax, Real ay, Real ux, Real uy,
-                                        const Real s[4], const Real tx[2], const Real ty[2],
-                                        Real f[4], Real ox[2], Real oy[2]) {
-  const Real axt0 = ax * tx[0], axt1 = ax * tx[1], ayt0 = ay * ty[0], ayt1 = ay * ty[1];
-  const Real r00 = s[0] + axt0 + ayt0;
-  const Real r10 = mad(-ux, axt0, s[1] + ayt1);
-  const Real r01 = mad(-uy, ayt0, s[2] + axt1);
-  const Real r11 = mad(-uy, ayt1, mad(-ux, axt1, s[3]));
-  const Real q0 = c + ay, q1 = mad(Real(2.0), ay, q0), beta = uy * ay;
-  const Real s1 = ax * (q0 + q1 + Real(4.0) * ax);
-  const Real s0 = mad(q0, q1, Real(3.0) * ay * ay - Real(6.0) * ax * ax);
-  // t = Q0 R1 + beta R0
-  const Real b0 = mad(ux, r11, r01), b1 = mad(-ux, r01, Real(3.0) * r11);
-  const Real t0 = mad(q0, r01, mad(ax, b0, beta * r00));
-  const Real t1 = mad(q0, r11, mad(ax, b1, beta * r10));
-  const Real e0 = mad(ux, t1, t0), e1 = mad(-ux, t0, Real(3.0) * t1);
-  const Real dS = mad(s0, s0 + Real(4.0) * s1, Real(6.0) * s1 * s1);
-  const Real pq = q0 + Real(4.0) * ax;
-  const Real dQ = mad(q0, pq, Real(6.0) * ax * ax);
-  Real kS, kQ;
+struct Q1Coef {
+  Real q0, beta, s1, ps, pq, kS, kQ;
+};
+template <class Real>
+__device__ __forceinline__ Q1Coef<Real> q1_coef(Real c, Real ax, Real ay) {
+  Q1Coef<Real> k;
+  k.q0 = c + ay;
+  const Real q1 = mad(Real(2.0), ay, k.q0);
+  k.beta = ay;   // times uy at the use
+  k.s1 = ax * (k.q0 + q1 + Real(4.0) * ax);
+  const Real s0 = mad(k.q0, q1, Real(3.0) * ay * ay - Real(6.0) * ax * ax);
+  const Real dS = mad(s0, s0 + Real(4.0) * k.s1, Real(6.0) * k.s1 * k.s1);
+  k.pq = k.q0 + Real(4.0) * ax;
+  const Real dQ = mad(k.q0, k.pq, Real(6.0) * ax * ax);
   if constexpr (sizeof(Real) == 8) {   // one division: 1 / (dS dQ), both about c^4
     const Real inv = Real(1) / (dS * dQ);
-    kS = dQ * inv;
-    kQ = dS * inv;
+    k.kS = dQ * inv;
+    k.kQ = dS * inv;
   } else {                             // FP32: their product could leave the exponent range
-    kS = Real(1) / dS;
-    kQ = Real(1) / dQ;
+    k.kS = Real(1) / dS;
+    k.kQ = Real(1) / dQ;
   }
-  const Real ps = s0 + Real(4.0) * s1;
-  const Real f01 = mad(ps, t0, -s1 * e0) * kS;
-  const Real f11 = mad(ps, t1, -s1 * e1) * kS;
-  const Real u0 = mad(-beta, f01, r00), u1 = mad(-beta, f11, r10);
+  k.ps = s0 + Real(4.0) * k.s1;
+  return k;
+}
+
+// F = L^-1 R for the right side r (r[a + 2b] = R[a][b]) by the closed form of the file comment.
+template <class Real>
+__device__ __forceinline__ void q1_apply(const Q1Coef<Real>& k, Real ax, Real ux, Real uy,
+                                         const Real r[4], Real f[4]) {
+  const Real beta = uy * k.beta;
+  // t = Q0 R1 + beta R0
+  const Real b0 = mad(ux, r[3], r[2]), b1 = mad(-ux, r[2], Real(3.0) * r[3]);
+  const Real t0 = mad(k.q0, r[2], mad(ax, b0, beta * r[0]));
+  const Real t1 = mad(k.q0, r[3], mad(ax, b1, beta * r[1]));
+  const Real e0 = mad(ux, t1, t0), e1 = mad(-ux, t0, Real(3.0) * t1);
+  const Real f01 = mad(k.ps, t0, -k.s1 * e0) * k.kS;
+  const Real f11 = mad(k.ps, t1, -k.s1 * e1) * k.kS;
+  const Real u0 = mad(-beta, f01, r[0]), u1 = mad(-beta, f11, r[1]);
   const Real g0 = mad(ux, u1, u0), g1 = mad(-ux, u0, Real(3.0) * u1);
-  const Real f00 = mad(pq, u0, -ax * g0) * kQ;
-  const Real f10 = mad(pq, u1, -ax * g1) * kQ;
-  f[0] = f00;
-  f[1] = f10;
+  f[0] = mad(k.pq, u0, -ax * g0) * k.kQ;
+  f[1] = mad(k.pq, u1, -ax * g1) * k.kQ;
   f[2] = f01;
   f[3] = f11;
-  ox[0] = mad(ux, f10, f00);
-  ox[1] = mad(ux, f11, f01);
-  oy[0] = mad(uy, f01, f00);
-  oy[1] = mad(uy, f11, f10);
+}
+
+// One cell solve.  s: source modes; tx: face modes (y mode b) of the upwind value on the
+// inflow x face; ty: face modes (x mode a) on the inflow y face; c = ch + cl (cl = 0 in FP64).
+// Returns the cell's modes in f and its outflow traces in ox (per y mode), oy (per x mode).
+// FP32: the closed form's factors carry FP32 roundings that are the same for every step and
+// every solve of the cell and direction, and the rounding of c = tau + sigma_t is the same for
+// all directions of the cell; left alone, they bias the operator (measured: the FP32 march
+// drifting from the FP64 one by 2.3e-8 per step on the 256^2 checkerboard).  One step of
+// refinement removes the bias: the residual R - L F is formed with the exact c = ch + cl and
+// the cell's equations term by term, and the closed form solves for the correction.  What is
+// left are the roundings of the residual, which change with the values from solve to solve.
+// u x + y with u = uh + ul given as a pair (FP32; FP64 takes u = uh)
+template <class Real>
+__device__ __forceinline__ Real madp(Real uh, Real ul, Real x, Real y) {
+  if constexpr (sizeof(Real) == 4) return mad(ul, x, mad(uh, x, y));
+  else return mad(uh, x, y);
+}
+
+template <class Real>
+__device__ __forceinline__ void q1_cell(Real ch, Real cl, Real ax, Real ay, Real ux, Real ul,
+                                        Real uy, Real vl, const Real s[4], const Real tx[2],
+                                        const Real ty[2], Real f[4], Real ox[2], Real oy[2]) {
+  // ux = ux + ul and uy = uy + vl (+-sqrt(3)) wherever they define the equations (the right
+  // side's inflow terms, the residual, the outflow traces); the closed form takes ux, uy
+  const Real axt0 = ax * tx[0], axt1 = ax * tx[1], ayt0 = ay * ty[0], ayt1 = ay * ty[1];
+  Real r[4];
+  r[0] = s[0] + axt0 + ayt0;
+  r[1] = madp(-ux, -ul, axt0, s[1] + ayt1);
+  r[2] = madp(-uy, -vl, ayt0, s[2] + axt1);
+  r[3] = madp(-uy, -vl, ayt1, madp(-ux, -ul, axt1, s[3]));
+  const Q1Coef<Real> k = q1_coef(ch, ax, ay);
+  q1_apply(k, ax, ux, uy, r, f);
+  if constexpr (sizeof(Real) == 4) {
+    // (L F)[a][b] = c F[a][b] + ax (Bx F)[a][b] + ay (F By^T)[a][b]
+    Real bx[4], by[4], d[4], g[4];
+    bx[0] = madp(ux, ul, f[1], f[0]);
+    bx[1] = madp(-ux, -ul, f[0], Real(3.0) * f[1]);
+    bx[2] = madp(ux, ul, f[3], f[2]);
+    bx[3] = madp(-ux, -ul, f[2], Real(3.0) * f[3]);
+    by[0] = madp(uy, vl, f[2], f[0]);
+    by[1] = madp(uy, vl, f[3], f[1]);
+    by[2] = madp(-uy, -vl, f[0], Real(3.0) * f[2]);
+    by[3] = madp(-uy, -vl, f[1], Real(3.0) * f[3]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Real e = mad(-ch, f[i], r[i]);
+      e = mad(-cl, f[i], e);
+      e = mad(-ax, bx[i], e);
+      d[i] = mad(-ay, by[i], e);
+    }
+    q1_apply(k, ax, ux, uy, d, g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f[i] += g[i];
+  }
+  ox[0] = madp(ux, ul, f[1], f[0]);
+  ox[1] = madp(ux, ul, f[3], f[2]);
+  oy[0] = madp(uy, vl, f[2], f[0]);
+  oy[1] = madp(uy, vl, f[3], f[1]);
 }
 
 // MODE 0: SI sweep (K1): source q [4][ncell], inflow ghosts gx / gy (face mode 0), moment.
@@ -124,8 +187,11 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
   const long ncell = (long)nx * ny;
   const int slot = fam * DL + dl;
   const Real ax = A.a[slot], ay = A.b[slot], cw = A.w[slot];
-  const Real ux = Real(xpos ? SQRT3 : -SQRT3), uy = Real(ypos ? SQRT3 : -SQRT3);
-  const Real tau = A.tau;
+  const Real ux = sizeof(Real) == 4 ? Real(xpos ? SQRT3_HI : -SQRT3_HI) : Real(xpos ? SQRT3 : -SQRT3);
+  const Real uy = sizeof(Real) == 4 ? Real(ypos ? SQRT3_HI : -SQRT3_HI) : Real(ypos ? SQRT3 : -SQRT3);
+  const Real ul = sizeof(Real) == 4 ? Real(xpos ? SQRT3_LO : -SQRT3_LO) : Real(0);
+  const Real vl = sizeof(Real) == 4 ? Real(ypos ? SQRT3_LO : -SQRT3_LO) : Real(0);
+  const Real tau = A.tau, tau_lo = A.tau_lo;
   const int row0 = blk * RW + gi * R;
   const Real gxA = A.gx[quad], gyA = A.gy[quad];
   Real* f_fam = (MODE != 0) ? A.f + (size_t)fam * ncell * 4 * DL : nullptr;
@@ -162,7 +228,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
   // itself: the second buffer's registers made their SI sweep 3 % slower.
   constexpr bool AHEAD = sizeof(Real) == 4 || MODE == 1;
   struct In {
-    Real st, q[4], fo[4], g[4];
+    Real st, stl, q[4], fo[4], g[4];
   };
   In buf[AHEAD ? 2 : 1][R];
   auto fetch = [&](int t, In (&d)[R]) {
@@ -173,6 +239,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
       if (x >= 0 && x < nx && jj < ny) {
         const long cell = cell_of(x, jj);
         d[m].st = A.sig_t[cell];
+        if constexpr (sizeof(Real) == 4) d[m].stl = A.sig_tl[cell];
 #pragma unroll
         for (int md = 0; md < 4; ++md) {
           if constexpr (MODE != 2) d[m].q[md] = A.q[md * ncell + cell];
@@ -247,7 +314,16 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
         if (x >= 0 && x < nx && jj < ny) {
           const In& in = buf[AHEAD ? (k & 1) : 0][m];
           const long cell = cell_of(x, jj);
-          const Real cc = tau + in.st;
+          // c = tau + sigma_t: in FP32 as an exact pair ch + cl (both given as exact pairs)
+          Real ch, cl = Real(0);
+          if constexpr (sizeof(Real) == 4) {
+            const Real sum = tau + in.st, bb = sum - tau;
+            const Real e = ((tau - (sum - bb)) + (in.st - bb)) + (tau_lo + in.stl);
+            ch = sum + e;
+            cl = e - (ch - sum);
+          } else {
+            ch = tau + in.st;
+          }
           const Real tyA[2] = {m == 0 ? upA[0] : yA[m > 0 ? m - 1 : 0][0],
                                  m == 0 ? upA[1] : yA[m > 0 ? m - 1 : 0][1]};
           Real s[4], fA[4], ox[2], oy[2];
@@ -257,7 +333,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
             else if constexpr (MODE == 2) s[md] = mad(tau, in.fo[md], in.g[md]);
             else s[md] = mad(tau, in.fo[md], in.q[md]);
           }
-          q1_cell(cc, ax, ay, ux, uy, s, xA[m], tyA, fA, ox, oy);
+          q1_cell(ch, cl, ax, ay, ux, ul, uy, vl, s, xA[m], tyA, fA, ox, oy);
           xA[m][0] = ox[0];
           xA[m][1] = ox[1];
           yA[m][0] = oy[0];
@@ -270,7 +346,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
             Real sB[4], fB[4];
 #pragma unroll
             for (int md = 0; md < 4; ++md) sB[md] = mad(tau, fA[md], in.g[md]);
-            q1_cell(cc, ax, ay, ux, uy, sB, xB[m], tyB, fB, ox, oy);
+            q1_cell(ch, cl, ax, ay, ux, ul, uy, vl, sB, xB[m], tyB, fB, ox, oy);
             xB[m][0] = ox[0];
             xB[m][1] = ox[1];
             yB[m][0] = oy[0];
