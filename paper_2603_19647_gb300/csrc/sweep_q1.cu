@@ -41,7 +41,12 @@ namespace rte {
 namespace {
 using namespace sweep_detail;
 
-constexpr int KQ1 = 4;   // columns per published edge chunk
+// Columns per published edge chunk: a CTA's strip starts K + RW steps after the strip above, so
+// narrow chunks fill the wavefront sooner, and every chunk costs a flag poll.  Measured at
+// 256^2 x 128 (SI / fused sweep): FP64 K = 2 against 4 2.88 / 5.09 against 3.30 / 5.62 ms,
+// FP32 1.03 / 1.28 against 0.79 / 1.17 ms.
+template <class Real>
+constexpr int KQ1 = sizeof(Real) == 8 ? 2 : 4;
 constexpr double SQRT3 = 1.7320508075688772;
 
 // sqrt(3) in FP32 as an exact pair: SQRT3_HI + SQRT3_LO (to about 2^-48)
@@ -169,7 +174,7 @@ template <class Real, int DL, int R, int MODE>
 __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A) {
   constexpr int NG = 32 / DL;
   constexpr int RW = NG * R;
-  constexpr int K = KQ1;
+  constexpr int K = KQ1<Real>;
   constexpr bool TWO = MODE == 1;
   constexpr int NV = 4 * R;   // moment values of one step: (mode, row)
   if (A.skip && *A.skip) return;   // before the ticket: the control block stays untouched
