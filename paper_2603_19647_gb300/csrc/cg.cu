@@ -43,21 +43,25 @@ constexpr int CT = 256;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned BARRIER_SPIN_LIMIT = 1u << 22;
 
+// S: the storage and arithmetic type of the solve's vectors and operator coefficients (double,
+// or float in the FP32 modes); the dot products, CG scalars and the FP64 inputs and outputs
+// (residual, delta, rho) stay in double.
+template <class S>
 struct CgArgs {
   int nx, ny, n;
-  const double* diag;
-  const double* cx;
-  const double* cy;
-  const double* blk;   // Q1: [14][ncell] Xd00 Xd01 Xd11 Yd00 Yd01 Yd11 Ex00 Ex01 Ex10 Ex11 Ny..
-  const double* dinv;  // Q1: [n] inverse diagonal of C (the Jacobi preconditioner)
+  const S* diag;
+  const S* cx;
+  const S* cy;
+  const S* blk;   // Q1: [14][ncell] Xd00 Xd01 Xd11 Yd00 Yd01 Yd11 Ex00 Ex01 Ex10 Ex11 Ny..
+  const S* dinv;  // Q1: [n] inverse diagonal of C (the Jacobi preconditioner)
   int ncell;           // Q1: cells (n = 4 ncell)
   const double* sig_s;
   const double* residual;
   const double* residual_b;   // optional: residual = residual - residual_b
   double rtol2;
   int max_iter;
-  double *r, *p0, *p1, *ap, *x;
-  double *r1, *w1, *s1;   // cg1_kernel: second buffers of r, w = A r (first: ap), s = A p (first: p1)
+  S *r, *p0, *p1, *ap, *x;
+  S *r1, *w1, *s1;   // cg1_kernel: second buffers of r, w = A r (first: ap), s = A p (first: p1)
   double* partial;     // [2 * gridDim.x]
   unsigned* bar;       // [0] arrive count, [1] generation, [2] error
   double* delta;       // output (may alias x)
@@ -67,6 +71,14 @@ struct CgArgs {
   int* iters;
   const unsigned* skip;   // set: the whole solve is skipped (speculative SI-SA work)
 };
+
+__device__ __forceinline__ float fmaS(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaS(double a, double b, double c) { return __fma_rn(a, b, c); }
+// whether a double output and an S vector are the same array (the solve may write delta into x)
+template <class S>
+__device__ __forceinline__ bool same_array(const double* d, const S* x) {
+  return (const void*)d == (const void*)x;
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -145,10 +157,10 @@ __device__ double grid_total(const double* part) {
 
 // (C v) at cell index c of the 5-point (1D: 3-point) stencil, for v given at c (vc) and at the
 // neighbours by a function of the index.
-template <class V>
-__device__ __forceinline__ double op_apply(const CgArgs& a, int c, double vc, V v) {
+template <class S, class V>
+__device__ __forceinline__ S op_apply(const CgArgs<S>& a, int c, S vc, V v) {
   const int i = c % a.nx;
-  double s = a.diag[c] * vc;
+  S s = a.diag[c] * vc;
   if (i + 1 < a.nx) s -= a.cx[c] * v(c + 1);
   if (i > 0) s -= a.cx[c - 1] * v(c - 1);
   if (a.ny > 1) {
@@ -164,15 +176,15 @@ __device__ __forceinline__ double op_apply(const CgArgs& a, int c, double vc, V 
 //   Y = Xd U + U Yd^T + Ex U_{+x} + Ex_{-x}^T U_{-x} + U_{+y} Ny^T + U_{-y} Ny_{-y}
 // (Xd, Yd symmetric; Ex, Ny the cell's own blocks to its +x and +y neighbours, Ex_{-x} and
 // Ny_{-y} those of the -x and -y neighbours, i.e. the transposes of the blocks seen from here).
-template <class V>
-__device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const double u[4], V v,
-                                              double y[4]) {
+template <class S, class V>
+__device__ __forceinline__ void q1_apply_cell(const CgArgs<S>& a, int cell, const S u[4], V v,
+                                              S y[4]) {
   const int nc = a.ncell, nx = a.nx;
   const int i = cell % nx, j = cell / nx;
-  const double* B = a.blk;
+  const S* B = a.blk;
   auto co = [&](int e, int cc) { return __ldg(B + (size_t)e * nc + cc); };
-  const double x00 = co(0, cell), x01 = co(1, cell), x11 = co(2, cell);
-  const double y00 = co(3, cell), y01 = co(4, cell), y11 = co(5, cell);
+  const S x00 = co(0, cell), x01 = co(1, cell), x11 = co(2, cell);
+  const S y00 = co(3, cell), y01 = co(4, cell), y11 = co(5, cell);
   // own block: y[a + 2b] = sum_c Xd[a][c] u[c + 2b] + sum_d Yd[b][d] u[a + 2d]
   y[0] = x00 * u[0] + x01 * u[1] + y00 * u[0] + y01 * u[2];
   y[1] = x01 * u[0] + x11 * u[1] + y00 * u[1] + y01 * u[3];
@@ -180,8 +192,8 @@ __device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const d
   y[3] = x01 * u[2] + x11 * u[3] + y01 * u[1] + y11 * u[3];
   if (i + 1 < nx) {   // sum_c Ex[a][c] v(c + 2b) of the +x neighbour
     const int nb = cell + 1;
-    const double e00 = co(6, cell), e01 = co(7, cell), e10 = co(8, cell), e11 = co(9, cell);
-    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    const S e00 = co(6, cell), e01 = co(7, cell), e10 = co(8, cell), e11 = co(9, cell);
+    const S w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
     y[0] += e00 * w0 + e01 * w1;
     y[1] += e10 * w0 + e11 * w1;
     y[2] += e00 * w2 + e01 * w3;
@@ -189,8 +201,8 @@ __device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const d
   }
   if (i > 0) {        // sum_c Ex_{-x}[c][a] v(c + 2b) of the -x neighbour
     const int nb = cell - 1;
-    const double e00 = co(6, nb), e01 = co(7, nb), e10 = co(8, nb), e11 = co(9, nb);
-    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    const S e00 = co(6, nb), e01 = co(7, nb), e10 = co(8, nb), e11 = co(9, nb);
+    const S w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
     y[0] += e00 * w0 + e10 * w1;
     y[1] += e01 * w0 + e11 * w1;
     y[2] += e00 * w2 + e10 * w3;
@@ -198,8 +210,8 @@ __device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const d
   }
   if (j + 1 < a.ny) { // sum_d Ny[b][d] v(a + 2d) of the +y neighbour
     const int nb = cell + nx;
-    const double n00 = co(10, cell), n01 = co(11, cell), n10 = co(12, cell), n11 = co(13, cell);
-    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    const S n00 = co(10, cell), n01 = co(11, cell), n10 = co(12, cell), n11 = co(13, cell);
+    const S w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
     y[0] += n00 * w0 + n01 * w2;
     y[1] += n00 * w1 + n01 * w3;
     y[2] += n10 * w0 + n11 * w2;
@@ -207,8 +219,8 @@ __device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const d
   }
   if (j > 0) {        // sum_d Ny_{-y}[d][b] v(a + 2d) of the -y neighbour
     const int nb = cell - nx;
-    const double n00 = co(10, nb), n01 = co(11, nb), n10 = co(12, nb), n11 = co(13, nb);
-    const double w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
+    const S n00 = co(10, nb), n01 = co(11, nb), n10 = co(12, nb), n11 = co(13, nb);
+    const S w0 = v(nb), w1 = v(nc + nb), w2 = v(2 * nc + nb), w3 = v(3 * nc + nb);
     y[0] += n00 * w0 + n10 * w2;
     y[1] += n00 * w1 + n10 * w3;
     y[2] += n01 * w0 + n11 * w2;
@@ -216,7 +228,8 @@ __device__ __forceinline__ void q1_apply_cell(const CgArgs& a, int cell, const d
   }
 }
 
-__global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
+template <class S>
+__global__ void __launch_bounds__(CT) cg_kernel(const CgArgs<S> a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
   const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
@@ -226,11 +239,11 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
   double acc = 0.0;
   for (int c = tid; c < a.n; c += nth) {
     const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
-    const double b = a.sig_s[c] * rc;
+    const S b = S(a.sig_s[c] * rc);
     a.r[c] = b;
-    a.x[c] = 0.0;
+    a.x[c] = S(0);
     a.p0[c] = b;
-    acc += b * b;
+    acc += double(b) * double(b);
   }
   block_sum_store(acc, partB + blockIdx.x);
   bool dead = grid_barrier(a.bar, gen);   // a barrier wait ran out: leave the solve
@@ -238,46 +251,48 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs a) {
   const double bb = rr;
   double beta = 0.0;
   int it = 0;
-  double* pold = a.p0;
-  double* pnew = a.p1;
+  S* pold = a.p0;
+  S* pnew = a.p1;
   while (!dead && it < a.max_iter && rr > a.rtol2 * bb) {
     // (1) p <- r + beta p ; Ap = C p ; p.Ap
     acc = 0.0;
+    const S bt = S(beta);
     for (int c = tid; c < a.n; c += nth) {
       // Neighbours belong to other blocks: read them through L2 (__ldcg), never a stale L1 line.
       auto pval = [&](int k) {
-        return (it == 0) ? __ldcg(pold + k) : __ldcg(a.r + k) + beta * __ldcg(pold + k);
+        return (it == 0) ? __ldcg(pold + k) : __ldcg(a.r + k) + bt * __ldcg(pold + k);
       };
-      const double pc = pval(c);
-      const double s = op_apply(a, c, pc, pval);
+      const S pc = pval(c);
+      const S sc = op_apply(a, c, pc, pval);
       pnew[c] = pc;
-      a.ap[c] = s;
-      acc += pc * s;
+      a.ap[c] = sc;
+      acc += double(pc) * double(sc);
     }
     block_sum_store(acc, partA + blockIdx.x);
     if ((dead = grid_barrier(a.bar, gen))) break;
     const double alpha = rr / grid_total(partA);
+    const S al = S(alpha);
     // (2) x += alpha p ; r -= alpha Ap ; r.r
     acc = 0.0;
     for (int c = tid; c < a.n; c += nth) {
-      a.x[c] += alpha * pnew[c];
-      const double rc = a.r[c] - alpha * a.ap[c];
+      a.x[c] += al * pnew[c];
+      const S rc = a.r[c] - al * a.ap[c];
       a.r[c] = rc;
-      acc += rc * rc;
+      acc += double(rc) * double(rc);
     }
     block_sum_store(acc, partB + blockIdx.x);
     if ((dead = grid_barrier(a.bar, gen))) break;
     const double rr_new = grid_total(partB);
     beta = rr_new / rr;
     rr = rr_new;
-    double* t = pold;
+    S* t = pold;
     pold = pnew;
     pnew = t;
     ++it;
   }
   for (int c = tid; c < a.n; c += nth) {
-    const double d = a.x[c];
-    if (a.delta != a.x) a.delta[c] = d;
+    const double d = double(a.x[c]);
+    if (!same_array(a.delta, a.x)) a.delta[c] = d;
     if (a.rho_out) {
       const double r = a.rho_half[c] + d;
       a.rho_out[c] = r;
@@ -299,7 +314,8 @@ __device__ void grid_total2(const double* part0, const double* part1, double& t0
 //       r.z (the next beta).
 // Three partial arrays: phase 1 writes the first while every block may still be reading the
 // second and third of the previous phase, and the reverse.
-__global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs a) {
+template <class S>
+__global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs<S> a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
   const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
@@ -310,13 +326,13 @@ __global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs a) {
   double accr = 0.0, accz = 0.0;
   for (int c = tid; c < a.n; c += nth) {
     const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
-    const double b = a.sig_s[c] * rc;
-    const double z = b * a.dinv[c];
+    const S b = S(a.sig_s[c] * rc);
+    const S z = b * a.dinv[c];
     a.r[c] = b;
-    a.x[c] = 0.0;
+    a.x[c] = S(0);
     a.p0[c] = z;
-    accr += b * b;
-    accz += b * z;
+    accr += double(b) * double(b);
+    accz += double(b) * double(z);
   }
   block_sum2_store(accr, accz, partR + blockIdx.x, partZ + blockIdx.x);
   bool dead = grid_barrier(a.bar, gen);
@@ -325,17 +341,18 @@ __global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs a) {
   const double bb = rr;
   double beta = 0.0;
   int it = 0;
-  double* pold = a.p0;
-  double* pnew = a.p1;
+  S* pold = a.p0;
+  S* pnew = a.p1;
   while (!dead && it < a.max_iter && rr > a.rtol2 * bb) {
     double acc = 0.0;
     const int nc = a.ncell;
+    const S bt = S(beta);
     for (int cell = tid; cell < nc; cell += nth) {   // one cell (its four modes) per thread
       auto pval = [&](int k) {
         return (it == 0) ? __ldcg(pold + k)
-                         : fma(beta, __ldcg(pold + k), __ldcg(a.r + k) * __ldg(a.dinv + k));
+                         : fmaS(bt, __ldcg(pold + k), __ldcg(a.r + k) * __ldg(a.dinv + k));
       };
-      double pc[4], y[4];
+      S pc[4], y[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) pc[k] = pval(k * nc + cell);
       q1_apply_cell(a, cell, pc, pval, y);
@@ -343,20 +360,21 @@ __global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs a) {
       for (int k = 0; k < 4; ++k) {
         pnew[k * nc + cell] = pc[k];
         a.ap[k * nc + cell] = y[k];
-        acc += pc[k] * y[k];
+        acc += double(pc[k]) * double(y[k]);
       }
     }
     block_sum_store(acc, partA + blockIdx.x);
     if ((dead = grid_barrier(a.bar, gen))) break;
     const double alpha = rz / grid_total(partA);
+    const S al = S(alpha);
     accr = 0.0;
     accz = 0.0;
     for (int c = tid; c < a.n; c += nth) {
-      a.x[c] += alpha * pnew[c];
-      const double rc = a.r[c] - alpha * a.ap[c];
+      a.x[c] += al * pnew[c];
+      const S rc = a.r[c] - al * a.ap[c];
       a.r[c] = rc;
-      accr += rc * rc;
-      accz += rc * (rc * a.dinv[c]);
+      accr += double(rc) * double(rc);
+      accz += double(rc) * double(rc * a.dinv[c]);
     }
     block_sum2_store(accr, accz, partR + blockIdx.x, partZ + blockIdx.x);
     if ((dead = grid_barrier(a.bar, gen))) break;
@@ -364,14 +382,14 @@ __global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs a) {
     grid_total2(partR, partZ, rr, rz_new);
     beta = rz_new / rz;
     rz = rz_new;
-    double* t = pold;
+    S* t = pold;
     pold = pnew;
     pnew = t;
     ++it;
   }
   for (int c = tid; c < a.n; c += nth) {
-    const double d = a.x[c];
-    if (a.delta != a.x) a.delta[c] = d;
+    const double d = double(a.x[c]);
+    if (!same_array(a.delta, a.x)) a.delta[c] = d;
     if (a.rho_out) {
       const double r = a.rho_half[c] + d;
       a.rho_out[c] = r;
@@ -448,7 +466,8 @@ __device__ void grid_total2(const double* part0, const double* part1, double& t0
 // The setup forms only r = b and (b, b); the first step length needs (C r, r), which one more
 // phase computes when the stopping test lets CG iterate at all (a solve of k >= 1 iterations
 // takes k + 2 barriers, a solve that stops at once one).
-__global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
+template <class S>
+__global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs<S> a) {
   if (a.skip && *a.skip) return;   // every block returns before the first barrier
   unsigned gen = ld_acquire(&a.bar[1]);
   const int tid = blockIdx.x * CT + threadIdx.x, nth = gridDim.x * CT;
@@ -456,14 +475,14 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
   double* partG = a.partial;
   double* partD = a.partial + gridDim.x;
   // (C v)_c for v given at c (vc) and elsewhere by a function of the vector index
-  auto apply = [&](int c, double vc, auto v) { return op_apply(a, c, vc, v); };
+  auto apply = [&](int c, S vc, auto v) { return op_apply(a, c, vc, v); };
   // r = b = sig_s .* residual and (b, b)
   double g = 0.0, d = 0.0;
   for (int c = tid; c < n; c += nth) {
     const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
-    const double b = a.sig_s[c] * rc;
+    const S b = S(a.sig_s[c] * rc);
     a.r[c] = b;
-    g += b * b;
+    g += double(b) * double(b);
   }
   block_sum2_store(g, 0.0, partG + blockIdx.x, partD + blockIdx.x);
   bool dead = grid_barrier(a.bar, gen);   // a barrier wait ran out: leave the solve
@@ -474,10 +493,10 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
     // w = C r and (w, r) for the first step length (only when CG iterates at all)
     d = 0.0;
     for (int c = tid; c < n; c += nth) {
-      const double rc = a.r[c];
-      const double w = apply(c, rc, [&](int k) { return __ldcg(a.r + k); });
+      const S rc = a.r[c];
+      const S w = apply(c, rc, [&](int k) { return __ldcg(a.r + k); });
       a.ap[c] = w;
-      d += w * rc;
+      d += double(w) * double(rc);
     }
     block_sum2_store(0.0, d, partG + blockIdx.x, partD + blockIdx.x);
     dead = grid_barrier(a.bar, gen);
@@ -490,32 +509,33 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
     const bool first = it == 0;   // p = r, s = w, x = alpha p (p, s, x start at zero)
     const double beta = first ? 0.0 : gamma / gamma_prev;
     const double alpha = first ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
+    const S bt = S(beta), al = S(alpha);
     const bool odd = (it & 1) != 0;
-    const double* r_o = odd ? a.r1 : a.r;
-    const double* w_o = odd ? a.w1 : a.ap;
-    const double* s_o = odd ? a.s1 : a.p1;
-    double* r_n = odd ? a.r : a.r1;
-    double* w_n = odd ? a.ap : a.w1;
-    double* s_n = odd ? a.p1 : a.s1;
+    const S* r_o = odd ? a.r1 : a.r;
+    const S* w_o = odd ? a.w1 : a.ap;
+    const S* s_o = odd ? a.s1 : a.p1;
+    S* r_n = odd ? a.r : a.r1;
+    S* w_n = odd ? a.ap : a.w1;
+    S* s_n = odd ? a.p1 : a.s1;
     auto rnext = [&](int k) {
-      const double sk = first ? __ldcg(w_o + k) : fma(beta, __ldcg(s_o + k), __ldcg(w_o + k));
-      return fma(-alpha, sk, __ldcg(r_o + k));
+      const S sk = first ? __ldcg(w_o + k) : fmaS(bt, __ldcg(s_o + k), __ldcg(w_o + k));
+      return fmaS(-al, sk, __ldcg(r_o + k));
     };
     g = 0.0;
     d = 0.0;
     for (int c = tid; c < n; c += nth) {
-      const double rc0 = r_o[c];
-      const double sc = first ? w_o[c] : fma(beta, s_o[c], w_o[c]);
-      const double pc = first ? rc0 : fma(beta, a.p0[c], rc0);
+      const S rc0 = r_o[c];
+      const S sc = first ? w_o[c] : fmaS(bt, s_o[c], w_o[c]);
+      const S pc = first ? rc0 : fmaS(bt, a.p0[c], rc0);
       a.p0[c] = pc;
       s_n[c] = sc;
-      a.x[c] = first ? alpha * pc : fma(alpha, pc, a.x[c]);
-      const double rc = fma(-alpha, sc, rc0);
-      const double wc = apply(c, rc, rnext);
+      a.x[c] = first ? al * pc : fmaS(al, pc, a.x[c]);
+      const S rc = fmaS(-al, sc, rc0);
+      const S wc = apply(c, rc, rnext);
       r_n[c] = rc;
       w_n[c] = wc;
-      g += rc * rc;
-      d += wc * rc;
+      g += double(rc) * double(rc);
+      d += double(wc) * double(rc);
     }
     block_sum2_store(g, d, partG + blockIdx.x, partD + blockIdx.x);
     if ((dead = grid_barrier(a.bar, gen))) break;
@@ -525,8 +545,8 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs a) {
     ++it;
   }
   for (int c = tid; c < n; c += nth) {
-    const double dd = it > 0 ? a.x[c] : 0.0;
-    if (a.delta != a.x || it == 0) a.delta[c] = dd;
+    const double dd = it > 0 ? double(a.x[c]) : 0.0;
+    if (!same_array(a.delta, a.x) || it == 0) a.delta[c] = dd;
     if (a.rho_out) {
       const double r = a.rho_half[c] + dd;
       a.rho_out[c] = r;
@@ -648,7 +668,7 @@ void dsa_q1_blocks(int nx, int ny, double hx, double hy, double tau, const doubl
 
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
                       const double* sig_t, const double* sig_s, cudaStream_t s, int max_blocks,
-                      int degree) {
+                      int degree, bool f32) {
   const int ncell = nx * ny;
   const int n = degree == 1 ? 4 * ncell : ncell;
   op.nx = nx;
@@ -656,6 +676,7 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   op.n = n;
   op.ncell = ncell;
   op.deg = degree;
+  op.f32 = f32;
   std::vector<double> diag, cx, cy, blk;
   if (degree == 1) {
     dsa_q1_blocks(nx, ny, hx, hy, tau, sig_t, sig_s, blk);
@@ -680,8 +701,11 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   // two-phase arrangement took 20 % less time per solve than the one-barrier one, whose
   // recomputation of a neighbour's r' costs three loads and the Q1 operator reads ten)
   op.single_phase = degree == 0 && n <= (1 << 18);
-  const void* kern = degree == 1 ? (const void*)pcg_q1_kernel
-                                 : (op.single_phase ? (const void*)cg1_kernel : (const void*)cg_kernel);
+  const void* kern =
+      f32 ? (degree == 1 ? (const void*)pcg_q1_kernel<float>
+                         : (op.single_phase ? (const void*)cg1_kernel<float> : (const void*)cg_kernel<float>))
+          : (degree == 1 ? (const void*)pcg_q1_kernel<double>
+                         : (op.single_phase ? (const void*)cg1_kernel<double> : (const void*)cg_kernel<double>));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CT, 0);
   if (per_sm < 1) per_sm = 1;
   const int want = (n + CT - 1) / CT;
@@ -691,12 +715,13 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   op.blocks = want < cap ? want : cap;
   if (op.blocks < 1) op.blocks = 1;
   cudaError_t e;
-  const size_t bytes = sizeof(double) * (size_t)n;
-  double** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x,
-                     &op.r1, &op.w1, &op.s1};
+  const size_t real = f32 ? sizeof(float) : sizeof(double);
+  const size_t bytes = real * (size_t)n;
+  void** bufs[] = {&op.diag, &op.cx, &op.cy, &op.r, &op.p0, &op.p1, &op.ap, &op.x,
+                   &op.r1, &op.w1, &op.s1};
   op.blk = nullptr;
   op.dinv = nullptr;
-  for (double** b : bufs) {
+  for (void** b : bufs) {
     *b = nullptr;
     if (!op.single_phase && (b == &op.r1 || b == &op.w1 || b == &op.s1)) continue;
     if (degree == 1 && (b == &op.diag || b == &op.cx || b == &op.cy)) continue;
@@ -705,6 +730,17 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   if ((e = cudaMalloc(&op.partial, sizeof(double) * 3 * op.blocks)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&op.scal, 64)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(op.scal, 0, 64, s)) != cudaSuccess) return e;
+  // coefficient arrays in the solve's storage (FP32: rounded once from the FP64 set-up)
+  auto upload = [&](void** dst, const std::vector<double>& v) -> cudaError_t {
+    cudaError_t err;
+    if (!*dst && (err = cudaMalloc(dst, real * v.size())) != cudaSuccess) return err;
+    if (!f32) return cudaMemcpyAsync(*dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s);
+    std::vector<float> w(v.begin(), v.end());
+    if ((err = cudaMemcpyAsync(*dst, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return err;
+    return cudaStreamSynchronize(s);   // w is a local
+  };
   if (degree == 1) {
     // inverse diagonal of C: mode k = a + 2b of a cell has Xd[a][a] + Yd[b][b]
     std::vector<double> dinv(n);
@@ -714,64 +750,57 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
                          blk[(size_t)((k >> 1) ? 5 : 3) * ncell + c];
         dinv[(size_t)k * ncell + c] = 1.0 / d;
       }
-    if ((e = cudaMalloc(&op.blk, sizeof(double) * blk.size())) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&op.dinv, sizeof(double) * dinv.size())) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(op.blk, blk.data(), sizeof(double) * blk.size(),
-                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
-      return e;
-    if ((e = cudaMemcpyAsync(op.dinv, dinv.data(), sizeof(double) * dinv.size(),
-                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
-      return e;
+    if ((e = upload(&op.blk, blk)) != cudaSuccess) return e;
+    if ((e = upload(&op.dinv, dinv)) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
   }
-  if ((e = cudaMemcpyAsync(op.diag, diag.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return e;
-  if ((e = cudaMemcpyAsync(op.cx, cx.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return e;
-  if ((e = cudaMemcpyAsync(op.cy, cy.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return e;
+  if ((e = upload(&op.diag, diag)) != cudaSuccess) return e;
+  if ((e = upload(&op.cx, cx)) != cudaSuccess) return e;
+  if ((e = upload(&op.cy, cy)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }
 
 void dsa_free(DsaOp& op) {
-  double* bufs[] = {op.diag, op.cx, op.cy, op.r,       op.p0,      op.p1,  op.ap,
-                    op.x,    op.r1, op.w1, op.s1, op.partial, op.scal, op.blk, op.dinv};
-  for (double* b : bufs)
+  void* bufs[] = {op.diag, op.cx, op.cy, op.r,       op.p0,      op.p1,  op.ap,
+                  op.x,    op.r1, op.w1, op.s1, op.partial, op.scal, op.blk, op.dinv};
+  for (void* b : bufs)
     if (b) cudaFree(b);
   op = DsaOp{};
 }
 
-cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
-                      const double* residual_b, double rtol, int max_iter, double* delta,
-                      const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
-                      cudaStream_t s, const unsigned* skip) {
-  CgArgs a{};
+namespace {
+template <class S>
+cudaError_t dsa_solve_impl(DsaOp& op, const double* sig_s, const double* residual,
+                           const double* residual_b, double rtol, int max_iter, double* delta,
+                           const double* rho_half, double* rho_out, double* q_out,
+                           int* iters_dev, cudaStream_t s, const unsigned* skip) {
+  CgArgs<S> a{};
   a.skip = skip;
   a.nx = op.nx;
   a.ny = op.ny;
   a.n = op.n;
-  a.diag = op.diag;
-  a.cx = op.cx;
-  a.cy = op.cy;
-  a.blk = op.blk;
-  a.dinv = op.dinv;
+  a.diag = static_cast<const S*>(op.diag);
+  a.cx = static_cast<const S*>(op.cx);
+  a.cy = static_cast<const S*>(op.cy);
+  a.blk = static_cast<const S*>(op.blk);
+  a.dinv = static_cast<const S*>(op.dinv);
   a.ncell = op.ncell;
   a.sig_s = sig_s;
   a.residual = residual;
   a.residual_b = residual_b;
   a.rtol2 = rtol * rtol;
   a.max_iter = max_iter;
-  a.r = op.r;
-  a.p0 = op.p0;
-  a.p1 = op.p1;
-  a.ap = op.ap;
-  a.x = op.x;
-  a.r1 = op.r1;
-  a.w1 = op.w1;
-  a.s1 = op.s1;
+  a.r = static_cast<S*>(op.r);
+  a.p0 = static_cast<S*>(op.p0);
+  a.p1 = static_cast<S*>(op.p1);
+  a.ap = static_cast<S*>(op.ap);
+  a.x = static_cast<S*>(op.x);
+  a.r1 = static_cast<S*>(op.r1);
+  a.w1 = static_cast<S*>(op.w1);
+  a.s1 = static_cast<S*>(op.s1);
   a.partial = op.partial;
   a.bar = reinterpret_cast<unsigned*>(op.scal);
-  a.delta = delta ? delta : op.x;
+  a.delta = delta;
   a.rho_half = rho_half;
   a.rho_out = rho_out;
   a.q_out = q_out;
@@ -779,9 +808,24 @@ cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
   void* args[] = {&a};
   ++g_launches;
   const void* kern = op.deg == 1
-                         ? (const void*)pcg_q1_kernel
-                         : (op.single_phase ? (const void*)cg1_kernel : (const void*)cg_kernel);
+                         ? (const void*)pcg_q1_kernel<S>
+                         : (op.single_phase ? (const void*)cg1_kernel<S> : (const void*)cg_kernel<S>);
   return cudaLaunchCooperativeKernel(kern, dim3(op.blocks), dim3(CT), args, 0, s);
+}
+}  // namespace
+
+cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
+                      const double* residual_b, double rtol, int max_iter, double* delta,
+                      const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
+                      cudaStream_t s, const unsigned* skip) {
+  if (op.f32) {
+    if (!delta) return cudaErrorInvalidValue;   // the FP32 iterate cannot hold the FP64 output
+    return dsa_solve_impl<float>(op, sig_s, residual, residual_b, rtol, max_iter, delta,
+                                 rho_half, rho_out, q_out, iters_dev, s, skip);
+  }
+  return dsa_solve_impl<double>(op, sig_s, residual, residual_b, rtol, max_iter,
+                                delta ? delta : static_cast<double*>(op.x), rho_half, rho_out,
+                                q_out, iters_dev, s, skip);
 }
 
 }  // namespace rte
@@ -862,7 +906,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<double>, CT, 0);
   int blocks = (n + CT - 1) / CT;
   int cap = (per_sm < 1 ? 1 : per_sm) * sms;
   if (cap > 2 * sms) cap = 2 * sms;
@@ -882,7 +926,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
     *err = std::string("rte_dsa_solve_noalloc: coefficient kernel: ") + cudaGetErrorString(e);
     return RTE_ECUDA;
   }
-  CgArgs a{};
+  CgArgs<double> a{};
   a.nx = nx;
   a.ny = ny;
   a.n = n;
@@ -908,7 +952,7 @@ rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, doub
   a.iters = iters_dev;
   void* args[] = {&a};
   ++g_launches;
-  e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(CT), args, 0, s);
+  e = cudaLaunchCooperativeKernel((const void*)cg_kernel<double>, dim3(blocks), dim3(CT), args, 0, s);
   if (e != cudaSuccess) {
     *err = std::string("rte_dsa_solve_noalloc: ") + cudaGetErrorString(e);
     return RTE_ECUDA;

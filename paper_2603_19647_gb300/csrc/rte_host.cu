@@ -1213,7 +1213,7 @@ rte_status set_tau(rte_handle h, double tau) {
   CK(cudaStreamSynchronize(h->st));
   dsa_free(h->dsa);
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, h->sig_t_host.data(),
-               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg));
+               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg, h->fp32));
   h->resp_ready = false;
   h->y_valid = false;
   return RTE_OK;
@@ -1738,8 +1738,11 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
       CK(cudaMemsetAsync(h->f_prev, 0, sizeof(double) * fc, h->st));
     }
   }
+  // the FP32 modes solve the DSA system in FP32 as well (dots and CG scalars in FP64): it only
+  // preconditions the SI iteration, whose residual stays FP64, so its precision moves the
+  // iteration count at most, never the fixed point
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st,
-               h->opt.cg_blocks, h->deg));
+               h->opt.cg_blocks, h->deg, h->fp32));
   CK(rom_alloc(h->ig, (int)nd, h->opt.r_max));
   if (h->opt.sa_kind == RTE_SA_DMD_ITER) {
     CK(rom_alloc(h->mh, (int)nd, h->opt.mh_window));

@@ -187,24 +187,27 @@ cudaError_t launch_bdf2_history(Real* f, Real* prev, long n, cudaStream_t s);
 struct DsaOp {
   int nx, ny, n;  // n: unknowns (Q0: cells; Q1: 4 modes per cell, mode-major)
   int ncell, deg;
-  double* diag;   // Q0 [n]
-  double* cx;     // Q0 [n] coupling of cell c with c+1 (0 at the east edge)
-  double* cy;     // Q0 [n] coupling of cell c with c+nx (0 at the north edge / 1D)
-  double* blk;    // Q1 [14][ncell] block coefficients
-  double* dinv;   // Q1 [n] inverse diagonal (the Jacobi preconditioner)
-  // CG workspace
-  double *r, *p0, *p1, *ap, *x;
-  double *r1, *w1, *s1;   // second buffers of the single-barrier CG (r, w = C r, s = C p)
-  double* partial;   // [2 * blocks]
+  bool f32;       // vectors, coefficients and their arithmetic in FP32 (dots and scalars FP64)
+  // coefficients and CG vectors, in FP64 or (f32) FP32 storage
+  void* diag;     // Q0 [n]
+  void* cx;       // Q0 [n] coupling of cell c with c+1 (0 at the east edge)
+  void* cy;       // Q0 [n] coupling of cell c with c+nx (0 at the north edge / 1D)
+  void* blk;      // Q1 [14][ncell] block coefficients
+  void* dinv;     // Q1 [n] inverse diagonal (the Jacobi preconditioner)
+  void *r, *p0, *p1, *ap, *x;
+  void *r1, *w1, *s1;   // second buffers of the single-barrier CG (r, w = C r, s = C p)
+  double* partial;   // [3 * blocks]
   double* scal;      // [8] device scalars
   int blocks;
   bool single_phase;   // cg1_kernel (one barrier per iteration) instead of cg_kernel
 };
 // max_blocks > 0 caps the blocks of the cooperative CG launch (default: one or two per SM).
 // degree 1: the Q1 interior-penalty operator (2D) on mode-major vectors of 4 nx ny values.
+// f32: the solve's vectors and operator arithmetic in FP32, dot products and CG scalars in
+// FP64 (the FP32 modes; the solve's inputs and outputs stay FP64).
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
                       const double* sig_t_host, const double* sig_s_host, cudaStream_t s,
-                      int max_blocks = 0, int degree = 0);
+                      int max_blocks = 0, int degree = 0, bool f32 = false);
 void dsa_free(DsaOp& op);
 // delta = C^{-1} (sig_s .* (residual - residual_b)) (residual_b may be nullptr);
 // rho_out = rho_half + delta and q_out = sig_s .* rho_out when rho_out != nullptr.
