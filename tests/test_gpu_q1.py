@@ -237,3 +237,13 @@ def test_q1_fp32_march_within_1e6_of_fp64_oracle(rom_on):
     if rom_on:
         assert h.rte_get_stats()["phase"] == 3
     h.destroy()
+
+
+@pytest.mark.slow
+def test_q1_full_size_march_against_oracle():
+    """The 256^2 x 128 benchmark grid in the Q1 scheme with the ROMs on, against the oracle's
+    march of the same algorithm for 24 steps: relative L2 <= 1e-10 with equal iteration counts,
+    ROM ranks and phase changes at every step."""
+    from test_gpu_march import _march
+    wl = inputs.checkerboard(steps=24)
+    _march(wl, 24, 1, rom_on=True, **Q1)
