@@ -53,6 +53,7 @@ struct rte_s {
   int* h_cg = nullptr;        // pinned, CG counts of one SI-SA solve
   int cg_slots = 0;
   bool blocking = false;             // wait on ev_wait (sleeping) instead of spinning
+  bool dsa_f32 = false;              // the DSA solve in FP32 (FP32 modes, single handles)
   cudaEvent_t ev_wait = nullptr;     // blocking-sync event
   unsigned* h_err = nullptr;         // pinned copy of the sweeps' error word
   // ROM update queued on the device, finished on the host after the step's last wait
@@ -163,6 +164,8 @@ struct rte_s {
 namespace {
 
 thread_local std::string g_create_error;
+// set while rte_batch_create creates its instances (they keep the FP64 DSA solve)
+thread_local bool g_batch_create = false;
 
 rte_status fail(rte_handle h, rte_status st, const std::string& msg) {
   if (h) h->err = msg;
@@ -1213,7 +1216,7 @@ rte_status set_tau(rte_handle h, double tau) {
   CK(cudaStreamSynchronize(h->st));
   dsa_free(h->dsa);
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, h->sig_t_host.data(),
-               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg, h->fp32));
+               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg, h->dsa_f32));
   h->resp_ready = false;
   h->y_valid = false;
   return RTE_OK;
@@ -1738,11 +1741,14 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
       CK(cudaMemsetAsync(h->f_prev, 0, sizeof(double) * fc, h->st));
     }
   }
-  // the FP32 modes solve the DSA system in FP32 as well (dots and CG scalars in FP64): it only
+  // The FP32 modes solve the DSA system in FP32 as well (dots and CG scalars in FP64): it only
   // preconditions the SI iteration, whose residual stays FP64, so its precision moves the
-  // iteration count at most, never the fixed point
+  // iteration count at most, never the fixed point.  Batched instances keep the FP64 solve:
+  // with the FP32 one, the 64-instance FP32 batch had a solve's bounded grid-barrier wait run
+  // out (RTE_ETIMEOUT) while the other instances' kernels filled the GPU.
+  h->dsa_f32 = h->fp32 && !g_batch_create;
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st,
-               h->opt.cg_blocks, h->deg, h->fp32));
+               h->opt.cg_blocks, h->deg, h->dsa_f32));
   CK(rom_alloc(h->ig, (int)nd, h->opt.r_max));
   if (h->opt.sa_kind == RTE_SA_DMD_ITER) {
     CK(rom_alloc(h->mh, (int)nd, h->opt.mh_window));
@@ -2492,8 +2498,10 @@ rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* proble
   }
   for (int i = 0; i < count; ++i) {
     const rte_problem& p = problems[i];
+    g_batch_create = true;
     rte_status s = rte_create(&b->h[i], &p.mesh, &p.quad, p.sigma_t, p.sigma_s, p.source, p.c_dt,
                               &bopt);
+    g_batch_create = false;
     if (s == RTE_OK) {
       b->h[i]->blocking = true;
       if (p.rho0) {
