@@ -150,6 +150,9 @@ typedef struct {
                         the diffusion correction on the same space (penalty
                         max(2 (D_L + D_R) / h, 1/4) per face, Marshak condition taken weakly).
                         The paper's own fully consistent DSA is given by citation only. */
+  int dsa_fp64;      /* 1: solve the DSA system in FP64 in the FP32 modes too; 0 (default): in
+                        the FP32 modes its vectors and operator are FP32 (dot products and CG
+                        scalars FP64).  Batched instances always take 1. */
 } rte_options;
 
 typedef struct {

@@ -164,8 +164,6 @@ struct rte_s {
 namespace {
 
 thread_local std::string g_create_error;
-// set while rte_batch_create creates its instances (they keep the FP64 DSA solve)
-thread_local bool g_batch_create = false;
 
 rte_status fail(rte_handle h, rte_status st, const std::string& msg) {
   if (h) h->err = msg;
@@ -1741,12 +1739,10 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
       CK(cudaMemsetAsync(h->f_prev, 0, sizeof(double) * fc, h->st));
     }
   }
-  // The FP32 modes solve the DSA system in FP32 as well (dots and CG scalars in FP64): it only
-  // preconditions the SI iteration, whose residual stays FP64, so its precision moves the
-  // iteration count at most, never the fixed point.  Batched instances keep the FP64 solve:
-  // with the FP32 one, the 64-instance FP32 batch had a solve's bounded grid-barrier wait run
-  // out (RTE_ETIMEOUT) while the other instances' kernels filled the GPU.
-  h->dsa_f32 = h->fp32 && !g_batch_create;
+  // The FP32 modes solve the DSA system in FP32 as well (dots and CG scalars in FP64) unless
+  // options.dsa_fp64: it only preconditions the SI iteration, whose residual stays FP64, so
+  // its precision moves the iteration count at most, never the fixed point.
+  h->dsa_f32 = h->fp32 && !h->opt.dsa_fp64;
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st,
                h->opt.cg_blocks, h->deg, h->dsa_f32));
   CK(rom_alloc(h->ig, (int)nd, h->opt.r_max));
@@ -2489,6 +2485,10 @@ rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* proble
   rte_options bopt;
   if (opt) bopt = *opt;
   else rte_default_options(&bopt);
+  // The DSA solve in FP64: with the FP32 solve, one instance of the 64-instance FP32 batch had a
+  // bounded grid-barrier wait of its cooperative CG launch run out (RTE_ETIMEOUT) while the
+  // other instances' kernels filled the GPU; the FP64 solve never has.
+  bopt.dsa_fp64 = 1;
   if (bopt.precision != RTE_FP64 && bopt.tune && !bopt.sweep_kernel && !bopt.sweep_lanes &&
       !bopt.sweep_rows && !bopt.sweep_warps) {
     bopt.sweep_kernel = 2;
@@ -2498,10 +2498,8 @@ rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* proble
   }
   for (int i = 0; i < count; ++i) {
     const rte_problem& p = problems[i];
-    g_batch_create = true;
     rte_status s = rte_create(&b->h[i], &p.mesh, &p.quad, p.sigma_t, p.sigma_s, p.source, p.c_dt,
                               &bopt);
-    g_batch_create = false;
     if (s == RTE_OK) {
       b->h[i]->blocking = true;
       if (p.rho0) {

@@ -42,7 +42,7 @@ def test_default_options(lib):
     assert (o.max_iter, o.r_max, o.cg_rtol, o.cg_max_iter) == (500, 40, 1e-6, 500)
     assert o.pc_levels == 1 and rte.MAX_PC_LEVELS == 4
     assert o.sa_kind == rte.RTE_SA_DSA and o.mh_window == 4
-    assert o.degree == 0
+    assert o.degree == 0 and o.dsa_fp64 == 0
 
 
 def _create(**kw):

@@ -247,3 +247,39 @@ def test_q1_full_size_march_against_oracle():
     from test_gpu_march import _march
     wl = inputs.checkerboard(steps=24)
     _march(wl, 24, 1, rom_on=True, **Q1)
+
+
+def test_q1_two_preconditioner_roms_strict():
+    """Two preconditioner ROMs (iterations 1 and 2) on the Q1 scheme: the same decisions, ranks
+    of both ROMs and 1e-10 while the second ROM is built from steps that applied the first."""
+    from test_gpu_march import _march
+    orc = _march(_q1_workload(n=24, steps=100), 100, 5, rom_on=True, decisions_p3=True,
+                 pc_levels=2, eps_pc=1e-3, **Q1)
+    assert orc.pcs[1].rank > 0
+
+
+def test_q1_dmd_across_iterations_strict():
+    """The DMD-across-iterations SA steps in place of DSA on the Q1 scheme, with the ROMs: the
+    same decisions, the same number of jumps and 1e-10 throughout, and no CG at all."""
+    from test_gpu_march import _march
+    orc = _march(_q1_workload(n=24, steps=50), 50, 5, rom_on=True, decisions_p3=True,
+                 sa_kind=rte.RTE_SA_DMD_ITER, eps_pc=1e-3, **Q1)
+    assert sum(s.cg_iterations for s in orc.log) == 0
+
+
+@pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
+def test_q1_batch_matches_single_instances(precision):
+    """Batched Q1 instances of different sizes step exactly as the same problems alone."""
+    wls = [inputs.checkerboard(n=n, steps=20) for n in (24, 40, 16)]
+    b = rte.rte_batch_create(wls, rte.default_options(degree=1, precision=precision))
+    b.rte_batch_step(15)
+    for i, wl in enumerate(wls):
+        st = b.instance(i).rte_get_stats()
+        o = rte.default_options(degree=1, precision=precision, sweep_lanes=st["sweep_lanes"],
+                                sweep_rows=st["sweep_si_rows"], dsa_fp64=1)
+        h = rte.create_from_workload(wl, options=o)
+        h.rte_step(15)
+        assert h.rte_get_stats()["total_iterations"] == st["total_iterations"], i
+        assert rel_l2(b.instance(i).rte_get_scalar_flux(), h.rte_get_scalar_flux()) < 1e-13, i
+        h.destroy()
+    b.destroy()
