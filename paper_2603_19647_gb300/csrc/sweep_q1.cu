@@ -438,6 +438,8 @@ cudaError_t launch_q1_dl(const Sweep2DArgs<Real>& a, int R, cudaStream_t s) {
 template <class Real, int MODE>
 cudaError_t launch_q1_mode(const Sweep2DArgs<Real>& a, int dl, int R, cudaStream_t s) {
   switch (dl) {
+    case 2: return launch_q1_dl<Real, 2, MODE>(a, R, s);
+    case 4: return launch_q1_dl<Real, 4, MODE>(a, R, s);
     case 8: return launch_q1_dl<Real, 8, MODE>(a, R, s);
     case 16: return launch_q1_dl<Real, 16, MODE>(a, R, s);
     case 32: return launch_q1_dl<Real, 32, MODE>(a, R, s);

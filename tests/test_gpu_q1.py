@@ -46,8 +46,8 @@ def test_q1_si_sweep(quad, shape):
     h.destroy()
 
 
-@pytest.mark.parametrize("lanes,rows", [(8, 1), (8, 2), (8, 4), (16, 1), (16, 4), (32, 1),
-                                        (32, 2), (32, 4)])
+@pytest.mark.parametrize("lanes,rows", [(2, 1), (2, 4), (4, 1), (4, 2), (8, 1), (8, 2), (8, 4),
+                                        (16, 1), (16, 4), (32, 1), (32, 2), (32, 4)])
 @pytest.mark.parametrize("mode", ["si", "f"])
 def test_q1_sweep_tilings(lanes, rows, mode):
     """Every tile (directions per lane group, rows per lane group) gives the same SI sweep and
@@ -193,7 +193,7 @@ def test_q1_full_size_sweeps():
 FP32 = dict(degree=1, precision=rte.RTE_FP32)
 
 
-@pytest.mark.parametrize("lanes,rows", [(8, 1), (8, 4), (16, 2), (32, 1)])
+@pytest.mark.parametrize("lanes,rows", [(2, 1), (4, 1), (8, 1), (8, 4), (16, 2), (32, 1)])
 def test_q1_fp32_sweeps(lanes, rows):
     """FP32 cell solves: the SI sweep and the fused sweep within 2e-6 (relative L2) of the FP64
     oracle, and element by element within 2e-5 relative for every value above 1 % of the field's
