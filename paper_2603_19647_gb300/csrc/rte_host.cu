@@ -1486,15 +1486,16 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
   }
   float best = INFINITY;
   TuneVal bv{};
-  // 2 and 4 lanes: the Q1 sweep only, where narrow lane groups stack more rows in a warp and
-  // halve the hand-offs between CTAs (measured at 256^2 x 128, FP64 SI sweep: 2.89 / 2.58 /
-  // 2.42 ms with 8 / 4 / 2 lanes; at 1024^2 FP32 the 2-lane groups lose: 5.6 against 4.6 ms)
+  // 2 and 4 lanes: the Q1 sweep and the FP64 Q0 strip chain, where narrow lane groups stack
+  // more rows in a warp and halve the hand-offs between CTAs (measured at 256^2 x 128, SI
+  // sweep with 8 / 4 / 2 lanes: Q1 FP64 2.89 / 2.58 / 2.42 ms, Q0 FP64 0.320 / 0.284 / 0.260 ms;
+  // at 1024^2 the tuner keeps wider groups: Q1 FP32 5.6 ms with 2 lanes against 4.6 with 4)
   const int dls[5] = {2, 4, 8, 16, 32};
   struct Cand {
     int kind, R, W;
   };
   for (int dl : dls) {
-    if (dl > dl_max || (dl < 8 && h->deg != 1)) continue;
+    if (dl > dl_max || (dl < 8 && h->deg != 1 && h->fp32)) continue;
     TRY(make_layout(h, dl));
     std::vector<Cand> cand;
     const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8}, ths[3] = {2, 4, 8};
@@ -1595,8 +1596,10 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
       h->opt.sweep_lanes != 32 &&
-      !((h->opt.sweep_lanes == 2 || h->opt.sweep_lanes == 4) && h->opt.degree == 1))
-    return fail(h, RTE_EINVAL, "sweep_lanes must be 0, 8, 16 or 32 (or 2, 4 with degree 1)");
+      !((h->opt.sweep_lanes == 2 || h->opt.sweep_lanes == 4) &&
+        (h->opt.degree == 1 || h->opt.precision == RTE_FP64)))
+    return fail(h, RTE_EINVAL,
+                "sweep_lanes must be 0, 8, 16 or 32 (2 and 4 also in RTE_FP64 and with degree 1)");
   if (h->opt.sweep_rows != 0 && h->opt.sweep_rows != 1 && h->opt.sweep_rows != 2 &&
       h->opt.sweep_rows != 4 && h->opt.sweep_rows != 8)
     return fail(h, RTE_EINVAL, "sweep_rows must be 0, 1, 2, 4 or 8");

@@ -498,8 +498,12 @@ cudaError_t launch_dl(const Sweep2DArgs<Real>& a, int R, cudaStream_t s) {
   switch (R) {
     case 1: return launch_dl_r<Real, DL, 1, MODE>(a, s);
     case 2: return launch_dl_r<Real, DL, 2, MODE>(a, s);
-    case 4: return launch_dl_r<Real, DL, 4, MODE>(a, s);
-    case 8: return launch_dl_r<Real, DL, 8, MODE>(a, s);
+    case 4:
+      if constexpr (DL >= 4) return launch_dl_r<Real, DL, 4, MODE>(a, s);
+      return cudaErrorInvalidValue;
+    case 8:
+      if constexpr (DL >= 8) return launch_dl_r<Real, DL, 8, MODE>(a, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -507,6 +511,13 @@ cudaError_t launch_dl(const Sweep2DArgs<Real>& a, int R, cudaStream_t s) {
 template <class Real, int MODE>
 cudaError_t launch_mode_impl(const Sweep2DArgs<Real>& a, int dl, int R, cudaStream_t s) {
   switch (dl) {
+    case 2:   // 2 and 4 lanes: FP64 only (their FP32 / BF16 families are less than one
+              // 16-byte piece of a cell)
+      if constexpr (sizeof(Real) == 8) return launch_dl<Real, 2, MODE>(a, R, s);
+      return cudaErrorInvalidValue;
+    case 4:
+      if constexpr (sizeof(Real) == 8) return launch_dl<Real, 4, MODE>(a, R, s);
+      return cudaErrorInvalidValue;
     case 8: return launch_dl<Real, 8, MODE>(a, R, s);
     case 16: return launch_dl<Real, 16, MODE>(a, R, s);
     case 32: return launch_dl<Real, 32, MODE>(a, R, s);

@@ -55,7 +55,8 @@ def test_sweep_2d(quad, shape):
 
 
 @pytest.mark.parametrize("lanes,rows,warps", [(32, 1, 1), (32, 2, 4), (32, 8, 8), (16, 4, 3),
-                                               (8, 2, 8), (8, 8, 2), (16, 1, 5)])
+                                               (8, 2, 8), (8, 8, 2), (16, 1, 5), (4, 1, 8),
+                                               (4, 4, 3), (2, 1, 8), (2, 2, 5)])
 @pytest.mark.parametrize("mode", ["si", "f"])
 def test_sweep_2d_tilings(lanes, rows, warps, mode):
     """Every tile shape (directions per lane group, rows per lane group, warps per CTA) gives
