@@ -31,6 +31,35 @@ TOL = 1e-10
 
 ENVELOPE_FACTOR = 50.0
 PERTURBATION = 2e-16
+# A phase change one step apart is accepted only where the oracle's own decision value stood
+# within this relative distance of its threshold.  The construction phases end on the ratio
+# s_last / sum s of Eq. (ig_stop) / Eq. (pc_stop).  The PC-ROM's snapshots are differences of
+# SI iterates converged to eps_SISA, so at eps_PC = 1e-6 its smallest singular values carry
+# the solves' tolerance relative to themselves: measured on the 48^2 checkerboard at
+# eps_SISA = 1e-12, library and oracle singular values agree to 2e-7 .. 1.5e-6 of the largest,
+# and the ratio at the Phase-2 end differs by 5 % (0.985e-6 against 1.040e-6 with one sweep
+# tile, 1.090e-6 against 1.040e-6 with another).  A decision 10 % or more from its threshold
+# must agree.
+DECISION_MARGIN = 0.1
+
+
+class _LoggedOracle(stepper.OracleRTE):
+    """The oracle's march with every decision recorded: (step, kind, value, threshold)."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.decisions = []
+
+    def decide(self, kind, own, value, threshold):
+        self.decisions.append((self.n + 1, kind, float(value), float(threshold)))
+        return own
+
+    def margin(self, kind, first, last):
+        """Smallest relative distance to the threshold of the decisions `kind` taken at the ends
+        of steps first .. last (0-based step indices; step k's decision sets step k+1's phase)."""
+        m = [abs(v - t) / abs(t) for n, k, v, t in self.decisions
+             if k == kind and first <= n <= last + 1 and t != 0]
+        return min(m) if m else float("inf")
 
 
 def _perturbed_oracles(wl, rom_on, oopts, k=3, degree=0):
@@ -69,7 +98,7 @@ def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, decisions
     if "time_scheme" in opts:
         oopts["scheme"] = "bdf2" if opts["time_scheme"] == rte.RTE_BDF2 else "be"
     deg = opts.get("degree", 0)
-    orc = stepper.OracleRTE(p, rom=rom_on, **oopts)
+    orc = _LoggedOracle(p, rom=rom_on, **oopts)
     orc.set_initial(cell_modes(wl.rho0, deg))
     pert = [] if exact else _perturbed_oracles(wl, rom_on, oopts, degree=deg)
     envelope = 0.0
@@ -103,11 +132,15 @@ def _march(wl, steps, check_every, rom_on, exact=True, inflow_at=None, decisions
             if rom_on and same_decisions:
                 assert st["ig_rank"] == orc.ig.rank and st["pc_rank"] == orc.pc.rank, n
                 assert st["pc_level_rank"][:len(orc.pcs)] == [v.rank for v in orc.pcs], n
-    if rom_on:   # the same N0 and N1
+    if rom_on:   # the same N0 and N1, up to a decision within rounding of its threshold
         for ph in (2, 3):
             a = phases_lib.index(ph) if ph in phases_lib else -1
             b = phases_orc.index(ph) if ph in phases_orc else -1
-            assert a == b, (ph, a, b)
+            if a != b:
+                kind = "ig_built" if ph == 2 else "pc_built"
+                assert min(a, b) >= 0 and abs(a - b) == 1, (ph, a, b)
+                margin = orc.margin(kind, min(a, b), max(a, b))
+                assert margin < DECISION_MARGIN, (ph, a, b, margin)
     h.destroy()
     return orc
 
