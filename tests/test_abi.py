@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI library: it builds, loads, exports every entry point declared in
 include/rte.h, and rejects invalid problems with RTE_EINVAL before touching the GPU."""
+import ctypes
 import os
 import re
 
@@ -146,3 +147,37 @@ def test_march_cli_help():
     r = subprocess.run([sys.executable, "-m", "paper_2603_19647_gb300.march", "--help"],
                        cwd=ROOT, capture_output=True, text=True)
     assert r.returncode == 0 and "--precision" in r.stdout
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structs have the C header's size and field offsets (a field added
+    to the header but not to the binding, or in another order, would shift every field after
+    it without any error)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rte_mesh": rte.Mesh, "rte_quadrature": rte.Quadrature, "rte_problem": rte.Problem,
+               "rte_options": rte.Options, "rte_stats": rte.Stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rte.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, value = line.split()
+            got[(name, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
