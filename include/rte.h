@@ -110,8 +110,9 @@ typedef struct {
   int tune;          /* 1 (default): pick sweep tile shapes by timing at create; 0: heuristic */
   int sweep_rows;    /* 2D sweep: rows per lane group, 1, 2, 4 or 8 (0 = automatic); the tile
                         sequence takes 2 (FP32 modes), 4 or 8 */
-  int sweep_lanes;   /* 2D sweep: directions per lane group, 8, 16 or 32, also 2 or 4 in
-                        RTE_FP64 and with degree 1 (0 = automatic) */
+  int sweep_lanes;   /* 2D sweep: directions per lane group, 8, 16 or 32; also 2 in RTE_FP64
+                        and with degree 1, 4 in RTE_FP64, RTE_FP32 and with degree 1
+                        (0 = automatic) */
   int sweep_warps;   /* 2D sweep: warps per CTA, 1..8 (0 = automatic); reduced to fit shared memory */
   int sweep_kernel;  /* 2D sweep kernel: 0 measured choice (with tune), 1 strip chain, 2 tile
                         sequence (sweep_rows then = rows per tile: 2 in the FP32 modes, 4 or 8) */

@@ -1391,12 +1391,17 @@ bool tile_fits(rte_handle h, int dl, int kind, int R, int W) {
   const int modes_plain[3] = {0, 1, 2}, modes_bf[3] = {0, 3, 4};
   const size_t real = h->fp32 ? sizeof(float) : sizeof(double);
   if (kind == 2) {
+    if (dl < 8) return false;   // the tile sequence takes 8, 16 or 32 lanes
     if (R != 4 && R != 8 && !(R == 2 && h->fp32)) return false;
     for (int mode : h->bf16 ? modes_bf : modes_plain)
       if (sweep2d_tile_smem_bytes(real, dl, R, W, mode) > 200 * 1024) return false;
     return true;
   }
   if (R > dl) return false;
+  // strip chain: 2 lanes in FP64 only, 4 lanes in FP64 and FP32 (a BF16 family of 4 lanes or
+  // an FP32 family of 2 is less than one 16-byte piece of a cell)
+  if (dl == 2 && h->fp32) return false;
+  if (dl == 4 && h->bf16) return false;
   for (int mode : h->bf16 ? modes_bf : modes_plain)
     if (sweep2d_smem_bytes(real, dl, R, W, mode, !h->fp32) > 200 * 1024) return false;
   return true;
@@ -1495,7 +1500,7 @@ rte_status choose_tiles(rte_handle h, int* dl_out) {
     int kind, R, W;
   };
   for (int dl : dls) {
-    if (dl > dl_max || (dl < 8 && h->deg != 1 && h->fp32)) continue;
+    if (dl > dl_max || (dl == 2 && h->deg != 1 && h->fp32) || (dl == 4 && h->bf16)) continue;
     TRY(make_layout(h, dl));
     std::vector<Cand> cand;
     const int rs[3] = {1, 2, 4}, ws[3] = {2, 4, 8}, ths[3] = {2, 4, 8};
@@ -1597,9 +1602,11 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
       h->opt.sweep_lanes != 32 &&
       !((h->opt.sweep_lanes == 2 || h->opt.sweep_lanes == 4) &&
-        (h->opt.degree == 1 || h->opt.precision == RTE_FP64)))
+        (h->opt.degree == 1 || h->opt.precision == RTE_FP64)) &&
+      !(h->opt.sweep_lanes == 4 && h->opt.precision == RTE_FP32))
     return fail(h, RTE_EINVAL,
-                "sweep_lanes must be 0, 8, 16 or 32 (2 and 4 also in RTE_FP64 and with degree 1)");
+                "sweep_lanes must be 0, 8, 16 or 32 (2 also in RTE_FP64 and with degree 1, "
+                "4 also in RTE_FP64 and RTE_FP32)");
   if (h->opt.sweep_rows != 0 && h->opt.sweep_rows != 1 && h->opt.sweep_rows != 2 &&
       h->opt.sweep_rows != 4 && h->opt.sweep_rows != 8)
     return fail(h, RTE_EINVAL, "sweep_rows must be 0, 1, 2, 4 or 8");

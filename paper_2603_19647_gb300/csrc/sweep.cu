@@ -511,12 +511,12 @@ cudaError_t launch_dl(const Sweep2DArgs<Real>& a, int R, cudaStream_t s) {
 template <class Real, int MODE>
 cudaError_t launch_mode_impl(const Sweep2DArgs<Real>& a, int dl, int R, cudaStream_t s) {
   switch (dl) {
-    case 2:   // 2 and 4 lanes: FP64 only (their FP32 / BF16 families are less than one
-              // 16-byte piece of a cell)
+    case 2:   // 2 lanes: FP64 only, 4 lanes: FP64 and FP32 (an FP32 family of 2 lanes, or a
+              // BF16 one of 4, is less than one 16-byte piece of a cell)
       if constexpr (sizeof(Real) == 8) return launch_dl<Real, 2, MODE>(a, R, s);
       return cudaErrorInvalidValue;
     case 4:
-      if constexpr (sizeof(Real) == 8) return launch_dl<Real, 4, MODE>(a, R, s);
+      if constexpr (sizeof(Real) == 8 || MODE < 3) return launch_dl<Real, 4, MODE>(a, R, s);
       return cudaErrorInvalidValue;
     case 8: return launch_dl<Real, 8, MODE>(a, R, s);
     case 16: return launch_dl<Real, 16, MODE>(a, R, s);

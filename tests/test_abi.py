@@ -75,7 +75,8 @@ def _create(**kw):
     dict(options=rte.default_options(time_scheme=rte.RTE_BDF2, precision=rte.RTE_FP32_BF16F)),
     dict(options=rte.default_options(pc_levels=-1)),
     dict(options=rte.default_options(degree=2)),
-    dict(options=rte.default_options(sweep_lanes=4, precision=rte.RTE_FP32)),  # FP64 / Q1 only
+    dict(options=rte.default_options(sweep_lanes=2, precision=rte.RTE_FP32)),  # FP64 / Q1 only
+    dict(options=rte.default_options(sweep_lanes=4, precision=rte.RTE_FP32_BF16F)),
     dict(options=rte.default_options(degree=1, precision=rte.RTE_FP32_BF16F)),
     dict(options=rte.default_options(degree=1), source=np.r_[np.zeros(63), np.inf]),
 ])

@@ -54,7 +54,8 @@ def test_fp32_sweep_2d(shape, quad):
     h.destroy()
 
 
-@pytest.mark.parametrize("lanes,rows,warps", [(32, 1, 1), (8, 1, 8), (16, 4, 3), (8, 8, 2)])
+@pytest.mark.parametrize("lanes,rows,warps", [(32, 1, 1), (8, 1, 8), (16, 4, 3), (8, 8, 2), (4, 1, 8),
+                                               (4, 4, 3)])
 def test_fp32_tilings_fused_f(lanes, rows, warps):
     wl, rng = _hetero_2d(45, 53, (32, 8), seed=lanes * rows + warps)
     h, p = make_pair(wl, sweep_lanes=lanes, sweep_rows=rows, sweep_warps=warps, **FP32)
