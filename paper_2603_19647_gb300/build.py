@@ -12,8 +12,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librte.so")
 # (source, object, extra flags): the sweep kernels are split into parts compiled in parallel
 SOURCES = [("sweep.cu", f"sweep_p{p}.o", [f"-DRTE_SWEEP_PART={p}"]) for p in range(9)] + [
-    (f, f.replace(".cu", ".o"), []) for f in ("vec.cu", "cg.cu", "rom.cu", "csvd.cu", "rte_host.cu",
-                                              "sweep_q1.cu")] + [
+    (f, f.replace(".cu", ".o"), []) for f in ("vec.cu", "cg.cu", "rom.cu", "csvd.cu", "rte_host.cu")] + [
+    ("sweep_q1.cu", f"sweep_q1_p{p}.o", [f"-DRTE_Q1_PART={p}"]) for p in range(6)] + [
     ("sweep_tile.cu", f"sweep_tile_p{p}.o", [f"-DRTE_TILE_PART={p}"]) for p in range(8)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -435,6 +435,11 @@ cudaError_t launch_q1_dl(const Sweep2DArgs<Real>& a, int R, cudaStream_t s) {
   }
 }
 
+}  // namespace
+
+// One (precision, mode) per translation unit: the build compiles the six parts in parallel
+// (RTE_Q1_PART 0-5 = FP64 modes 0-2, FP32 modes 0-2; -1 builds all), and part 0 also holds
+// the public entry points.
 template <class Real, int MODE>
 cudaError_t launch_q1_mode(const Sweep2DArgs<Real>& a, int dl, int R, cudaStream_t s) {
   switch (dl) {
@@ -447,6 +452,48 @@ cudaError_t launch_q1_mode(const Sweep2DArgs<Real>& a, int dl, int R, cudaStream
   }
 }
 
+#ifndef RTE_Q1_PART
+#define RTE_Q1_PART -1
+#endif
+#define RTE_Q1_INST(REAL, MODE)                                                               \
+  template cudaError_t launch_q1_mode<REAL, MODE>(const Sweep2DArgs<REAL>&, int, int,        \
+                                                  cudaStream_t);
+#define RTE_Q1_EXTERN(REAL, MODE)                                                            \
+  extern template cudaError_t launch_q1_mode<REAL, MODE>(const Sweep2DArgs<REAL>&, int, int, \
+                                                         cudaStream_t);
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 0
+RTE_Q1_INST(double, 0)
+#else
+RTE_Q1_EXTERN(double, 0)
+#endif
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 1
+RTE_Q1_INST(double, 1)
+#else
+RTE_Q1_EXTERN(double, 1)
+#endif
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 2
+RTE_Q1_INST(double, 2)
+#else
+RTE_Q1_EXTERN(double, 2)
+#endif
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 3
+RTE_Q1_INST(float, 0)
+#else
+RTE_Q1_EXTERN(float, 0)
+#endif
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 4
+RTE_Q1_INST(float, 1)
+#else
+RTE_Q1_EXTERN(float, 1)
+#endif
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 5
+RTE_Q1_INST(float, 2)
+#else
+RTE_Q1_EXTERN(float, 2)
+#endif
+
+#if RTE_Q1_PART == -1 || RTE_Q1_PART == 0
+namespace {
 template <class Real>
 cudaError_t launch_sweep_q1_impl(const Sweep2DArgs<Real>& a, int mode, int dl, int R,
                                  cudaStream_t s) {
@@ -458,7 +505,6 @@ cudaError_t launch_sweep_q1_impl(const Sweep2DArgs<Real>& a, int mode, int dl, i
     default: return cudaErrorInvalidValue;
   }
 }
-
 }  // namespace
 
 cudaError_t launch_sweep_q1(const Sweep2DArgs<double>& a, int mode, int dl, int R,
@@ -468,5 +514,6 @@ cudaError_t launch_sweep_q1(const Sweep2DArgs<double>& a, int mode, int dl, int 
 cudaError_t launch_sweep_q1(const Sweep2DArgs<float>& a, int mode, int dl, int R, cudaStream_t s) {
   return launch_sweep_q1_impl(a, mode, dl, R, s);
 }
+#endif
 
 }  // namespace rte
