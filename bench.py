@@ -168,7 +168,8 @@ def extra_workloads(rte, inputs, torch):
     lengths (500 and 300 steps) in FP64 (ROM-accelerated and plain SI-DSA) and in the reduced
     precisions (FP32 sweeps; BF16-stored f at 2048^2), each reduced-precision march compared
     with the FP64 ROM march of the same GPU every few steps (final and worst relative L2 of the
-    scalar flux); and the 64 batched instances (20 of 100 steps).  Time per step counts the
+    scalar flux); and the 64 batched instances (20 of 100 steps), with the kernels launched one
+    by one and with each SI iteration as a captured CUDA graph.  Time per step counts the
     steps alone (the comparisons' reads of rho are outside it)."""
     import numpy as np
     out = {}
@@ -240,16 +241,18 @@ def extra_workloads(rte, inputs, torch):
     out[f"checkerboard_256sq_128dirs_q1_{cb.steps}steps"] = {"rom_fp64": k64, "rom_fp32": k32,
                                                             "sidsa_fp64": k0}
     wls = inputs.batched()
-    b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32))
-    b.rte_batch_step(2)
-    b.rte_batch_restart()
-    t0 = time.perf_counter()
-    b.rte_batch_step(20)
-    dt = time.perf_counter() - t0
-    upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b)))
-    b.destroy()
-    out["batched_64_instances_20steps_fp32_rom"] = {"ms_per_step": 1e3 * dt / 20,
-                                                   "updates_per_s": upd / dt}
+    arms = {}
+    for graph in (0, 1):   # kernels launched one by one; SI iterations as captured CUDA graphs
+        b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32, graph=graph))
+        b.rte_batch_step(2)
+        b.rte_batch_restart()
+        t0 = time.perf_counter()
+        b.rte_batch_step(20)
+        dt = time.perf_counter() - t0
+        upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b)))
+        b.destroy()
+        arms[graph] = {"ms_per_step": 1e3 * dt / 20, "updates_per_s": upd / dt}
+    out["batched_64_instances_20steps_fp32_rom"] = dict(arms[0], graph=arms[1])
     return out
 
 

@@ -155,6 +155,17 @@ typedef struct {
   int dsa_fp64;      /* 1: solve the DSA system in FP64 in the FP32 modes too; 0 (default): in
                         the FP32 modes its vectors and operator are FP32 (dot products and CG
                         scalars FP64).  Batched instances always take 1. */
+  int graph;         /* 1: each SI iteration after its stopping test (the DSA solve of l, the
+                        sweep and the residual of l + 1) runs as one CUDA graph, captured from
+                        the handle's stream the first time iteration l is reached and replayed
+                        in every later step (a new time step constant, as the first BDF2 step
+                        after a restart sets, captures them again); the ROM-preconditioned
+                        iteration and the steps of RTE_SA_DMD_ITER are launched one by one.
+                        The stream given to rte_set_stream must then be a created stream, not
+                        the legacy default stream (RTE_ECUDA otherwise).  The statistics'
+                        device times (time_sweep_ms, time_dsa_ms, si_sweep_kernel_ms) then
+                        leave out the work inside the graphs.  0 (default): launch every kernel
+                        one by one. */
 } rte_options;
 
 typedef struct {

@@ -40,6 +40,14 @@ struct rte_s {
     int kind, a, b, iter;   // iter > 0: work of SI iteration iter, dropped if it never ran
   };
   std::vector<Span> spans;
+  // options.graph: SI iteration l (DSA of l, sweep and residual of l + 1) as a CUDA graph,
+  // indexed by l, with the kernels each replay launches
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+  };
+  std::vector<IterGraph> graphs;
+  bool capturing = false;                 // no timing events while a graph is captured
   unsigned* d_conv = nullptr;             // skip word of the speculative SI-SA loop
   unsigned* res_ticket = nullptr;         // arrival counter of the fused residual + norms kernel
   const unsigned* skip_now = nullptr;     // skip word the sweep helpers pass on (or none)
@@ -357,6 +365,14 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * count);
 }
 
+// The captured SI iterations hold the device pointers and the time step constant of the
+// launches they replay: dropped whenever either changes.
+void drop_graphs(rte_handle h) {
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
 void free_all(rte_handle h) {
   void* ptrs[] = {h->sig_t, h->sig_s, h->src, h->ca, h->cb, h->cw, h->fam_quad, h->dir_sign,
                   h->inv_d, h->f, h->pm, h->pm_a, h->edge, h->ctrl, h->psi_w, h->psi_w_a,
@@ -386,6 +402,7 @@ void free_all(rte_handle h) {
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  drop_graphs(h);
   if (h->st2) cudaStreamDestroy(h->st2);
   if (h->st3) cudaStreamDestroy(h->st3);
   if (h->h_norms) cudaFreeHost(h->h_norms);
@@ -723,6 +740,7 @@ rte_status make_btilde(rte_handle h) {
 enum SpanKind { SPAN_SWEEP = 0, SPAN_DSA, SPAN_ROM, SPAN_K1, SPAN_K2 };
 
 int rec(rte_handle h) {
+  if (h->capturing) return -1;
   if (h->evnext == (int)h->evpool.size()) {
     cudaEvent_t e = nullptr;
     if (cudaEventCreate(&e) != cudaSuccess) return -1;
@@ -830,7 +848,11 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
                                  absmode, h->rho, half1, h->res_ticket));
     CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
     span(h, SPAN_SWEEP, r0, rec(h), l);
-    CK(cudaEventRecord(h->blocking ? h->ev_norm_b[p] : h->ev_norm[p], h->st));
+    return RTE_OK;
+  };
+  // the host waits for the norms of iteration l on this event
+  auto norms_ready = [&](int l) -> rte_status {
+    CK(cudaEventRecord(h->blocking ? h->ev_norm_b[l & 1] : h->ev_norm[l & 1], h->st));
     return RTE_OK;
   };
   // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta.  Its
@@ -875,18 +897,56 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
   const bool mh = h->opt.sa_kind == RTE_SA_DMD_ITER;
   if (mh) rom_reset(h->mh);
   auto sa_step = [&](int l) -> rte_status { return mh ? mh_step(l) : dsa_step(l); };
+  // The SA step of iteration l, the sweep and the residual of l + 1.  With options.graph (DSA
+  // steps only) they run as one CUDA graph, captured from the stream the first time l is
+  // reached; every pointer and value they take is fixed for the handle until drop_graphs.
+  auto iteration = [&](int l) -> rte_status {
+    if (!h->opt.graph || mh) {
+      TRY(sa_step(l));
+      TRY(sweep_increment(l + 1));
+      TRY(residual(l + 1));
+      return norms_ready(l + 1);
+    }
+    if ((int)h->graphs.size() <= l) h->graphs.resize(l + 1);
+    rte_s::IterGraph& g = h->graphs[l];
+    if (!g.exec) {
+      const long long k0 = g_launches;
+      CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+      h->capturing = true;
+      rte_status st = dsa_step(l);
+      if (st == RTE_OK) st = sweep_increment(l + 1);
+      if (st == RTE_OK) st = residual(l + 1);
+      h->capturing = false;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+      g.kernels = g_launches - k0;
+      g_launches = k0;
+      if (st != RTE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st != RTE_OK) return st;
+        return cuda_fail(h, e, "capturing an SI iteration as a CUDA graph");
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(h, ei, "instantiating the SI iteration's CUDA graph");
+      }
+    }
+    CK(cudaGraphLaunch(g.exec, h->st));
+    g_launches += g.kernels;
+    return norms_ready(l + 1);
+  };
   bool conv = false;
   int l = 1;
   for (bool& a : h->pc_applied) a = false;
   TRY(sweep_increment(1));
   TRY(residual(1));
+  TRY(norms_ready(1));
   for (l = 1;; ++l) {
     const bool pc_now = l <= pc_active;
-    if (h->opt.lookahead && !mh && l < h->opt.max_iter && !pc_now) {   // l + 1, queued ahead
-      TRY(dsa_step(l));
-      TRY(sweep_increment(l + 1));
-      TRY(residual(l + 1));
-    }
+    if (h->opt.lookahead && !mh && l < h->opt.max_iter && !pc_now)   // l + 1, queued ahead
+      TRY(iteration(l));
     CK(cudaEventSynchronize(h->blocking ? h->ev_norm_b[l & 1] : h->ev_norm[l & 1]));
     const Norms nm = h->h_norms[l & 1];
     const double res = absmode ? nm.diff_inf
@@ -894,11 +954,7 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
     conv = absmode ? nm.diff_inf <= h->opt.eps_sisa : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
     h->stats.last_residual = res;
     if (conv || l == h->opt.max_iter) break;
-    if ((!h->opt.lookahead || mh) && !pc_now) {
-      TRY(sa_step(l));
-      TRY(sweep_increment(l + 1));
-      TRY(residual(l + 1));
-    }
+    if ((!h->opt.lookahead || mh) && !pc_now) TRY(iteration(l));
     if (pc_now) {
       // ROM preconditioner of iteration l, Eq. (dmd-sa):
       // delta = dU C_r^{-1} dU^T (rho^{l-1/2} - rho^{l-1})  (rho^{0} = the initial guess)
@@ -912,6 +968,7 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
       h->pc_applied[k] = true;
       TRY(sweep_increment(l + 1));
       TRY(residual(l + 1));
+      TRY(norms_ready(l + 1));
     }
   }
   h->skip_now = nullptr;
@@ -1197,6 +1254,7 @@ void fp32_ct_pairs(rte_handle h, std::vector<float>& cth, std::vector<float>& ct
 rte_status set_tau(rte_handle h, double tau) {
   if (h->tau == tau) return RTE_OK;
   h->tau = tau;
+  drop_graphs(h);   // the sweeps take tau by value and the DSA operator is rebuilt
   const Layout& L = h->L;
   if (!h->fp32 && h->dim == 2 && h->inv_d)
     CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)h->ncell, L.nslot, L.dl,
@@ -1599,6 +1657,7 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.mh_window < 2 || h->opt.mh_window > 16)
     return fail(h, RTE_EINVAL, "mh_window must be in [2, 16]");
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
+  if (h->opt.graph != 0 && h->opt.graph != 1) return fail(h, RTE_EINVAL, "graph must be 0 or 1");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
       h->opt.sweep_lanes != 32 &&
       !((h->opt.sweep_lanes == 2 || h->opt.sweep_lanes == 4) &&

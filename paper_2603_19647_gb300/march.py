@@ -31,6 +31,8 @@ def main(argv=None):
                     help="DG degree: 0 (one value per cell) or 1 (bilinear, 2D FP64)")
     ap.add_argument("--lanes", type=int, default=0, help="sweep_lanes (0: the library's choice)")
     ap.add_argument("--rows", type=int, default=0, help="sweep_rows (0: the library's choice)")
+    ap.add_argument("--graph", type=int, choices=[0, 1], default=0,
+                    help="1: each SI iteration as a captured CUDA graph")
     a = ap.parse_args(argv)
     wl = inputs.BY_NAME[a.workload]()
     steps = a.steps if a.steps is not None else wl.steps
@@ -40,7 +42,7 @@ def main(argv=None):
         pc_levels=a.pc_levels, r_max=a.r_max,
         sa_kind=rte.RTE_SA_DMD_ITER if a.sa == "dmd" else rte.RTE_SA_DSA,
         time_scheme=rte.RTE_BDF2 if a.scheme == "bdf2" else rte.RTE_BE,
-        degree=a.degree, sweep_lanes=a.lanes, sweep_rows=a.rows)
+        degree=a.degree, sweep_lanes=a.lanes, sweep_rows=a.rows, graph=a.graph)
     h = rte.create_from_workload(wl, options=opts)
     t0 = time.perf_counter()
     h.rte_step(steps)
