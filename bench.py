@@ -169,7 +169,8 @@ def extra_workloads(rte, inputs, torch):
     precisions (FP32 sweeps; BF16-stored f at 2048^2), each reduced-precision march compared
     with the FP64 ROM march of the same GPU every few steps (final and worst relative L2 of the
     scalar flux); and the 64 batched instances (20 of 100 steps), with the kernels launched one
-    by one and with each SI iteration as a captured CUDA graph.  Time per step counts the
+    by one and with the SI iterations in captured CUDA graphs (a while node around them).
+    Time per step counts the
     steps alone (the comparisons' reads of rho are outside it)."""
     import numpy as np
     out = {}
@@ -242,7 +243,7 @@ def extra_workloads(rte, inputs, torch):
                                                             "sidsa_fp64": k0}
     wls = inputs.batched()
     arms = {}
-    for graph in (0, 1):   # kernels launched one by one; SI iterations as captured CUDA graphs
+    for graph in (0, 2):   # kernels launched one by one; SI iterations in CUDA graphs (while node)
         b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32, graph=graph))
         b.rte_batch_step(2)
         b.rte_batch_restart()
@@ -252,7 +253,7 @@ def extra_workloads(rte, inputs, torch):
         upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b)))
         b.destroy()
         arms[graph] = {"ms_per_step": 1e3 * dt / 20, "updates_per_s": upd / dt}
-    out["batched_64_instances_20steps_fp32_rom"] = dict(arms[0], graph=arms[1])
+    out["batched_64_instances_20steps_fp32_rom"] = dict(arms[0], graph=arms[2])
     return out
 
 

@@ -160,7 +160,12 @@ typedef struct {
                         the handle's stream the first time iteration l is reached and replayed
                         in every later step (a new time step constant, as the first BDF2 step
                         after a restart sets, captures them again); the ROM-preconditioned
-                        iteration and the steps of RTE_SA_DMD_ITER are launched one by one.
+                        iterations and the steps of RTE_SA_DMD_ITER are launched one by one.
+                        2: as 1, and once the iterations left are all DSA steps (from
+                        iteration pc_levels on), they run as one graph whose while node
+                        repeats the iteration until the stopping test of Algorithm 1 (or
+                        max_iter) ends it on the device: one host wait for all of them
+                        (with lookahead = 1, as 1).
                         The stream given to rte_set_stream must then be a created stream, not
                         the legacy default stream (RTE_ECUDA otherwise).  The statistics'
                         device times (time_sweep_ms, time_dsa_ms, si_sweep_kernel_ms) then

@@ -69,6 +69,7 @@ struct CgArgs {
   double* rho_out;
   double* q_out;
   int* iters;
+  int iters_add;       // 1: add the count to *iters (solves repeated by a device-side loop)
   const unsigned* skip;   // set: the whole solve is skipped (speculative SI-SA work)
 };
 
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs<S> a) {
       a.q_out[c] = a.sig_s[c] * r;
     }
   }
-  if (tid == 0) *a.iters = it;
+  if (tid == 0) *a.iters = a.iters_add ? *a.iters + it : it;
 }
 
 // Forward declarations of the two-value block and grid sums (defined below).
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(CT) pcg_q1_kernel(const CgArgs<S> a) {
       a.q_out[c] = a.sig_s[c] * r;
     }
   }
-  if (tid == 0) *a.iters = it;
+  if (tid == 0) *a.iters = a.iters_add ? *a.iters + it : it;
 }
 
 // Block sums of two values, thread 0 storing them to dst0 / dst1.
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(CT) cg1_kernel(const CgArgs<S> a) {
       a.q_out[c] = a.sig_s[c] * r;
     }
   }
-  if (tid == 0) *a.iters = it;
+  if (tid == 0) *a.iters = a.iters_add ? *a.iters + it : it;
 }
 
 }  // namespace
@@ -773,9 +774,10 @@ template <class S>
 cudaError_t dsa_solve_impl(DsaOp& op, const double* sig_s, const double* residual,
                            const double* residual_b, double rtol, int max_iter, double* delta,
                            const double* rho_half, double* rho_out, double* q_out,
-                           int* iters_dev, cudaStream_t s, const unsigned* skip) {
+                           int* iters_dev, cudaStream_t s, const unsigned* skip, int iters_add) {
   CgArgs<S> a{};
   a.skip = skip;
+  a.iters_add = iters_add;
   a.nx = op.nx;
   a.ny = op.ny;
   a.n = op.n;
@@ -817,15 +819,15 @@ cudaError_t dsa_solve_impl(DsaOp& op, const double* sig_s, const double* residua
 cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
                       const double* residual_b, double rtol, int max_iter, double* delta,
                       const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
-                      cudaStream_t s, const unsigned* skip) {
+                      cudaStream_t s, const unsigned* skip, int iters_add) {
   if (op.f32) {
     if (!delta) return cudaErrorInvalidValue;   // the FP32 iterate cannot hold the FP64 output
     return dsa_solve_impl<float>(op, sig_s, residual, residual_b, rtol, max_iter, delta,
-                                 rho_half, rho_out, q_out, iters_dev, s, skip);
+                                 rho_half, rho_out, q_out, iters_dev, s, skip, iters_add);
   }
   return dsa_solve_impl<double>(op, sig_s, residual, residual_b, rtol, max_iter,
                                 delta ? delta : static_cast<double*>(op.x), rho_half, rho_out,
-                                q_out, iters_dev, s, skip);
+                                q_out, iters_dev, s, skip, iters_add);
 }
 
 }  // namespace rte

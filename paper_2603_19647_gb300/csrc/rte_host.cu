@@ -47,6 +47,11 @@ struct rte_s {
     long long kernels = 0;
   };
   std::vector<IterGraph> graphs;
+  // options.graph = 2: the remaining SI iterations from iteration l on as one graph with a
+  // while node, indexed by l (kernels: of one pass of the loop body)
+  std::vector<IterGraph> loops;
+  unsigned* d_loop = nullptr;             // the loop's iteration counter
+  unsigned* h_loop = nullptr;             // pinned copy
   bool capturing = false;                 // no timing events while a graph is captured
   unsigned* d_conv = nullptr;             // skip word of the speculative SI-SA loop
   unsigned* res_ticket = nullptr;         // arrival counter of the fused residual + norms kernel
@@ -368,9 +373,11 @@ cudaError_t dalloc(T** p, size_t count) {
 // The captured SI iterations hold the device pointers and the time step constant of the
 // launches they replay: dropped whenever either changes.
 void drop_graphs(rte_handle h) {
-  for (auto& g : h->graphs)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-  h->graphs.clear();
+  for (auto* v : {&h->graphs, &h->loops}) {
+    for (auto& g : *v)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    v->clear();
+  }
 }
 
 void free_all(rte_handle h) {
@@ -408,6 +415,8 @@ void free_all(rte_handle h) {
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->h_cg) cudaFreeHost(h->h_cg);
   if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_loop) cudaFreeHost(h->h_loop);
+  if (h->d_loop) cudaFree(h->d_loop);
   if (h->d_conv) cudaFree(h->d_conv);
   if (h->res_ticket) cudaFree(h->res_ticket);
   for (cudaEvent_t e : h->ev_norm)
@@ -833,20 +842,25 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
   // rho^{l-1/2}, its norms (pinned copy, parity l & 1) and the device stopping test; the
   // kernel also writes rho^{l-1/2} to rho (the iterate the step returns once converged, work
   // past convergence skips itself) and, for l = 1, to rho^{n,1/2}
-  auto residual = [&](int l) -> rte_status {
+  // loop (optional): the while loop of a graph around the iteration (options.graph = 2), whose
+  // residual leaves its norms on the device
+  auto residual = [&](int l, const ResidualLoop* loop = nullptr) -> rte_status {
     const int p = l & 1;
     const int r0 = rec(h);
+    const ResidualLoop lc = loop ? *loop : ResidualLoop{0, nullptr, 0, nullptr, nullptr};
     // rho^{n,(l-1/2)} kept for the snapshot pairs of the preconditioner ROM of iteration l
     double* half1 = l == 1 ? h->rho_half1 : (l <= h->levels ? h->lv_half[l - 1] : nullptr);
     if (h->fp32)
       CK(launch_combine_residual(h->y_ir, 1, h->btilde, h->rho_prev, n, h->rho_half, h->partials,
                                  nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa, absmode,
-                                 h->rho, half1, h->res_ticket));
+                                 h->rho, half1, h->res_ticket, lc));
     else
       CK(launch_combine_residual(h->pm, nparts(h), h->btilde, h->rho_prev, n, h->rho_half,
                                  h->partials, nb, h->norms + p, h->st, h->d_conv, h->opt.eps_sisa,
-                                 absmode, h->rho, half1, h->res_ticket));
-    CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
+                                 absmode, h->rho, half1, h->res_ticket, lc));
+    if (!loop)
+      CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost,
+                         h->st));
     span(h, SPAN_SWEEP, r0, rec(h), l);
     return RTE_OK;
   };
@@ -857,10 +871,11 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
   };
   // DSA, Eq. (rho_residual); the CG kernel also forms rho^l = rho^{l-1/2} + delta.  Its
   // iteration count stays on the device until the step ends.
-  auto dsa_step = [&](int l) -> rte_status {
+  auto dsa_step = [&](int l, int iters_add = 0) -> rte_status {
     const int d0 = rec(h);
     CK(dsa_solve(h->dsa, h->sig_s, h->rho_half, h->rho_prev, h->opt.cg_rtol, h->opt.cg_max_iter,
-                 h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters + l, h->st, h->d_conv));
+                 h->delta, h->rho_half, h->rho_prev, h->q, h->cg_iters + l, h->st, h->d_conv,
+                 iters_add));
     span(h, SPAN_DSA, d0, rec(h), l + 1);
     return RTE_OK;
   };
@@ -937,6 +952,74 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
     g_launches += g.kernels;
     return norms_ready(l + 1);
   };
+  // options.graph = 2: once iteration l has failed its stopping test, and every iteration from
+  // l on is a DSA step whose launches do not depend on its index (l >= the preconditioner ROM
+  // levels), the iterations l, l + 1, ... run inside one CUDA graph: a while node whose body
+  // is the SA step of l, the sweep and the residual of l + 1, and whose condition the residual
+  // kernel sets from the stopping test and the iteration cap.  The CG counts of the loop add
+  // up in slot l.  The host waits once, for the end of the loop; *l_out = the last iteration.
+  const bool use_loop = h->opt.graph == 2 && !mh && !h->opt.lookahead;
+  auto run_loop = [&](int l0, int* l_out) -> rte_status {
+    if (!h->d_loop) {
+      CK(cudaMalloc(&h->d_loop, sizeof(unsigned)));
+      CK(cudaMallocHost(&h->h_loop, sizeof(unsigned)));
+    }
+    if ((int)h->loops.size() <= l0) h->loops.resize(l0 + 1);
+    rte_s::IterGraph& g = h->loops[l0];
+    if (!g.exec) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle cond = 0;
+      cudaGraphNodeParams cp{};
+      cudaGraphNode_t node = nullptr;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+      if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+      }
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(h->st, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                          0, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "building the SI loop's CUDA graph");
+      }
+      const long long k0 = g_launches;
+      const ResidualLoop lc{cond, h->d_loop, (unsigned)(h->opt.max_iter - l0),
+                            h->dim == 2 ? &h->ctrl->err : nullptr,
+                            reinterpret_cast<const unsigned*>(h->dsa.scal) + 2};
+      h->capturing = true;
+      rte_status st = dsa_step(l0, 1);
+      if (st == RTE_OK) st = sweep_increment(l0 + 1);
+      if (st == RTE_OK) st = residual(l0 + 1, &lc);
+      h->capturing = false;
+      cudaGraph_t body = nullptr;
+      e = cudaStreamEndCapture(h->st, &body);
+      g.kernels = g_launches - k0;
+      g_launches = k0;
+      if (st == RTE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (st != RTE_OK) return st;
+      if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(h, e, "capturing the SI loop as a CUDA graph");
+      }
+    }
+    const int p = (l0 + 1) & 1;
+    CK(cudaMemsetAsync(h->d_loop, 0, sizeof(unsigned), h->st));
+    CK(cudaGraphLaunch(g.exec, h->st));
+    CK(cudaMemcpyAsync(h->h_norms + p, h->norms + p, sizeof(Norms), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_loop, h->d_loop, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaEventRecord(h->blocking ? h->ev_norm_b[p] : h->ev_norm[p], h->st));
+    CK(cudaEventSynchronize(h->blocking ? h->ev_norm_b[p] : h->ev_norm[p]));
+    const unsigned c = *h->h_loop;
+    g_launches += g.kernels * (long long)c;
+    *l_out = l0 + (int)c;
+    return RTE_OK;
+  };
   bool conv = false;
   int l = 1;
   for (bool& a : h->pc_applied) a = false;
@@ -954,6 +1037,16 @@ rte_status si_sa(rte_handle h, int pc_active, int* iters_out, bool* converged_ou
     conv = absmode ? nm.diff_inf <= h->opt.eps_sisa : nm.diff_inf <= h->opt.eps_sisa * nm.half_inf;
     h->stats.last_residual = res;
     if (conv || l == h->opt.max_iter) break;
+    if (use_loop && !pc_now && l >= h->levels) {
+      const int p = (l + 1) & 1;
+      TRY(run_loop(l, &l));
+      const Norms nl = h->h_norms[p];
+      h->stats.last_residual =
+          absmode ? nl.diff_inf : (nl.half_inf > 0 ? nl.diff_inf / nl.half_inf : nl.diff_inf);
+      conv = absmode ? nl.diff_inf <= h->opt.eps_sisa
+                     : nl.diff_inf <= h->opt.eps_sisa * nl.half_inf;
+      break;
+    }
     if ((!h->opt.lookahead || mh) && !pc_now) TRY(iteration(l));
     if (pc_now) {
       // ROM preconditioner of iteration l, Eq. (dmd-sa):
@@ -1657,7 +1750,7 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
   if (h->opt.mh_window < 2 || h->opt.mh_window > 16)
     return fail(h, RTE_EINVAL, "mh_window must be in [2, 16]");
   if (h->opt.max_iter < 1 || h->opt.cg_max_iter < 0) return fail(h, RTE_EINVAL, "bad iteration caps");
-  if (h->opt.graph != 0 && h->opt.graph != 1) return fail(h, RTE_EINVAL, "graph must be 0 or 1");
+  if (h->opt.graph < 0 || h->opt.graph > 2) return fail(h, RTE_EINVAL, "graph must be 0, 1 or 2");
   if (h->opt.sweep_lanes != 0 && h->opt.sweep_lanes != 8 && h->opt.sweep_lanes != 16 &&
       h->opt.sweep_lanes != 32 &&
       !((h->opt.sweep_lanes == 2 || h->opt.sweep_lanes == 4) &&

@@ -133,12 +133,24 @@ struct Norms {             // device-side reduction results of one residual eval
 // conv (optional): skip word of a speculative SI-SA loop; the residual does nothing when it
 // is set and otherwise sets it to the outcome of the stopping test (eps, absolute or relative).
 // copy1 / copy2 (optional): further destinations of rho^{l-1/2}.
+// loop.count (optional): iteration counter of a CUDA graph's while loop around the SI
+// iteration; the residual adds one and sets loop.cond to 1 while the stopping test fails, the
+// counter is below loop.limit and neither error word (optional: the sweep's and the CG's
+// bounded waits) is set, else to 0.  A residual skipped on a set skip word sets it to 0.
+struct ResidualLoop {
+  cudaGraphConditionalHandle cond;
+  unsigned* count;
+  unsigned limit;
+  const unsigned* err0;
+  const unsigned* err1;
+};
 cudaError_t launch_combine_residual(const double* pm, int nfam, const double* btilde,
                                     const double* rho_prev, int ncell, double* rho_half,
                                     double* partials, int nblocks, Norms* out, cudaStream_t s,
                                     unsigned* conv = nullptr, double eps = 0.0, int absmode = 0,
                                     double* copy1 = nullptr, double* copy2 = nullptr,
-                                    unsigned* ticket = nullptr);
+                                    unsigned* ticket = nullptr,
+                                    ResidualLoop loop = ResidualLoop{0, nullptr, 0, nullptr, nullptr});
 // ticket: a zeroed device word; the residual kernel's last block forms the norms and the
 // stopping test and zeroes it again.
 // Start of an SI-SA solve: src -> dst1 (and dst2 when given), *conv = 0, slots[0..nslots) = 0.
@@ -215,7 +227,7 @@ void dsa_free(DsaOp& op);
 cudaError_t dsa_solve(DsaOp& op, const double* sig_s, const double* residual,
                       const double* residual_b, double rtol, int max_iter, double* delta,
                       const double* rho_half, double* rho_out, double* q_out, int* iters_dev,
-                      cudaStream_t s, const unsigned* skip = nullptr);
+                      cudaStream_t s, const unsigned* skip = nullptr, int iters_add = 0);
 
 // Allocation-free DSA solve behind rte_dsa_solve_noalloc (cg.cu); *err receives the message.
 rte_status dsa_solve_noalloc(int dim, int nx, int ny, double x0, double x1, double y0, double y1,

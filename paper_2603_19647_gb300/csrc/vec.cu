@@ -31,8 +31,11 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
                                         double* __restrict__ rho_half, double* __restrict__ copy1,
                                         double* __restrict__ copy2, double* partials,
                                         unsigned* skip, unsigned* ticket, Norms* out, double eps,
-                                        int absmode) {
-  if (skip && *skip) return;   // the solve has converged: speculative work does nothing
+                                        int absmode, ResidualLoop loop) {
+  if (skip && *skip) {   // the solve has converged: speculative work does nothing
+    if (loop.count && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop.cond, 0u);
+    return;
+  }
   __shared__ double sh[3][VT / 32];
   double dinf = 0.0, hinf = 0.0, d2 = 0.0;
   for (int c = blockIdx.x * VT + threadIdx.x; c < n; c += gridDim.x * VT) {
@@ -94,7 +97,15 @@ __global__ void combine_residual_kernel(const double* __restrict__ pm, int nfam,
         out->diff_inf = dmax;
         out->half_inf = hmax;
         out->diff_l2sq = dsum;
-        if (skip) *skip = (absmode ? dmax <= eps : dmax <= eps * hmax) ? 1u : 0u;
+        const bool conv = absmode ? dmax <= eps : dmax <= eps * hmax;
+        if (skip) *skip = conv ? 1u : 0u;
+        if (loop.count) {   // one more iteration of the graph's loop unless this one converged,
+                            // the cap is reached or a bounded wait of the iteration ran out
+          const unsigned c = *loop.count + 1u;
+          *loop.count = c;
+          const bool failed = (loop.err0 && __ldcg(loop.err0)) || (loop.err1 && __ldcg(loop.err1));
+          cudaGraphSetConditional(loop.cond, !conv && !failed && c < loop.limit ? 1u : 0u);
+        }
         *ticket = 0u;
       }
     }
@@ -339,11 +350,12 @@ cudaError_t launch_combine_residual(const double* pm, int nfam, const double* bt
                                     const double* rho_prev, int n, double* rho_half,
                                     double* partials, int nblocks, Norms* out, cudaStream_t s,
                                     unsigned* conv, double eps, int absmode, double* copy1,
-                                    double* copy2, unsigned* ticket) {
+                                    double* copy2, unsigned* ticket, ResidualLoop loop) {
   if (!ticket) return cudaErrorInvalidValue;
   ++g_launches;
   combine_residual_kernel<<<nblocks, VT, 0, s>>>(pm, nfam, btilde, rho_prev, n, rho_half, copy1,
-                                                 copy2, partials, conv, ticket, out, eps, absmode);
+                                                 copy2, partials, conv, ticket, out, eps, absmode,
+                                                 loop);
   return cudaGetLastError();
 }
 

@@ -31,8 +31,9 @@ def main(argv=None):
                     help="DG degree: 0 (one value per cell) or 1 (bilinear, 2D FP64)")
     ap.add_argument("--lanes", type=int, default=0, help="sweep_lanes (0: the library's choice)")
     ap.add_argument("--rows", type=int, default=0, help="sweep_rows (0: the library's choice)")
-    ap.add_argument("--graph", type=int, choices=[0, 1], default=0,
-                    help="1: each SI iteration as a captured CUDA graph")
+    ap.add_argument("--graph", type=int, choices=[0, 1, 2], default=0,
+                    help="1: each SI iteration as a captured CUDA graph; 2: also the remaining "
+                         "DSA iterations in one graph with a while node")
     a = ap.parse_args(argv)
     wl = inputs.BY_NAME[a.workload]()
     steps = a.steps if a.steps is not None else wl.steps

@@ -71,7 +71,7 @@ def _create(**kw):
     dict(options=rte.default_options(sa_kind=2)),
     dict(options=rte.default_options(mh_window=1)),
     dict(options=rte.default_options(mh_window=17)),
-    dict(options=rte.default_options(graph=2)),
+    dict(options=rte.default_options(graph=3)),
     dict(options=rte.default_options(time_scheme=2)),
     dict(options=rte.default_options(time_scheme=rte.RTE_BDF2, precision=rte.RTE_FP32_BF16F)),
     dict(options=rte.default_options(pc_levels=-1)),

@@ -1,6 +1,7 @@
 """options.graph: each DSA-preconditioned SI iteration (the DSA solve of l, the sweep and the
 residual of l + 1; Algorithm 1) runs as one CUDA graph captured from the handle's stream the
-first time l is reached and replayed in later steps.
+first time l is reached and replayed in later steps (graph = 1); with graph = 2 the remaining
+DSA iterations run inside one graph whose while node the residual kernel's stopping test ends.
 
 A replay launches the kernels of the one-by-one loop with the same arguments, so the march
 must be the one-by-one march bit for bit: scalar flux, iteration counts, CG counts, ROM ranks,
@@ -36,12 +37,15 @@ def _run(wl, steps, restart_at=None, stream=None, **opts):
     return rho, log
 
 
-def _same(wl, steps, **opts):
+def _same(wl, steps, graph, **opts):
     rho0, log0 = _run(wl, steps, graph=0, **opts)
-    rho1, log1 = _run(wl, steps, graph=1, **opts)
+    rho1, log1 = _run(wl, steps, graph=graph, **opts)
     assert log0 == log1
     assert np.array_equal(rho0, rho1)
     return log1
+
+
+GRAPH = pytest.mark.parametrize("graph", [1, 2], ids=["per_iteration", "while_loop"])
 
 
 @pytest.mark.parametrize("case", [
@@ -55,31 +59,57 @@ def _same(wl, steps, **opts):
     dict(precision=rte.RTE_FP32, degree=1),
 ], ids=["fp64", "fp32", "bf16f", "two_pc_levels", "lookahead", "tile_kernel", "q1_fp64",
         "q1_fp32"])
-def test_graph_march_is_the_launch_by_launch_march(case):
-    log = _same(inputs.checkerboard(n=48), 80, **case)
+@GRAPH
+def test_graph_march_is_the_launch_by_launch_march(case, graph):
+    log = _same(inputs.checkerboard(n=48), 80, graph, **case)
     assert max(t[4] for t in log) == 3   # the ROM-preconditioned iteration was reached too
 
 
-def test_graph_march_slab():
-    _same(inputs.slab_1d(steps=60), 60)
+@GRAPH
+def test_graph_march_slab(graph):
+    _same(inputs.slab_1d(steps=60), 60, graph)
 
 
-def test_graph_bdf2_and_restart():
+@GRAPH
+def test_graph_bdf2_and_restart(graph):
     """BDF2 changes the time step constant after its first (backward-Euler) step, and a
     restart changes it back: the captured iterations are dropped and captured again."""
-    _same(inputs.checkerboard(n=48), 40, restart_at=21, time_scheme=rte.RTE_BDF2)
+    _same(inputs.checkerboard(n=48), 40, graph, restart_at=21, time_scheme=rte.RTE_BDF2)
 
 
-def test_graph_on_a_caller_stream():
+@GRAPH
+def test_graph_on_a_caller_stream(graph):
     wl = inputs.checkerboard(n=48)
     s = torch.cuda.Stream()
     rho0, log0 = _run(wl, 30, graph=0)
-    rho1, log1 = _run(wl, 30, graph=1, stream=s)
+    rho1, log1 = _run(wl, 30, graph=graph, stream=s)
     assert log0 == log1
     assert np.array_equal(rho0, rho1)
 
 
-def test_graph_march_against_the_oracle_through_phase3():
-    orc = _march(inputs.checkerboard(n=48), 80, 5, rom_on=True, decisions_p3=True, graph=1,
+@GRAPH
+def test_graph_march_against_the_oracle_through_phase3(graph):
+    orc = _march(inputs.checkerboard(n=48), 80, 5, rom_on=True, decisions_p3=True, graph=graph,
                  **WELL_CONDITIONED_PC)
     assert sum(s.phase == 3 for s in orc.log) >= 60
+
+
+def test_graph_loop_stops_at_the_iteration_cap():
+    """A cap of max_iter SI iterations ends the device-side loop too: every step stops at the
+    cap (RTE_ENOCONV from rte_step, the iterate still usable), as the launch-by-launch loop
+    does."""
+    wl = inputs.checkerboard(n=48)
+    out = []
+    for graph in (0, 2):
+        h, _ = make_pair(wl, rom=rte.RTE_ROM_OFF, max_iter=3, eps_sisa=1e-14, graph=graph)
+        h.rte_set_initial(rho0=wl.rho0)
+        with pytest.raises(rte.RteError) as err:
+            h.rte_step(1)
+        assert err.value.status == rte.RTE_ENOCONV
+        st = h.rte_get_stats()
+        out.append((h.rte_get_scalar_flux(), st["last_iterations"], st["last_cg_iterations"],
+                    st["kernel_launches"]))
+        h.destroy()
+    assert out[0][1] == out[1][1] == 3
+    assert out[0][2:] == out[1][2:]
+    assert np.array_equal(out[0][0], out[1][0])
