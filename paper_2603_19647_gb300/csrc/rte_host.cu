@@ -1349,9 +1349,14 @@ rte_status set_tau(rte_handle h, double tau) {
   h->tau = tau;
   drop_graphs(h);   // the sweeps take tau by value and the DSA operator is rebuilt
   const Layout& L = h->L;
-  if (!h->fp32 && h->dim == 2 && h->inv_d)
-    CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)h->ncell, L.nslot, L.dl,
-                            h->inv_d, h->st));
+  if (!h->fp32 && h->dim == 2 && h->inv_d) {
+    if (h->deg == 0)
+      CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)h->ncell, L.nslot,
+                              L.dl, h->inv_d, h->st));
+    else
+      CK(launch_q1_table(h->sig_t, h->ca, h->cb, h->tau, (int)h->ncell, L.nslot, L.dl, h->inv_d,
+                         h->st));
+  }
   if (h->fp32 && h->cth_f) {
     std::vector<float> cth, ctl;
     fp32_ct_pairs(h, cth, ctl);
@@ -1493,10 +1498,14 @@ rte_status alloc_sweep(rte_handle h) {
     // two passes (the fused sweep), times the face modes a row hands on (Q1: two)
     const size_t edge = (size_t)2 * L.nfam * h->nblk_max * h->nx * L.dl * (h->deg == 1 ? 2 : 1);
     if (!h->fp32) {
-      if (h->deg == 0) {   // the Q1 sweeps form their cell solves without a table
+      if (h->deg == 0) {
         CK(dalloc(&h->inv_d, (size_t)n * L.nslot));
         CK(launch_inv_d<double>(h->sig_t, h->ca, h->cb, h->cw, h->tau, (int)n, L.nslot, L.dl,
                                 h->inv_d, h->st));
+      } else {   // Q1: four factors of the cell solve per cell and direction
+        CK(dalloc(&h->inv_d, (size_t)4 * n * L.nslot));
+        CK(launch_q1_table(h->sig_t, h->ca, h->cb, h->tau, (int)n, L.nslot, L.dl, h->inv_d,
+                           h->st));
       }
       CK(dalloc(&h->pm, (size_t)L.nfam * nd));
       CK(dalloc(&h->edge, edge));

@@ -53,7 +53,8 @@ struct Sweep2DArgs {
   const int* fam_quad;  // [nfam]
   const Real* sig_t;    // [ncell]
   const Real* sig_tl;   // [ncell] FP32: sigma_t - sig_t exactly (the low part), or nullptr
-  const Real* inv_d;    // FP64: [nfam][ncell][dl] w / (tau + sigma_t + a + b); FP32: nullptr
+  const Real* inv_d;    // FP64: [nfam][ncell][dl] w / (tau + sigma_t + a + b) (Q1: the cell
+                        // solve's factors, launch_q1_table); FP32: nullptr
   const unsigned* skip; // set: the launch does nothing (speculative SI-SA work past convergence)
   const Real* cth;      // [nslot] tau + a + b, high part, or nullptr (formed from tau, a, b)
   const Real* ctl;      // [nslot] its low part (FP32: the exact sum is cth + ctl)
@@ -97,6 +98,10 @@ struct Sweep1DArgs {
 // edge: per pass [nfam][nblk][nx][2][dl] (mode 1: two passes).
 cudaError_t launch_sweep_q1(const Sweep2DArgs<double>& a, int mode, int dl, int R, cudaStream_t s);
 cudaError_t launch_sweep_q1(const Sweep2DArgs<float>& a, int mode, int dl, int R, cudaStream_t s);
+// The FP64 Q1 sweeps' table (their inv_d): the closed form's factors kS, kQ, s1, ps of every
+// cell and direction slot, [nfam][ncell][4][dl] (nslot = nfam dl), for c = tau + sigma_t.
+cudaError_t launch_q1_table(const double* sig_t, const double* a, const double* b, double tau,
+                            int ncell, int nslot, int dl, double* out, cudaStream_t s);
 // FP32: f[fam][cell][k][dl] = float(rho[k ncell + cell])
 cudaError_t launch_isotropic_f32_q1(const double* rho, int ncell, int nslot, int dl, float* f,
                                     cudaStream_t s);

@@ -86,6 +86,21 @@ __device__ __forceinline__ Q1Coef<Real> q1_coef(Real c, Real ax, Real ay) {
   return k;
 }
 
+// The same factors with the four that cost most (the division among them) read from the FP64
+// table of q1_table_kernel: t = {kS, kQ, s1, ps} of the cell and direction.
+template <class Real>
+__device__ __forceinline__ Q1Coef<Real> q1_coef_from(Real c, Real ax, Real ay, const Real t[4]) {
+  Q1Coef<Real> k;
+  k.q0 = c + ay;
+  k.beta = ay;
+  k.pq = k.q0 + Real(4.0) * ax;
+  k.kS = t[0];
+  k.kQ = t[1];
+  k.s1 = t[2];
+  k.ps = t[3];
+  return k;
+}
+
 // F = L^-1 R for the right side r (r[a + 2b] = R[a][b]) by the closed form of the file comment.
 template <class Real>
 __device__ __forceinline__ void q1_apply(const Q1Coef<Real>& k, Real ax, Real ux, Real uy,
@@ -123,10 +138,12 @@ __device__ __forceinline__ Real madp(Real uh, Real ul, Real x, Real y) {
   else return mad(uh, x, y);
 }
 
+// kt (FP64, optional): the cell and direction's factors from the table, else computed here.
 template <class Real>
 __device__ __forceinline__ void q1_cell(Real ch, Real cl, Real ax, Real ay, Real ux, Real ul,
                                         Real uy, Real vl, const Real s[4], const Real tx[2],
-                                        const Real ty[2], Real f[4], Real ox[2], Real oy[2]) {
+                                        const Real ty[2], Real f[4], Real ox[2], Real oy[2],
+                                        const Real* kt = nullptr) {
   // ux = ux + ul and uy = uy + vl (+-sqrt(3)) wherever they define the equations (the right
   // side's inflow terms, the residual, the outflow traces); the closed form takes ux, uy
   const Real axt0 = ax * tx[0], axt1 = ax * tx[1], ayt0 = ay * ty[0], ayt1 = ay * ty[1];
@@ -135,7 +152,7 @@ __device__ __forceinline__ void q1_cell(Real ch, Real cl, Real ax, Real ay, Real
   r[1] = madp(-ux, -ul, axt0, s[1] + ayt1);
   r[2] = madp(-uy, -vl, ayt0, s[2] + axt1);
   r[3] = madp(-uy, -vl, ayt1, madp(-ux, -ul, axt1, s[3]));
-  const Q1Coef<Real> k = q1_coef(ch, ax, ay);
+  const Q1Coef<Real> k = kt ? q1_coef_from(ch, ax, ay, kt) : q1_coef(ch, ax, ay);
   q1_apply(k, ax, ux, uy, r, f);
   if constexpr (sizeof(Real) == 4) {
     // (L F)[a][b] = c F[a][b] + ax (Bx F)[a][b] + ay (F By^T)[a][b]
@@ -258,6 +275,25 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
   };
   static_assert(K % 2 == 0, "the double buffer alternates within a chunk");
   if constexpr (AHEAD) fetch(0, buf[0]);
+  // FP64: four of the closed form's factors per cell and direction (q1_table_kernel, family
+  // layout [fam][cell][4][dl]), read one step ahead: the table is too large for L2, and the
+  // factors take the division and about a third of the FP64 operations of a cell solve
+  constexpr bool TABLE = sizeof(Real) == 8;
+  Real kt[2][R][4];
+  const Real* tab = TABLE ? A.inv_d + (size_t)fam * ncell * 4 * DL : nullptr;
+  auto fetch_k = [&](int t, Real (&d)[R][4]) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int x = t - m - gi * R;
+      const int jj = row0 + m;
+      if (x >= 0 && x < nx && jj < ny) {
+        const Real* p = tab + (size_t)cell_of(x, jj) * 4 * DL + dl;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[m][i] = __ldcs(p + i * DL);
+      }
+    }
+  };
+  if constexpr (TABLE) fetch_k(0, kt[0]);
 
   for (int c = 0; c < nchunk; ++c) {
     const int tb = c * K;
@@ -309,6 +345,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
       }
       if constexpr (AHEAD) fetch(t + 1, buf[(k + 1) & 1]);
       else fetch(t, buf[0]);
+      if constexpr (TABLE) fetch_k(t + 1, kt[(k + 1) & 1]);
       Real mv[NV];
 #pragma unroll
       for (int m = R - 1; m >= 0; --m) {
@@ -338,7 +375,8 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
             else if constexpr (MODE == 2) s[md] = mad(tau, in.fo[md], in.g[md]);
             else s[md] = mad(tau, in.fo[md], in.q[md]);
           }
-          q1_cell(ch, cl, ax, ay, ux, ul, uy, vl, s, xA[m], tyA, fA, ox, oy);
+          const Real* kc = TABLE ? kt[k & 1][m] : nullptr;
+          q1_cell(ch, cl, ax, ay, ux, ul, uy, vl, s, xA[m], tyA, fA, ox, oy, kc);
           xA[m][0] = ox[0];
           xA[m][1] = ox[1];
           yA[m][0] = oy[0];
@@ -351,7 +389,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
             Real sB[4], fB[4];
 #pragma unroll
             for (int md = 0; md < 4; ++md) sB[md] = mad(tau, fA[md], in.g[md]);
-            q1_cell(ch, cl, ax, ay, ux, ul, uy, vl, sB, xB[m], tyB, fB, ox, oy);
+            q1_cell(ch, cl, ax, ay, ux, ul, uy, vl, sB, xB[m], tyB, fB, ox, oy, kc);
             xB[m][0] = ox[0];
             xB[m][1] = ox[1];
             yB[m][0] = oy[0];
@@ -494,6 +532,24 @@ RTE_Q1_EXTERN(float, 2)
 
 #if RTE_Q1_PART == -1 || RTE_Q1_PART == 0
 namespace {
+// {kS, kQ, s1, ps} of q1_coef for every cell and direction slot (slot = fam dl + d), in the
+// family layout [fam][cell][4][dl]: one thread per (cell, slot).
+__global__ void q1_table_kernel(const double* __restrict__ sig_t, const double* __restrict__ a,
+                                const double* __restrict__ b, double tau, int ncell, int nslot,
+                                int dl, double* __restrict__ out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)ncell * nslot) return;
+  const int slot = (int)(i % nslot);
+  const long cell = i / nslot;
+  const Q1Coef<double> k = q1_coef(tau + sig_t[cell], a[slot], b[slot]);
+  const int fam = slot / dl, d = slot % dl;
+  double* o = out + ((size_t)fam * ncell + cell) * 4 * dl + d;
+  o[0] = k.kS;
+  o[(size_t)dl] = k.kQ;
+  o[2 * (size_t)dl] = k.s1;
+  o[3 * (size_t)dl] = k.ps;
+}
+
 template <class Real>
 cudaError_t launch_sweep_q1_impl(const Sweep2DArgs<Real>& a, int mode, int dl, int R,
                                  cudaStream_t s) {
@@ -506,6 +562,16 @@ cudaError_t launch_sweep_q1_impl(const Sweep2DArgs<Real>& a, int mode, int dl, i
   }
 }
 }  // namespace
+
+cudaError_t launch_q1_table(const double* sig_t, const double* a, const double* b, double tau,
+                            int ncell, int nslot, int dl, double* out, cudaStream_t s) {
+  if (dl < 1 || nslot % dl != 0) return cudaErrorInvalidValue;
+  const long n = (long)ncell * nslot;
+  ++g_launches;
+  q1_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sig_t, a, b, tau, ncell, nslot, dl,
+                                                            out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sweep_q1(const Sweep2DArgs<double>& a, int mode, int dl, int R,
                             cudaStream_t s) {
