@@ -25,8 +25,10 @@
 // is one warp that takes the top row of its strip from the CTA above through global memory,
 // published in chunks of K columns behind a release flag.  CTAs take tickets in
 // row-block-major order, so a CTA only waits for CTAs that already started.  A cell solve is
-// about a hundred flops: in FP64 the kernel is bound by the FP64 pipe, not by memory.  Each
-// row's per-cell data are read from global memory one step ahead of their use.  The FP32 instantiation (options.precision
+// about a hundred flops: in FP64 the kernel is bound by the FP64 pipe, not by memory, so four
+// of the closed form's factors, the division among them, come from a table per cell and
+// direction (built once per time step constant, 32 B per cell-direction).  Each row's
+// per-cell data are read from global memory one step ahead of their use.  The FP32 instantiation (options.precision
 // RTE_FP32) runs the same solve in FP32 arithmetic; the SI-SA loop's FP64 residual refines its
 // increments.  All waits are bounded.
 #include <cuda_runtime.h>
@@ -246,13 +248,12 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
   // step ahead of their use, into the other half of a double buffer, so that the loads' latency
   // overlaps the current step's cell solves instead of stalling the wavefront (measured at
   // 256^2 x 128: FP32 SI sweep 0.79 -> 0.69 ms, fused sweep 1.38 -> 1.04-1.10 ms, FP64 fused
-  // sweep 5.86 -> 5.76 ms).  The FP64 SI and b~ sweeps, bound by the FP64 pipe, load at the step
-  // itself: the second buffer's registers made their SI sweep 3 % slower.
-  constexpr bool AHEAD = sizeof(Real) == 4 || MODE == 1;
+  // sweep 5.86 -> 5.76 ms; the FP64 SI sweep, once the table below took a third of its FP64
+  // work, 1.99 -> 1.86 ms).
   struct In {
     Real st, stl, q[4], fo[4], g[4];
   };
-  In buf[AHEAD ? 2 : 1][R];
+  In buf[2][R];
   auto fetch = [&](int t, In (&d)[R]) {
 #pragma unroll
     for (int m = 0; m < R; ++m) {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
     }
   };
   static_assert(K % 2 == 0, "the double buffer alternates within a chunk");
-  if constexpr (AHEAD) fetch(0, buf[0]);
+  fetch(0, buf[0]);
   // FP64: four of the closed form's factors per cell and direction (q1_table_kernel, family
   // layout [fam][cell][4][dl]), read one step ahead: the table is too large for L2, and the
   // factors take the division and about a third of the FP64 operations of a cell solve
@@ -343,8 +344,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
           upB[md] = eB[k][md];
         }
       }
-      if constexpr (AHEAD) fetch(t + 1, buf[(k + 1) & 1]);
-      else fetch(t, buf[0]);
+      fetch(t + 1, buf[(k + 1) & 1]);
       if constexpr (TABLE) fetch_k(t + 1, kt[(k + 1) & 1]);
       Real mv[NV];
 #pragma unroll
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(32) sweep_q1_kernel(const Sweep2DArgs<Real> A)
 #pragma unroll
         for (int md = 0; md < 4; ++md) mv[md * R + m] = Real(0);
         if (x >= 0 && x < nx && jj < ny) {
-          const In& in = buf[AHEAD ? (k & 1) : 0][m];
+          const In& in = buf[k & 1][m];
           const long cell = cell_of(x, jj);
           // c = tau + sigma_t: in FP32 as an exact pair ch + cl (both given as exact pairs)
           Real ch, cl = Real(0);
