@@ -245,11 +245,16 @@ def extra_workloads(rte, inputs, torch):
     arms = {}
     for graph in (0, 2):   # kernels launched one by one; SI iterations in CUDA graphs (while node)
         b = rte.rte_batch_create(wls, rte.default_options(precision=rte.RTE_FP32, graph=graph))
-        b.rte_batch_step(2)
-        b.rte_batch_restart()
-        t0 = time.perf_counter()
-        b.rte_batch_step(20)
-        dt = time.perf_counter() - t0
+        try:
+            b.rte_batch_step(2)
+            b.rte_batch_restart()
+            t0 = time.perf_counter()
+            b.rte_batch_step(20)
+            dt = time.perf_counter() - t0
+        except rte.RteError as e:   # reported in the line instead of ending the run
+            arms[graph] = {"error": str(e)}
+            b.destroy()
+            continue
         upd = sum(b.instance(i).rte_get_stats()["cell_direction_updates"] for i in range(len(b)))
         b.destroy()
         arms[graph] = {"ms_per_step": 1e3 * dt / 20, "updates_per_s": upd / dt}

@@ -171,6 +171,15 @@ typedef struct {
                         device times (time_sweep_ms, time_dsa_ms, si_sweep_kernel_ms) then
                         leave out the work inside the graphs.  0 (default): launch every kernel
                         one by one. */
+  int dsa_cluster;   /* 1: the DSA solve (degree 0) runs in one thread-block cluster of 8 CTAs
+                        instead of a cooperative launch over every SM: slower alone, but the
+                        hardware starts the cluster's CTAs together, so a solve never waits at
+                        its barrier on blocks that concurrent kernels keep off the SMs (two
+                        cooperative solves running beside each other and other work can each
+                        hold part of their blocks and wait on the rest until the bounded wait
+                        runs out, RTE_ETIMEOUT).  The same CG iteration as the two-phase
+                        cooperative solve; degree 1 keeps its cooperative solve.  Batched
+                        instances always take 1.  0 (default): cooperative launch. */
 } rte_options;
 
 typedef struct {
@@ -373,7 +382,9 @@ typedef struct {
 /* Create `count` instances (1 .. 4096) with the same options (NULL = defaults).  In the FP32
  * modes, when the options leave the sweep choice to the library, every instance takes the
  * tile sequence with 32 directions per lane group, 4-row tiles and 8 warps per CTA (measured
- * faster beside other instances than each instance's own tuning, which times it alone).  Arrays are
+ * faster beside other instances than each instance's own tuning, which times it alone).  Every
+ * instance solves its DSA system in FP64 in one thread-block cluster (options dsa_fp64 = 1,
+ * dsa_cluster = 1), whatever the options say.  Arrays are
  * copied.  On failure nothing is kept; rte_last_error(NULL) names the failing instance. */
 rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* problems,
                             const rte_options* opt);

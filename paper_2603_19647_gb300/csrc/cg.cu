@@ -13,6 +13,12 @@
 //   (1) p <- r + beta p (double-buffered, neighbours recomputed from r and the old p),
 //       Ap = C p, and the block partials of p.Ap;
 //   (2) x += alpha p, r -= alpha Ap and the block partials of r.r.
+// With options.dsa_cluster (batched instances) the same two-phase solve runs in one
+// thread-block cluster (cg_cluster_kernel): the hardware schedules the cluster's CTAs together
+// and its barrier is the cluster barrier, so no solve waits on blocks that other kernels keep
+// from starting.  A cooperative launch gives no such guarantee beside other work: two solves
+// that each got only some of their blocks onto the SMs could wait on each other until their
+// bounded barrier waits ran out.
 //
 // Q1 scheme (bilinear modes per cell, mode-major vectors): C is the symmetric interior-penalty
 // DG discretisation of the same correction equation on the same bilinear space, with the
@@ -24,6 +30,7 @@
 // On a tensor-product basis every term acts on the x modes or on the y modes alone, so the
 // operator of a cell is Xd (x) I + I (x) Yd on its own modes plus one 2 x 2 block per
 // neighbour: 14 coefficients per cell, set up on the host.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -301,6 +308,134 @@ __global__ void __launch_bounds__(CT) cg_kernel(const CgArgs<S> a) {
     }
   }
   if (tid == 0) *a.iters = a.iters_add ? *a.iters + it : it;
+}
+
+// One thread-block cluster per solve: CL_CTAS CTAs of CL_CT threads.
+constexpr int CL_CTAS = 8;   // the portable maximum cluster size
+constexpr int CL_CT = 512;
+
+// Sum of a CTA's CL_CT values into *slot (the CTA's own shared memory).  Every call is
+// followed by a cluster barrier before the next one, which keeps the staging array's reuse
+// ordered.
+__device__ void cta_sum_to(double v, double* slot) {
+  __shared__ double sh[CL_CT / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < CL_CT / 32 ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) *slot = v;
+  }
+}
+
+// The two-phase solve of cg_kernel inside one cluster.  The grid is the cluster; a phase ends
+// with a fence and the cluster barrier (release / acquire at cluster scope); the CTA partials
+// stay in each CTA's shared memory and every thread sums them over the distributed shared
+// memory in CTA-rank order, so all CTAs hold the same CG scalars bit for bit and take the same
+// branch.  Two partial slots: phase 1 writes slot 0 while a slower CTA may still be reading
+// slot 1 of the previous phase, and the reverse.  No software wait: nothing here can time out.
+template <class S>
+__global__ void __launch_bounds__(CL_CT) cg_cluster_kernel(const CgArgs<S> a) {
+  if (a.skip && *a.skip) return;   // every CTA returns before any shared-memory exchange
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const unsigned ncta = cl.num_blocks();
+  const int tid = (int)cl.block_rank() * CL_CT + (int)threadIdx.x;
+  const int nth = (int)ncta * CL_CT;
+  __shared__ double s_part[2];
+  auto phase_end = [&]() {
+    __threadfence();
+    cl.sync();
+  };
+  auto total = [&](int k) {
+    double t = 0.0;
+    for (unsigned b = 0; b < ncta; ++b) t += *cl.map_shared_rank(&s_part[k], b);
+    return t;
+  };
+  // r = b = sig_s .* residual, x = 0, p = r
+  double acc = 0.0;
+  for (int c = tid; c < a.n; c += nth) {
+    const double rc = a.residual_b ? a.residual[c] - a.residual_b[c] : a.residual[c];
+    const S b = S(a.sig_s[c] * rc);
+    a.r[c] = b;
+    a.x[c] = S(0);
+    a.p0[c] = b;
+    acc += double(b) * double(b);
+  }
+  cta_sum_to(acc, &s_part[1]);
+  phase_end();
+  double rr = total(1);
+  const double bb = rr;
+  double beta = 0.0;
+  int it = 0;
+  S* pold = a.p0;
+  S* pnew = a.p1;
+  while (it < a.max_iter && rr > a.rtol2 * bb) {
+    // (1) p <- r + beta p ; Ap = C p ; p.Ap
+    acc = 0.0;
+    const S bt = S(beta);
+    for (int c = tid; c < a.n; c += nth) {
+      // neighbours belong to other CTAs: read them through L2 (__ldcg), never a stale L1 line
+      auto pval = [&](int k) {
+        return (it == 0) ? __ldcg(pold + k) : __ldcg(a.r + k) + bt * __ldcg(pold + k);
+      };
+      const S pc = pval(c);
+      const S sc = op_apply(a, c, pc, pval);
+      pnew[c] = pc;
+      a.ap[c] = sc;
+      acc += double(pc) * double(sc);
+    }
+    cta_sum_to(acc, &s_part[0]);
+    phase_end();
+    const double alpha = rr / total(0);
+    const S al = S(alpha);
+    // (2) x += alpha p ; r -= alpha Ap ; r.r
+    acc = 0.0;
+    for (int c = tid; c < a.n; c += nth) {
+      a.x[c] += al * pnew[c];
+      const S rc = a.r[c] - al * a.ap[c];
+      a.r[c] = rc;
+      acc += double(rc) * double(rc);
+    }
+    cta_sum_to(acc, &s_part[1]);
+    phase_end();
+    const double rr_new = total(1);
+    beta = rr_new / rr;
+    rr = rr_new;
+    S* t = pold;
+    pold = pnew;
+    pnew = t;
+    ++it;
+  }
+  for (int c = tid; c < a.n; c += nth) {
+    const double d = double(a.x[c]);
+    if (!same_array(a.delta, a.x)) a.delta[c] = d;
+    if (a.rho_out) {
+      const double r = a.rho_half[c] + d;
+      a.rho_out[c] = r;
+      a.q_out[c] = a.sig_s[c] * r;
+    }
+  }
+  if (tid == 0) *a.iters = a.iters_add ? *a.iters + it : it;
+  cl.sync();   // no CTA leaves while another may still read its partials
+}
+
+template <class S>
+cudaError_t launch_cg_cluster(const CgArgs<S>& a, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(CL_CTAS);
+  cfg.blockDim = dim3(CL_CT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cg_cluster_kernel<S>, a);
 }
 
 // Forward declarations of the two-value block and grid sums (defined below).
@@ -669,7 +804,7 @@ void dsa_q1_blocks(int nx, int ny, double hx, double hy, double tau, const doubl
 
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
                       const double* sig_t, const double* sig_s, cudaStream_t s, int max_blocks,
-                      int degree, bool f32) {
+                      int degree, bool f32, bool cluster) {
   const int ncell = nx * ny;
   const int n = degree == 1 ? 4 * ncell : ncell;
   op.nx = nx;
@@ -701,7 +836,10 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   // Q1: the Jacobi-preconditioned two-phase solve (measured with plain CG at 256^2 cells, the
   // two-phase arrangement took 20 % less time per solve than the one-barrier one, whose
   // recomputation of a neighbour's r' costs three loads and the Q1 operator reads ten)
-  op.single_phase = degree == 0 && n <= (1 << 18);
+  // cluster: the Q0 solve in one thread-block cluster (cg_cluster_kernel), for solves that run
+  // beside other work (batched instances); the Q1 solve keeps its cooperative launch.
+  op.cluster = cluster && degree == 0;
+  op.single_phase = degree == 0 && n <= (1 << 18) && !op.cluster;
   const void* kern =
       f32 ? (degree == 1 ? (const void*)pcg_q1_kernel<float>
                          : (op.single_phase ? (const void*)cg1_kernel<float> : (const void*)cg_kernel<float>))
@@ -715,6 +853,7 @@ cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, 
   if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
   op.blocks = want < cap ? want : cap;
   if (op.blocks < 1) op.blocks = 1;
+  if (op.cluster) op.blocks = CL_CTAS;
   cudaError_t e;
   const size_t real = f32 ? sizeof(float) : sizeof(double);
   const size_t bytes = real * (size_t)n;
@@ -807,8 +946,9 @@ cudaError_t dsa_solve_impl(DsaOp& op, const double* sig_s, const double* residua
   a.rho_out = rho_out;
   a.q_out = q_out;
   a.iters = iters_dev;
-  void* args[] = {&a};
   ++g_launches;
+  if (op.cluster) return launch_cg_cluster<S>(a, s);
+  void* args[] = {&a};
   const void* kern = op.deg == 1
                          ? (const void*)pcg_q1_kernel<S>
                          : (op.single_phase ? (const void*)cg1_kernel<S> : (const void*)cg_kernel<S>);

@@ -1370,7 +1370,8 @@ rte_status set_tau(rte_handle h, double tau) {
   CK(cudaStreamSynchronize(h->st));
   dsa_free(h->dsa);
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, h->sig_t_host.data(),
-               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg, h->dsa_f32));
+               h->sig_s_host.data(), h->st, h->opt.cg_blocks, h->deg, h->dsa_f32,
+               h->opt.dsa_cluster != 0));
   h->resp_ready = false;
   h->y_valid = false;
   return RTE_OK;
@@ -1748,6 +1749,8 @@ rte_status validate_impl(rte_handle h, const rte_mesh* mesh, const rte_quadratur
     return fail(h, RTE_EINVAL, "pc_levels must be in [1, RTE_MAX_PC_LEVELS]");
   h->levels = h->opt.pc_levels;
   if (h->opt.cg_blocks < 0) return fail(h, RTE_EINVAL, "cg_blocks must be >= 0");
+  if (h->opt.dsa_cluster != 0 && h->opt.dsa_cluster != 1)
+    return fail(h, RTE_EINVAL, "dsa_cluster must be 0 or 1");
   if (h->opt.time_scheme != RTE_BE && h->opt.time_scheme != RTE_BDF2)
     return fail(h, RTE_EINVAL, "time_scheme must be RTE_BE or RTE_BDF2");
   if (h->opt.time_scheme == RTE_BDF2 && h->opt.precision == RTE_FP32_BF16F)
@@ -1919,7 +1922,7 @@ rte_status create_impl(rte_handle h, const rte_mesh* mesh, const rte_quadrature*
   // its precision moves the iteration count at most, never the fixed point.
   h->dsa_f32 = h->fp32 && !h->opt.dsa_fp64;
   CK(dsa_setup(h->dsa, h->dim, h->nx, h->ny, h->hx, h->hy, h->tau, sigma_t, sigma_s, h->st,
-               h->opt.cg_blocks, h->deg, h->dsa_f32));
+               h->opt.cg_blocks, h->deg, h->dsa_f32, h->opt.dsa_cluster != 0));
   CK(rom_alloc(h->ig, (int)nd, h->opt.r_max));
   if (h->opt.sa_kind == RTE_SA_DMD_ITER) {
     CK(rom_alloc(h->mh, (int)nd, h->opt.mh_window));
@@ -2660,9 +2663,12 @@ rte_status rte_batch_create(rte_batch* out, int count, const rte_problem* proble
   rte_options bopt;
   if (opt) bopt = *opt;
   else rte_default_options(&bopt);
-  // The DSA solve in FP64: with the FP32 solve, one instance of the 64-instance FP32 batch had a
-  // bounded grid-barrier wait of its cooperative CG launch run out (RTE_ETIMEOUT) while the
-  // other instances' kernels filled the GPU; the FP64 solve never has.
+  // The DSA solve in one thread-block cluster: with cooperative launches over every SM, an
+  // instance of the 64-instance FP32 batch had a bounded grid-barrier wait run out
+  // (RTE_ETIMEOUT) while the other instances' kernels, their solves among them, filled the GPU
+  // (first with the FP32 solve, later with the FP64 one).  A cluster's CTAs are started
+  // together by the hardware, so no solve waits on blocks that have not started.
+  bopt.dsa_cluster = 1;
   bopt.dsa_fp64 = 1;
   if (bopt.precision != RTE_FP64 && bopt.tune && !bopt.sweep_kernel && !bopt.sweep_lanes &&
       !bopt.sweep_rows && !bopt.sweep_warps) {

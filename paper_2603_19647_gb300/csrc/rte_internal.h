@@ -217,14 +217,17 @@ struct DsaOp {
   double* scal;      // [8] device scalars
   int blocks;
   bool single_phase;   // cg1_kernel (one barrier per iteration) instead of cg_kernel
+  bool cluster;        // cg_cluster_kernel: the solve in one thread-block cluster (Q0)
 };
 // max_blocks > 0 caps the blocks of the cooperative CG launch (default: one or two per SM).
 // degree 1: the Q1 interior-penalty operator (2D) on mode-major vectors of 4 nx ny values.
 // f32: the solve's vectors and operator arithmetic in FP32, dot products and CG scalars in
 // FP64 (the FP32 modes; the solve's inputs and outputs stay FP64).
+// cluster: the Q0 solve in one thread-block cluster instead of a cooperative launch over the
+// GPU (max_blocks then has no effect; the Q1 solve ignores it).
 cudaError_t dsa_setup(DsaOp& op, int dim, int nx, int ny, double hx, double hy, double tau,
                       const double* sig_t_host, const double* sig_s_host, cudaStream_t s,
-                      int max_blocks = 0, int degree = 0, bool f32 = false);
+                      int max_blocks = 0, int degree = 0, bool f32 = false, bool cluster = false);
 void dsa_free(DsaOp& op);
 // delta = C^{-1} (sig_s .* (residual - residual_b)) (residual_b may be nullptr);
 // rho_out = rho_half + delta and q_out = sig_s .* rho_out when rho_out != nullptr.

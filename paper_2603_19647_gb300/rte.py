@@ -68,7 +68,8 @@ class Options(ctypes.Structure):
                 ("lookahead", ctypes.c_int), ("pc_levels", ctypes.c_int),
                 ("sa_kind", ctypes.c_int), ("mh_window", ctypes.c_int),
                 ("cg_blocks", ctypes.c_int), ("time_scheme", ctypes.c_int),
-                ("degree", ctypes.c_int), ("dsa_fp64", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("degree", ctypes.c_int), ("dsa_fp64", ctypes.c_int), ("graph", ctypes.c_int),
+                ("dsa_cluster", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

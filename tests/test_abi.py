@@ -43,7 +43,7 @@ def test_default_options(lib):
     assert (o.max_iter, o.r_max, o.cg_rtol, o.cg_max_iter) == (500, 40, 1e-6, 500)
     assert o.pc_levels == 1 and rte.MAX_PC_LEVELS == 4
     assert o.sa_kind == rte.RTE_SA_DSA and o.mh_window == 4
-    assert o.degree == 0 and o.dsa_fp64 == 0 and o.graph == 0
+    assert o.degree == 0 and o.dsa_fp64 == 0 and o.graph == 0 and o.dsa_cluster == 0
 
 
 def _create(**kw):
@@ -72,6 +72,7 @@ def _create(**kw):
     dict(options=rte.default_options(mh_window=1)),
     dict(options=rte.default_options(mh_window=17)),
     dict(options=rte.default_options(graph=3)),
+    dict(options=rte.default_options(dsa_cluster=2)),
     dict(options=rte.default_options(time_scheme=2)),
     dict(options=rte.default_options(time_scheme=rte.RTE_BDF2, precision=rte.RTE_FP32_BF16F)),
     dict(options=rte.default_options(pc_levels=-1)),

@@ -18,15 +18,15 @@ def _small_batch(count=6, steps=24, seed=4):
 
 
 def _alone_options(inst, precision):
-    """Options that give a handle stepped alone the same sweep tiles and DSA precision as batch
-    instance `inst` (FP32 batches take a fixed tile and the FP64 DSA solve; FP64 instances tune
-    exactly as a handle alone does)."""
+    """Options that give a handle stepped alone the same sweep tiles and DSA solve as batch
+    instance `inst` (every batch solves its DSA system in FP64 in one thread-block cluster;
+    FP32 batches take a fixed tile; FP64 instances tune exactly as a handle alone does)."""
     if precision == rte.RTE_FP64:
-        return rte.default_options(precision=precision)
+        return rte.default_options(precision=precision, dsa_cluster=1)
     st = inst.rte_get_stats()
     return rte.default_options(precision=precision, sweep_kernel=st["sweep_si_kernel"],
                                sweep_lanes=st["sweep_lanes"], sweep_rows=st["sweep_si_rows"],
-                               sweep_warps=st["sweep_si_warps"], dsa_fp64=1)
+                               sweep_warps=st["sweep_si_warps"], dsa_fp64=1, dsa_cluster=1)
 
 
 @pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])

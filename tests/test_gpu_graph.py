@@ -57,8 +57,9 @@ GRAPH = pytest.mark.parametrize("graph", [1, 2], ids=["per_iteration", "while_lo
     dict(precision=rte.RTE_FP64, sweep_kernel=2),
     dict(precision=rte.RTE_FP64, degree=1),
     dict(precision=rte.RTE_FP32, degree=1),
+    dict(precision=rte.RTE_FP32, dsa_cluster=1, dsa_fp64=1),
 ], ids=["fp64", "fp32", "bf16f", "two_pc_levels", "lookahead", "tile_kernel", "q1_fp64",
-        "q1_fp32"])
+        "q1_fp32", "dsa_cluster"])
 @GRAPH
 def test_graph_march_is_the_launch_by_launch_march(case, graph):
     log = _same(inputs.checkerboard(n=48), 80, graph, **case)

@@ -164,6 +164,28 @@ def test_dsa_cg(name, rtol):
     h.destroy()
 
 
+@pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
+@pytest.mark.parametrize("rtol", [1e-6, 1e-10])
+@pytest.mark.parametrize("name", ["checkerboard", "slab", "ragged", "batch_max"])
+def test_dsa_cg_in_one_cluster(name, rtol, precision):
+    """options.dsa_cluster: the same CG solve in one thread-block cluster, against the
+    oracle's CG on grids from a 1D slab to the largest batched instance (512^2 cells); FP32
+    with dsa_fp64 = 1, as batched instances take it."""
+    wl = (inputs.checkerboard(n=40) if name == "checkerboard"
+          else inputs.slab_1d(n=256) if name == "slab"
+          else inputs.checkerboard(n=512) if name == "batch_max" else inputs.checkerboard(n=37))
+    h, p = make_pair(wl, cg_rtol=rtol, dsa_cluster=1, precision=precision, dsa_fp64=1, tune=0)
+    rng = np.random.default_rng(9)
+    res = rng.uniform(-1, 1, wl.ncell)
+    got, its = h.rte_op_dsa(res)
+    ref, its_ref = dsa.dsa_correction(p, dsa.dsa_matrix(p), res, rtol, 500)
+    assert its == its_ref
+    assert rel_l2(got, ref) < 1e-10
+    got2, its2 = h.rte_op_dsa(res)   # a second solve on the same buffers: the same bits
+    assert its2 == its and np.array_equal(got2, got)
+    h.destroy()
+
+
 def test_rom_incremental_svd_and_apply():
     wl = inputs.checkerboard(n=24)
     h, p = make_pair(wl, r_max=12)

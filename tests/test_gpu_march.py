@@ -196,6 +196,26 @@ def test_checkerboard_phase3_working_tolerance_strict():
     assert sum(s.phase == 3 for s in orc.log) >= 60
 
 
+@pytest.mark.parametrize("precision", [rte.RTE_FP64, rte.RTE_FP32])
+def test_checkerboard_dsa_in_one_cluster_strict(precision):
+    """options.dsa_cluster (the DSA solve batched instances take): the FP64 march through
+    Phase 3 with the same decisions and 1e-10 throughout; the FP32 march (FP32 sweeps, FP64
+    residual and DSA) within 1e-6."""
+    if precision == rte.RTE_FP64:
+        orc = _march(inputs.checkerboard(n=48), 80, 5, rom_on=True, decisions_p3=True,
+                     dsa_cluster=1, **WELL_CONDITIONED_PC)
+        assert sum(s.phase == 3 for s in orc.log) >= 60
+        return
+    wl = inputs.checkerboard(n=48)
+    h, p = make_pair(wl, precision=precision, dsa_cluster=1, dsa_fp64=1, **WELL_CONDITIONED_PC)
+    orc = stepper.OracleRTE(p, rom=True, **WELL_CONDITIONED_PC)
+    orc.set_initial(wl.rho0)
+    h.rte_step(80)
+    orc.step(80)
+    assert rel_l2(h.rte_get_scalar_flux(), orc.rho) < 1e-6
+    h.destroy()
+
+
 def test_slab_phase3_working_tolerance_strict():
     orc = _march(inputs.slab_1d(steps=60), 60, 5, rom_on=True, decisions_p3=True,
                  **WELL_CONDITIONED_PC)
