@@ -136,7 +136,7 @@ typedef struct {
   int mh_window;     /* residuals per DMD-across-iterations cycle, 2 .. 16 (default 4) */
   int cg_blocks;     /* blocks of the DSA solve's cooperative CG launch: 0 (default) one per SM
                         (two above 2^18 cells); a cap leaves the other SMs to concurrent work
-                        (batched instances) at the price of a longer solve */
+                        at the price of a longer solve; no effect with dsa_cluster = 1 */
   int time_scheme;   /* RTE_BE (default): backward Euler, Sec. 2.1 | RTE_BDF2: the second-order
                         backward difference formula Sec. 2.1 names as an alternative: the step's
                         system is backward Euler's with tau' = 3 / (2 c dt) and the history
