@@ -162,7 +162,7 @@ def oracle_sample(wl, budget_s, min_steps=2):
     return updates / dt, k, dt, transport.num_threads(), o
 
 
-def extra_workloads(rte, inputs, torch):
+def extra_workloads(rte, inputs, torch, out):
     """The other rows of the method on this GPU, each a separately timed run beside the
     headline line: the 1024^2 log-normal workload and the 2048^2 diffusive disc for their full
     lengths (500 and 300 steps) in FP64 (ROM-accelerated and plain SI-DSA) and in the reduced
@@ -171,9 +171,9 @@ def extra_workloads(rte, inputs, torch):
     scalar flux); and the 64 batched instances (20 of 100 steps), with the kernels launched one
     by one and with the SI iterations in captured CUDA graphs (a while node around them).
     Time per step counts the
-    steps alone (the comparisons' reads of rho are outside it)."""
+    steps alone (the comparisons' reads of rho are outside it).  The rows go into `out` as they
+    are measured, so that rows measured before a failure stay in the line."""
     import numpy as np
-    out = {}
 
     def march(wl, steps, sample_every, **o):
         h = rte.create_from_workload(wl, options=rte.default_options(**o))
@@ -488,7 +488,12 @@ def run_ours(args):
     if cpu:
         line["cpu_baseline"] = cpu
     if not args.no_extras and world == 1:
-        line["other_workloads"] = extra_workloads(rte, inputs, torch)
+        extras = {}
+        try:
+            extra_workloads(rte, inputs, torch, extras)
+        except rte.RteError as e:   # the headline figures stand; the line says what failed
+            extras["error"] = str(e)
+        line["other_workloads"] = extras
     elif sharded is not None:
         line["other_workloads"] = {"batched_64_instances_20steps_fp32_rom_sharded": sharded}
     print(json.dumps(line))
